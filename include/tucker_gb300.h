@@ -1,0 +1,193 @@
+/*
+ * tucker_gb300.h -- C ABI of the GB300 (sm_103a) ST-HOSVD Tucker library.
+ *
+ * The library computes the hot path of sequentially truncated HOSVD
+ * (Ballard, Klinvex, Kolda, "TuckerMPI", arXiv 1901.06043, Algorithm 1):
+ * per mode n the Gram matrix of the mode-n unfolding (Algorithm 2), its
+ * eigendecomposition (Section 5.2), the eps rank cut (Eq. Un) and the TTM
+ * that shrinks the working tensor (Algorithm 3); plus the multi-TTM that
+ * reconstructs a tensor or a subtensor from the core and factors (Section 7).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * - Tensors are dense and stored in natural-descending order (Section 4.1,
+ *   Eq. idxtolin): element (j_0, ..., j_{N-1}) of a J_0 x ... x J_{N-1}
+ *   tensor sits at sum_n j_n * (J_0 * ... * J_{n-1}); the first index is
+ *   fastest.  1 <= N <= TUCKER_MAX_MODES, every J_n >= 1.
+ * - "_dev" pointers are CUDA device pointers of the current device; "_host"
+ *   pointers are host memory.  The library never frees memory it did not
+ *   allocate, and never writes through a const pointer.
+ * - Every call is enqueued on the context's stream.  Calls that return a
+ *   value to the host (a rank, a norm, a status that depends on device
+ *   data) synchronise that stream before returning.
+ * - Every entry point returns a tucker_status.  On failure nothing is
+ *   freed that the caller owns, results are left undefined, and
+ *   tucker_last_error() describes the failure.  No failure is reported by
+ *   trapping or hanging the device: device-side checks write an error word
+ *   that the host reads.
+ * - Matrices of FP64 values: U_n (I_n x R_n) and eigenvector matrices are
+ *   column-major; Gram matrices are symmetric I x I (either order).
+ */
+#ifndef TUCKER_GB300_H
+#define TUCKER_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TUCKER_MAX_MODES 8
+
+typedef enum {
+  TUCKER_OK = 0,
+  TUCKER_ERR_INVALID = 1,    /* bad argument: ndim, dims, eps, ranks, ranges, order, null */
+  TUCKER_ERR_OOM = 2,        /* device allocation failed or predicted to fail */
+  TUCKER_ERR_NONFINITE = 3,  /* NaN or Inf in the input tensor */
+  TUCKER_ERR_EIG_NOCONV = 4, /* Jacobi sweep cap reached (results still written) */
+  TUCKER_ERR_CUDA = 5,       /* a CUDA runtime error, or a device-side wait that gave up */
+  TUCKER_ERR_UNSUPPORTED = 6 /* valid request this build cannot serve (e.g. dtype/precision pair) */
+} tucker_status;
+
+typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
+
+/* Arithmetic of the Gram and TTM steps.  The eigensolve and the rank cut
+ * are FP64 in every mode, and the Gram is always reduced across slabs in
+ * FP64.
+ *   FP64  : products and sums in FP64 (any input dtype); core in FP64.
+ *   FP32  : FP32 products, FP32 sums over short chunks, FP64 across chunks;
+ *           working tensor and core in the input dtype.
+ *   MIXED : tensor cores (tcgen05) on a two-term FP16 split of each FP32
+ *           value (hi + lo, all four products kept), FP32 accumulation in
+ *           tensor memory over short chunks, FP64 across chunks; FP32
+ *           input only; working tensor and core in FP32. */
+typedef enum { TUCKER_PREC_FP64 = 0, TUCKER_PREC_FP32 = 1, TUCKER_PREC_MIXED = 2 } tucker_prec;
+
+typedef struct tucker_ctx tucker_ctx;
+
+/* Result of tucker_sthosvd.  All pointers are device memory owned by the
+ * result and released by tucker_result_destroy. */
+typedef struct tucker_result {
+  int ndim;
+  tucker_dtype core_dtype;
+  int64_t dims[TUCKER_MAX_MODES];    /* I_n of the input                               */
+  int64_t ranks[TUCKER_MAX_MODES];   /* R_n chosen (eps) or given (ranks)              */
+  int mode_order[TUCKER_MAX_MODES];  /* order in which the modes were processed        */
+  void* core;                        /* R_0 x ... x R_{N-1}, natural-descending        */
+  double* factors[TUCKER_MAX_MODES]; /* U_n: I_n x R_n column-major, orthonormal cols  */
+  double* eigvals[TUCKER_MAX_MODES]; /* all I_n eigenvalues of the mode-n Gram, desc.  */
+  double norm_x_sq;                  /* ||X||^2 (FP64 sum of squares)                  */
+  double threshold;                  /* eps^2 ||X||^2 / N (0 when ranks were given)    */
+  double discarded_sq[TUCKER_MAX_MODES]; /* sum of discarded eigenvalues per mode      */
+  int jacobi_sweeps[TUCKER_MAX_MODES];
+  float ms_norm;                     /* device time per step (CUDA events), ms         */
+  float ms_gram[TUCKER_MAX_MODES];
+  float ms_eig[TUCKER_MAX_MODES];
+  float ms_ttm[TUCKER_MAX_MODES];
+  float ms_total;
+} tucker_result;
+
+/* Context: a stream, a device workspace and the last error string.
+ * `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  The context must be used from one host thread at a time. */
+tucker_status tucker_create(tucker_ctx** ctx, void* stream);
+tucker_status tucker_destroy(tucker_ctx* ctx);
+const char* tucker_last_error(const tucker_ctx* ctx);
+
+/* Options (key, value):
+ *   TUCKER_OPT_TIMING      1 = record per-step CUDA-event times into results
+ *   TUCKER_OPT_MAX_SWEEPS  Jacobi sweep cap (default 40; 0 = no sweep)
+ *   TUCKER_OPT_JACOBI_TOL  relative off-diagonal tolerance (default 1e-15) */
+#define TUCKER_OPT_TIMING 1
+#define TUCKER_OPT_MAX_SWEEPS 2
+#define TUCKER_OPT_JACOBI_TOL 3
+tucker_status tucker_set_option(tucker_ctx* ctx, int key, double value);
+
+/* ST-HOSVD, Algorithm 1 (Section 3.3).
+ *   x_dev      input tensor (dtype, dims), read only.
+ *   eps        relative accuracy; R_n = min{R in 1..I_n : sum_{i>=R} lambda_i
+ *              <= eps^2 ||X||^2 / N} (Eq. Un, 0-based, inclusive, negative
+ *              eigenvalues counted as 0).  Ignored when ranks_or_null != NULL.
+ *   ranks      the core size of the rank-specified variant (Section 8.4),
+ *              1 <= R_n <= I_n.
+ *   mode_order permutation of 0..N-1 (NULL = 0..N-1).
+ * On success *out receives a result to release with tucker_result_destroy.
+ * Errors: INVALID, OOM, NONFINITE (input has NaN/Inf), EIG_NOCONV (a
+ * result is still returned), UNSUPPORTED (MIXED with FP64 input), CUDA. */
+tucker_status tucker_sthosvd(tucker_ctx* ctx, const void* x_dev, tucker_dtype dtype,
+                             int ndim, const int64_t* dims, double eps,
+                             const int64_t* ranks_or_null, const int* mode_order_or_null,
+                             tucker_prec prec, tucker_result** out);
+tucker_status tucker_result_destroy(tucker_result* res);
+
+/* (Partial) reconstruction, Section 7: Z = G x_n A_n over the modes in
+ * `mode_order_or_null` (NULL = the flop-minimal order by exhaustive
+ * search), with A_n = rows begin_n..end_n-1 of U_n.  NULL begin/end = the
+ * whole range.  out_dev (caller-owned) holds prod(end_n - begin_n)
+ * elements of out_dtype.  Errors: INVALID (ranges, order), OOM, CUDA. */
+tucker_status tucker_reconstruct(tucker_ctx* ctx, const tucker_result* res,
+                                 const int64_t* begin_or_null, const int64_t* end_or_null,
+                                 const int* mode_order_or_null, tucker_prec prec,
+                                 void* out_dev, tucker_dtype out_dtype);
+
+/* General multi-TTM, Section 7: Z = G x_{p(0)} A_{p(0)} ... x_{p(N-1)} A_{p(N-1)}.
+ *   core_dev   R_0 x ... x R_{N-1} tensor (core_dtype).
+ *   mats_dev   N device pointers; A_n is out_dims[n] x core_dims[n], FP64,
+ *              column-major with leading dimension lda[n] >= out_dims[n]
+ *              (so a row range of U_n is U_n + begin with lda = I_n).
+ *   order      permutation (NULL = flop-minimal order, exhaustive search).
+ * out_dev holds prod(out_dims) elements.  The last TTM writes straight
+ * into out_dev; intermediates live in the context workspace. */
+tucker_status tucker_multi_ttm(tucker_ctx* ctx, const void* core_dev, tucker_dtype core_dtype,
+                               int ndim, const int64_t* core_dims,
+                               const double* const* mats_dev, const int64_t* lda,
+                               const int64_t* out_dims, const int* mode_order_or_null,
+                               tucker_prec prec, void* out_dev, tucker_dtype out_dtype);
+
+/* Mode order of a multi-TTM chain from core_dims to out_dims (host only).
+ * objective 0 = fewest multiply-adds sum_steps J^* K_n (Section 5.3 cost),
+ * 1 = smallest peak input+output of one step; exhaustive over N! orders,
+ * ties to the lexicographically first.  order_out receives N modes. */
+tucker_status tucker_ttm_order(int ndim, const int64_t* core_dims, const int64_t* out_dims,
+                               int objective, int* order_out);
+
+/* ---- single steps of the hot path (each one row of Algorithm 1) ---- */
+
+/* ||Y||^2 as an FP64 sum of squares (Section 2.2.2).  Synchronises.
+ * Returns NONFINITE (with *out_host set to the sum) if Y holds NaN/Inf. */
+tucker_status tucker_norm_sq(tucker_ctx* ctx, const void* y_dev, tucker_dtype dtype,
+                             int64_t count, double* out_host);
+
+/* Gram S = Y_(n) Y_(n)^T of the mode-n unfolding (Algorithm 2) over the
+ * strided slab view (Rt, I, L) of Y, with no unfolding materialised.
+ * S_dev: caller-owned I x I FP64 (full symmetric matrix written). */
+tucker_status tucker_gram(tucker_ctx* ctx, const void* y_dev, tucker_dtype dtype, int ndim,
+                          const int64_t* dims, int mode, tucker_prec prec, double* S_dev);
+
+/* All eigenpairs of the symmetric I x I FP64 matrix S (Section 5.2) by
+ * parallel cyclic Jacobi in FP64 on the whole GPU.  eigvals_dev (I) gets
+ * them in descending order, V_dev (I x I, column-major) the matching
+ * orthonormal eigenvectors.  *sweeps_host (may be NULL) the sweeps used.
+ * Synchronises.  EIG_NOCONV if the sweep cap was reached. */
+tucker_status tucker_eig(tucker_ctx* ctx, const double* S_dev, int64_t I,
+                         double* eigvals_dev, double* V_dev, int* sweeps_host);
+
+/* Rank cut of Eq. Un on descending eigenvalues: R = min{R in 1..I :
+ * sum_{i>=R} max(lambda_i, 0) <= thr}, accumulated from the smallest
+ * eigenvalue up.  Synchronises; *R_host and *discarded_host = tail(R). */
+tucker_status tucker_rank_cut(tucker_ctx* ctx, const double* eigvals_dev, int64_t I, double thr,
+                              int64_t* R_host, double* discarded_host);
+
+/* TTM Z = Y x_n A (Algorithm 3) for A of size K x J_n, FP64, column-major
+ * with leading dimension lda >= K, or row-major (a_rowmajor = 1, leading
+ * dimension lda >= J_n).  A = U_n^T is U_n's column-major storage read
+ * row-major.  z_dev (caller-owned) holds Y's dims with J_n -> K. */
+tucker_status tucker_ttm(tucker_ctx* ctx, const void* y_dev, tucker_dtype y_dtype, int ndim,
+                         const int64_t* dims, int mode, const double* A_dev, int64_t K,
+                         int64_t lda, int a_rowmajor, tucker_prec prec,
+                         void* z_dev, tucker_dtype z_dtype);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TUCKER_GB300_H */

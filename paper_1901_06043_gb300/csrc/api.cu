@@ -1,0 +1,631 @@
+// C ABI of the library: argument checks, workspace, and the host loop of
+// ST-HOSVD (Algorithm 1 of the TuckerMPI paper) and of the multi-TTM
+// reconstruction (Section 7).  Every arithmetic step runs in a device kernel.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace tk;
+
+struct tucker_ctx {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  int timing = 0;
+  int max_sweeps = 40;
+  double tol_rel = 1e-15;
+  double tol_abs = 1e-15;
+  std::string err;
+  // small device scratch
+  unsigned* d_words = nullptr;   // 256 words
+  double* d_small = nullptr;     // 64 doubles
+  int* d_info = nullptr;         // 16 ints
+  int64_t* d_i64 = nullptr;      // 16 int64
+};
+
+namespace {
+
+constexpr size_t kWords = 256;
+
+tucker_status set_err(tucker_ctx* c, tucker_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+tucker_status cuda_status(tucker_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return TUCKER_OK;
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return set_err(c, TUCKER_ERR_OOM, m);
+  return set_err(c, TUCKER_ERR_CUDA, m);
+}
+
+#define TK_CUDA(ctx, expr)                                              \
+  do {                                                                  \
+    cudaError_t _e = (expr);                                            \
+    if (_e != cudaSuccess) return cuda_status((ctx), _e, #expr);        \
+  } while (0)
+
+#define TK_TRY(expr)                                                    \
+  do {                                                                  \
+    tucker_status _s = (expr);                                          \
+    if (_s != TUCKER_OK) return _s;                                     \
+  } while (0)
+
+// Stream-ordered device buffer, freed on the context stream.
+struct DevBuf {
+  void* p = nullptr;
+  cudaStream_t st = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { reset(); }
+  void reset() {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+  }
+  void* release() { void* q = p; p = nullptr; return q; }
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+tucker_status dev_alloc(tucker_ctx* c, DevBuf& b, size_t bytes) {
+  b.reset();
+  b.st = c->stream;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMallocAsync(&b.p, bytes, c->stream);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    cudaGetLastError();
+    char m[128];
+    snprintf(m, sizeof m, "device allocation of %zu bytes failed", bytes);
+    return set_err(c, TUCKER_ERR_OOM, m);
+  }
+  return TUCKER_OK;
+}
+
+bool check_dims(int ndim, const int64_t* dims) {
+  if (ndim < 1 || ndim > TUCKER_MAX_MODES || !dims) return false;
+  for (int k = 0; k < ndim; ++k)
+    if (dims[k] < 1) return false;
+  return true;
+}
+
+int64_t numel(int ndim, const int64_t* dims) {
+  int64_t n = 1;
+  for (int k = 0; k < ndim; ++k) n *= dims[k];
+  return n;
+}
+
+bool check_order(int ndim, const int* order, int* out) {
+  bool seen[TUCKER_MAX_MODES] = {false};
+  for (int k = 0; k < ndim; ++k) {
+    int m = order ? order[k] : k;
+    if (m < 0 || m >= ndim || seen[m]) return false;
+    seen[m] = true;
+    out[k] = m;
+  }
+  return true;
+}
+
+tucker_status sync(tucker_ctx* c) {
+  TK_CUDA(c, cudaStreamSynchronize(c->stream));
+  return TUCKER_OK;
+}
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  bool on = false;
+  void start(tucker_ctx* c) {
+    on = c->timing != 0;
+    if (!on) return;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, c->stream);
+  }
+  void stop(tucker_ctx* c) {
+    if (on) cudaEventRecord(b, c->stream);
+  }
+  float ms() {
+    if (!on) return 0.f;
+    float t = 0.f;
+    cudaEventSynchronize(b);
+    cudaEventElapsedTime(&t, a, b);
+    return t;
+  }
+  ~Timer() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
+// ---------------------------------------------------------------- steps
+
+tucker_status do_norm(tucker_ctx* c, const void* y, tucker_dtype dt, int64_t n, double* out) {
+  int nb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8);
+  if (nb < 1) nb = 1;
+  DevBuf part;
+  TK_TRY(dev_alloc(c, part, sizeof(double) * nb));
+  TK_CUDA(c, cudaMemsetAsync(c->d_words, 0, sizeof(unsigned), c->stream));
+  TK_CUDA(c, launch_sumsq(y, dt, n, part.as<double>(), nb, c->d_words, c->d_small, c->stream));
+  double h = 0.0;
+  unsigned bad = 0;
+  TK_CUDA(c, cudaMemcpyAsync(&h, c->d_small, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TK_CUDA(c, cudaMemcpyAsync(&bad, c->d_words, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+  TK_TRY(sync(c));
+  *out = h;
+  if (bad) return set_err(c, TUCKER_ERR_NONFINITE, "tensor holds NaN or Inf");
+  return TUCKER_OK;
+}
+
+// Which kernel serves a Gram / TTM step: 0 SIMT FP64, 1 SIMT FP32, 2 tcgen05.
+int gram_kernel_for(tucker_prec prec, tucker_dtype dt, const SlabView& v, int sms) {
+  if (prec == TUCKER_PREC_FP64) return 0;
+  if (prec == TUCKER_PREC_MIXED && dt == TUCKER_F32 && plan_gram_tc(v.L, v.I, v.Rt, sms).ok) return 2;
+  return 1;
+}
+
+tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabView& v,
+                      tucker_prec prec, double* S, int* kernel_used) {
+  int kern = gram_kernel_for(prec, dt, v, c->num_sms);
+  if (kernel_used) *kernel_used = kern;
+  if (kern == 2) {
+    TcGramPlan p = plan_gram_tc(v.L, v.I, v.Rt, c->num_sms);
+    DevBuf scratch;
+    TK_TRY(dev_alloc(c, scratch, p.scratch_bytes));
+    TK_CUDA(c, cudaMemsetAsync(c->d_words + 8, 0, sizeof(unsigned), c->stream));
+    TK_CUDA(c, launch_gram_tc((const float*)y, v.L, v.I, v.Rt, p, scratch.as<double>(),
+                              c->d_words + 8, S, c->stream));
+    unsigned err = 0;
+    TK_CUDA(c, cudaMemcpyAsync(&err, c->d_words + 8, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                               c->stream));
+    TK_TRY(sync(c));
+    if (err) {
+      char m[96];
+      snprintf(m, sizeof m, "tensor-core Gram reported device error word 0x%x", err);
+      return set_err(c, TUCKER_ERR_CUDA, m);
+    }
+    return TUCKER_OK;
+  }
+  GramPlan p = plan_gram_simt(v.L, v.I, v.Rt, c->num_sms);
+  DevBuf scratch;
+  TK_TRY(dev_alloc(c, scratch, p.scratch_bytes));
+  TK_CUDA(c, launch_gram_simt(y, dt, kern == 0, v.L, v.I, v.Rt, p, scratch.as<double>(), S,
+                              c->stream));
+  return TUCKER_OK;
+}
+
+tucker_status do_eig(tucker_ctx* c, const double* S, int n, double* w, double* V, int* sweeps) {
+  DevBuf work;
+  TK_TRY(dev_alloc(c, work, jacobi_work_bytes(n)));
+  // ||S||_F^2 for the absolute part of the Jacobi threshold
+  int nb = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 1024);
+  DevBuf part;
+  TK_TRY(dev_alloc(c, part, sizeof(double) * std::max(nb, 1)));
+  TK_CUDA(c, launch_sumsq(S, TUCKER_F64, (int64_t)n * n, part.as<double>(), std::max(nb, 1),
+                          c->d_words + 16, c->d_small + 1, c->stream));
+  int ms = c->max_sweeps;
+  if (ms > 200) ms = 200;
+  TK_CUDA(c, launch_jacobi(S, n, work.as<double>(), c->d_small + 1, c->d_words + 32, ms,
+                           c->tol_rel, c->tol_abs, c->num_sms, w, V, c->d_info, c->stream));
+  int info[4] = {0, 0, 0, -1};
+  unsigned words[3] = {0, 0, 0};
+  TK_CUDA(c, cudaMemcpyAsync(info, c->d_info, sizeof(info), cudaMemcpyDeviceToHost, c->stream));
+  TK_CUDA(c, cudaMemcpyAsync(words, c->d_words + 32, sizeof(words), cudaMemcpyDeviceToHost,
+                             c->stream));
+  TK_TRY(sync(c));
+  if (words[2] & DEV_ERR_BARRIER_TIMEOUT)
+    return set_err(c, TUCKER_ERR_CUDA, "Jacobi grid barrier gave up waiting");
+  if (ms == 0) { info[2] = 0; info[3] = (n & 1) ? n : -1; }
+  TK_CUDA(c, launch_eig_finish(n, work.as<double>(), info, c->d_info, w, V, c->stream));
+  TK_TRY(sync(c));
+  if (sweeps) *sweeps = info[0];
+  if (!info[1] && ms > 0)
+    return set_err(c, TUCKER_ERR_EIG_NOCONV, "Jacobi reached the sweep cap without converging");
+  if (ms == 0) return set_err(c, TUCKER_ERR_EIG_NOCONV, "Jacobi sweep cap is 0");
+  return TUCKER_OK;
+}
+
+tucker_status do_cut(tucker_ctx* c, const double* w, int n, double thr, int fixed_R, int64_t* R,
+                     double* disc) {
+  DevBuf tail;
+  TK_TRY(dev_alloc(c, tail, sizeof(double) * (n + 1)));
+  TK_CUDA(c, launch_rank_cut(w, n, thr, fixed_R, c->d_i64, c->d_small + 2, tail.as<double>(),
+                             c->stream));
+  TK_CUDA(c, cudaMemcpyAsync(R, c->d_i64, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  TK_CUDA(c, cudaMemcpyAsync(disc, c->d_small + 2, sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
+  return sync(c);
+}
+
+tucker_status do_ttm(tucker_ctx* c, const void* y, tucker_dtype ydt, const SlabView& v,
+                     const double* A, int64_t K, int64_t lda, int arow, tucker_prec prec, void* z,
+                     tucker_dtype zdt, int* kernel_used) {
+  const bool tc = prec == TUCKER_PREC_MIXED && ydt == TUCKER_F32 && zdt == TUCKER_F32 &&
+                  ttm_tc_supported(v.L, v.I, v.Rt, K);
+  if (kernel_used) *kernel_used = tc ? 2 : (prec == TUCKER_PREC_FP64 ? 0 : 1);
+  if (tc) {
+    DevBuf scratch;
+    TK_TRY(dev_alloc(c, scratch, ttm_tc_scratch_bytes(v.I, K)));
+    TK_CUDA(c, cudaMemsetAsync(c->d_words + 9, 0, sizeof(unsigned), c->stream));
+    TK_CUDA(c, launch_ttm_tc((const float*)y, v.L, v.I, v.Rt, A, K, lda, arow, (float*)z,
+                             scratch.p, c->d_words + 9, c->stream));
+    unsigned err = 0;
+    TK_CUDA(c, cudaMemcpyAsync(&err, c->d_words + 9, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                               c->stream));
+    TK_TRY(sync(c));
+    if (err) {
+      char m[96];
+      snprintf(m, sizeof m, "tensor-core TTM reported device error word 0x%x", err);
+      return set_err(c, TUCKER_ERR_CUDA, m);
+    }
+    return TUCKER_OK;
+  }
+  TK_CUDA(c, launch_ttm_simt(y, ydt, prec == TUCKER_PREC_FP64, v.L, v.I, v.Rt, A, K, lda, arow, z,
+                             zdt, c->stream));
+  return TUCKER_OK;
+}
+
+void order_search(int N, const int64_t* R, const int64_t* K, int objective, int* out) {
+  std::vector<int> perm(N);
+  for (int k = 0; k < N; ++k) perm[k] = k;
+  bool first = true;
+  long double best = 0;
+  do {
+    int64_t cur[TUCKER_MAX_MODES];
+    for (int k = 0; k < N; ++k) cur[k] = R[k];
+    long double cost = 0, prev = 1;
+    for (int k = 0; k < N; ++k) prev *= (long double)cur[k];
+    long double peak = 0;
+    for (int s = 0; s < N; ++s) {
+      int n = perm[s];
+      long double sz = 1;
+      for (int k = 0; k < N; ++k) sz *= (long double)cur[k];
+      cost += sz * (long double)K[n];
+      cur[n] = K[n];
+      long double nsz = 1;
+      for (int k = 0; k < N; ++k) nsz *= (long double)cur[k];
+      peak = std::max(peak, sz + nsz);
+    }
+    long double obj = objective == 0 ? cost : peak;
+    if (first || obj < best) {
+      best = obj;
+      first = false;
+      for (int k = 0; k < N; ++k) out[k] = perm[k];
+    }
+  } while (std::next_permutation(perm.begin(), perm.end()));
+}
+
+}  // namespace
+
+extern "C" {
+
+tucker_status tucker_create(tucker_ctx** out, void* stream) {
+  if (!out) return TUCKER_ERR_INVALID;
+  *out = nullptr;
+  tucker_ctx* c = new tucker_ctx();
+  c->stream = (cudaStream_t)stream;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+      uint64_t thr = std::numeric_limits<uint64_t>::max();
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    e = cudaMalloc(&c->d_words, sizeof(unsigned) * kWords);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_small, sizeof(double) * 64);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_info, sizeof(int) * 16);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_i64, sizeof(int64_t) * 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->d_words); cudaFree(c->d_small); cudaFree(c->d_info); cudaFree(c->d_i64);
+    delete c;
+    return e == cudaErrorMemoryAllocation ? TUCKER_ERR_OOM : TUCKER_ERR_CUDA;
+  }
+  *out = c;
+  return TUCKER_OK;
+}
+
+tucker_status tucker_destroy(tucker_ctx* c) {
+  if (!c) return TUCKER_ERR_INVALID;
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->d_words);
+  cudaFree(c->d_small);
+  cudaFree(c->d_info);
+  cudaFree(c->d_i64);
+  delete c;
+  return TUCKER_OK;
+}
+
+const char* tucker_last_error(const tucker_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+tucker_status tucker_set_option(tucker_ctx* c, int key, double value) {
+  if (!c) return TUCKER_ERR_INVALID;
+  switch (key) {
+    case TUCKER_OPT_TIMING: c->timing = value != 0.0; return TUCKER_OK;
+    case TUCKER_OPT_MAX_SWEEPS:
+      if (value < 0 || value > 200) return set_err(c, TUCKER_ERR_INVALID, "sweep cap out of [0, 200]");
+      c->max_sweeps = (int)value;
+      return TUCKER_OK;
+    case TUCKER_OPT_JACOBI_TOL:
+      if (!(value > 0.0 && value < 1e-3)) return set_err(c, TUCKER_ERR_INVALID, "tolerance out of (0, 1e-3)");
+      c->tol_rel = value;
+      return TUCKER_OK;
+    default: return set_err(c, TUCKER_ERR_INVALID, "unknown option");
+  }
+}
+
+tucker_status tucker_norm_sq(tucker_ctx* c, const void* y, tucker_dtype dt, int64_t count,
+                             double* out) {
+  if (!c) return TUCKER_ERR_INVALID;
+  if (!y || !out || count < 0 || (dt != TUCKER_F32 && dt != TUCKER_F64))
+    return set_err(c, TUCKER_ERR_INVALID, "tucker_norm_sq: bad argument");
+  if (count == 0) { *out = 0.0; return TUCKER_OK; }
+  return do_norm(c, y, dt, count, out);
+}
+
+tucker_status tucker_gram(tucker_ctx* c, const void* y, tucker_dtype dt, int ndim,
+                          const int64_t* dims, int mode, tucker_prec prec, double* S) {
+  if (!c) return TUCKER_ERR_INVALID;
+  if (!y || !S || !check_dims(ndim, dims) || mode < 0 || mode >= ndim ||
+      (dt != TUCKER_F32 && dt != TUCKER_F64) || prec < 0 || prec > 2)
+    return set_err(c, TUCKER_ERR_INVALID, "tucker_gram: bad argument");
+  if (prec == TUCKER_PREC_MIXED && dt != TUCKER_F32)
+    return set_err(c, TUCKER_ERR_UNSUPPORTED, "MIXED precision needs FP32 input");
+  SlabView v = slab_view(ndim, dims, mode);
+  TK_TRY(do_gram(c, y, dt, v, prec, S, nullptr));
+  return sync(c);
+}
+
+tucker_status tucker_eig(tucker_ctx* c, const double* S, int64_t I, double* w, double* V,
+                         int* sweeps) {
+  if (!c) return TUCKER_ERR_INVALID;
+  if (!S || !w || !V || I < 1 || I > 32768)
+    return set_err(c, TUCKER_ERR_INVALID, "tucker_eig: bad argument");
+  return do_eig(c, S, (int)I, w, V, sweeps);
+}
+
+tucker_status tucker_rank_cut(tucker_ctx* c, const double* w, int64_t I, double thr, int64_t* R,
+                              double* disc) {
+  if (!c) return TUCKER_ERR_INVALID;
+  if (!w || !R || !disc || I < 1 || !(thr >= 0.0))
+    return set_err(c, TUCKER_ERR_INVALID, "tucker_rank_cut: bad argument");
+  return do_cut(c, w, (int)I, thr, 0, R, disc);
+}
+
+tucker_status tucker_ttm(tucker_ctx* c, const void* y, tucker_dtype ydt, int ndim,
+                         const int64_t* dims, int mode, const double* A, int64_t K, int64_t lda,
+                         int arow, tucker_prec prec, void* z, tucker_dtype zdt) {
+  if (!c) return TUCKER_ERR_INVALID;
+  if (!y || !A || !z || !check_dims(ndim, dims) || mode < 0 || mode >= ndim || K < 1 ||
+      (ydt != TUCKER_F32 && ydt != TUCKER_F64) || (zdt != TUCKER_F32 && zdt != TUCKER_F64) ||
+      prec < 0 || prec > 2)
+    return set_err(c, TUCKER_ERR_INVALID, "tucker_ttm: bad argument");
+  if (arow ? lda < dims[mode] : lda < K)
+    return set_err(c, TUCKER_ERR_INVALID, "tucker_ttm: leading dimension too small");
+  SlabView v = slab_view(ndim, dims, mode);
+  TK_TRY(do_ttm(c, y, ydt, v, A, K, lda, arow, prec, z, zdt, nullptr));
+  return sync(c);
+}
+
+tucker_status tucker_result_destroy(tucker_result* r) {
+  if (!r) return TUCKER_ERR_INVALID;
+  cudaDeviceSynchronize();
+  cudaFree(r->core);
+  for (int k = 0; k < TUCKER_MAX_MODES; ++k) {
+    cudaFree(r->factors[k]);
+    cudaFree(r->eigvals[k]);
+  }
+  delete r;
+  return TUCKER_OK;
+}
+
+tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int ndim,
+                             const int64_t* dims, double eps, const int64_t* ranks,
+                             const int* order_in, tucker_prec prec, tucker_result** out) {
+  if (!c) return TUCKER_ERR_INVALID;
+  if (!out) return set_err(c, TUCKER_ERR_INVALID, "null result pointer");
+  *out = nullptr;
+  if (!x || !check_dims(ndim, dims) || (dt != TUCKER_F32 && dt != TUCKER_F64) || prec < 0 ||
+      prec > 2)
+    return set_err(c, TUCKER_ERR_INVALID, "tucker_sthosvd: bad argument");
+  if (!ranks && !(eps >= 0.0 && std::isfinite(eps)))
+    return set_err(c, TUCKER_ERR_INVALID, "eps must be finite and >= 0");
+  if (ranks)
+    for (int k = 0; k < ndim; ++k)
+      if (ranks[k] < 1 || ranks[k] > dims[k])
+        return set_err(c, TUCKER_ERR_INVALID, "ranks must satisfy 1 <= R_n <= I_n");
+  int order[TUCKER_MAX_MODES];
+  if (!check_order(ndim, order_in, order))
+    return set_err(c, TUCKER_ERR_INVALID, "mode order is not a permutation");
+  if (prec == TUCKER_PREC_MIXED && dt != TUCKER_F32)
+    return set_err(c, TUCKER_ERR_UNSUPPORTED, "MIXED precision needs FP32 input");
+  int64_t imax = 0;
+  for (int k = 0; k < ndim; ++k) imax = std::max(imax, dims[k]);
+  if (imax > 32768) return set_err(c, TUCKER_ERR_INVALID, "mode size above 32768");
+
+  tucker_result* r = new tucker_result();
+  memset(r, 0, sizeof(*r));
+  struct Guard {
+    tucker_result*& r;
+    ~Guard() { if (r) tucker_result_destroy(r); }
+  } guard{r};
+  r->ndim = ndim;
+  const tucker_dtype wdt = (prec == TUCKER_PREC_FP64) ? TUCKER_F64 : dt;
+  r->core_dtype = wdt;
+  for (int k = 0; k < ndim; ++k) { r->dims[k] = dims[k]; r->mode_order[k] = order[k]; }
+
+  Timer t_total, t_norm;
+  t_total.start(c);
+  t_norm.start(c);
+  const int64_t nx = numel(ndim, dims);
+  double nrm2 = 0.0;
+  TK_TRY(do_norm(c, x, dt, nx, &nrm2));
+  t_norm.stop(c);
+  r->norm_x_sq = nrm2;
+  const double thr = ranks ? 0.0 : eps * eps * nrm2 / ndim;
+  r->threshold = thr;
+
+  DevBuf S, V, ycur;
+  TK_TRY(dev_alloc(c, S, sizeof(double) * imax * imax));
+  TK_TRY(dev_alloc(c, V, sizeof(double) * imax * imax));
+  const void* y = x;
+  tucker_dtype ydt = dt;
+  int64_t cur[TUCKER_MAX_MODES];
+  for (int k = 0; k < ndim; ++k) cur[k] = dims[k];
+  bool noconv = false;
+  for (int s = 0; s < ndim; ++s) {
+    const int n = order[s];
+    const SlabView v = slab_view(ndim, cur, n);
+    const int I = (int)v.I;
+    Timer tmg, tme, tmt;
+    tmg.start(c);
+    TK_TRY(do_gram(c, y, ydt, v, prec, S.as<double>(), nullptr));
+    tmg.stop(c);
+    DevBuf w;
+    TK_TRY(dev_alloc(c, w, sizeof(double) * I));
+    tme.start(c);
+    int sweeps = 0;
+    tucker_status es = do_eig(c, S.as<double>(), I, w.as<double>(), V.as<double>(), &sweeps);
+    tme.stop(c);
+    if (es != TUCKER_OK && es != TUCKER_ERR_EIG_NOCONV) return es;
+    r->jacobi_sweeps[n] = sweeps;
+    int64_t R = 0;
+    double disc = 0.0;
+    TK_TRY(do_cut(c, w.as<double>(), I, thr, ranks ? (int)ranks[n] : 0, &R, &disc));
+    r->ranks[n] = R;
+    r->discarded_sq[n] = disc;
+    r->eigvals[n] = w.as<double>();
+    w.release();
+    DevBuf U;
+    TK_TRY(dev_alloc(c, U, sizeof(double) * I * R));
+    TK_CUDA(c, cudaMemcpyAsync(U.p, V.p, sizeof(double) * I * R, cudaMemcpyDeviceToDevice,
+                               c->stream));
+    r->factors[n] = U.as<double>();
+    U.release();
+    // Y <- Y x_n U_n^T : A = U^T is U's column-major storage read row-major
+    int64_t nd[TUCKER_MAX_MODES];
+    for (int k = 0; k < ndim; ++k) nd[k] = cur[k];
+    nd[n] = R;
+    DevBuf z;
+    TK_TRY(dev_alloc(c, z, dtype_size(wdt) * numel(ndim, nd)));
+    tmt.start(c);
+    TK_TRY(do_ttm(c, y, ydt, v, r->factors[n], R, I, 1, prec, z.p, wdt, nullptr));
+    tmt.stop(c);
+    ycur.reset();
+    ycur.p = z.release();
+    ycur.st = c->stream;
+    y = ycur.p;
+    ydt = wdt;
+    cur[n] = R;
+    if (es == TUCKER_ERR_EIG_NOCONV) noconv = true;
+    TK_TRY(sync(c));
+    if (c->timing) {
+      r->ms_gram[n] = tmg.ms();
+      r->ms_eig[n] = tme.ms();
+      r->ms_ttm[n] = tmt.ms();
+    }
+  }
+  r->core = ycur.release();
+  t_total.stop(c);
+  TK_TRY(sync(c));
+  if (c->timing) {
+    r->ms_norm = t_norm.ms();
+    r->ms_total = t_total.ms();
+  }
+  *out = r;
+  r = nullptr;  // disarm guard
+  if (noconv) return set_err(c, TUCKER_ERR_EIG_NOCONV, "Jacobi reached the sweep cap in some mode");
+  return TUCKER_OK;
+}
+
+tucker_status tucker_ttm_order(int ndim, const int64_t* core_dims, const int64_t* out_dims,
+                               int objective, int* order_out) {
+  if (!check_dims(ndim, core_dims) || !check_dims(ndim, out_dims) || !order_out ||
+      (objective != 0 && objective != 1))
+    return TUCKER_ERR_INVALID;
+  order_search(ndim, core_dims, out_dims, objective, order_out);
+  return TUCKER_OK;
+}
+
+tucker_status tucker_multi_ttm(tucker_ctx* c, const void* core, tucker_dtype cdt, int ndim,
+                               const int64_t* core_dims, const double* const* mats,
+                               const int64_t* lda, const int64_t* out_dims, const int* order_in,
+                               tucker_prec prec, void* out, tucker_dtype odt) {
+  if (!c) return TUCKER_ERR_INVALID;
+  if (!core || !mats || !lda || !out || !check_dims(ndim, core_dims) ||
+      !check_dims(ndim, out_dims) || (cdt != TUCKER_F32 && cdt != TUCKER_F64) ||
+      (odt != TUCKER_F32 && odt != TUCKER_F64) || prec < 0 || prec > 2)
+    return set_err(c, TUCKER_ERR_INVALID, "tucker_multi_ttm: bad argument");
+  for (int k = 0; k < ndim; ++k)
+    if (!mats[k] || lda[k] < out_dims[k])
+      return set_err(c, TUCKER_ERR_INVALID, "tucker_multi_ttm: bad factor or leading dimension");
+  int order[TUCKER_MAX_MODES];
+  if (order_in) {
+    if (!check_order(ndim, order_in, order))
+      return set_err(c, TUCKER_ERR_INVALID, "mode order is not a permutation");
+  } else {
+    order_search(ndim, core_dims, out_dims, 0, order);
+  }
+  const tucker_dtype wdt = (prec == TUCKER_PREC_FP64) ? TUCKER_F64 : (cdt == TUCKER_F64 ? TUCKER_F64 : TUCKER_F32);
+  int64_t cur[TUCKER_MAX_MODES];
+  for (int k = 0; k < ndim; ++k) cur[k] = core_dims[k];
+  const void* y = core;
+  tucker_dtype ydt = cdt;
+  DevBuf hold;
+  for (int s = 0; s < ndim; ++s) {
+    const int n = order[s];
+    const SlabView v = slab_view(ndim, cur, n);
+    int64_t nd[TUCKER_MAX_MODES];
+    for (int k = 0; k < ndim; ++k) nd[k] = cur[k];
+    nd[n] = out_dims[n];
+    const bool last = (s == ndim - 1);
+    DevBuf z;
+    void* zp = out;
+    tucker_dtype zdt = odt;
+    if (!last) {
+      TK_TRY(dev_alloc(c, z, dtype_size(wdt) * numel(ndim, nd)));
+      zp = z.p;
+      zdt = wdt;
+    }
+    TK_TRY(do_ttm(c, y, ydt, v, mats[n], out_dims[n], lda[n], 0, prec, zp, zdt, nullptr));
+    if (!last) {
+      hold.reset();
+      hold.p = z.release();
+      hold.st = c->stream;
+      y = hold.p;
+      ydt = wdt;
+    }
+    cur[n] = out_dims[n];
+  }
+  return sync(c);
+}
+
+tucker_status tucker_reconstruct(tucker_ctx* c, const tucker_result* r, const int64_t* begin,
+                                 const int64_t* end, const int* order, tucker_prec prec,
+                                 void* out, tucker_dtype odt) {
+  if (!c) return TUCKER_ERR_INVALID;
+  if (!r || !out) return set_err(c, TUCKER_ERR_INVALID, "tucker_reconstruct: bad argument");
+  const int N = r->ndim;
+  const double* mats[TUCKER_MAX_MODES];
+  int64_t lda[TUCKER_MAX_MODES], od[TUCKER_MAX_MODES];
+  for (int k = 0; k < N; ++k) {
+    int64_t b = begin ? begin[k] : 0, e = end ? end[k] : r->dims[k];
+    if (b < 0 || e > r->dims[k] || e <= b)
+      return set_err(c, TUCKER_ERR_INVALID, "reconstruction range out of bounds or empty");
+    mats[k] = r->factors[k] + b;
+    lda[k] = r->dims[k];
+    od[k] = e - b;
+  }
+  return tucker_multi_ttm(c, r->core, r->core_dtype, N, r->ranks, mats, lda, od, order, prec,
+                          out, odt);
+}
+
+}  // extern "C"

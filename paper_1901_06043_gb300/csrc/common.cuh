@@ -1,0 +1,80 @@
+// Shared device/host helpers of the tucker_gb300 library (internal).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tucker_gb300.h"
+
+namespace tk {
+
+// Error words written by kernels (bit flags, read by the host after a call).
+enum : unsigned {
+  DEV_ERR_BARRIER_TIMEOUT = 1u,   // a grid barrier gave up waiting
+  DEV_ERR_BOUNDS = 2u,            // an index check failed and the access was skipped
+  DEV_ERR_MBAR_TIMEOUT = 4u,      // an mbarrier wait gave up
+};
+
+template <typename T> struct dtype_of;
+template <> struct dtype_of<float> { static constexpr tucker_dtype value = TUCKER_F32; };
+template <> struct dtype_of<double> { static constexpr tucker_dtype value = TUCKER_F64; };
+
+inline size_t dtype_size(tucker_dtype d) { return d == TUCKER_F64 ? 8 : 4; }
+
+// Slab view of mode n of a tensor with dims J: element (l, i, r) at
+// l + L*(i + I*r) with L = prod_{k<n} J_k, I = J_n, Rt = prod_{k>n} J_k.
+struct SlabView {
+  int64_t L, I, Rt;
+};
+
+inline SlabView slab_view(int ndim, const int64_t* dims, int n) {
+  SlabView v{1, dims[n], 1};
+  for (int k = 0; k < n; ++k) v.L *= dims[k];
+  for (int k = n + 1; k < ndim; ++k) v.Rt *= dims[k];
+  return v;
+}
+
+// Grid-wide barrier for a cooperatively launched kernel (all CTAs resident).
+// Every wait is bounded: after `limit` polls the CTA records
+// DEV_ERR_BARRIER_TIMEOUT in *err and returns false; callers then exit.
+struct GridBarrier {
+  unsigned* count;     // arrivals in the current generation
+  unsigned* gen;       // generation counter
+  unsigned* err;       // error word
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ bool grid_sync(const GridBarrier& b, unsigned& my_gen,
+                                          unsigned long long limit = (1ull << 24)) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned g = my_gen;
+    __threadfence();
+    unsigned arrived = atomicAdd(b.count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(b.count, 0u);
+      __threadfence();
+      atomicAdd(b.gen, 1u);
+    } else {
+      unsigned long long it = 0;
+      while (ld_acquire_u32(b.gen) == g) {
+        if (++it > limit) { atomicOr(b.err, DEV_ERR_BARRIER_TIMEOUT); ok = 0; break; }
+        if (it > 64) __nanosleep(64);
+      }
+    }
+    __threadfence();
+    my_gen = g + 1;
+    if (ld_acquire_u32(b.err) & DEV_ERR_BARRIER_TIMEOUT) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+}  // namespace tk

@@ -1,0 +1,55 @@
+// Launchers of the device kernels (internal to the library).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tucker_gb300.h"
+
+namespace tk {
+
+// ---- FP64 sum of squares: partial per block, then a fixed-order reduction
+cudaError_t launch_sumsq(const void* y, tucker_dtype dt, int64_t n, double* partial, int nblocks,
+                         unsigned* nonfinite, double* out, cudaStream_t st);
+
+// ---- SIMT Gram (FP64 or FP32 products), split-K partial tiles + reduction
+struct GramPlan {
+  int ntiles = 0, ksplit = 0;
+  size_t scratch_bytes = 0;
+};
+GramPlan plan_gram_simt(int64_t L, int64_t I, int64_t Rt, int num_sms);
+cudaError_t launch_gram_simt(const void* y, tucker_dtype dt, bool fp64, int64_t L, int64_t I,
+                             int64_t Rt, const GramPlan& p, double* scratch, double* S,
+                             cudaStream_t st);
+
+// ---- SIMT TTM
+cudaError_t launch_ttm_simt(const void* y, tucker_dtype ydt, bool fp64, int64_t L, int64_t I,
+                            int64_t Rt, const double* A, int64_t K, int64_t lda, int a_rowmajor,
+                            void* z, tucker_dtype zdt, cudaStream_t st);
+
+// ---- tensor-core (tcgen05) Gram and TTM on the FP16 hi/lo split
+struct TcGramPlan {
+  int ok = 0;
+  int64_t ntiles = 0, nsplit = 0;
+  size_t scratch_bytes = 0;
+};
+TcGramPlan plan_gram_tc(int64_t L, int64_t I, int64_t Rt, int num_sms);
+cudaError_t launch_gram_tc(const float* y, int64_t L, int64_t I, int64_t Rt, const TcGramPlan& p,
+                           double* scratch, unsigned* err, double* S, cudaStream_t st);
+int ttm_tc_supported(int64_t L, int64_t I, int64_t Rt, int64_t K);
+cudaError_t launch_ttm_tc(const float* y, int64_t L, int64_t I, int64_t Rt, const double* A,
+                          int64_t K, int64_t lda, int a_rowmajor, float* z, void* scratch,
+                          unsigned* err, cudaStream_t st);
+size_t ttm_tc_scratch_bytes(int64_t I, int64_t K);
+
+// ---- Jacobi eigensolver, sort and rank cut
+size_t jacobi_work_bytes(int n);
+cudaError_t launch_jacobi(const double* S, int n, double* work, const double* fro2, unsigned* words,
+                          int max_sweeps, double tol_rel, double tol_abs, int num_sms,
+                          double* w_out, double* V_out, int* info_dev, cudaStream_t st);
+cudaError_t launch_eig_finish(int n, double* work, const int* info_host, int* info_dev,
+                              double* w_out, double* V_out, cudaStream_t st);
+cudaError_t launch_rank_cut(const double* w, int n, double thr, int fixed_R, int64_t* out_R,
+                            double* out_d, double* tail, cudaStream_t st);
+
+}  // namespace tk

@@ -1,0 +1,379 @@
+// SIMT kernels of the ST-HOSVD path: FP64 sum of squares (Section 2.2.2),
+// slab-batched Gram (Algorithm 2) and slab TTM (Algorithm 3) in FP64 or
+// FP32 arithmetic, over the unfolding-free strided view (Rt, I, L) of
+// Section 4.2: element (l, i, r) of the mode-n view sits at l + L*(i + I*r).
+#include <cstdio>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace tk {
+
+// ------------------------------------------------------------ sum of squares
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sumsq(const T* __restrict__ y, int64_t n,
+                                               double* __restrict__ partial,
+                                               unsigned* __restrict__ nonfinite) {
+  double acc = 0.0;
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double v = (double)y[i];
+    bad |= !isfinite(v);
+    acc = fma(v, v, acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double s[8];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  if (bad) atomicOr(nonfinite, 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// Fixed-order reduction of `count` partial sums into out[0] (one block).
+__global__ void __launch_bounds__(256) k_reduce_sum(const double* __restrict__ partial, int count,
+                                                    double* __restrict__ out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) acc += partial[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double s[8];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+    out[0] = t;
+  }
+}
+
+cudaError_t launch_sumsq(const void* y, tucker_dtype dt, int64_t n, double* partial, int nblocks,
+                         unsigned* nonfinite, double* out, cudaStream_t st) {
+  if (dt == TUCKER_F64)
+    k_sumsq<double><<<nblocks, 256, 0, st>>>((const double*)y, n, partial, nonfinite);
+  else
+    k_sumsq<float><<<nblocks, 256, 0, st>>>((const float*)y, n, partial, nonfinite);
+  k_reduce_sum<<<1, 256, 0, st>>>(partial, nblocks, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Gram
+
+// Geometry of the K (contraction) dimension of a slab view.  K runs over
+// (r, l) pairs.  With L == 1 a K-block is BK consecutive slabs (column mode,
+// contiguous along i); otherwise a K-block is BK consecutive l of one slab
+// (row mode, contiguous along l), masked at l >= L.
+struct KGeom {
+  int64_t L, I, Rt;
+  int64_t nLB;   // K-blocks per slab in row mode
+  int64_t NKB;   // total K-blocks
+};
+
+constexpr int GT = 64;    // Gram output tile
+constexpr int GBK = 16;   // K-block
+
+__host__ __device__ inline KGeom make_kgeom(int64_t L, int64_t I, int64_t Rt, int bk) {
+  KGeom g{L, I, Rt, 1, 0};
+  if (L == 1) {
+    g.NKB = (Rt + bk - 1) / bk;
+  } else {
+    g.nLB = (L + bk - 1) / bk;
+    g.NKB = Rt * g.nLB;
+  }
+  return g;
+}
+
+// Loads the (GBK x GT) panel of rows [i0, i0+GT) for K-block kb into regs.
+template <typename TIn, typename TC>
+__device__ __forceinline__ void gram_load(const TIn* __restrict__ y, const KGeom& g, int64_t kb,
+                                          int64_t i0, TC (&reg)[4]) {
+  const int tid = threadIdx.x;
+  if (g.L == 1) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int idx = tid + 256 * e;
+      int ii = idx % GT, kk = idx / GT;
+      int64_t r = kb * GBK + kk, i = i0 + ii;
+      reg[e] = (r < g.Rt && i < g.I) ? (TC)y[i + g.I * r] : (TC)0;
+    }
+  } else {
+    int64_t r = kb / g.nLB;
+    int64_t l0 = (kb - r * g.nLB) * GBK;
+    const TIn* base = y + g.L * g.I * r;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int idx = tid + 256 * e;
+      int kk = idx % GBK, ii = idx / GBK;
+      int64_t l = l0 + kk, i = i0 + ii;
+      reg[e] = (l < g.L && i < g.I) ? (TC)base[l + g.L * i] : (TC)0;
+    }
+  }
+}
+
+template <typename TC>
+__device__ __forceinline__ void gram_store(TC (*sm)[GT + 1], const KGeom& g, const TC (&reg)[4]) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    int idx = tid + 256 * e;
+    int ii, kk;
+    if (g.L == 1) { ii = idx % GT; kk = idx / GT; }
+    else { kk = idx % GBK; ii = idx / GBK; }
+    sm[kk][ii] = reg[e];
+  }
+}
+
+// One CTA: lower-triangle tile (ta >= tb) of S over K-blocks [kb0, kb1).
+// TC = product type.  FP32 products are summed in FP32 over chunks of
+// CHUNK K-blocks and the chunks in FP64; FP64 products in FP64 throughout.
+// Writes the FP64 partial tile to part[(ks * ntiles + tile) * GT * GT].
+template <typename TIn, typename TC>
+__global__ void __launch_bounds__(256) k_gram_simt(const TIn* __restrict__ y, KGeom g, int ntiles,
+                                                   int ksplit, double* __restrict__ part) {
+  constexpr int CHUNK = 4;
+  __shared__ TC As[GBK][GT + 1];
+  __shared__ TC Bs[GBK][GT + 1];
+  const int tile = blockIdx.x;
+  const int ks = blockIdx.y;
+  // tile -> (ta, tb), ta >= tb, row-major over the lower triangle
+  int ta = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);
+  while ((ta + 1) * (ta + 2) / 2 <= tile) ++ta;
+  while (ta * (ta + 1) / 2 > tile) --ta;
+  const int tb = tile - ta * (ta + 1) / 2;
+  const bool diag = (ta == tb);
+  const int64_t ia0 = (int64_t)ta * GT, ib0 = (int64_t)tb * GT;
+  const int64_t kb0 = g.NKB * ks / ksplit, kb1 = g.NKB * (ks + 1) / ksplit;
+
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc64[4][4];
+  TC acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) { acc64[u][v] = 0.0; acc[u][v] = (TC)0; }
+
+  TC ra[4], rb[4];
+  if (kb0 < kb1) {
+    gram_load<TIn, TC>(y, g, kb0, ia0, ra);
+    if (!diag) gram_load<TIn, TC>(y, g, kb0, ib0, rb);
+  }
+  int chunk = 0;
+  for (int64_t kb = kb0; kb < kb1; ++kb) {
+    gram_store<TC>(As, g, ra);
+    if (!diag) gram_store<TC>(Bs, g, rb);
+    __syncthreads();
+    if (kb + 1 < kb1) {
+      gram_load<TIn, TC>(y, g, kb + 1, ia0, ra);
+      if (!diag) gram_load<TIn, TC>(y, g, kb + 1, ib0, rb);
+    }
+    TC (*Bp)[GT + 1] = diag ? As : Bs;
+#pragma unroll
+    for (int kk = 0; kk < GBK; ++kk) {
+      TC a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = As[kk][ty + 16 * u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) b[v] = Bp[kk][tx + 16 * v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+    if (sizeof(TC) == 4 && ++chunk == CHUNK) {
+      chunk = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) { acc64[u][v] += (double)acc[u][v]; acc[u][v] = (TC)0; }
+    }
+  }
+  double* out = part + ((int64_t)ks * ntiles + tile) * GT * GT;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      out[(ty + 16 * u) * GT + tx + 16 * v] = acc64[u][v] + (double)acc[u][v];
+}
+
+// S[i][j] = S[j][i] = sum over ks (fixed order) of the partial tiles.
+__global__ void k_gram_reduce(const double* __restrict__ part, int ntiles, int ksplit, int64_t I,
+                              double* __restrict__ S) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)ntiles * GT * GT) return;
+  int tile = (int)(idx / (GT * GT));
+  int e = (int)(idx % (GT * GT));
+  int ta = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);
+  while ((ta + 1) * (ta + 2) / 2 <= tile) ++ta;
+  while (ta * (ta + 1) / 2 > tile) --ta;
+  int tb = tile - ta * (ta + 1) / 2;
+  int64_t i = (int64_t)ta * GT + e / GT, j = (int64_t)tb * GT + e % GT;
+  if (i >= I || j >= I) return;
+  if (ta == tb && j > i) return;  // diagonal tile: write its lower half (and mirror)
+  double s = 0.0;
+  for (int k = 0; k < ksplit; ++k) s += part[((int64_t)k * ntiles + tile) * GT * GT + e];
+  S[i * I + j] = s;
+  S[j * I + i] = s;
+}
+
+GramPlan plan_gram_simt(int64_t L, int64_t I, int64_t Rt, int num_sms) {
+  GramPlan p;
+  KGeom g = make_kgeom(L, I, Rt, GBK);
+  int T = (int)((I + GT - 1) / GT);
+  p.ntiles = T * (T + 1) / 2;
+  int64_t want = ((int64_t)num_sms * 4 + p.ntiles - 1) / p.ntiles;
+  int64_t cap = (int64_t)(256ll << 20) / ((int64_t)p.ntiles * GT * GT * 8);
+  if (want > cap) want = cap;
+  if (want > g.NKB) want = g.NKB;
+  if (want < 1) want = 1;
+  p.ksplit = (int)want;
+  p.scratch_bytes = (size_t)p.ksplit * p.ntiles * GT * GT * sizeof(double);
+  return p;
+}
+
+cudaError_t launch_gram_simt(const void* y, tucker_dtype dt, bool fp64, int64_t L, int64_t I,
+                             int64_t Rt, const GramPlan& p, double* scratch, double* S,
+                             cudaStream_t st) {
+  KGeom g = make_kgeom(L, I, Rt, GBK);
+  dim3 grid(p.ntiles, p.ksplit);
+  if (dt == TUCKER_F64) {
+    if (fp64) k_gram_simt<double, double><<<grid, 256, 0, st>>>((const double*)y, g, p.ntiles, p.ksplit, scratch);
+    else k_gram_simt<double, float><<<grid, 256, 0, st>>>((const double*)y, g, p.ntiles, p.ksplit, scratch);
+  } else {
+    if (fp64) k_gram_simt<float, double><<<grid, 256, 0, st>>>((const float*)y, g, p.ntiles, p.ksplit, scratch);
+    else k_gram_simt<float, float><<<grid, 256, 0, st>>>((const float*)y, g, p.ntiles, p.ksplit, scratch);
+  }
+  int64_t tot = (int64_t)p.ntiles * GT * GT;
+  k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(scratch, p.ntiles, p.ksplit, I, S);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- TTM
+
+constexpr int TT = 64;    // output tile (k and m)
+constexpr int TBI = 16;   // contraction step
+
+// Z (K x M) = A (K x I) * Y (I x M), M = the (r, l) pairs of the slab view.
+// Row mode (L > 1): an m-tile is 64 consecutive l of one slab.  Column mode
+// (L == 1): an m-tile is 64 consecutive slabs.
+template <typename TIn, typename TOut, typename TC>
+__global__ void __launch_bounds__(256) k_ttm_simt(const TIn* __restrict__ y, int64_t L, int64_t I,
+                                                  int64_t Rt, int64_t nLT,
+                                                  const double* __restrict__ A, int64_t K,
+                                                  int64_t lda, int a_rowmajor,
+                                                  TOut* __restrict__ z) {
+  __shared__ TC As[TBI][TT + 1];   // As[i][k]
+  __shared__ TC Ys[TBI][TT + 1];   // Ys[i][m]
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int64_t mt = blockIdx.x;
+  const int64_t k0 = (int64_t)blockIdx.y * TT;
+  int64_t r0, l0;
+  if (L == 1) { r0 = mt * TT; l0 = 0; }
+  else { r0 = mt / nLT; l0 = (mt - r0 * nLT) * TT; }
+  const TIn* ybase = (L == 1) ? y : y + L * I * r0;
+
+  TC acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = (TC)0;
+
+  for (int64_t i0 = 0; i0 < I; i0 += TBI) {
+    // A tile: 64 k x 16 i
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int idx = tid + 256 * e;
+      int ii, kk;
+      if (a_rowmajor) { ii = idx % TBI; kk = idx / TBI; }
+      else { kk = idx % TT; ii = idx / TT; }
+      int64_t k = k0 + kk, i = i0 + ii;
+      TC v = (TC)0;
+      if (k < K && i < I) v = (TC)(a_rowmajor ? A[k * lda + i] : A[k + lda * i]);
+      As[ii][kk] = v;
+    }
+    // Y tile: 16 i x 64 m
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int idx = tid + 256 * e;
+      int ii, mm;
+      TC v = (TC)0;
+      if (L == 1) {
+        ii = idx % TBI; mm = idx / TBI;
+        int64_t i = i0 + ii, r = r0 + mm;
+        if (i < I && r < Rt) v = (TC)ybase[i + I * r];
+      } else {
+        mm = idx % TT; ii = idx / TT;
+        int64_t i = i0 + ii, l = l0 + mm;
+        if (i < I && l < L) v = (TC)ybase[l + L * i];
+      }
+      Ys[ii][mm] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ii = 0; ii < TBI; ++ii) {
+      TC a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = As[ii][ty + 16 * u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) b[v] = Ys[ii][tx + 16 * v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  // write Z: (k, m) -> l + L*(k + K*r)
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int64_t k = k0 + ty + 16 * u;
+    if (k >= K) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int mm = tx + 16 * v;
+      if (L == 1) {
+        int64_t r = r0 + mm;
+        if (r < Rt) z[k + K * r] = (TOut)acc[u][v];
+      } else {
+        int64_t l = l0 + mm;
+        if (l < L) z[l + L * (k + K * r0)] = (TOut)acc[u][v];
+      }
+    }
+  }
+}
+
+template <typename TIn, typename TOut>
+static void ttm_dispatch_c(bool fp64, dim3 grid, cudaStream_t st, const void* y, int64_t L, int64_t I,
+                           int64_t Rt, int64_t nLT, const double* A, int64_t K, int64_t lda,
+                           int arow, void* z) {
+  if (fp64)
+    k_ttm_simt<TIn, TOut, double><<<grid, 256, 0, st>>>((const TIn*)y, L, I, Rt, nLT, A, K, lda, arow, (TOut*)z);
+  else
+    k_ttm_simt<TIn, TOut, float><<<grid, 256, 0, st>>>((const TIn*)y, L, I, Rt, nLT, A, K, lda, arow, (TOut*)z);
+}
+
+cudaError_t launch_ttm_simt(const void* y, tucker_dtype ydt, bool fp64, int64_t L, int64_t I,
+                            int64_t Rt, const double* A, int64_t K, int64_t lda, int a_rowmajor,
+                            void* z, tucker_dtype zdt, cudaStream_t st) {
+  int64_t nLT = 1, nMT;
+  if (L == 1) nMT = (Rt + TT - 1) / TT;
+  else { nLT = (L + TT - 1) / TT; nMT = Rt * nLT; }
+  if (nMT <= 0 || K <= 0) return cudaSuccess;
+  if (nMT > 0x7fffffffll) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)nMT, (unsigned)((K + TT - 1) / TT));
+  if (ydt == TUCKER_F64) {
+    if (zdt == TUCKER_F64) ttm_dispatch_c<double, double>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, z);
+    else ttm_dispatch_c<double, float>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, z);
+  } else {
+    if (zdt == TUCKER_F64) ttm_dispatch_c<float, double>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, z);
+    else ttm_dispatch_c<float, float>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, z);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace tk

@@ -1,0 +1,357 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every comparison runs on the same seeded inputs on both sides.  Tolerances
+(FP64 path): relative reconstruction-error difference <= 1e-12, eigenvalues
+<= 1e-10 relative to the largest, factor subspaces by largest principal
+angle <= 1e-8 rad where the eigenvalue gap at the cut is wide, identical
+ranks.  FP32 products get the bound derived from single rounding of each
+product (documented beside each test).
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_06043_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1901_06043_gb300 import tucker
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    c = tucker.Context(timing=True)
+    yield c
+    c.close()
+
+
+def dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    return t.detach().double().cpu().numpy()
+
+
+def max_angle(U, W):
+    """Largest principal angle between span(U) and span(W) (orthonormal)."""
+    s = np.linalg.svd(U.T @ W, compute_uv=False)
+    return float(np.arccos(np.clip(s.min(), -1.0, 1.0)))
+
+
+def sin_angle(U, W):
+    """sin of the largest principal angle (accurate for small angles)."""
+    P = W - U @ (U.T @ W)
+    return float(np.linalg.norm(P, 2))
+
+
+# ----------------------------------------------------------------- norm
+
+@pytest.mark.parametrize("n", [1, 255, 256, 1000, 65537])
+@pytest.mark.parametrize("dt", [torch.float32, torch.float64])
+def test_norm_sq(ctx, n, dt):
+    x = np.random.default_rng(n).standard_normal(n)
+    t = dev(x, dt)
+    want = oracle.norm_sq(host(t))
+    got = ctx.norm_sq(t)
+    assert abs(got - want) <= 1e-13 * want
+
+
+def test_norm_nonfinite_is_reported(ctx):
+    from paper_1901_06043_gb300.tucker import TuckerError
+    x = np.ones(1000)
+    x[777] = np.nan
+    with pytest.raises(TuckerError) as e:
+        ctx.norm_sq(dev(x))
+    assert e.value.name == "NONFINITE"
+    x[777] = np.inf
+    with pytest.raises(TuckerError):
+        ctx.sthosvd(dev(x), (10, 100), eps=1e-3)
+
+
+# ----------------------------------------------------------------- Gram
+
+GRAM_SHAPES = [
+    (7,), (1, 5), (130, 3), (3, 130), (65, 9, 4), (5, 64, 3), (4, 3, 70), (33, 1, 17, 2),
+    (2, 3, 2, 3, 2), (200, 300), (17, 129, 5), (3, 2, 1000),
+]
+
+
+@pytest.mark.parametrize("dims", GRAM_SHAPES)
+def test_gram_fp64(ctx, dims):
+    x = np.random.default_rng(sum(dims)).standard_normal(oracle.linear_size(dims))
+    t = dev(x)
+    for n in range(len(dims)):
+        want = oracle.gram(x, dims, n)
+        got = host(ctx.gram(t, dims, n, "fp64"))
+        scale = np.abs(want).max()
+        assert np.abs(got - want).max() <= 1e-13 * scale * max(1, math.log2(x.size)), (dims, n)
+        assert np.array_equal(got, got.T)
+
+
+@pytest.mark.parametrize("dims", GRAM_SHAPES)
+def test_gram_fp32_products(ctx, dims):
+    """FP32 products of FP32 inputs: each product rounds once (rel 2^-24), the
+    FP32 chunk sums add <= 64 terms, chunks are summed in FP64: the error
+    stays below 1e-6 of max|S| for these sizes."""
+    x = np.random.default_rng(sum(dims) + 1).standard_normal(oracle.linear_size(dims))
+    t = dev(x, torch.float32)
+    xs = host(t)
+    for n in range(len(dims)):
+        want = oracle.gram(xs, dims, n)
+        got = host(ctx.gram(t, dims, n, "fp32"))
+        assert np.abs(got - want).max() <= 1e-6 * np.abs(want).max(), (dims, n)
+
+
+# ---------------------------------------------------------------- eigen
+
+def _spd(n, seed, spectrum=None):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    if spectrum is None:
+        spectrum = np.abs(rng.standard_normal(n)) * 10.0 ** -rng.uniform(0, 8, n)
+    return (Q * spectrum) @ Q.T
+
+
+EIG_CASES = [
+    ("one", np.array([[3.0]])),
+    ("two", np.array([[2.0, 1.0], [1.0, 2.0]])),
+    ("diag", np.diag([5.0, 1.0, 3.0, 0.0, 2.0])),
+    ("spd65", _spd(65, 1)),
+    ("spd64", _spd(64, 2)),
+    ("spd200", _spd(200, 3)),
+    ("spd257_odd", _spd(257, 4)),
+    ("rankdef", _spd(50, 5, np.r_[np.linspace(10, 1, 10), np.zeros(40)])),
+    ("repeated", _spd(40, 6, np.r_[np.full(20, 2.0), np.full(20, 1.0)])),
+    ("gram", None),
+]
+
+
+@pytest.mark.parametrize("name,S", EIG_CASES, ids=[c[0] for c in EIG_CASES])
+def test_eig_fp64(ctx, name, S):
+    if S is None:
+        x, _ = synth.tucker_numpy((60, 40, 30), (6, 5, 4), decay=0.2, eta=1e-4, seed=7)
+        S = oracle.gram(x, (60, 40, 30), 0)
+    S = (S + S.T) / 2
+    w_ref, V_ref = oracle.eig_desc(S)
+    w, V, sweeps = ctx.eig(dev(S))
+    w, V = host(w), host(V)
+    lmax = max(abs(w_ref).max(), 1e-300)
+    assert np.abs(w - w_ref).max() <= 1e-10 * lmax
+    assert np.abs(w - w_ref).max() <= 1e-13 * np.linalg.norm(S) * S.shape[0]
+    assert np.all(np.diff(w) <= 0)
+    n = S.shape[0]
+    assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-13 * n
+    assert np.abs(S @ V - V * w).max() <= 1e-13 * np.linalg.norm(S) * n
+    # individual vectors where the eigenvalue is isolated
+    gaps = np.minimum(np.r_[np.inf, -np.diff(w_ref)], np.r_[-np.diff(w_ref), np.inf])
+    for k in range(n):
+        if gaps[k] > 1e-3 * lmax:
+            assert abs(abs(V[:, k] @ V_ref[:, k]) - 1) <= 1e-12
+
+
+def test_eig_sweep_cap_zero_reports_noconv(ctx):
+    from paper_1901_06043_gb300.tucker import OPT_MAX_SWEEPS, TuckerError
+    ctx.set_option(OPT_MAX_SWEEPS, 0)
+    try:
+        with pytest.raises(TuckerError) as e:
+            ctx.eig(dev(_spd(10, 9)))
+        assert e.value.name == "EIG_NOCONV"
+    finally:
+        ctx.set_option(OPT_MAX_SWEEPS, 40)
+
+
+# ------------------------------------------------------------- rank cut
+
+def test_rank_cut_cases(ctx):
+    cases = [([4, 2, 1, 0.5], 1.5), ([4, 2, 1, 0.5], 1.49), ([3, 1, 0, 0], 0.0),
+             ([3, 1, -1e-18], 0.0), ([3, 1, 1], 100.0), ([3, 2, 1], 0.0)]
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        w = np.sort(rng.exponential(size=rng.integers(1, 300)))[::-1] * 10.0 ** rng.uniform(-5, 5)
+        cases.append((w, float(rng.uniform(0, 1) * w.sum())))
+    for w, thr in cases:
+        R, tail = oracle.rank_cut(w, thr)
+        gR, gd = ctx.rank_cut(dev(np.asarray(w, float)), thr)
+        assert gR == R
+        assert gd == tail[R] or abs(gd - tail[R]) <= 1e-15 * abs(tail[0])
+
+
+# ------------------------------------------------------------------- TTM
+
+TTM_SHAPES = [((7,), 3), ((130, 3), 5), ((3, 130), 70), ((65, 9, 4), 2), ((5, 64, 3), 64),
+              ((4, 3, 70), 1), ((33, 1, 17, 2), 9), ((2, 3, 2, 3, 2), 4), ((200, 300), 130)]
+
+
+@pytest.mark.parametrize("dims,K", TTM_SHAPES)
+def test_ttm_fp64(ctx, dims, K):
+    rng = np.random.default_rng(K + len(dims))
+    x = rng.standard_normal(oracle.linear_size(dims))
+    t = dev(x)
+    for n in range(len(dims)):
+        A = rng.standard_normal((K, dims[n]))
+        want = oracle.ttm(x, dims, n, A)
+        got = host(ctx.ttm(t, dims, n, dev(A), "fp64"))
+        assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max() * dims[n], (dims, n)
+        # column-major A (a transposed view)
+        Ac = dev(np.asfortranarray(A)).t().contiguous().t()
+        got = host(ctx.ttm(t, dims, n, Ac, "fp64"))
+        assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max() * dims[n], (dims, n)
+
+
+@pytest.mark.parametrize("dims,K", TTM_SHAPES)
+def test_ttm_fp32(ctx, dims, K):
+    rng = np.random.default_rng(K + 2 * len(dims))
+    x = rng.standard_normal(oracle.linear_size(dims))
+    t = dev(x, torch.float32)
+    xs = host(t)
+    for n in range(len(dims)):
+        A = rng.standard_normal((K, dims[n]))
+        want = oracle.ttm(xs, dims, n, A)
+        got = host(ctx.ttm(t, dims, n, dev(A), "fp32"))
+        # FP32 factor and products: ~2^-24 relative per term, dims[n] terms
+        assert np.abs(got - want).max() <= 2e-7 * np.abs(A).max() * np.abs(xs).max() * dims[n]
+
+
+# --------------------------------------------------------- whole ST-HOSVD
+
+def _check_against_oracle(x, dims, res, ref, err_tol=1e-12, eig_tol=1e-10, angle_tol=1e-8):
+    assert res.ranks == ref["ranks"]
+    for n in range(len(dims)):
+        lam = host(res.eigvals[n])
+        lmax = abs(ref["eigvals"][n]).max()
+        assert np.abs(lam - ref["eigvals"][n]).max() <= eig_tol * lmax
+        U = host(res.factors[n])
+        assert np.abs(U.T @ U - np.eye(U.shape[1])).max() <= 1e-12
+        w = ref["eigvals"][n]
+        R = ref["ranks"][n]
+        gap = (w[R - 1] - (w[R] if R < len(w) else 0.0)) / lmax
+        if gap > 1e-6:
+            assert sin_angle(ref["factors"][n], U) <= angle_tol, (n, gap)
+    core = host(res.core)
+    ours = {"core": core, "core_dims": res.ranks, "factors": [host(f) for f in res.factors],
+            "discarded": res.discarded, "norm_sq": res.norm_sq}
+    e_ours = oracle.relative_errors(x, dims, ours)
+    e_ref = oracle.relative_errors(x, dims, ref)
+    assert abs(e_ours["err_explicit"] - e_ref["err_explicit"]) <= err_tol
+    assert abs(e_ours["err_est"] - e_ref["err_est"]) <= err_tol
+    assert abs(res.norm_sq - ref["norm_sq"]) <= 1e-13 * ref["norm_sq"]
+
+
+def test_sthosvd_40x50x30_fp64(ctx):
+    dims = (40, 50, 30)
+    x, _ = synth.tucker_numpy(dims, (5, 6, 4), eta=1e-4, seed=0)
+    ref = oracle.sthosvd(x, dims, eps=1e-3)
+    res = ctx.sthosvd(dev(x), dims, eps=1e-3, prec="fp64")
+    assert res.ranks == (5, 6, 4)
+    _check_against_oracle(x, dims, res, ref)
+    # full reconstruction by the multi-TTM, against the oracle's multi-TTM of
+    # the same core and factors
+    full = host(res.reconstruct())
+    want, _ = oracle.reconstruct(host(res.core), res.ranks, [host(f) for f in res.factors])
+    assert np.abs(full - want).max() <= 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("case", [
+    dict(dims=(12, 10, 8, 6), core=(4, 3, 3, 2), decay=0.1, eta=1e-3, eps=1e-2),
+    dict(dims=(9, 8, 7, 6, 5), core=(3, 3, 3, 2, 2), decay=0.2, eta=1e-3, eps=1e-2),
+    dict(dims=(30, 20), core=(6, 5), decay=0.3, eta=1e-3, eps=1e-2),
+    dict(dims=(257,), core=(1,), decay=0.0, eta=0.0, eps=1e-3),
+    dict(dims=(1, 40, 1, 30), core=(1, 5, 1, 4), decay=0.0, eta=1e-4, eps=1e-3),
+    dict(dims=(65, 33, 17), core=(10, 8, 6), decay=0.1, eta=1e-5, eps=1e-4),
+])
+def test_sthosvd_shapes_fp64(ctx, case):
+    dims = case["dims"]
+    x, _ = synth.tucker_numpy(dims, case["core"], decay=case["decay"], eta=case["eta"], seed=3)
+    ref = oracle.sthosvd(x, dims, eps=case["eps"])
+    res = ctx.sthosvd(dev(x), dims, eps=case["eps"], prec="fp64")
+    _check_against_oracle(x, dims, res, ref)
+
+
+def test_sthosvd_rank_specified_and_mode_order(ctx):
+    dims = (20, 16, 12)
+    x, _ = synth.tucker_numpy(dims, (6, 5, 4), decay=0.2, eta=1e-3, seed=4)
+    ref = oracle.sthosvd(x, dims, ranks=(4, 3, 2))
+    res = ctx.sthosvd(dev(x), dims, ranks=(4, 3, 2), prec="fp64")
+    _check_against_oracle(x, dims, res, ref)
+    ref = oracle.sthosvd(x, dims, eps=1e-2, mode_order=(2, 0, 1))
+    res = ctx.sthosvd(dev(x), dims, eps=1e-2, mode_order=(2, 0, 1), prec="fp64")
+    assert res.mode_order == (2, 0, 1)
+    _check_against_oracle(x, dims, res, ref)
+
+
+def test_sthosvd_fp32_input_fp64_path(ctx):
+    dims = (48, 40, 36)
+    x, _ = synth.tucker_numpy(dims, (8, 7, 6), decay=0.15, eta=1e-4, seed=5)
+    t = dev(x, torch.float32)
+    xs = host(t)
+    ref = oracle.sthosvd(xs, dims, eps=1e-3)
+    res = ctx.sthosvd(t, dims, eps=1e-3, prec="fp64")
+    _check_against_oracle(xs, dims, res, ref)
+
+
+def test_sthosvd_fp32_path_ranks_and_error(ctx):
+    """FP32 products: identical ranks (the cut margins here are wide) and an
+    error within 1e-6 of the oracle's."""
+    dims = (48, 40, 36)
+    x, _ = synth.tucker_numpy(dims, (8, 7, 6), decay=0.15, eta=1e-4, seed=5)
+    t = dev(x, torch.float32)
+    xs = host(t)
+    ref = oracle.sthosvd(xs, dims, eps=1e-3)
+    res = ctx.sthosvd(t, dims, eps=1e-3, prec="fp32")
+    assert res.ranks == ref["ranks"]
+    ours = {"core": host(res.core), "core_dims": res.ranks,
+            "factors": [host(f) for f in res.factors], "discarded": res.discarded,
+            "norm_sq": res.norm_sq}
+    e1 = oracle.relative_errors(xs, dims, ours)["err_explicit"]
+    e0 = oracle.relative_errors(xs, dims, ref)["err_explicit"]
+    assert abs(e1 - e0) <= 1e-6
+
+
+def test_bad_arguments_are_rejected(ctx):
+    from paper_1901_06043_gb300.tucker import TuckerError
+    t = dev(np.ones(24))
+    for kw in [dict(eps=-1.0), dict(ranks=(0, 2, 2)), dict(ranks=(3, 5, 2)),
+               dict(eps=1e-2, mode_order=(0, 0, 1))]:
+        with pytest.raises(TuckerError) as e:
+            ctx.sthosvd(t, (2, 3, 4), **kw)
+        assert e.value.name == "INVALID"
+    with pytest.raises(TuckerError) as e:
+        ctx.sthosvd(t, (2, 3, 4), eps=1e-2, prec="mixed")
+    assert e.value.name == "UNSUPPORTED"
+
+
+# -------------------------------------------------------- reconstruction
+
+def test_partial_reconstruction_and_order_independence(ctx):
+    dims = (20, 18, 16, 6)
+    x, _ = synth.tucker_numpy(dims, (5, 4, 4, 3), eta=1e-3, seed=6)
+    res = ctx.sthosvd(dev(x), dims, eps=1e-2, prec="fp64")
+    core, F = host(res.core), [host(f) for f in res.factors]
+    b, e = (3, 0, 15, 2), (17, 18, 16, 3)
+    want, wd = oracle.reconstruct(core, res.ranks, F, b, e)
+    for order in itertools.permutations(range(4)):
+        got = host(res.reconstruct(b, e, order))
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max(), order
+    got = host(res.reconstruct(b, e))   # library-chosen order
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_multi_ttm_general_operators(ctx):
+    """Section 7's operators folded into the factors: averaging pairs
+    (downsampling), one-hot selection and all-ones summaries."""
+    rng = np.random.default_rng(12)
+    cd = (4, 5, 3)
+    g = rng.standard_normal(oracle.linear_size(cd))
+    U = [np.linalg.qr(rng.standard_normal((I, R)))[0] for I, R in zip((10, 12, 7), cd)]
+    C0 = np.zeros((10, 5)); C0[np.arange(10), np.arange(10) // 2] = 0.5
+    C1 = np.zeros((12, 1)); C1[7, 0] = 1.0
+    C2 = np.ones((7, 1))
+    mats = [C0.T @ U[0], C1.T @ U[1], C2.T @ U[2]]
+    want, od = oracle.multi_ttm(g, cd, mats)
+    got = host(ctx.multi_ttm(dev(g), cd, [dev(m) for m in mats], od, prec="fp64"))
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
