@@ -1,0 +1,411 @@
+"""ST-HOSVD throughput benchmark (input GB/s) on GB300.
+
+One step = one whole ST-HOSVD (Algorithm 1: norm, then per mode Gram,
+eigensolve, rank cut, TTM) of one synthetic tensor already resident in HBM,
+through the library's C ABI.  Default workload: the 5-way 500x500x500x11x8
+FP32 tensor (44 GB, core 60x60x60x11x6 with decay 10^(-0.08 sum idx),
+relative noise 1e-7, eps = 1e-4).  The input is larger than L2, so no L2
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp32|fp64]
+  python bench.py --impl reference      # the FP64 CPU oracle on host cores
+
+Prints one JSON line (rank 0).  N > 1 runs N independent replicas, one per
+GPU (the path has no cross-GPU exchange): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ST-HOSVD input GB/s at eps=1e-4, mixed vs FP64 path; Gram/TTM % of roofline"
+
+WORKLOADS = {
+    "large": dict(dims=(500, 500, 500, 11, 8), core=(60, 60, 60, 11, 6), decay=0.08, eta=1e-7,
+                  eps=1e-4, dtype="f32"),
+    "c256": dict(dims=(256, 256, 256, 11, 32), core=(40, 40, 40, 11, 16), decay=0.1, eta=1e-7,
+                 eps=1e-4, dtype="f32"),
+    "c200": dict(dims=(200, 200, 200, 50), core=(30, 30, 30, 12), decay=0.15, eta=1e-6,
+                 eps=1e-4, dtype="f64"),
+    "small": dict(dims=(40, 50, 30), core=(5, 6, 4), decay=0.0, eta=1e-4, eps=1e-3, dtype="f64"),
+}
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 x max clock
+
+
+def peaks():
+    p = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        p.update({k: float(m[k]) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")})
+        p["src"] = "measured"
+    except Exception:
+        pass
+    return p
+
+
+def describe(w):
+    d = "x".join(map(str, w["dims"]))
+    c = "x".join(map(str, w["core"]))
+    gb = np.prod(w["dims"]) * (4 if w["dtype"] == "f32" else 8) / 1e9
+    return (f"{d} {w['dtype']} ({gb:.1f} GB), core {c}, decay 10^(-{w['decay']}*sum idx), "
+            f"noise {w['eta']:g}, eps {w['eps']:g}, mode order 0..N-1")
+
+
+# ------------------------------------------------------------- clocks
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.p = None
+        self.idx = gpu_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------- distributed
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(val, ws):
+    """Max over ranks (identity for one process)."""
+    if ws == 1:
+        return val
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(val)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------- CPU oracle leg
+
+def cpu_sample(x_dev, w, frac_slices):
+    """A bounded sample of the same tensor for the CPU oracle: the first time
+    step and the first `frac_slices` slices of mode 2 (every other index
+    kept), copied to the host in FP64."""
+    import torch
+    dims = w["dims"]
+    rev = tuple(reversed(dims))
+    t = x_dev.view(rev)
+    idx = [slice(None)] * len(dims)
+    # natural-descending mode n is torch dim N-1-n
+    N = len(dims)
+    if N >= 5:
+        idx[N - 1 - 4] = slice(0, 1)
+    if N >= 3:
+        idx[N - 1 - 2] = slice(0, frac_slices)
+    sub = t[tuple(idx)].contiguous()
+    sdims = tuple(reversed(sub.shape))
+    return sub.reshape(-1).double().cpu().numpy(), sdims
+
+
+def run_cpu_oracle(xs, sdims, eps):
+    import oracle
+    t0 = time.perf_counter()
+    res = oracle.sthosvd(xs, sdims, eps=eps)
+    return time.perf_counter() - t0, res
+
+
+def blas_threads():
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    return len(os.sched_getaffinity(0))
+
+
+# ---------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large")
+    ap.add_argument("--prec", choices=["mixed", "fp32", "fp64"], default=None)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the one-step FP64-path leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-slices", type=int, default=None)
+    ap.add_argument("--seed", type=int, default=0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+
+    from paper_1901_06043_gb300 import synth, tucker
+
+    w = WORKLOADS[args.workload]
+    prec = args.prec or ("mixed" if tucker_mixed_available() else "fp32")
+    if w["dtype"] == "f64" and prec == "mixed":
+        prec = "fp32"
+    tdt = torch.float32 if w["dtype"] == "f32" else torch.float64
+    x = synth.tucker_torch(w["dims"], w["core"], decay=w["decay"], eta=w["eta"],
+                           seed=args.seed + rank, dtype=tdt)
+    torch.cuda.synchronize()
+    in_bytes = x.numel() * x.element_size()
+    N = len(w["dims"])
+    cpu_slices = args.cpu_slices or (40 if args.workload == "large" else None)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        ref_ms = []
+        xs, sdims = cpu_sample(x, w, cpu_slices or (w["dims"][2] if N >= 3 else None))
+        del x
+        for _ in range(args.warmup):
+            run_cpu_oracle(xs, sdims, w["eps"])
+        for _ in range(args.steps):
+            t, _ = run_cpu_oracle(xs, sdims, w["eps"])
+            ref_ms.append(t * 1e3)
+        ms = statistics.mean(ref_ms)
+        sbytes = xs.size * (4 if w["dtype"] == "f32" else 8)
+        val = sbytes / 1e9 / (ms / 1e3)
+        sample = f"oracle ST-HOSVD of the {'x'.join(map(str, sdims))} sub-tensor of the workload"
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {describe(w)}", "prec": "fp64-cpu-oracle"},
+            "cpu_baseline": {"value": val, "unit": "GB/s", "cores": len(os.sched_getaffinity(0)),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+
+    ctx = tucker.Context(timing=True)
+    # warm-up
+    for _ in range(args.warmup):
+        r = ctx.sthosvd(x, w["dims"], eps=w["eps"], prec=prec)
+        last = r
+    ranks = last.ranks
+    ms_detail = last.ms
+    torch.cuda.synchronize()
+    # timed region
+    clocks = Clocks(torch.cuda.current_device())
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = tucker.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        r = ctx.sthosvd(x, w["dims"], eps=w["eps"], prec=prec)
+        r.close()
+    ev1.record()
+    torch.cuda.synchronize()
+    launches = (tucker.kernel_launches() - l0) // args.steps
+    barrier(ws)
+    clk = clocks.stop()
+    ms_local = ev0.elapsed_time(ev1) / args.steps
+    ms = reduce_max(ms_local, ws)
+    value = ws * in_bytes / 1e9 / (ms / 1e3)
+
+    # per-step kernel times from the library's own CUDA events (last warm-up step)
+    pk = peaks()
+    dom = dominant(ms_detail, w, ranks, prec, pk, in_bytes)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {describe(w)}", "prec": prec,
+                   "l2": "input larger than L2 (no flush)", "ranks": list(ranks),
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": dom,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "per_mode_ms": {k: v for k, v in ms_detail.items()},
+    }
+
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = e2e_leg(ctx, x, w, prec, args)
+    if rank == 0 and not args.no_fp64 and prec != "fp64":
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        r64 = ctx.sthosvd(x, w["dims"], eps=w["eps"], prec="fp64")
+        t1.record()
+        torch.cuda.synchronize()
+        ms64 = t0.elapsed_time(t1)
+        out["fp64_path"] = {"value": in_bytes / 1e9 / (ms64 / 1e3), "unit": "GB/s", "ms": ms64,
+                            "steps": 1, "ranks": list(r64.ranks),
+                            "ranks_equal": tuple(r64.ranks) == tuple(ranks),
+                            "speedup_of_value": ms64 / ms_local, "per_mode_ms": r64.ms}
+        r64.close()
+    if rank == 0 and not args.no_cpu:
+        xs, sdims = cpu_sample(x, w, cpu_slices if N >= 3 else None)
+        t, _ = run_cpu_oracle(xs, sdims, w["eps"])
+        sbytes = xs.size * (4 if w["dtype"] == "f32" else 8)
+        out["cpu_baseline"] = {
+            "value": sbytes / 1e9 / t, "unit": "GB/s", "cores": len(os.sched_getaffinity(0)),
+            "blas_threads": blas_threads(), "kind": "oracle",
+            "sample": (f"FP64 numpy oracle ST-HOSVD (Algorithm 1-3, eps {w['eps']:g}) of the "
+                       f"{'x'.join(map(str, sdims))} sub-tensor of the workload "
+                       f"({sbytes / 1e9:.2f} GB as {w['dtype']}), {t:.1f} s")}
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def tucker_mixed_available():
+    from paper_1901_06043_gb300 import tucker
+    return getattr(tucker, "MIXED_AVAILABLE", False)
+
+
+def dominant(ms, w, ranks, prec, pk, in_bytes):
+    """Roofline of the longest step of one ST-HOSVD (from the library's CUDA
+    events on its stream): Gram, eigensolve or TTM of some mode."""
+    dims = list(w["dims"])
+    cur = list(dims)
+    esz = 4 if (w["dtype"] == "f32" and prec != "fp64") else 8
+    best = None
+    for n in range(len(dims)):
+        L = int(np.prod(cur[:n])) if n else 1
+        I = cur[n]
+        Rt = int(np.prod(cur[n + 1:])) if n + 1 < len(cur) else 1
+        R = ranks[n]
+        K = L * Rt
+        in_esz = esz if n else (4 if w["dtype"] == "f32" else 8)
+        cand = [
+            ("gram", n, ms["gram"][n], I * (I + 1) * K, L * I * Rt * in_esz),
+            ("ttm", n, ms["ttm"][n], 2 * R * I * K, L * I * Rt * in_esz + L * R * Rt * esz),
+            ("eig", n, ms["eig"][n], 0, 0),
+        ]
+        for c in cand:
+            if best is None or c[2] > best[2]:
+                best = c
+        cur[n] = R
+    kind, n, t_ms, flops, nbytes = best
+    t = t_ms / 1e3
+    if kind == "gram" and prec == "mixed":
+        ach = nbytes / t / 1e9
+        return {"kernel": f"gram mode {n} (tcgen05 split-FP16)", "bound": "hbm", "achieved": ach,
+                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                "traffic": None, "ms": t_ms, "peak_src": pk["src"]}
+    if kind in ("gram", "ttm"):
+        if prec == "fp64":
+            peak = 1.2   # measured FP64 FMA throughput (probe), TFLOP/s
+        else:
+            peak = FP32_PEAK_TFLOPS
+        ach = flops / t / 1e12
+        hbm = nbytes / t / 1e9
+        return {"kernel": f"{kind} mode {n} (SIMT {prec})", "bound": "alu", "achieved": ach,
+                "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "ms": t_ms, "hbm_gbs_achieved": hbm, "peak_src": "derived: 152 SMs x 128 lanes x 2 x 2070 MHz"
+                if prec != "fp64" else "measured FP64 FMA probe"}
+    I = dims[n]
+    flops = 0
+    return {"kernel": f"eig mode {n} (FP64 Jacobi)", "bound": "alu", "achieved": None,
+            "peak": 1.2, "unit": "TFLOP/s", "frac": None, "traffic": None, "ms": t_ms}
+
+
+def e2e_leg(ctx, x, w, prec, args):
+    """Same metric end to end: pinned host input -> device copy -> ST-HOSVD
+    through the C ABI -> core and factors back to the host, per step."""
+    import torch
+    try:
+        xh = torch.empty(x.numel(), dtype=x.dtype, pin_memory=True)
+        pinned = True
+    except Exception:
+        xh = torch.empty(x.numel(), dtype=x.dtype)
+        pinned = False
+    xh.copy_(x)
+    xd = torch.empty_like(x)
+    steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        xd.copy_(xh, non_blocking=True)
+        r = ctx.sthosvd(xd, w["dims"], eps=w["eps"], prec=prec)
+        core, fac = r.to_host()
+        d2h = core.nbytes + sum(f.nbytes for f in fac)
+        r.close()
+    torch.cuda.synchronize()
+    el = (time.perf_counter() - t0) / steps
+    nb = x.numel() * x.element_size()
+    del xd, xh
+    return {"value": nb / 1e9 / el, "unit": "GB/s", "h2d_bytes_per_step": nb,
+            "d2h_bytes_per_step": int(d2h), "steps": steps, "pinned": pinned, "ms": el * 1e3}
+
+
+if __name__ == "__main__":
+    main()

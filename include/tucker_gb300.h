@@ -103,6 +103,10 @@ const char* tucker_last_error(const tucker_ctx* ctx);
 #define TUCKER_OPT_JACOBI_TOL 3
 tucker_status tucker_set_option(tucker_ctx* ctx, int key, double value);
 
+/* Diagnostics: number of device kernels this library has launched in the
+ * process so far (all contexts).  Host only; never fails. */
+uint64_t tucker_kernel_launches(void);
+
 /* ST-HOSVD, Algorithm 1 (Section 3.3).
  *   x_dev      input tensor (dtype, dims), read only.
  *   eps        relative accuracy; R_n = min{R in 1..I_n : sum_{i>=R} lambda_i

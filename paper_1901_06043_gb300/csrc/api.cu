@@ -14,6 +14,10 @@
 
 using namespace tk;
 
+#include <atomic>
+static std::atomic<unsigned long long> g_launches{0};
+void tk::count_launches(int n) { g_launches.fetch_add((unsigned long long)n); }
+
 struct tucker_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
@@ -345,6 +349,8 @@ tucker_status tucker_destroy(tucker_ctx* c) {
 }
 
 const char* tucker_last_error(const tucker_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+uint64_t tucker_kernel_launches(void) { return g_launches.load(); }
 
 tucker_status tucker_set_option(tucker_ctx* c, int key, double value) {
   if (!c) return TUCKER_ERR_INVALID;

@@ -20,6 +20,9 @@ template <> struct dtype_of<double> { static constexpr tucker_dtype value = TUCK
 
 inline size_t dtype_size(tucker_dtype d) { return d == TUCKER_F64 ? 8 : 4; }
 
+// Process-wide count of kernels this library has launched (diagnostics).
+void count_launches(int n);
+
 // Slab view of mode n of a tensor with dims J: element (l, i, r) at
 // l + L*(i + I*r) with L = prod_{k<n} J_k, I = J_n, Rt = prod_{k>n} J_k.
 struct SlabView {

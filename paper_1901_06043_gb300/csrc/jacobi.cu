@@ -212,6 +212,7 @@ cudaError_t launch_jacobi(const double* S, int n, double* work, const double* fr
   cudaError_t e = cudaMemsetAsync(words, 0, sizeof(unsigned) * (3 + max_sweeps + 1), st);
   if (e != cudaSuccess) return e;
   k_jacobi_init<<<256, 256, 0, st>>>(S, n, np, A0, V0);
+  count_launches(max_sweeps > 0 ? 2 : 1);
   JacobiArgs a;
   a.A[0] = A0; a.A[1] = A1; a.V[0] = V0; a.V[1] = V1;
   a.rot = rot;
@@ -256,6 +257,7 @@ cudaError_t launch_eig_finish(int n, double* work, const int* info_host, int* in
   const double* A = cur ? A1 : A0;
   const double* V = cur ? V1 : V0;
   k_eig_rank<<<1, 1024, 0, st>>>(A, n, np, info_dev, rank, w_out);
+  count_launches(2);
   int64_t tot = (int64_t)n * np;
   int blocks = (int)((tot + 255) / 256);
   if (blocks > 4096) blocks = 4096;
@@ -271,6 +273,7 @@ size_t jacobi_work_bytes(int n) {
 cudaError_t launch_rank_cut(const double* w, int n, double thr, int fixed_R, int64_t* out_R,
                             double* out_d, double* tail, cudaStream_t st) {
   k_rank_cut<<<1, 32, 0, st>>>(w, n, thr, fixed_R, out_R, out_d, tail);
+  count_launches(1);
   return cudaGetLastError();
 }
 

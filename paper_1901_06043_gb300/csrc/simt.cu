@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(256) k_reduce_sum(const double* __restrict__ p
 
 cudaError_t launch_sumsq(const void* y, tucker_dtype dt, int64_t n, double* partial, int nblocks,
                          unsigned* nonfinite, double* out, cudaStream_t st) {
+  count_launches(2);
   if (dt == TUCKER_F64)
     k_sumsq<double><<<nblocks, 256, 0, st>>>((const double*)y, n, partial, nonfinite);
   else
@@ -240,6 +241,7 @@ cudaError_t launch_gram_simt(const void* y, tucker_dtype dt, bool fp64, int64_t 
                              cudaStream_t st) {
   KGeom g = make_kgeom(L, I, Rt, GBK);
   dim3 grid(p.ntiles, p.ksplit);
+  count_launches(2);
   if (dt == TUCKER_F64) {
     if (fp64) k_gram_simt<double, double><<<grid, 256, 0, st>>>((const double*)y, g, p.ntiles, p.ksplit, scratch);
     else k_gram_simt<double, float><<<grid, 256, 0, st>>>((const double*)y, g, p.ntiles, p.ksplit, scratch);
@@ -366,6 +368,7 @@ cudaError_t launch_ttm_simt(const void* y, tucker_dtype ydt, bool fp64, int64_t 
   if (nMT <= 0 || K <= 0) return cudaSuccess;
   if (nMT > 0x7fffffffll) return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)nMT, (unsigned)((K + TT - 1) / TT));
+  count_launches(1);
   if (ydt == TUCKER_F64) {
     if (zdt == TUCKER_F64) ttm_dispatch_c<double, double>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, z);
     else ttm_dispatch_c<double, float>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, z);

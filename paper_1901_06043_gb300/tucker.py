@@ -25,7 +25,7 @@ OPT_TIMING, OPT_MAX_SWEEPS, OPT_JACOBI_TOL = 1, 2, 3
 EXPORTS = ["tucker_create", "tucker_destroy", "tucker_last_error", "tucker_set_option",
            "tucker_sthosvd", "tucker_result_destroy", "tucker_reconstruct",
            "tucker_multi_ttm", "tucker_ttm_order", "tucker_norm_sq", "tucker_gram",
-           "tucker_eig", "tucker_rank_cut", "tucker_ttm"]
+           "tucker_eig", "tucker_rank_cut", "tucker_ttm", "tucker_kernel_launches"]
 
 
 class TuckerError(RuntimeError):
@@ -89,8 +89,10 @@ def lib():
         L.tucker_ttm.argtypes = [vp, vp, c_int, c_int, i64p, c_int, vp, ctypes.c_int64,
                                  ctypes.c_int64, c_int, c_int, vp, c_int]
         for name in EXPORTS:
-            if name != "tucker_last_error":
+            if name not in ("tucker_last_error", "tucker_kernel_launches"):
                 getattr(L, name).restype = c_int
+        L.tucker_kernel_launches.argtypes = []
+        L.tucker_kernel_launches.restype = ctypes.c_uint64
         _lib = L
     return _lib
 
@@ -137,7 +139,8 @@ def _check_dev(t, name):
 
 
 class Result:
-    """ST-HOSVD result.  Device arrays are copied into torch tensors."""
+    """ST-HOSVD result.  Scalars are read at once; the device arrays (core,
+    factors, eigenvalues) are copied into torch tensors on first access."""
 
     def __init__(self, ctx, ptr):
         self._ctx, self._p = ctx, ptr
@@ -156,12 +159,45 @@ class Result:
                    "gram": [r.ms_gram[k] for k in range(N)],
                    "eig": [r.ms_eig[k] for k in range(N)],
                    "ttm": [r.ms_ttm[k] for k in range(N)]}
-        ncore = int(np.prod(self.ranks))
-        self.core = _view(r.core, (ncore,), r.core_dtype).clone()
+        self._core = self._factors = self._eigvals = None
+
+    def _r(self):
+        if self._p is None:
+            raise RuntimeError("result was closed")
+        return self._p.contents
+
+    @property
+    def core(self):
+        if self._core is None:
+            self._core = _view(self._r().core, (int(np.prod(self.ranks)),), self.core_dtype).clone()
+        return self._core
+
+    @property
+    def factors(self):
         # U_n is I_n x R_n column-major == (R_n, I_n) row-major
-        self.factors = [_view(r.factors[k], (self.ranks[k], self.dims[k]), F64).clone().t()
-                        for k in range(N)]
-        self.eigvals = [_view(r.eigvals[k], (self.dims[k],), F64).clone() for k in range(N)]
+        if self._factors is None:
+            r = self._r()
+            self._factors = [_view(r.factors[k], (self.ranks[k], self.dims[k]), F64).clone().t()
+                             for k in range(self.ndim)]
+        return self._factors
+
+    @property
+    def eigvals(self):
+        if self._eigvals is None:
+            r = self._r()
+            self._eigvals = [_view(r.eigvals[k], (self.dims[k],), F64).clone()
+                             for k in range(self.ndim)]
+        return self._eigvals
+
+    def to_host(self):
+        """Device -> host copy of core and factors (numpy), straight from
+        the library-owned buffers."""
+        import torch
+        r = self._r()
+        core = _view(r.core, (int(np.prod(self.ranks)),), self.core_dtype).cpu().numpy()
+        fac = [_view(r.factors[k], (self.ranks[k], self.dims[k]), F64).cpu().numpy().T
+               for k in range(self.ndim)]
+        return core, fac
 
     def reconstruct(self, begin=None, end=None, mode_order=None, prec="fp64", out_dtype=None):
         return self._ctx.reconstruct(self, begin, end, mode_order, prec, out_dtype)
@@ -330,3 +366,8 @@ def ttm_order(core_dims, out_dims, objective="flops"):
     if st != 0:
         raise TuckerError(st, "tucker_ttm_order")
     return tuple(out[k] for k in range(N))
+
+
+def kernel_launches():
+    """Kernels launched by the library in this process so far."""
+    return int(lib().tucker_kernel_launches())
