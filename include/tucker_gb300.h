@@ -110,8 +110,9 @@ uint64_t tucker_kernel_launches(void);
 /* ST-HOSVD, Algorithm 1 (Section 3.3).
  *   x_dev      input tensor (dtype, dims), read only.
  *   eps        relative accuracy; R_n = min{R in 1..I_n : sum_{i>=R} lambda_i
- *              <= eps^2 ||X||^2 / N} (Eq. Un, 0-based, inclusive, negative
- *              eigenvalues counted as 0).  Ignored when ranks_or_null != NULL.
+ *              <= eps^2 ||X||^2 / N} (Eq. Un, 0-based, inclusive; the
+ *              computed eigenvalues are summed with their signs, as
+ *              Algorithm 1 does).  Ignored when ranks_or_null != NULL.
  *   ranks      the core size of the rank-specified variant (Section 8.4),
  *              1 <= R_n <= I_n.
  *   mode_order permutation of 0..N-1 (NULL = 0..N-1).
@@ -177,8 +178,9 @@ tucker_status tucker_eig(tucker_ctx* ctx, const double* S_dev, int64_t I,
                          double* eigvals_dev, double* V_dev, int* sweeps_host);
 
 /* Rank cut of Eq. Un on descending eigenvalues: R = min{R in 1..I :
- * sum_{i>=R} max(lambda_i, 0) <= thr}, accumulated from the smallest
- * eigenvalue up.  Synchronises; *R_host and *discarded_host = tail(R). */
+ * sum_{i>=R} lambda_i <= thr}, the signed computed eigenvalues accumulated
+ * in FP64 from the smallest up.  Synchronises; *R_host and
+ * *discarded_host = tail(R). */
 tucker_status tucker_rank_cut(tucker_ctx* ctx, const double* eigvals_dev, int64_t I, double thr,
                               int64_t* R_host, double* discarded_host);
 

@@ -38,8 +38,11 @@ the design notes of the repository):
   (it reproduces the tensor exactly); R = 0 gives no core.  The search is
   over R in {1..I_n}; R = I_n always qualifies since its tail is empty.
 * The cut uses "<=" (inclusive), as printed.
-* Computed eigenvalues below zero (rounding) are clamped to zero in the
-  tail sums; the paper states lambda >= 0 (Eq. Xeigprob).
+* The tail sums add the eigenvalues exactly as eig(S) returns them, signs
+  included (Algorithm 1 sums the computed lambda_i; lambda >= 0 in Eq.
+  Xeigprob describes the exact S).  Clamping negative rounding-level
+  eigenvalues to zero would turn symmetric rounding noise into a one-sided
+  bias that grows with the number of discarded eigenvalues.
 * The threshold is eps^2 ||X||^2 / N with N the number of modes and ||X||
   the norm of the ORIGINAL tensor, for every mode and any mode order.
 * Section 3.3 says "for n > 1" the partial core is used; Algorithm 1 uses
@@ -192,10 +195,10 @@ def eig_desc(S):
 
 def rank_cut(lam, thr: float):
     """R_n = min R in {1..I_n} with sum_{i>=R} lambda_i <= thr (Eq. Un,
-    0-based: keeping R eigenvectors discards lambda[R:]).  Negative
-    eigenvalues count as zero.  Returns (R, tail) with tail[R] the sum of
-    the discarded eigenvalues, tail[I] = 0."""
-    lam = np.maximum(np.asarray(lam, dtype=np.float64), 0.0)
+    0-based: keeping R eigenvectors discards lambda[R:]).  The computed
+    eigenvalues are summed as they are (Algorithm 1).  Returns (R, tail)
+    with tail[R] the sum of the discarded eigenvalues, tail[I] = 0."""
+    lam = np.asarray(lam, dtype=np.float64)
     I = lam.shape[0]
     tail = np.zeros(I + 1, dtype=np.float64)
     for i in range(I - 1, -1, -1):       # smallest eigenvalue first

@@ -187,7 +187,7 @@ __global__ void k_rank_cut(const double* __restrict__ w, int n, double thr, int 
                            int64_t* out_R, double* out_d, double* tail) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   tail[n] = 0.0;
-  for (int i = n - 1; i >= 0; --i) tail[i] = tail[i + 1] + fmax(w[i], 0.0);
+  for (int i = n - 1; i >= 0; --i) tail[i] = tail[i + 1] + w[i];
   int R = n;
   if (fixed_R > 0) {
     R = fixed_R;

@@ -83,7 +83,7 @@ def _eig_ascending(S):
 
 
 def _rank_cut_strict(lam, thr):
-    lam = np.maximum(np.asarray(lam, dtype=np.float64), 0.0)
+    lam = np.asarray(lam, dtype=np.float64)
     I = lam.shape[0]
     tail = np.zeros(I + 1)
     for i in range(I - 1, -1, -1):

@@ -126,7 +126,10 @@ def test_rank_cut_hand_cases():
     assert oracle.rank_cut([4, 2, 1, 0.5], 1.5)[0] == 2      # tail(2) = 1.5 <= 1.5
     assert oracle.rank_cut([4, 2, 1, 0.5], 1.49)[0] == 3
     assert oracle.rank_cut([3, 1, 0, 0], 0.0)[0] == 2
-    assert oracle.rank_cut([3, 1, -1e-18], 0.0)[0] == 2       # clamp
+    assert oracle.rank_cut([3, 1, -1e-18], 0.0)[0] == 2       # signed tail -1e-18 <= 0
+    assert oracle.rank_cut([3, 1, 1e-18, -2e-18], 0.0)[0] == 2  # tail(2) = -1e-18
+    R, tail = oracle.rank_cut([3, 1, 1e-18, -2e-18], 0.0)
+    assert tail[3] == -2e-18
     assert oracle.rank_cut([3, 1, 1], 100.0)[0] == 1          # never 0
     assert oracle.rank_cut([3, 2, 1], 0.0)[0] == 3            # R = I allowed
     R, tail = oracle.rank_cut([4, 2, 1, 0.5], 0.0)
