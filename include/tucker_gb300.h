@@ -193,6 +193,34 @@ tucker_status tucker_ttm(tucker_ctx* ctx, const void* y_dev, tucker_dtype y_dtyp
                          int64_t lda, int a_rowmajor, tucker_prec prec,
                          void* z_dev, tucker_dtype z_dtype);
 
+/* ---- Gram without allocation ----
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- code whose device memory is all owned by its own
+ * allocator (a framework's caching pool that reserved the device), or code
+ * on a path where an allocation may not happen or may not stall (a
+ * fixed-budget service loop).  It computes exactly what tucker_gram
+ * computes, with the SIMT kernel (prec FP64 or FP32; MIXED is UNSUPPORTED),
+ * and needs no context.
+ *   - Its split-K scratch is a static 16 MiB device array inside the
+ *     library, so every GPU that loads the library holds those 16 MiB until
+ *     the process exits.  The partial tiles of one call must fit in it:
+ *     I_n <= 1984 (larger I_n returns TUCKER_ERR_INVALID, nothing launched).
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array: calls that overlap on the GPU (other
+ *     streams, other host threads) race and corrupt each other's results.
+ *     Every call overwrites the partial tiles it reads, so nothing carries
+ *     over from the previous call.
+ *   - The call is asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream); S_dev (I_n x I_n FP64, caller-owned) is complete when
+ *     the stream reaches this point.  It calls no cudaMalloc, cudaFree or
+ *     allocating library routine.
+ * Errors: INVALID (arguments, size limit), UNSUPPORTED (MIXED), CUDA. */
+tucker_status tucker_gram_noalloc(const void* y_dev, tucker_dtype dtype, int ndim,
+                                  const int64_t* dims, int mode, tucker_prec prec,
+                                  double* S_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

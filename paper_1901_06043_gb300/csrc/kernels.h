@@ -18,6 +18,8 @@ struct GramPlan {
   size_t scratch_bytes = 0;
 };
 GramPlan plan_gram_simt(int64_t L, int64_t I, int64_t Rt, int num_sms);
+GramPlan plan_gram_simt_capped(int64_t L, int64_t I, int64_t Rt, int num_sms, size_t max_bytes,
+                               int* ok);
 cudaError_t launch_gram_simt(const void* y, tucker_dtype dt, bool fp64, int64_t L, int64_t I,
                              int64_t Rt, const GramPlan& p, double* scratch, double* S,
                              cudaStream_t st);

@@ -236,6 +236,21 @@ GramPlan plan_gram_simt(int64_t L, int64_t I, int64_t Rt, int num_sms) {
   return p;
 }
 
+// Same split as plan_gram_simt, with the partial-tile scratch held to at most
+// max_bytes (fewer K-splits).  ok == 0 when even one split does not fit.
+GramPlan plan_gram_simt_capped(int64_t L, int64_t I, int64_t Rt, int num_sms, size_t max_bytes,
+                               int* ok) {
+  GramPlan p = plan_gram_simt(L, I, Rt, num_sms);
+  const size_t per_split = (size_t)p.ntiles * GT * GT * sizeof(double);
+  *ok = per_split <= max_bytes;
+  if (!*ok) return p;
+  if (p.scratch_bytes > max_bytes) {
+    p.ksplit = (int)(max_bytes / per_split);
+    p.scratch_bytes = (size_t)p.ksplit * per_split;
+  }
+  return p;
+}
+
 cudaError_t launch_gram_simt(const void* y, tucker_dtype dt, bool fp64, int64_t L, int64_t I,
                              int64_t Rt, const GramPlan& p, double* scratch, double* S,
                              cudaStream_t st) {

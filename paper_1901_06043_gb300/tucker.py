@@ -25,7 +25,8 @@ OPT_TIMING, OPT_MAX_SWEEPS, OPT_JACOBI_TOL = 1, 2, 3
 EXPORTS = ["tucker_create", "tucker_destroy", "tucker_last_error", "tucker_set_option",
            "tucker_sthosvd", "tucker_result_destroy", "tucker_reconstruct",
            "tucker_multi_ttm", "tucker_ttm_order", "tucker_norm_sq", "tucker_gram",
-           "tucker_eig", "tucker_rank_cut", "tucker_ttm", "tucker_kernel_launches"]
+           "tucker_eig", "tucker_rank_cut", "tucker_ttm", "tucker_kernel_launches",
+           "tucker_gram_noalloc"]
 
 
 class TuckerError(RuntimeError):
@@ -93,6 +94,7 @@ def lib():
                 getattr(L, name).restype = c_int
         L.tucker_kernel_launches.argtypes = []
         L.tucker_kernel_launches.restype = ctypes.c_uint64
+        L.tucker_gram_noalloc.argtypes = [vp, c_int, c_int, i64p, c_int, c_int, vp, vp]
         _lib = L
     return _lib
 
@@ -371,3 +373,22 @@ def ttm_order(core_dims, out_dims, objective="flops"):
 def kernel_launches():
     """Kernels launched by the library in this process so far."""
     return int(lib().tucker_kernel_launches())
+
+
+def gram_noalloc(y, dims, mode, S, prec="fp64", stream=None):
+    """tucker_gram_noalloc: the Gram of one mode into the caller's FP64
+    (I, I) device tensor S, with the library's fixed device scratch instead
+    of any allocation.  Asynchronous on `stream` (default: torch's current).
+    For callers that cannot allocate device memory; calls that overlap on
+    the GPU share the scratch and race."""
+    import torch
+    _check_dev(y, "y")
+    _check_dev(S, "S")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    st = lib().tucker_gram_noalloc(ctypes.c_void_p(y.data_ptr()), _dtype_code(y), len(dims),
+                                   _i64(dims), int(mode), PREC[prec],
+                                   ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(stream))
+    if st != 0:
+        raise TuckerError(st, "tucker_gram_noalloc")
+    return S
