@@ -51,13 +51,79 @@ __global__ void __launch_bounds__(256) k_reduce_sum(const double* __restrict__ p
   }
 }
 
+// Error-free FP32 sum: s + e == a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// FP32 input: x^2 = p + e exactly (p = fl(x*x), e = fma(x, x, -p)); the p
+// are summed as an FP32 pair (hi, lo) with TwoSum, flushed into FP64 every
+// 64 elements, so the result matches an FP64 sum of the exact squares to
+// ~1e-15 while the kernel stays on the FP32 pipe and the HBM roofline.
+struct SumSqF32 {
+  double acc = 0.0;
+  float hi = 0.f, lo = 0.f;
+  bool bad = false;
+  __device__ __forceinline__ void add(float x) {
+    bad |= !isfinite(x);
+    const float p = x * x;
+    if (!isfinite(p)) {            // |x| > ~1.8e19: square in FP64 instead
+      acc = fma((double)x, (double)x, acc);
+      return;
+    }
+    const float e = fmaf(x, x, -p);
+    float s, err;
+    two_sum(hi, p, s, err);
+    hi = s;
+    lo += err + e;
+  }
+  __device__ __forceinline__ void flush() {
+    acc += (double)hi + (double)lo;
+    hi = lo = 0.f;
+  }
+};
+
+__global__ void __launch_bounds__(256) k_sumsq_f32(const float* __restrict__ y, int64_t n,
+                                                   double* __restrict__ partial,
+                                                   unsigned* __restrict__ nonfinite) {
+  SumSqF32 s;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t head = (int64_t)(((16 - ((uintptr_t)y & 15)) & 15) / 4);
+  if (head > n) head = n;
+  const int64_t nv = (n - head) / 4;
+  const float4* yv = reinterpret_cast<const float4*>(y + head);
+  int cnt = 0;
+  for (int64_t v = tid; v < nv; v += stride) {
+    const float4 q = __ldcs(yv + v);
+    s.add(q.x); s.add(q.y); s.add(q.z); s.add(q.w);
+    if (++cnt == 16) { s.flush(); cnt = 0; }
+  }
+  for (int64_t i = tid; i < head; i += stride) s.add(y[i]);
+  for (int64_t i = head + 4 * nv + tid; i < n; i += stride) s.add(y[i]);
+  s.flush();
+  double acc = s.acc;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double sh[8];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  if (s.bad) atomicOr(nonfinite, 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
 cudaError_t launch_sumsq(const void* y, tucker_dtype dt, int64_t n, double* partial, int nblocks,
                          unsigned* nonfinite, double* out, cudaStream_t st) {
   count_launches(2);
   if (dt == TUCKER_F64)
     k_sumsq<double><<<nblocks, 256, 0, st>>>((const double*)y, n, partial, nonfinite);
   else
-    k_sumsq<float><<<nblocks, 256, 0, st>>>((const float*)y, n, partial, nonfinite);
+    k_sumsq_f32<<<nblocks, 256, 0, st>>>((const float*)y, n, partial, nonfinite);
   k_reduce_sum<<<1, 256, 0, st>>>(partial, nblocks, out);
   return cudaGetLastError();
 }
@@ -128,14 +194,65 @@ __device__ __forceinline__ void gram_store(TC (*sm)[GT + 1], const KGeom& g, con
   }
 }
 
-// One CTA: lower-triangle tile (ta >= tb) of S over K-blocks [kb0, kb1).
-// TC = product type.  FP32 products are summed in FP32 over chunks of
-// CHUNK K-blocks and the chunks in FP64; FP64 products in FP64 throughout.
-// Writes the FP64 partial tile to part[(ks * ntiles + tile) * GT * GT].
+// Order in which one CTA (split ks of ksplit) visits its K-blocks, and where
+// its FP32 chunks end.  FP32 rounding of a running sum only stays unbiased
+// when the terms added to it have comparable size; the l index of a row-mode
+// view runs over already-truncated modes, whose energy decays with the index
+// (their eigenvalues are in descending order), so summing one slab's l-run
+// into one FP32 accumulator drops the small terms systematically.
+//   column mode (L == 1):  blocks kb0..kb1-1 (BK slabs each, unordered
+//                          energies); a chunk is CHUNK blocks.
+//   row mode, Rt >= ksplit: the CTA owns slabs [r0, r0+nr) and visits l-block
+//                          lb of all of them before lb+1; a chunk never mixes
+//                          l-blocks.
+//   row mode, Rt < ksplit:  blocks kb0..kb1-1 (lb fastest); every block is
+//                          its own chunk.
+struct KOrder {
+  int mode;
+  int64_t kb0, r0, nr, count;
+};
+
+constexpr int GCHUNK = 16;
+
+__device__ __forceinline__ KOrder make_korder(const KGeom& g, int ks, int ksplit) {
+  KOrder o{0, 0, 0, 1, 0};
+  if (g.L == 1) {
+    o.mode = 0;
+    o.kb0 = g.NKB * ks / ksplit;
+    o.count = g.NKB * (ks + 1) / ksplit - o.kb0;
+  } else if (g.Rt >= ksplit) {
+    o.mode = 1;
+    o.r0 = g.Rt * ks / ksplit;
+    o.nr = g.Rt * (ks + 1) / ksplit - o.r0;
+    o.count = o.nr * g.nLB;
+  } else {
+    o.mode = 2;
+    o.kb0 = g.NKB * ks / ksplit;
+    o.count = g.NKB * (ks + 1) / ksplit - o.kb0;
+  }
+  return o;
+}
+
+__device__ __forceinline__ int64_t korder_block(const KGeom& g, const KOrder& o, int64_t idx,
+                                                bool& chunk_end) {
+  if (o.mode == 1) {
+    const int64_t lb = idx / o.nr, rr = idx - lb * o.nr;
+    chunk_end = (rr == o.nr - 1) || ((rr + 1) % GCHUNK == 0);
+    return (o.r0 + rr) * g.nLB + lb;
+  }
+  chunk_end = (o.mode == 2) || ((idx + 1) % GCHUNK == 0);
+  return o.kb0 + idx;
+}
+
+// One CTA: lower-triangle tile (ta >= tb) of S over its K-blocks.  TC is the
+// product type.  FP64 products are summed in FP64.  FP32 products are summed
+// by FMA in FP32 within a chunk, and the chunk sums are combined as an exact
+// FP32 pair (TwoSum), which keeps the FP64 pipe (1/62 of the FP32 rate on
+// this part) out of the inner loop.  Writes the FP64 partial tile to
+// part[(ks * ntiles + tile) * GT * GT].
 template <typename TIn, typename TC>
 __global__ void __launch_bounds__(256) k_gram_simt(const TIn* __restrict__ y, KGeom g, int ntiles,
                                                    int ksplit, double* __restrict__ part) {
-  constexpr int CHUNK = 4;
   __shared__ TC As[GBK][GT + 1];
   __shared__ TC Bs[GBK][GT + 1];
   const int tile = blockIdx.x;
@@ -147,29 +264,32 @@ __global__ void __launch_bounds__(256) k_gram_simt(const TIn* __restrict__ y, KG
   const int tb = tile - ta * (ta + 1) / 2;
   const bool diag = (ta == tb);
   const int64_t ia0 = (int64_t)ta * GT, ib0 = (int64_t)tb * GT;
-  const int64_t kb0 = g.NKB * ks / ksplit, kb1 = g.NKB * (ks + 1) / ksplit;
+  const KOrder ord = make_korder(g, ks, ksplit);
 
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc64[4][4];
   TC acc[4][4];
+  float hi[4][4], lo[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) { acc64[u][v] = 0.0; acc[u][v] = (TC)0; }
+    for (int v = 0; v < 4; ++v) { acc[u][v] = (TC)0; hi[u][v] = 0.f; lo[u][v] = 0.f; }
 
   TC ra[4], rb[4];
-  if (kb0 < kb1) {
-    gram_load<TIn, TC>(y, g, kb0, ia0, ra);
-    if (!diag) gram_load<TIn, TC>(y, g, kb0, ib0, rb);
+  bool end_cur = false, end_next = false;
+  int64_t kb = 0;
+  if (ord.count > 0) {
+    kb = korder_block(g, ord, 0, end_cur);
+    gram_load<TIn, TC>(y, g, kb, ia0, ra);
+    if (!diag) gram_load<TIn, TC>(y, g, kb, ib0, rb);
   }
-  int chunk = 0;
-  for (int64_t kb = kb0; kb < kb1; ++kb) {
+  for (int64_t idx = 0; idx < ord.count; ++idx) {
     gram_store<TC>(As, g, ra);
     if (!diag) gram_store<TC>(Bs, g, rb);
     __syncthreads();
-    if (kb + 1 < kb1) {
-      gram_load<TIn, TC>(y, g, kb + 1, ia0, ra);
-      if (!diag) gram_load<TIn, TC>(y, g, kb + 1, ib0, rb);
+    if (idx + 1 < ord.count) {
+      const int64_t kbn = korder_block(g, ord, idx + 1, end_next);
+      gram_load<TIn, TC>(y, g, kbn, ia0, ra);
+      if (!diag) gram_load<TIn, TC>(y, g, kbn, ib0, rb);
     }
     TC (*Bp)[GT + 1] = diag ? As : Bs;
 #pragma unroll
@@ -185,20 +305,29 @@ __global__ void __launch_bounds__(256) k_gram_simt(const TIn* __restrict__ y, KG
         for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
     }
     __syncthreads();
-    if (sizeof(TC) == 4 && ++chunk == CHUNK) {
-      chunk = 0;
+    if constexpr (sizeof(TC) == 4) {
+      if (end_cur) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) { acc64[u][v] += (double)acc[u][v]; acc[u][v] = (TC)0; }
+          for (int v = 0; v < 4; ++v) {
+            float s, e;
+            two_sum(hi[u][v], (float)acc[u][v], s, e);
+            hi[u][v] = s;
+            lo[u][v] += e;
+            acc[u][v] = (TC)0;
+          }
+      }
     }
+    end_cur = end_next;
   }
   double* out = part + ((int64_t)ks * ntiles + tile) * GT * GT;
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v)
-      out[(ty + 16 * u) * GT + tx + 16 * v] = acc64[u][v] + (double)acc[u][v];
+      out[(ty + 16 * u) * GT + tx + 16 * v] =
+          (double)hi[u][v] + (double)lo[u][v] + (double)acc[u][v];
 }
 
 // S[i][j] = S[j][i] = sum over ks (fixed order) of the partial tiles.

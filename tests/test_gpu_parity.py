@@ -107,6 +107,24 @@ def test_gram_fp32_products(ctx, dims):
         assert np.abs(got - want).max() <= 1e-6 * np.abs(want).max(), (dims, n)
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_gram_fp32_no_bias_on_decaying_rows(ctx, mode):
+    """The l index of a row-mode view runs over already-truncated modes whose
+    energy decays geometrically.  FP32 accumulation must not drop the small
+    terms systematically: the trace (= ||Y||^2) of the FP32-product Gram has
+    to stay within 1e-9 of the oracle's, far below the ~2e-8 loss that one
+    FP32 accumulator per slab run would show."""
+    rng = np.random.default_rng(21)
+    dims = (64, 200, 300)
+    x = rng.standard_normal(dims[::-1]) * (0.5 ** np.arange(64))      # (r, i, l), l decays
+    x = x.reshape(-1)
+    t = dev(x, torch.float32)
+    xs = host(t)
+    want = oracle.gram(xs, dims, mode)
+    got = host(ctx.gram(t, dims, mode, "fp32"))
+    assert abs(np.trace(got) - np.trace(want)) <= 1e-9 * np.trace(want)
+
+
 # ---------------------------------------------------------------- eigen
 
 def _spd(n, seed, spectrum=None):
