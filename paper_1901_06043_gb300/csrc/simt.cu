@@ -292,6 +292,12 @@ __global__ void __launch_bounds__(256) k_gram_simt(const TIn* __restrict__ y, KG
       if (!diag) gram_load<TIn, TC>(y, g, kbn, ib0, rb);
     }
     TC (*Bp)[GT + 1] = diag ? As : Bs;
+    // FP32: the 16 products of a K-block are summed into a fresh register
+    // first and only that block sum enters the chunk accumulator.  Squares
+    // x^2 pile up near zero (chi-square), and adding them one by one to a
+    // large FP32 sum rounds with a negative bias ~ (terms in the sum)^1.5;
+    // 16-term block sums have a smooth density and round without bias.
+    TC t[4][4];
 #pragma unroll
     for (int kk = 0; kk < GBK; ++kk) {
       TC a[4], b[4];
@@ -302,7 +308,18 @@ __global__ void __launch_bounds__(256) k_gram_simt(const TIn* __restrict__ y, KG
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < 4; ++v) {
+          if constexpr (sizeof(TC) == 4)
+            t[u][v] = (kk == 0) ? a[u] * b[v] : fma(a[u], b[v], t[u][v]);
+          else
+            acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        }
+    }
+    if constexpr (sizeof(TC) == 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] += t[u][v];
     }
     __syncthreads();
     if constexpr (sizeof(TC) == 4) {

@@ -107,22 +107,25 @@ def test_gram_fp32_products(ctx, dims):
         assert np.abs(got - want).max() <= 1e-6 * np.abs(want).max(), (dims, n)
 
 
+@pytest.mark.parametrize("decay", [False, True])
 @pytest.mark.parametrize("mode", [0, 1, 2])
-def test_gram_fp32_no_bias_on_decaying_rows(ctx, mode):
-    """The l index of a row-mode view runs over already-truncated modes whose
-    energy decays geometrically.  FP32 accumulation must not drop the small
-    terms systematically: the trace (= ||Y||^2) of the FP32-product Gram has
-    to stay within 1e-9 of the oracle's, far below the ~2e-8 loss that one
-    FP32 accumulator per slab run would show."""
-    rng = np.random.default_rng(21)
-    dims = (64, 200, 300)
-    x = rng.standard_normal(dims[::-1]) * (0.5 ** np.arange(64))      # (r, i, l), l decays
-    x = x.reshape(-1)
-    t = dev(x, torch.float32)
-    xs = host(t)
-    want = oracle.gram(xs, dims, mode)
-    got = host(ctx.gram(t, dims, mode, "fp32"))
-    assert abs(np.trace(got) - np.trace(want)) <= 1e-9 * np.trace(want)
+def test_gram_fp32_trace_unbiased(ctx, mode, decay):
+    """trace(S) = ||Y||^2.  The eps cut is decided by the trace of S's error
+    on the discarded subspace, so the FP32-product Gram must not round with
+    a bias: on 1.3e8 Gaussian entries its trace must match the FP64 sum of
+    squares to 3e-10 (random rounding leaves ~1e-10; summing squares one by
+    one into long FP32 runs leaves a -2e-9 bias).  With `decay` the entries
+    shrink geometrically along mode 0, as the l index of a row-mode view does
+    after truncation."""
+    dims = (64, 512, 4000)
+    g = torch.Generator(device="cuda").manual_seed(21 + mode)
+    t = torch.randn(dims[::-1], generator=g, device="cuda", dtype=torch.float32)
+    if decay:
+        t *= 0.8 ** torch.arange(64, device="cuda", dtype=torch.float32)
+    t = t.reshape(-1)
+    want = float((t.double() ** 2).sum())
+    got = float(torch.trace(ctx.gram(t, dims, mode, "fp32")))
+    assert abs(got - want) <= 3e-10 * want, (got - want) / want
 
 
 # ---------------------------------------------------------------- eigen
