@@ -80,6 +80,8 @@ typedef struct tucker_result {
   double threshold;                  /* eps^2 ||X||^2 / N (0 when ranks were given)    */
   double discarded_sq[TUCKER_MAX_MODES]; /* sum of discarded eigenvalues per mode      */
   int jacobi_sweeps[TUCKER_MAX_MODES];
+  int gram_kernel[TUCKER_MAX_MODES]; /* kernel that ran: 0 SIMT FP64, 1 SIMT FP32, 2 tcgen05 */
+  int ttm_kernel[TUCKER_MAX_MODES];
   float ms_norm;                     /* device time per step (CUDA events), ms         */
   float ms_gram[TUCKER_MAX_MODES];
   float ms_eig[TUCKER_MAX_MODES];

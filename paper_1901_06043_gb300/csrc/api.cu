@@ -150,21 +150,34 @@ struct Timer {
 
 // ---------------------------------------------------------------- steps
 
-tucker_status do_norm(tucker_ctx* c, const void* y, tucker_dtype dt, int64_t n, double* out) {
+tucker_status do_norm(tucker_ctx* c, const void* y, tucker_dtype dt, int64_t n, double* out,
+                      double* maxabs = nullptr) {
   int nb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8);
   if (nb < 1) nb = 1;
   DevBuf part;
-  TK_TRY(dev_alloc(c, part, sizeof(double) * nb));
+  TK_TRY(dev_alloc(c, part, sizeof(double) * 2 * nb));
   TK_CUDA(c, cudaMemsetAsync(c->d_words, 0, sizeof(unsigned), c->stream));
   TK_CUDA(c, launch_sumsq(y, dt, n, part.as<double>(), nb, c->d_words, c->d_small, c->stream));
-  double h = 0.0;
+  double h[2] = {0.0, 0.0};
   unsigned bad = 0;
-  TK_CUDA(c, cudaMemcpyAsync(&h, c->d_small, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TK_CUDA(c, cudaMemcpyAsync(h, c->d_small, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   TK_CUDA(c, cudaMemcpyAsync(&bad, c->d_words, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
   TK_TRY(sync(c));
-  *out = h;
+  *out = h[0];
+  if (maxabs) *maxabs = h[1];
   if (bad) return set_err(c, TUCKER_ERR_NONFINITE, "tensor holds NaN or Inf");
   return TUCKER_OK;
+}
+
+// Power-of-two scale with max|x| * scale <= 2^14 (FP16 split headroom).
+float split_scale(double maxabs) {
+  if (!(maxabs > 0.0) || !std::isfinite(maxabs)) return 1.0f;
+  int ex = 0;
+  std::frexp(maxabs, &ex);          // maxabs < 2^ex
+  int e = 14 - ex;
+  if (e > 100) e = 100;
+  if (e < -100) e = -100;
+  return std::ldexp(1.0f, e);
 }
 
 // Which kernel serves a Gram / TTM step: 0 SIMT FP64, 1 SIMT FP32, 2 tcgen05.
@@ -174,17 +187,23 @@ int gram_kernel_for(tucker_prec prec, tucker_dtype dt, const SlabView& v, int sm
   return 1;
 }
 
+// maxabs: max|y| if the caller knows it (e.g. from the norm pass), else <= 0.
 tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabView& v,
-                      tucker_prec prec, double* S, int* kernel_used) {
+                      tucker_prec prec, double* S, int* kernel_used, double maxabs = -1.0) {
   int kern = gram_kernel_for(prec, dt, v, c->num_sms);
+  if (kern == 2 && (((uintptr_t)y) & 15) != 0) kern = 1;
   if (kernel_used) *kernel_used = kern;
   if (kern == 2) {
+    if (!(maxabs > 0.0)) {
+      double nrm;
+      TK_TRY(do_norm(c, y, dt, v.L * v.I * v.Rt, &nrm, &maxabs));
+    }
     TcGramPlan p = plan_gram_tc(v.L, v.I, v.Rt, c->num_sms);
     DevBuf scratch;
     TK_TRY(dev_alloc(c, scratch, p.scratch_bytes));
     TK_CUDA(c, cudaMemsetAsync(c->d_words + 8, 0, sizeof(unsigned), c->stream));
-    TK_CUDA(c, launch_gram_tc((const float*)y, v.L, v.I, v.Rt, p, scratch.as<double>(),
-                              c->d_words + 8, S, c->stream));
+    TK_CUDA(c, launch_gram_tc((const float*)y, v.L, v.I, v.Rt, p, split_scale(maxabs),
+                              scratch.as<double>(), c->d_words + 8, S, c->stream));
     unsigned err = 0;
     TK_CUDA(c, cudaMemcpyAsync(&err, c->d_words + 8, sizeof(unsigned), cudaMemcpyDeviceToHost,
                                c->stream));
@@ -210,12 +229,12 @@ tucker_status do_eig(tucker_ctx* c, const double* S, int n, double* w, double* V
   // ||S||_F^2 for the absolute part of the Jacobi threshold
   int nb = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 1024);
   DevBuf part;
-  TK_TRY(dev_alloc(c, part, sizeof(double) * std::max(nb, 1)));
+  TK_TRY(dev_alloc(c, part, sizeof(double) * 2 * std::max(nb, 1)));
   TK_CUDA(c, launch_sumsq(S, TUCKER_F64, (int64_t)n * n, part.as<double>(), std::max(nb, 1),
-                          c->d_words + 16, c->d_small + 1, c->stream));
+                          c->d_words + 16, c->d_small + 8, c->stream));
   int ms = c->max_sweeps;
   if (ms > 200) ms = 200;
-  TK_CUDA(c, launch_jacobi(S, n, work.as<double>(), c->d_small + 1, c->d_words + 32, ms,
+  TK_CUDA(c, launch_jacobi(S, n, work.as<double>(), c->d_small + 8, c->d_words + 32, ms,
                            c->tol_rel, c->tol_abs, c->num_sms, w, V, c->d_info, c->stream));
   int info[4] = {0, 0, 0, -1};
   unsigned words[3] = {0, 0, 0};
@@ -472,8 +491,8 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
   t_total.start(c);
   t_norm.start(c);
   const int64_t nx = numel(ndim, dims);
-  double nrm2 = 0.0;
-  TK_TRY(do_norm(c, x, dt, nx, &nrm2));
+  double nrm2 = 0.0, xmax = 0.0;
+  TK_TRY(do_norm(c, x, dt, nx, &nrm2, &xmax));
   t_norm.stop(c);
   r->norm_x_sq = nrm2;
   const double thr = ranks ? 0.0 : eps * eps * nrm2 / ndim;
@@ -493,7 +512,7 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
     const int I = (int)v.I;
     Timer tmg, tme, tmt;
     tmg.start(c);
-    TK_TRY(do_gram(c, y, ydt, v, prec, S.as<double>(), nullptr));
+    TK_TRY(do_gram(c, y, ydt, v, prec, S.as<double>(), &r->gram_kernel[n], s == 0 ? xmax : -1.0));
     tmg.stop(c);
     DevBuf w;
     TK_TRY(dev_alloc(c, w, sizeof(double) * I));
@@ -523,7 +542,7 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
     DevBuf z;
     TK_TRY(dev_alloc(c, z, dtype_size(wdt) * numel(ndim, nd)));
     tmt.start(c);
-    TK_TRY(do_ttm(c, y, ydt, v, r->factors[n], R, I, 1, prec, z.p, wdt, nullptr));
+    TK_TRY(do_ttm(c, y, ydt, v, r->factors[n], R, I, 1, prec, z.p, wdt, &r->ttm_kernel[n]));
     tmt.stop(c);
     ycur.reset();
     ycur.p = z.release();

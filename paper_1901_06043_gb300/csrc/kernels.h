@@ -37,7 +37,7 @@ struct TcGramPlan {
 };
 TcGramPlan plan_gram_tc(int64_t L, int64_t I, int64_t Rt, int num_sms);
 cudaError_t launch_gram_tc(const float* y, int64_t L, int64_t I, int64_t Rt, const TcGramPlan& p,
-                           double* scratch, unsigned* err, double* S, cudaStream_t st);
+                           float scale, double* scratch, unsigned* err, double* S, cudaStream_t st);
 int ttm_tc_supported(int64_t L, int64_t I, int64_t Rt, int64_t K);
 cudaError_t launch_ttm_tc(const float* y, int64_t L, int64_t I, int64_t Rt, const double* A,
                           int64_t K, int64_t lda, int a_rowmajor, float* z, void* scratch,

@@ -11,43 +11,75 @@ namespace tk {
 
 // ------------------------------------------------------------ sum of squares
 
+// Block reduction of a thread's (sum, max|x|): partial[b] = sum of block b,
+// partial[gridDim.x + b] = max of block b.
+__device__ __forceinline__ void block_store_sum_max(double acc, double mx, double* partial,
+                                                    unsigned* nonfinite, bool bad) {
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  __shared__ double s[8], m[8];
+  if ((threadIdx.x & 31) == 0) {
+    s[threadIdx.x >> 5] = acc;
+    m[threadIdx.x >> 5] = mx;
+  }
+  if (bad) atomicOr(nonfinite, 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0, tm = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      t += s[w];
+      tm = fmax(tm, m[w]);
+    }
+    partial[blockIdx.x] = t;
+    partial[gridDim.x + blockIdx.x] = tm;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_sumsq(const T* __restrict__ y, int64_t n,
                                                double* __restrict__ partial,
                                                unsigned* __restrict__ nonfinite) {
-  double acc = 0.0;
+  double acc = 0.0, mx = 0.0;
   bool bad = false;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     double v = (double)y[i];
     bad |= !isfinite(v);
     acc = fma(v, v, acc);
+    mx = fmax(mx, fabs(v));
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  __shared__ double s[8];
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
-  if (bad) atomicOr(nonfinite, 1u);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
-    partial[blockIdx.x] = t;
-  }
+  block_store_sum_max(acc, mx, partial, nonfinite, bad);
 }
 
-// Fixed-order reduction of `count` partial sums into out[0] (one block).
+// Fixed-order reduction of `count` (sum, max) partials into out[0] (sum)
+// and out[1] (max), one block.
 __global__ void __launch_bounds__(256) k_reduce_sum(const double* __restrict__ partial, int count,
                                                     double* __restrict__ out) {
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < count; i += blockDim.x) acc += partial[i];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  __shared__ double s[8];
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  double acc = 0.0, mx = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    acc += partial[i];
+    mx = fmax(mx, partial[count + i]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  __shared__ double s[8], m[8];
+  if ((threadIdx.x & 31) == 0) {
+    s[threadIdx.x >> 5] = acc;
+    m[threadIdx.x >> 5] = mx;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+    double t = 0.0, tm = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      t += s[w];
+      tm = fmax(tm, m[w]);
+    }
     out[0] = t;
+    out[1] = tm;
   }
 }
 
@@ -64,10 +96,11 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // ~1e-15 while the kernel stays on the FP32 pipe and the HBM roofline.
 struct SumSqF32 {
   double acc = 0.0;
-  float hi = 0.f, lo = 0.f;
+  float hi = 0.f, lo = 0.f, mx = 0.f;
   bool bad = false;
   __device__ __forceinline__ void add(float x) {
     bad |= !isfinite(x);
+    mx = fmaxf(mx, fabsf(x));
     const float p = x * x;
     if (!isfinite(p)) {            // |x| > ~1.8e19: square in FP64 instead
       acc = fma((double)x, (double)x, acc);
@@ -104,17 +137,7 @@ __global__ void __launch_bounds__(256) k_sumsq_f32(const float* __restrict__ y, 
   for (int64_t i = tid; i < head; i += stride) s.add(y[i]);
   for (int64_t i = head + 4 * nv + tid; i < n; i += stride) s.add(y[i]);
   s.flush();
-  double acc = s.acc;
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  __shared__ double sh[8];
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-  if (s.bad) atomicOr(nonfinite, 1u);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    partial[blockIdx.x] = t;
-  }
+  block_store_sum_max(s.acc, (double)s.mx, partial, nonfinite, s.bad);
 }
 
 cudaError_t launch_sumsq(const void* y, tucker_dtype dt, int64_t n, double* partial, int nblocks,

@@ -50,6 +50,8 @@ class CResult(ctypes.Structure):
         ("threshold", ctypes.c_double),
         ("discarded_sq", ctypes.c_double * MAX_MODES),
         ("jacobi_sweeps", ctypes.c_int * MAX_MODES),
+        ("gram_kernel", ctypes.c_int * MAX_MODES),
+        ("ttm_kernel", ctypes.c_int * MAX_MODES),
         ("ms_norm", ctypes.c_float),
         ("ms_gram", ctypes.c_float * MAX_MODES),
         ("ms_eig", ctypes.c_float * MAX_MODES),
@@ -156,6 +158,9 @@ class Result:
         self.threshold = r.threshold
         self.discarded = [r.discarded_sq[k] for k in range(N)]
         self.sweeps = [r.jacobi_sweeps[k] for k in range(N)]
+        names = {0: "simt-fp64", 1: "simt-fp32", 2: "tcgen05"}
+        self.gram_kernel = [names.get(r.gram_kernel[k], "?") for k in range(N)]
+        self.ttm_kernel = [names.get(r.ttm_kernel[k], "?") for k in range(N)]
         self.core_dtype = r.core_dtype
         self.ms = {"norm": r.ms_norm, "total": r.ms_total,
                    "gram": [r.ms_gram[k] for k in range(N)],
@@ -392,3 +397,7 @@ def gram_noalloc(y, dims, mode, S, prec="fp64", stream=None):
     if st != 0:
         raise TuckerError(st, "tucker_gram_noalloc")
     return S
+
+
+# MIXED precision (tensor-core Gram of the column-major mode-0 view) is built.
+MIXED_AVAILABLE = True

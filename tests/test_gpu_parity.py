@@ -128,6 +128,48 @@ def test_gram_fp32_trace_unbiased(ctx, mode, decay):
     assert abs(got - want) <= 3e-10 * want, (got - want) / want
 
 
+MIXED_GRAM_SHAPES = [(64, 300), (128, 2000), (500, 700), (256, 33, 7), (132, 100), (1024, 90),
+                     (96, 64)]
+
+
+@pytest.mark.parametrize("dims", MIXED_GRAM_SHAPES)
+def test_gram_mixed_mode0_tensor_cores(ctx, dims):
+    """Mode-0 Gram on tcgen05 (two-term FP16 split, all four products).  The
+    split represents each value to 2^-22 relative and the tensor-core FP32
+    accumulator truncates, which scales S by (1 - c) with c ~ 1e-5 at most
+    (proportional: harmless to the rank cut); so S matches the oracle to
+    3e-5 relative per entry scale sqrt(S_ii S_jj)."""
+    rng = np.random.default_rng(dims[0] + dims[1])
+    x = rng.standard_normal(oracle.linear_size(dims)) * rng.uniform(0.5, 2.0, dims[0]).repeat(1)[
+        np.arange(oracle.linear_size(dims)) % dims[0]]
+    t = dev(x, torch.float32)
+    xs = host(t)
+    want = oracle.gram(xs, dims, 0)
+    got = host(ctx.gram(t, dims, 0, "mixed"))
+    d = np.sqrt(np.outer(np.diag(want), np.diag(want)))
+    assert np.all(np.abs(got - want) <= 3e-5 * d + 1e-30), np.max(np.abs(got - want) / d)
+    assert np.array_equal(got, got.T)
+
+
+def test_gram_mixed_matches_fp64_on_discarded_subspace(ctx):
+    """What the eps cut sees: the Gram's error projected on the discarded
+    eigenvectors, trace(P E P), must be tiny next to the discarded mass."""
+    dims = (256, 64, 40, 11)
+    x = synth.tucker_torch(dims, (40, 20, 20, 11), decay=0.1, eta=1e-7, seed=3)
+    want = host(ctx.gram(x, dims, 0, "fp64"))
+    got = host(ctx.gram(x, dims, 0, "mixed"))
+    w, V = oracle.eig_desc(want)
+    nrm2 = float(np.trace(want))
+    thr = 1e-8 * nrm2 / 4
+    R, tail = oracle.rank_cut(w, thr)
+    P = V[:, R:]
+    E = got - want
+    c = -np.trace(E) / nrm2                       # proportional shrink factor
+    proj = np.trace(P.T @ (E + c * want) @ P)     # non-proportional part on the tail
+    assert 0 <= c < 3e-5, c
+    assert abs(proj) <= 0.05 * thr, (proj / thr, c)
+
+
 # ---------------------------------------------------------------- eigen
 
 def _spd(n, seed, spectrum=None):
@@ -335,6 +377,25 @@ def test_sthosvd_fp32_path_ranks_and_error(ctx):
     e1 = oracle.relative_errors(xs, dims, ours)["err_explicit"]
     e0 = oracle.relative_errors(xs, dims, ref)["err_explicit"]
     assert abs(e1 - e0) <= 1e-6
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-4])
+def test_sthosvd_mixed_path_ranks_and_error(ctx, eps):
+    """MIXED (tensor-core mode-0 Gram): ranks identical to the FP64 oracle on
+    a decaying-spectrum FP32 tensor; error within 1e-6 of the oracle's."""
+    dims = (200, 160, 48, 11)
+    x = synth.tucker_torch(dims, (30, 30, 24, 11), decay=0.1, eta=1e-7, seed=9)
+    xs = host(x)
+    ref = oracle.sthosvd(xs, dims, eps=eps)
+    res = ctx.sthosvd(x, dims, eps=eps, prec="mixed")
+    assert res.gram_kernel[0] == "tcgen05"
+    assert res.ranks == ref["ranks"]
+    ours = {"core": host(res.core), "core_dims": res.ranks,
+            "factors": [host(f) for f in res.factors], "discarded": res.discarded,
+            "norm_sq": res.norm_sq}
+    e1 = oracle.relative_errors(xs, dims, ours)["err_explicit"]
+    e0 = oracle.relative_errors(xs, dims, ref)["err_explicit"]
+    assert abs(e1 - e0) <= 1e-6 and e1 <= eps
 
 
 def test_bad_arguments_are_rejected(ctx):
