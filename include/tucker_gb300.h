@@ -54,14 +54,27 @@ typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
 /* Arithmetic of the Gram and TTM steps.  The eigensolve and the rank cut
  * are FP64 in every mode, and the Gram is always reduced across slabs in
  * FP64.
- *   FP64  : products and sums in FP64 (any input dtype); core in FP64.
- *   FP32  : FP32 products, FP32 sums over short chunks, FP64 across chunks;
- *           working tensor and core in the input dtype.
- *   MIXED : tensor cores (tcgen05) on a two-term FP16 split of each FP32
- *           value (hi + lo, all four products kept), FP32 accumulation in
- *           tensor memory over short chunks, FP64 across chunks; FP32
- *           input only; working tensor and core in FP32. */
-typedef enum { TUCKER_PREC_FP64 = 0, TUCKER_PREC_FP32 = 1, TUCKER_PREC_MIXED = 2 } tucker_prec;
+ *   FP64   : products and sums in FP64 (any input dtype); core in FP64.
+ *   FP32   : FP32 products, round-to-nearest FP32 sums over short chunks
+ *            combined exactly (TwoSum) and in FP64; working tensor and core
+ *            in the input dtype.
+ *   MIXED  : FP32 Gram as above; TTMs on the tensor cores (tcgen05) with a
+ *            two-term FP16 split of both operands where the shape allows.
+ *            FP32 input only.  The rank cut at small eps is decided by a
+ *            tail sum that is ~1e-9 of the trace; the Gram needs unbiased
+ *            rounding for that, while TTM rounding errors act as
+ *            perturbations of the data and do not bias the next cut.
+ *   TENSOR : MIXED plus the Gram of the column-major mode-0 view on tcgen05
+ *            (two-term FP16 split, all four products).  The tensor-core FP32
+ *            accumulator truncates toward zero, a relative bias of ~1e-7
+ *            per accumulation step; safe for the rank cut when
+ *            eps^2 / N >> 1e-8 (e.g. eps = 1e-2), not at eps = 1e-4. */
+typedef enum {
+  TUCKER_PREC_FP64 = 0,
+  TUCKER_PREC_FP32 = 1,
+  TUCKER_PREC_MIXED = 2,
+  TUCKER_PREC_TENSOR = 3
+} tucker_prec;
 
 typedef struct tucker_ctx tucker_ctx;
 

@@ -183,7 +183,7 @@ float split_scale(double maxabs) {
 // Which kernel serves a Gram / TTM step: 0 SIMT FP64, 1 SIMT FP32, 2 tcgen05.
 int gram_kernel_for(tucker_prec prec, tucker_dtype dt, const SlabView& v, int sms) {
   if (prec == TUCKER_PREC_FP64) return 0;
-  if (prec == TUCKER_PREC_MIXED && dt == TUCKER_F32 && plan_gram_tc(v.L, v.I, v.Rt, sms).ok) return 2;
+  if (prec == TUCKER_PREC_TENSOR && dt == TUCKER_F32 && plan_gram_tc(v.L, v.I, v.Rt, sms).ok) return 2;
   return 1;
 }
 
@@ -269,7 +269,8 @@ tucker_status do_cut(tucker_ctx* c, const double* w, int n, double thr, int fixe
 tucker_status do_ttm(tucker_ctx* c, const void* y, tucker_dtype ydt, const SlabView& v,
                      const double* A, int64_t K, int64_t lda, int arow, tucker_prec prec, void* z,
                      tucker_dtype zdt, int* kernel_used) {
-  const bool tc = prec == TUCKER_PREC_MIXED && ydt == TUCKER_F32 && zdt == TUCKER_F32 &&
+  const bool tc = (prec == TUCKER_PREC_MIXED || prec == TUCKER_PREC_TENSOR) && ydt == TUCKER_F32 &&
+                  zdt == TUCKER_F32 &&
                   ttm_tc_supported(v.L, v.I, v.Rt, K);
   if (kernel_used) *kernel_used = tc ? 2 : (prec == TUCKER_PREC_FP64 ? 0 : 1);
   if (tc) {
@@ -400,10 +401,10 @@ tucker_status tucker_gram(tucker_ctx* c, const void* y, tucker_dtype dt, int ndi
                           const int64_t* dims, int mode, tucker_prec prec, double* S) {
   if (!c) return TUCKER_ERR_INVALID;
   if (!y || !S || !check_dims(ndim, dims) || mode < 0 || mode >= ndim ||
-      (dt != TUCKER_F32 && dt != TUCKER_F64) || prec < 0 || prec > 2)
+      (dt != TUCKER_F32 && dt != TUCKER_F64) || prec < 0 || prec > 3)
     return set_err(c, TUCKER_ERR_INVALID, "tucker_gram: bad argument");
-  if (prec == TUCKER_PREC_MIXED && dt != TUCKER_F32)
-    return set_err(c, TUCKER_ERR_UNSUPPORTED, "MIXED precision needs FP32 input");
+  if ((prec == TUCKER_PREC_MIXED || prec == TUCKER_PREC_TENSOR) && dt != TUCKER_F32)
+    return set_err(c, TUCKER_ERR_UNSUPPORTED, "MIXED/TENSOR precision needs FP32 input");
   SlabView v = slab_view(ndim, dims, mode);
   TK_TRY(do_gram(c, y, dt, v, prec, S, nullptr));
   return sync(c);
@@ -431,7 +432,7 @@ tucker_status tucker_ttm(tucker_ctx* c, const void* y, tucker_dtype ydt, int ndi
   if (!c) return TUCKER_ERR_INVALID;
   if (!y || !A || !z || !check_dims(ndim, dims) || mode < 0 || mode >= ndim || K < 1 ||
       (ydt != TUCKER_F32 && ydt != TUCKER_F64) || (zdt != TUCKER_F32 && zdt != TUCKER_F64) ||
-      prec < 0 || prec > 2)
+      prec < 0 || prec > 3)
     return set_err(c, TUCKER_ERR_INVALID, "tucker_ttm: bad argument");
   if (arow ? lda < dims[mode] : lda < K)
     return set_err(c, TUCKER_ERR_INVALID, "tucker_ttm: leading dimension too small");
@@ -459,7 +460,7 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
   if (!out) return set_err(c, TUCKER_ERR_INVALID, "null result pointer");
   *out = nullptr;
   if (!x || !check_dims(ndim, dims) || (dt != TUCKER_F32 && dt != TUCKER_F64) || prec < 0 ||
-      prec > 2)
+      prec > 3)
     return set_err(c, TUCKER_ERR_INVALID, "tucker_sthosvd: bad argument");
   if (!ranks && !(eps >= 0.0 && std::isfinite(eps)))
     return set_err(c, TUCKER_ERR_INVALID, "eps must be finite and >= 0");
@@ -470,8 +471,8 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
   int order[TUCKER_MAX_MODES];
   if (!check_order(ndim, order_in, order))
     return set_err(c, TUCKER_ERR_INVALID, "mode order is not a permutation");
-  if (prec == TUCKER_PREC_MIXED && dt != TUCKER_F32)
-    return set_err(c, TUCKER_ERR_UNSUPPORTED, "MIXED precision needs FP32 input");
+  if ((prec == TUCKER_PREC_MIXED || prec == TUCKER_PREC_TENSOR) && dt != TUCKER_F32)
+    return set_err(c, TUCKER_ERR_UNSUPPORTED, "MIXED/TENSOR precision needs FP32 input");
   int64_t imax = 0;
   for (int k = 0; k < ndim; ++k) imax = std::max(imax, dims[k]);
   if (imax > 32768) return set_err(c, TUCKER_ERR_INVALID, "mode size above 32768");
@@ -587,7 +588,7 @@ tucker_status tucker_multi_ttm(tucker_ctx* c, const void* core, tucker_dtype cdt
   if (!c) return TUCKER_ERR_INVALID;
   if (!core || !mats || !lda || !out || !check_dims(ndim, core_dims) ||
       !check_dims(ndim, out_dims) || (cdt != TUCKER_F32 && cdt != TUCKER_F64) ||
-      (odt != TUCKER_F32 && odt != TUCKER_F64) || prec < 0 || prec > 2)
+      (odt != TUCKER_F32 && odt != TUCKER_F64) || prec < 0 || prec > 3)
     return set_err(c, TUCKER_ERR_INVALID, "tucker_multi_ttm: bad argument");
   for (int k = 0; k < ndim; ++k)
     if (!mats[k] || lda[k] < out_dims[k])

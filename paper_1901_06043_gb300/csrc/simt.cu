@@ -128,11 +128,19 @@ __global__ void __launch_bounds__(256) k_sumsq_f32(const float* __restrict__ y, 
   if (head > n) head = n;
   const int64_t nv = (n - head) / 4;
   const float4* yv = reinterpret_cast<const float4*>(y + head);
-  int cnt = 0;
-  for (int64_t v = tid; v < nv; v += stride) {
+  // four independent 16-byte loads in flight per thread per iteration
+  int64_t v = tid;
+  for (; v + 3 * stride < nv; v += 4 * stride) {
+    float4 q[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) q[u] = __ldcs(yv + v + u * stride);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { s.add(q[u].x); s.add(q[u].y); s.add(q[u].z); s.add(q[u].w); }
+    s.flush();
+  }
+  for (; v < nv; v += stride) {
     const float4 q = __ldcs(yv + v);
     s.add(q.x); s.add(q.y); s.add(q.z); s.add(q.w);
-    if (++cnt == 16) { s.flush(); cnt = 0; }
   }
   for (int64_t i = tid; i < head; i += stride) s.add(y[i]);
   for (int64_t i = head + 4 * nv + tid; i < n; i += stride) s.add(y[i]);

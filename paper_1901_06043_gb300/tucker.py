@@ -19,7 +19,7 @@ MAX_MODES = 8
 STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "NONFINITE", 4: "EIG_NOCONV", 5: "CUDA",
           6: "UNSUPPORTED"}
 F32, F64 = 0, 1
-PREC = {"fp64": 0, "fp32": 1, "mixed": 2}
+PREC = {"fp64": 0, "fp32": 1, "mixed": 2, "tensor": 3}
 OPT_TIMING, OPT_MAX_SWEEPS, OPT_JACOBI_TOL = 1, 2, 3
 
 EXPORTS = ["tucker_create", "tucker_destroy", "tucker_last_error", "tucker_set_option",
