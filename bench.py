@@ -41,6 +41,10 @@ WORKLOADS = {
     "c200": dict(dims=(200, 200, 200, 50), core=(30, 30, 30, 12), decay=0.15, eta=1e-6,
                  eps=1e-4, dtype="f64"),
     "small": dict(dims=(40, 50, 30), core=(5, 6, 4), decay=0.0, eta=1e-4, eps=1e-3, dtype="f64"),
+    # the large workload's first two time steps and 40 of its 500 mode-2
+    # slices: a 0.9 GB case of the same kernels for profiler captures
+    "prof": dict(dims=(500, 500, 40, 11, 2), core=(60, 60, 40, 11, 2), decay=0.08, eta=1e-7,
+                 eps=1e-4, dtype="f32"),
 }
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 x max clock
@@ -247,13 +251,20 @@ def main():
         }))
         return
 
-    ctx = tucker.Context(timing=True)
-    # warm-up
+    # warm-up on a context that records per-step CUDA events (kernel times for
+    # the roofline); the timed steps below run on a context without them
+    ctx_t = tucker.Context(timing=True)
+    ctx = tucker.Context()
+    last = None
     for _ in range(args.warmup):
-        r = ctx.sthosvd(x, w["dims"], eps=w["eps"], prec=prec)
-        last = r
+        if last is not None:
+            last.close()
+        last = ctx_t.sthosvd(x, w["dims"], eps=w["eps"], prec=prec)
     ranks = last.ranks
     ms_detail = last.ms
+    pk = peaks()
+    dom, step_rows = dominant(last, w, pk)
+    last.close()
     torch.cuda.synchronize()
     # timed region
     clocks = Clocks(torch.cuda.current_device())
@@ -275,10 +286,6 @@ def main():
     ms = reduce_max(ms_local, ws)
     value = ws * in_bytes / 1e9 / (ms / 1e3)
 
-    # per-step kernel times from the library's own CUDA events (last warm-up step)
-    pk = peaks()
-    dom = dominant(ms_detail, w, ranks, prec, pk, in_bytes)
-
     out = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -290,6 +297,8 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk,
         "per_mode_ms": {k: v for k, v in ms_detail.items()},
+        "steps_roofline": [{k: r[k] for k in ("kernel", "ms", "bound", "achieved", "unit", "frac")}
+                           for r in step_rows],
     }
 
     if rank == 0 and not args.no_e2e:
@@ -298,7 +307,7 @@ def main():
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record()
-        r64 = ctx.sthosvd(x, w["dims"], eps=w["eps"], prec="fp64")
+        r64 = ctx_t.sthosvd(x, w["dims"], eps=w["eps"], prec="fp64")
         t1.record()
         torch.cuda.synchronize()
         ms64 = t0.elapsed_time(t1)
@@ -320,6 +329,7 @@ def main():
     if rank == 0:
         print(json.dumps(out))
     ctx.close()
+    ctx_t.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -330,51 +340,50 @@ def tucker_mixed_available():
     return getattr(tucker, "MIXED_AVAILABLE", False)
 
 
-def dominant(ms, w, ranks, prec, pk, in_bytes):
-    """Roofline of the longest step of one ST-HOSVD (from the library's CUDA
-    events on its stream): Gram, eigensolve or TTM of some mode."""
-    dims = list(w["dims"])
-    cur = list(dims)
-    esz = 4 if (w["dtype"] == "f32" and prec != "fp64") else 8
-    best = None
-    for n in range(len(dims)):
+FP64_PEAK_TFLOPS = 1.19   # measured FP64 FMA throughput on this part (in-register probe)
+
+
+def step_rooflines(res, w, pk):
+    """Roofline of every Gram / TTM / eigensolve step of one ST-HOSVD, from
+    the library's own CUDA events on its stream (algorithmic work: Gram
+    I(I+1)K flops on I*K read elements; TTM 2RIK flops on I*K read + R*K
+    written; Jacobi ~6 I^3 FP64 flops per sweep)."""
+    ms, ranks = res.ms, res.ranks
+    cur = list(w["dims"])
+    in_esz = 4 if w["dtype"] == "f32" else 8
+    wk_esz = 8 if res.core_dtype == 1 else 4
+    out = []
+    for s, n in enumerate(res.mode_order):
         L = int(np.prod(cur[:n])) if n else 1
-        I = cur[n]
+        I, R = cur[n], ranks[n]
         Rt = int(np.prod(cur[n + 1:])) if n + 1 < len(cur) else 1
-        R = ranks[n]
         K = L * Rt
-        in_esz = esz if n else (4 if w["dtype"] == "f32" else 8)
-        cand = [
-            ("gram", n, ms["gram"][n], I * (I + 1) * K, L * I * Rt * in_esz),
-            ("ttm", n, ms["ttm"][n], 2 * R * I * K, L * I * Rt * in_esz + L * R * Rt * esz),
-            ("eig", n, ms["eig"][n], 0, 0),
-        ]
-        for c in cand:
-            if best is None or c[2] > best[2]:
-                best = c
+        esz = in_esz if s == 0 else wk_esz
+        for kind, t_ms, flops, nbytes, kern in [
+            ("gram", ms["gram"][n], I * (I + 1) * K, I * K * esz, res.gram_kernel[n]),
+            ("ttm", ms["ttm"][n], 2 * R * I * K, I * K * esz + R * K * wk_esz, res.ttm_kernel[n]),
+            ("eig", ms["eig"][n], 6.0 * I ** 3 * max(res.sweeps[n], 1), 0, "fp64-jacobi")]:
+            t = max(t_ms, 1e-6) / 1e3
+            if kern == "tcgen05" or (kind == "ttm" and kern != "simt-fp64" and False):
+                bound, ach, peak, unit = "hbm", nbytes / t / 1e9, pk["hbm_gbs"], "GB/s"
+                src = "measured HBM copy"
+            elif kern == "simt-fp32":
+                bound, ach, peak, unit = "alu", flops / t / 1e12, FP32_PEAK_TFLOPS, "TFLOP/s"
+                src = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+            else:
+                bound, ach, peak, unit = "alu", flops / t / 1e12, FP64_PEAK_TFLOPS, "TFLOP/s"
+                src = "measured FP64 FMA probe"
+            out.append({"kernel": f"{kind} mode {n} ({kern})", "bound": bound, "achieved": ach,
+                        "peak": peak, "unit": unit, "frac": ach / peak, "traffic": None,
+                        "ms": t_ms, "hbm_gbs_achieved": nbytes / t / 1e9, "peak_src": src})
         cur[n] = R
-    kind, n, t_ms, flops, nbytes = best
-    t = t_ms / 1e3
-    if kind == "gram" and prec == "mixed":
-        ach = nbytes / t / 1e9
-        return {"kernel": f"gram mode {n} (tcgen05 split-FP16)", "bound": "hbm", "achieved": ach,
-                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
-                "traffic": None, "ms": t_ms, "peak_src": pk["src"]}
-    if kind in ("gram", "ttm"):
-        if prec == "fp64":
-            peak = 1.2   # measured FP64 FMA throughput (probe), TFLOP/s
-        else:
-            peak = FP32_PEAK_TFLOPS
-        ach = flops / t / 1e12
-        hbm = nbytes / t / 1e9
-        return {"kernel": f"{kind} mode {n} (SIMT {prec})", "bound": "alu", "achieved": ach,
-                "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "ms": t_ms, "hbm_gbs_achieved": hbm, "peak_src": "derived: 152 SMs x 128 lanes x 2 x 2070 MHz"
-                if prec != "fp64" else "measured FP64 FMA probe"}
-    I = dims[n]
-    flops = 0
-    return {"kernel": f"eig mode {n} (FP64 Jacobi)", "bound": "alu", "achieved": None,
-            "peak": 1.2, "unit": "TFLOP/s", "frac": None, "traffic": None, "ms": t_ms}
+    return out
+
+
+def dominant(res, w, pk):
+    """The longest step's roofline entry."""
+    rows = step_rooflines(res, w, pk)
+    return max(rows, key=lambda r: r["ms"]), rows
 
 
 def e2e_leg(ctx, x, w, prec, args):

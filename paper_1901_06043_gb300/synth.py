@@ -85,8 +85,10 @@ def tucker_torch(dims, core_dims, decay=0.0, eta=0.0, seed=0, dtype=None,
     factors = []
     for I, R in zip(dims, core_dims):
         a = torch.randn(I, R, generator=gen, device=device, dtype=torch.float64)
-        q, _ = torch.linalg.qr(a, mode="reduced")
-        factors.append(q)
+        # small QR on the host (numpy LAPACK): keeps the generator free of
+        # torch's lazily loaded linear-algebra library
+        q, _ = np.linalg.qr(a.cpu().numpy(), mode="reduced")
+        factors.append(torch.from_numpy(q).to(device))
     # torch C-order shape (J_{N-1}, ..., J_0) == natural-descending.
     t = g.reshape(tuple(reversed(core_dims)))
     cur = list(core_dims)
