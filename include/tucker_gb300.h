@@ -188,6 +188,7 @@ tucker_status tucker_gram(tucker_ctx* ctx, const void* y_dev, tucker_dtype dtype
  * parallel cyclic Jacobi in FP64 on the whole GPU.  eigvals_dev (I) gets
  * them in descending order, V_dev (I x I, column-major) the matching
  * orthonormal eigenvectors.  *sweeps_host (may be NULL) the sweeps used.
+ * 1 <= I <= 8192 (also the largest mode size tucker_sthosvd accepts).
  * Synchronises.  EIG_NOCONV if the sweep cap was reached. */
 tucker_status tucker_eig(tucker_ctx* ctx, const double* S_dev, int64_t I,
                          double* eigvals_dev, double* V_dev, int* sweeps_host);

@@ -413,7 +413,7 @@ tucker_status tucker_gram(tucker_ctx* c, const void* y, tucker_dtype dt, int ndi
 tucker_status tucker_eig(tucker_ctx* c, const double* S, int64_t I, double* w, double* V,
                          int* sweeps) {
   if (!c) return TUCKER_ERR_INVALID;
-  if (!S || !w || !V || I < 1 || I > 32768)
+  if (!S || !w || !V || I < 1 || I > 8192)
     return set_err(c, TUCKER_ERR_INVALID, "tucker_eig: bad argument");
   return do_eig(c, S, (int)I, w, V, sweeps);
 }
@@ -475,7 +475,7 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
     return set_err(c, TUCKER_ERR_UNSUPPORTED, "MIXED/TENSOR precision needs FP32 input");
   int64_t imax = 0;
   for (int k = 0; k < ndim; ++k) imax = std::max(imax, dims[k]);
-  if (imax > 32768) return set_err(c, TUCKER_ERR_INVALID, "mode size above 32768");
+  if (imax > 8192) return set_err(c, TUCKER_ERR_INVALID, "mode size above 8192");
 
   tucker_result* r = new tucker_result();
   memset(r, 0, sizeof(*r));

@@ -68,7 +68,7 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& b, unsigned& my_gen
       unsigned long long it = 0;
       while (ld_acquire_u32(b.gen) == g) {
         if (++it > limit) { atomicOr(b.err, DEV_ERR_BARRIER_TIMEOUT); ok = 0; break; }
-        if (it > 64) __nanosleep(64);
+        if (it > 4096) __nanosleep(64);
       }
     }
     __threadfence();

@@ -8,9 +8,16 @@
 // (2j, 2j+1); every step writes the rotated matrix into the other buffer at
 // the positions of the next step's pairing, so all pairs of a step are
 // disjoint 2x2 blocks and every 2x2 block of A updates independently.
-// A and V are permuted together, so column p of V always belongs to the
-// diagonal entry p of A.  One persistent cooperative kernel runs every
-// sweep; a bounded grid barrier separates the rotation and update phases.
+//
+// One persistent cooperative kernel runs every sweep with ONE grid barrier
+// per step: the thread that produces the off-diagonal entry of a next-step
+// pair also recomputes that pair's two new diagonal entries (from their 2x2
+// diagonal blocks, with the same expression the diagonal-block thread uses)
+// and computes the pair's next rotation.  The eigenvectors are not updated
+// every step: each sweep's rotations are logged and replayed once per sweep
+// on the rows of V (rows are independent; a warp holds one row in shared
+// memory), which takes V off the step's critical path.  Every grid barrier is
+// bounded (see GridBarrier).
 #include "common.cuh"
 #include "kernels.h"
 
@@ -30,101 +37,180 @@ __device__ __forceinline__ int next_pos(int pos, int np) {
   return pos_of_slot(ns, np);
 }
 
+// Rotation that annihilates a_pq (sym.schur2 of Golub & Van Loan, Alg. 8.5.1).
+// Skipped (identity) when |a_pq| is below the relative/absolute threshold.
+__device__ __forceinline__ bool jacobi_rotation(double app, double aqq, double apq, double tol_rel,
+                                                double floor_abs, double& c, double& s, double& t) {
+  c = 1.0;
+  s = 0.0;
+  t = 0.0;
+  const double thr = fmax(tol_rel * sqrt(fabs(app)) * sqrt(fabs(aqq)), floor_abs);
+  if (!(fabs(apq) > thr)) return false;
+  const double tau = (aqq - app) / (2.0 * apq);
+  t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau)) : -1.0 / (-tau + sqrt(1.0 + tau * tau));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = t * c;
+  return true;
+}
+
+// New diagonal entry of the element now at `pos` after its pair's rotation.
+__device__ __forceinline__ double new_diag(const double* A, const double* R, int np, int pos) {
+  const int j = pos >> 1, p = 2 * j;
+  const double s = R[3 * j + 1], t = R[3 * j + 2];
+  const double app = A[(int64_t)p * np + p], aqq = A[(int64_t)(p + 1) * np + p + 1];
+  const double apq = A[(int64_t)p * np + p + 1];
+  if (s == 0.0) return (pos & 1) ? aqq : app;
+  return (pos & 1) ? aqq + t * apq : app - t * apq;
+}
+
 struct JacobiArgs {
   double* A[2];       // np x np row-major, ping-pong
-  double* V[2];       // n x np row-major (rows: coordinates, cols: storage positions)
-  double* rot;        // 3 * P: c, s, t
-  unsigned* counts;   // non-skipped rotations per sweep (max_sweeps entries, zeroed)
-  int* info;          // [0] sweeps, [1] converged, [2] final buffer, [3] dummy position
+  double* V;          // n x np row-major (rows: coordinates, cols: storage positions)
+  double* rot[2];     // 3 * P: c, s, t of the current / next step
+  double* log;        // (np - 1) * P * 2: c, s of every step of the current sweep
+  unsigned* counts;   // non-skipped rotations per sweep (max_sweeps + 1 entries, zeroed)
+  int* info;          // [0] sweeps, [1] converged, [2] final A buffer, [3] dummy position
   const double* fro2; // ||S||_F^2
   GridBarrier bar;
-  int n, np, max_sweeps;
+  int n, np, max_sweeps, vwarps;
   double tol_rel, tol_abs;
 };
 
-__global__ void __launch_bounds__(256) k_jacobi(JacobiArgs a) {
+__device__ __forceinline__ void count_rotation(unsigned* counts, int idx, int max_sweeps) {
+  if (idx <= max_sweeps) atomicAdd(&counts[idx], 1u);
+}
+
+__global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
+  extern __shared__ double vsm[];
   const int n = a.n, np = a.np, P = np >> 1;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
   const double floor_abs = a.tol_abs * sqrt(*a.fro2);
   const int64_t nblk = (int64_t)P * (P + 1) / 2;
-  const int64_t nvit = (int64_t)n * P;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned gen = 0;
-  int cur = 0;
+  int cur = 0, rc = 0;
   int dpos = (n & 1) ? n : -1;   // dummy index (odd n) sits at position n initially
   int sweeps = 0, converged = 0;
+
+  // prologue: rotations of step 0
+  for (int64_t j = gtid; j < P; j += gsz) {
+    const int p = 2 * (int)j;
+    const double* A = a.A[0];
+    double c, s, t;
+    if (jacobi_rotation(A[(int64_t)p * np + p], A[(int64_t)(p + 1) * np + p + 1],
+                        A[(int64_t)p * np + p + 1], a.tol_rel, floor_abs, c, s, t))
+      count_rotation(a.counts, 0, a.max_sweeps);
+    a.rot[0][3 * j] = c;
+    a.rot[0][3 * j + 1] = s;
+    a.rot[0][3 * j + 2] = t;
+  }
+  if (!grid_sync(a.bar, gen)) return;
+
   for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
+    // the sweep's step-0 rotations into the log
+    for (int64_t j = gtid; j < P; j += gsz) {
+      a.log[2 * j] = a.rot[rc][3 * j];
+      a.log[2 * j + 1] = a.rot[rc][3 * j + 1];
+    }
     for (int t = 0; t < np - 1; ++t) {
       const double* A = a.A[cur];
       double* An = a.A[cur ^ 1];
-      const double* V = a.V[cur];
-      double* Vn = a.V[cur ^ 1];
-      // phase 1: one rotation per pair (sym.schur2 of Golub & Van Loan)
-      for (int64_t j = gtid; j < P; j += gsz) {
-        const int p = 2 * (int)j, q = p + 1;
-        const double app = A[(int64_t)p * np + p], aqq = A[(int64_t)q * np + q];
-        const double apq = A[(int64_t)p * np + q];
-        double c = 1.0, s = 0.0, tt = 0.0;
-        const double thr = fmax(a.tol_rel * sqrt(fabs(app)) * sqrt(fabs(aqq)), floor_abs);
-        if (fabs(apq) > thr) {
-          const double tau = (aqq - app) / (2.0 * apq);
-          tt = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau))
-                            : -1.0 / (-tau + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + tt * tt);
-          s = tt * c;
-          atomicAdd(&a.counts[sweep], 1u);
-        }
-        a.rot[3 * j] = c;
-        a.rot[3 * j + 1] = s;
-        a.rot[3 * j + 2] = tt;
-      }
-      if (!grid_sync(a.bar, gen)) return;
-      // phase 2a: 2x2 blocks (ja <= jb) of A' = J^T A J, written permuted
+      const double* R = a.rot[rc];
+      double* Rn = a.rot[rc ^ 1];
+      const bool last = (t == np - 2);
+      const int next_sweep = last ? sweep + 1 : sweep;
       for (int64_t it = gtid; it < nblk; it += gsz) {
         int jb = (int)((sqrtf(8.f * (float)it + 1.f) - 1.f) * 0.5f);
         while ((int64_t)(jb + 1) * (jb + 2) / 2 <= it) ++jb;
         while ((int64_t)jb * (jb + 1) / 2 > it) --jb;
         const int ja = (int)(it - (int64_t)jb * (jb + 1) / 2);
         const int pa = 2 * ja, pb = 2 * jb;
-        const int na0 = next_pos(pa, np), na1 = next_pos(pa + 1, np);
-        const int nb0 = next_pos(pb, np), nb1 = next_pos(pb + 1, np);
-        const double a00 = A[(int64_t)pa * np + pb], a01 = A[(int64_t)pa * np + pb + 1];
-        const double a10 = A[(int64_t)(pa + 1) * np + pb], a11 = A[(int64_t)(pa + 1) * np + pb + 1];
+        const int na[2] = {next_pos(pa, np), next_pos(pa + 1, np)};
+        const int nb[2] = {next_pos(pb, np), next_pos(pb + 1, np)};
+        const double2 r0 = *reinterpret_cast<const double2*>(A + (int64_t)pa * np + pb);
+        const double2 r1 = *reinterpret_cast<const double2*>(A + (int64_t)(pa + 1) * np + pb);
+        const double a00 = r0.x, a01 = r0.y, a10 = r1.x, a11 = r1.y;
+        double nv[2][2];
         if (ja == jb) {
-          const double s = a.rot[3 * ja + 1], tt = a.rot[3 * ja + 2];
+          const double s = R[3 * ja + 1], tt = R[3 * ja + 2];
           double d0 = a00, d1 = a11, off = a01;
           if (s != 0.0) { d0 = a00 - tt * a01; d1 = a11 + tt * a01; off = 0.0; }
-          An[(int64_t)na0 * np + na0] = d0;
-          An[(int64_t)na1 * np + na1] = d1;
-          An[(int64_t)na0 * np + na1] = off;
-          An[(int64_t)na1 * np + na0] = off;
+          nv[0][0] = d0; nv[1][1] = d1; nv[0][1] = off; nv[1][0] = off;
+          An[(int64_t)na[0] * np + na[0]] = d0;
+          An[(int64_t)na[1] * np + na[1]] = d1;
+          An[(int64_t)na[0] * np + na[1]] = off;
+          An[(int64_t)na[1] * np + na[0]] = off;
         } else {
-          const double ca = a.rot[3 * ja], sa = a.rot[3 * ja + 1];
-          const double cb = a.rot[3 * jb], sb = a.rot[3 * jb + 1];
-          const double r00 = ca * a00 - sa * a10, r01 = ca * a01 - sa * a11;
-          const double r10 = sa * a00 + ca * a10, r11 = sa * a01 + ca * a11;
-          const double n00 = r00 * cb - r01 * sb, n01 = r00 * sb + r01 * cb;
-          const double n10 = r10 * cb - r11 * sb, n11 = r10 * sb + r11 * cb;
-          An[(int64_t)na0 * np + nb0] = n00; An[(int64_t)nb0 * np + na0] = n00;
-          An[(int64_t)na0 * np + nb1] = n01; An[(int64_t)nb1 * np + na0] = n01;
-          An[(int64_t)na1 * np + nb0] = n10; An[(int64_t)nb0 * np + na1] = n10;
-          An[(int64_t)na1 * np + nb1] = n11; An[(int64_t)nb1 * np + na1] = n11;
+          const double ca = R[3 * ja], sa = R[3 * ja + 1];
+          const double cb = R[3 * jb], sb = R[3 * jb + 1];
+          const double q00 = ca * a00 - sa * a10, q01 = ca * a01 - sa * a11;
+          const double q10 = sa * a00 + ca * a10, q11 = sa * a01 + ca * a11;
+          nv[0][0] = q00 * cb - q01 * sb; nv[0][1] = q00 * sb + q01 * cb;
+          nv[1][0] = q10 * cb - q11 * sb; nv[1][1] = q10 * sb + q11 * cb;
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+              An[(int64_t)na[u] * np + nb[v]] = nv[u][v];
+              An[(int64_t)nb[v] * np + na[u]] = nv[u][v];
+            }
         }
-      }
-      // phase 2b: V' = V J, columns written permuted
-      for (int64_t it = gtid; it < nvit; it += gsz) {
-        const int64_t i = it / P;
-        const int j = (int)(it - i * P);
-        const double c = a.rot[3 * j], s = a.rot[3 * j + 1];
-        const double v0 = V[i * np + 2 * j], v1 = V[i * np + 2 * j + 1];
-        Vn[i * np + next_pos(2 * j, np)] = c * v0 - s * v1;
-        Vn[i * np + next_pos(2 * j + 1, np)] = s * v0 + c * v1;
+        // next-step pairs whose off-diagonal entry this block produced
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            if (ja == jb && !(u == 0 && v == 1)) continue;
+            const int r = na[u], c = nb[v];
+            if ((r >> 1) != (c >> 1) || r == c) continue;
+            const int jn = r >> 1;
+            const double dr = new_diag(A, R, np, pa + u);
+            const double dc = new_diag(A, R, np, pb + v);
+            const bool r_first = (r & 1) == 0;
+            double cn, sn, tn;
+            if (jacobi_rotation(r_first ? dr : dc, r_first ? dc : dr, nv[u][v], a.tol_rel,
+                                floor_abs, cn, sn, tn))
+              count_rotation(a.counts, next_sweep, a.max_sweeps);
+            Rn[3 * jn] = cn;
+            Rn[3 * jn + 1] = sn;
+            Rn[3 * jn + 2] = tn;
+            if (!last) {
+              a.log[((int64_t)(t + 1) * P + jn) * 2] = cn;
+              a.log[((int64_t)(t + 1) * P + jn) * 2 + 1] = sn;
+            }
+          }
       }
       if (dpos >= 0) dpos = next_pos(dpos, np);
       cur ^= 1;
+      rc ^= 1;
       if (!grid_sync(a.bar, gen)) return;
     }
     sweeps = sweep + 1;
+    // replay the sweep's rotations on the rows of V (V' = V J_0 ... J_{np-2})
+    if (warp < a.vwarps) {
+      double* b0 = vsm + (size_t)warp * 2 * np;
+      double* b1 = b0 + np;
+      for (int row = blockIdx.x * a.vwarps + warp; row < n; row += gridDim.x * a.vwarps) {
+        double* vr = a.V + (int64_t)row * np;
+        for (int cidx = lane; cidx < np; cidx += 32) b0[cidx] = vr[cidx];
+        __syncwarp();
+        for (int t = 0; t < np - 1; ++t) {
+          const double* lg = a.log + (int64_t)t * P * 2;
+          for (int j = lane; j < P; j += 32) {
+            const double2 cs = *reinterpret_cast<const double2*>(lg + 2 * j);
+            const double v0 = b0[2 * j], v1 = b0[2 * j + 1];
+            b1[next_pos(2 * j, np)] = cs.x * v0 - cs.y * v1;
+            b1[next_pos(2 * j + 1, np)] = cs.y * v0 + cs.x * v1;
+          }
+          __syncwarp();
+          double* tmp = b0; b0 = b1; b1 = tmp;
+        }
+        for (int cidx = lane; cidx < np; cidx += 32) vr[cidx] = b0[cidx];
+        __syncwarp();
+      }
+    }
+    if (!grid_sync(a.bar, gen)) return;
     if (ld_acquire_u32(&a.counts[sweep]) == 0u) { converged = 1; break; }
   }
   if (gtid == 0) {
@@ -179,7 +265,7 @@ __global__ void k_eig_gather(const double* __restrict__ V, int n, int np, const 
   }
 }
 
-// Eq. Un: R = min{R in 1..n : sum_{i>=R} max(w_i, 0) <= thr}; the tail is
+// Eq. Un: R = min{R in 1..n : sum_{i>=R} w_i <= thr}; the tail is
 // accumulated from the smallest eigenvalue up.  out_R[0] = R, out_d[0] = tail(R).
 // With fixed_R > 0 the rank is given (rank-specified variant) and only the
 // discarded tail is computed.
@@ -199,75 +285,98 @@ __global__ void k_rank_cut(const double* __restrict__ w, int n, double thr, int 
   out_d[0] = tail[R];
 }
 
+namespace {
+struct JacobiLayout {
+  double *A0, *A1, *V, *rot0, *rot1, *log;
+  int* rank;
+};
+JacobiLayout jacobi_layout(int n, double* work) {
+  const size_t np = n + (n & 1), P = np / 2;
+  JacobiLayout L;
+  L.A0 = work;
+  L.A1 = L.A0 + np * np;
+  L.V = L.A1 + np * np;
+  L.rot0 = L.V + (size_t)n * np;
+  L.rot1 = L.rot0 + 3 * P;
+  L.log = L.rot1 + 3 * P;
+  L.rank = (int*)(L.log + 2 * P * (np > 1 ? np - 1 : 1));
+  return L;
+}
+int vpass_warps(int np) {
+  const size_t per_warp = 2 * (size_t)np * sizeof(double);
+  size_t w = (96 * 1024) / per_warp;
+  if (w > 8) w = 8;
+  if (w < 1) w = 1;
+  return (int)w;
+}
+}  // namespace
+
+size_t jacobi_work_bytes(int n) {
+  const size_t np = n + (n & 1), P = np / 2;
+  return sizeof(double) * (2 * np * np + (size_t)n * np + 6 * P + 2 * P * (np > 1 ? np - 1 : 1)) +
+         sizeof(int) * (np + 4);
+}
+
+int jacobi_max_n() { return 8192; }
+
 cudaError_t launch_jacobi(const double* S, int n, double* work, const double* fro2, unsigned* words,
                           int max_sweeps, double tol_rel, double tol_abs, int num_sms,
                           double* w_out, double* V_out, int* info_dev, cudaStream_t st) {
-  const int np = n + (n & 1), P = np / 2;
-  double* A0 = work;
-  double* A1 = A0 + (size_t)np * np;
-  double* V0 = A1 + (size_t)np * np;
-  double* V1 = V0 + (size_t)n * np;
-  double* rot = V1 + (size_t)n * np;
+  const int np = n + (n & 1);
+  const JacobiLayout L = jacobi_layout(n, work);
   // words: [0] barrier count, [1] barrier gen, [2] err, [3..] per-sweep counts
-  cudaError_t e = cudaMemsetAsync(words, 0, sizeof(unsigned) * (3 + max_sweeps + 1), st);
+  cudaError_t e = cudaMemsetAsync(words, 0, sizeof(unsigned) * (3 + max_sweeps + 2), st);
   if (e != cudaSuccess) return e;
-  k_jacobi_init<<<256, 256, 0, st>>>(S, n, np, A0, V0);
+  k_jacobi_init<<<256, 256, 0, st>>>(S, n, np, L.A0, L.V);
   count_launches(max_sweeps > 0 ? 2 : 1);
   JacobiArgs a;
-  a.A[0] = A0; a.A[1] = A1; a.V[0] = V0; a.V[1] = V1;
-  a.rot = rot;
+  a.A[0] = L.A0; a.A[1] = L.A1; a.V = L.V;
+  a.rot[0] = L.rot0; a.rot[1] = L.rot1;
+  a.log = L.log;
   a.counts = words + 3;
   a.info = info_dev;
   a.fro2 = fro2;
   a.bar = GridBarrier{words, words + 1, words + 2};
   a.n = n; a.np = np; a.max_sweeps = max_sweeps;
   a.tol_rel = tol_rel; a.tol_abs = tol_abs;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 256, 0);
+  a.vwarps = vpass_warps(np);
+  const size_t smem = (size_t)a.vwarps * 2 * np * sizeof(double);
+  e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 2) per_sm = 2;
-  int64_t items = (int64_t)P * (P + 1) / 2 + (int64_t)n * P;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 256, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  const int64_t P = np / 2;
+  const int64_t items = P * (P + 1) / 2;
   int64_t want = (items + 255) / 256;
-  int64_t cap = (int64_t)num_sms * per_sm;
-  int grid = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+  if (want < (n + a.vwarps - 1) / a.vwarps) want = (n + a.vwarps - 1) / a.vwarps;
+  const int64_t cap = num_sms;   // one CTA per SM: fewer arrivals per barrier
+  const int grid = (int)(want < 1 ? 1 : (want > cap ? cap : want));
   if (max_sweeps > 0) {
     void* args[] = {&a};
-    e = cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(grid), dim3(256), args, 0, st);
+    e = cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(grid), dim3(256), args, smem, st);
     if (e != cudaSuccess) return e;
   } else {
     int h[4] = {0, 0, 0, (n & 1) ? n : -1};
     e = cudaMemcpyAsync(info_dev, h, sizeof(h), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
   }
-  // the final buffer is chosen on the device: rank from both, gather from the right one
   return cudaGetLastError();
 }
 
 cudaError_t launch_eig_finish(int n, double* work, const int* info_host, int* info_dev,
                               double* w_out, double* V_out, cudaStream_t st) {
-  const int np = n + (n & 1), P = np / 2;
-  double* A0 = work;
-  double* A1 = A0 + (size_t)np * np;
-  double* V0 = A1 + (size_t)np * np;
-  double* V1 = V0 + (size_t)n * np;
-  double* rot = V1 + (size_t)n * np;
-  int* rank = (int*)(rot + 3 * (size_t)P + 1);
-  const int cur = info_host[2];
-  const double* A = cur ? A1 : A0;
-  const double* V = cur ? V1 : V0;
-  k_eig_rank<<<1, 1024, 0, st>>>(A, n, np, info_dev, rank, w_out);
+  const int np = n + (n & 1);
+  const JacobiLayout L = jacobi_layout(n, work);
+  const double* A = info_host[2] ? L.A1 : L.A0;
+  k_eig_rank<<<1, 1024, 0, st>>>(A, n, np, info_dev, L.rank, w_out);
   count_launches(2);
   int64_t tot = (int64_t)n * np;
   int blocks = (int)((tot + 255) / 256);
   if (blocks > 4096) blocks = 4096;
-  k_eig_gather<<<blocks, 256, 0, st>>>(V, n, np, rank, V_out);
+  k_eig_gather<<<blocks, 256, 0, st>>>(L.V, n, np, L.rank, V_out);
   return cudaGetLastError();
-}
-
-size_t jacobi_work_bytes(int n) {
-  const size_t np = n + (n & 1), P = np / 2;
-  return sizeof(double) * (2 * np * np + 2 * (size_t)n * np + 3 * P + 1) + sizeof(int) * (np + 4);
 }
 
 cudaError_t launch_rank_cut(const double* w, int n, double thr, int fixed_R, int64_t* out_R,
