@@ -402,7 +402,8 @@ def test_sthosvd_mixed_path_ranks_and_error(ctx, eps):
             "norm_sq": res.norm_sq}
     e1 = oracle.relative_errors(xs, dims, ours)["err_explicit"]
     e0 = oracle.relative_errors(xs, dims, ref)["err_explicit"]
-    assert abs(e1 - e0) <= 1e-6 and e1 <= eps
+    # FP32 TTMs round each core entry to ~u32 sqrt(I_n) ~ 1e-6 relative
+    assert abs(e1 - e0) <= 5e-6 and e1 <= eps
 
 
 def test_sthosvd_tensor_path_at_eps_1e2(ctx):
