@@ -51,29 +51,25 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
+// Arrival: one release-add per CTA on a counter that only grows (barrier k
+// completes when it reaches k * gridDim.x); departure: acquire polling.  The
+// CTA's writes are ordered before thread 0's release by the preceding
+// __syncthreads.  The counter starts at 0 (memset by the host).
 __device__ __forceinline__ bool grid_sync(const GridBarrier& b, unsigned& my_gen,
                                           unsigned long long limit = (1ull << 24)) {
   __syncthreads();
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     int ok = 1;
-    unsigned g = my_gen;
-    __threadfence();
-    unsigned arrived = atomicAdd(b.count, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(b.count, 0u);
-      __threadfence();
-      atomicAdd(b.gen, 1u);
-    } else {
-      unsigned long long it = 0;
-      while (ld_acquire_u32(b.gen) == g) {
-        if (++it > limit) { atomicOr(b.err, DEV_ERR_BARRIER_TIMEOUT); ok = 0; break; }
-        if (it > 4096) __nanosleep(64);
-      }
+    const unsigned target = (my_gen + 1) * gridDim.x;
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(b.count), "r"(1u) : "memory");
+    unsigned long long it = 0;
+    while (ld_acquire_u32(b.count) < target) {
+      if (++it > limit) { atomicOr(b.err, DEV_ERR_BARRIER_TIMEOUT); ok = 0; break; }
+      if ((it & 1023) == 0 && (ld_acquire_u32(b.err) & DEV_ERR_BARRIER_TIMEOUT)) { ok = 0; break; }
+      if (it > 4096) __nanosleep(64);
     }
-    __threadfence();
-    my_gen = g + 1;
-    if (ld_acquire_u32(b.err) & DEV_ERR_BARRIER_TIMEOUT) ok = 0;
+    my_gen += 1;
     s_ok = ok;
   }
   __syncthreads();

@@ -37,30 +37,57 @@ __device__ __forceinline__ int next_pos(int pos, int np) {
   return pos_of_slot(ns, np);
 }
 
+// FP64 reciprocal and reciprocal square root from an FP32 hardware seed
+// (~2^-22) and two Newton steps (quadratic: ~2^-44, then rounding-limited).
+// On this part a dependent FP64 FMA takes ~64 cycles while the IEEE FP64
+// divide takes ~440 and the square root ~670, and the rotation sits on the
+// critical path of every Jacobi step.  Outside the FP32 normal range the
+// IEEE operations are used.
+__device__ __forceinline__ double rcp64(double x) {
+  const double ax = fabs(x);
+  if (!(ax > 1e-36 && ax < 1e36)) return 1.0 / x;
+  double r = (double)__frcp_rn((float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+__device__ __forceinline__ double rsqrt64(double x) {   // x > 0
+  if (!(x > 1e-36 && x < 1e36)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf((float)x);
+  const double h = 0.5 * x;
+  y = y * fma(-h * y, y, 1.5);
+  return y * fma(-h * y, y, 1.5);
+}
+
 // Rotation that annihilates a_pq (sym.schur2 of Golub & Van Loan, Alg. 8.5.1).
-// Skipped (identity) when |a_pq| is below the relative/absolute threshold.
+// Skipped (identity) when |a_pq| <= max(tol_rel sqrt(|a_pp a_qq|), floor_abs).
 __device__ __forceinline__ bool jacobi_rotation(double app, double aqq, double apq, double tol_rel,
                                                 double floor_abs, double& c, double& s, double& t) {
   c = 1.0;
   s = 0.0;
   t = 0.0;
-  const double thr = fmax(tol_rel * sqrt(fabs(app)) * sqrt(fabs(aqq)), floor_abs);
-  if (!(fabs(apq) > thr)) return false;
-  const double tau = (aqq - app) / (2.0 * apq);
-  t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau)) : -1.0 / (-tau + sqrt(1.0 + tau * tau));
-  c = 1.0 / sqrt(1.0 + t * t);
+  const double aapq = fabs(apq);
+  if (!(aapq > floor_abs) || !(apq * apq > tol_rel * tol_rel * fabs(app) * fabs(aqq))) return false;
+  const double d = aqq - app;
+  if (fabs(d) > 1e15 * 2.0 * aapq) {
+    t = apq * rcp64(d);                       // tau huge: t = 1 / (2 tau) to O(tau^-3)
+  } else {
+    const double tau = d * rcp64(2.0 * apq);
+    const double q = fma(tau, tau, 1.0);
+    const double sq = q * rsqrt64(q);         // sqrt(1 + tau^2)
+    t = (tau >= 0.0) ? rcp64(tau + sq) : -rcp64(sq - tau);
+  }
+  c = rsqrt64(fma(t, t, 1.0));
   s = t * c;
   return true;
 }
 
-// New diagonal entry of the element now at `pos` after its pair's rotation.
-__device__ __forceinline__ double new_diag(const double* A, const double* R, int np, int pos) {
-  const int j = pos >> 1, p = 2 * j;
-  const double s = R[3 * j + 1], t = R[3 * j + 2];
-  const double app = A[(int64_t)p * np + p], aqq = A[(int64_t)(p + 1) * np + p + 1];
-  const double apq = A[(int64_t)p * np + p + 1];
-  if (s == 0.0) return (pos & 1) ? aqq : app;
-  return (pos & 1) ? aqq + t * apq : app - t * apq;
+// New diagonal entry of member `q` (0: p, 1: q) of a pair after its rotation
+// (s, t) of the pair's diagonal block (app, apq; aqq).
+__device__ __forceinline__ double new_diag(double2 pp_pq, double aqq, double s, double t, int q) {
+  if (s == 0.0) return q ? aqq : pp_pq.x;
+  return q ? aqq + t * pp_pq.y : pp_pq.x - t * pp_pq.y;
 }
 
 struct JacobiArgs {
@@ -88,6 +115,10 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
   const double floor_abs = a.tol_abs * sqrt(*a.fro2);
   const int64_t nblk = (int64_t)P * (P + 1) / 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* const A0 = a.A[0];
+  double* const A1 = a.A[1];
+  double* const rot0 = a.rot[0];
+  double* const rot1 = a.rot[1];
   unsigned gen = 0;
   int cur = 0, rc = 0;
   int dpos = (n & 1) ? n : -1;   // dummy index (odd n) sits at position n initially
@@ -96,28 +127,31 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
   // prologue: rotations of step 0
   for (int64_t j = gtid; j < P; j += gsz) {
     const int p = 2 * (int)j;
-    const double* A = a.A[0];
+    const double* A = A0;
     double c, s, t;
     if (jacobi_rotation(A[(int64_t)p * np + p], A[(int64_t)(p + 1) * np + p + 1],
                         A[(int64_t)p * np + p + 1], a.tol_rel, floor_abs, c, s, t))
       count_rotation(a.counts, 0, a.max_sweeps);
-    a.rot[0][3 * j] = c;
-    a.rot[0][3 * j + 1] = s;
-    a.rot[0][3 * j + 2] = t;
+    rot0[3 * j] = c;
+    rot0[3 * j + 1] = s;
+    rot0[3 * j + 2] = t;
   }
   if (!grid_sync(a.bar, gen)) return;
 
   for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
     // the sweep's step-0 rotations into the log
     for (int64_t j = gtid; j < P; j += gsz) {
-      a.log[2 * j] = a.rot[rc][3 * j];
-      a.log[2 * j + 1] = a.rot[rc][3 * j + 1];
+      const double* Rc = rc ? rot1 : rot0;
+      a.log[2 * j] = Rc[3 * j];
+      a.log[2 * j + 1] = Rc[3 * j + 1];
     }
     for (int t = 0; t < np - 1; ++t) {
-      const double* A = a.A[cur];
-      double* An = a.A[cur ^ 1];
-      const double* R = a.rot[rc];
-      double* Rn = a.rot[rc ^ 1];
+      // pointer selects, not runtime-indexed parameter arrays (those would go
+      // through local memory, which the barrier's acquire sends back to L2)
+      const double* A = cur ? A1 : A0;
+      double* An = cur ? A0 : A1;
+      const double* R = rc ? rot1 : rot0;
+      double* Rn = rc ? rot0 : rot1;
       const bool last = (t == np - 2);
       const int next_sweep = last ? sweep + 1 : sweep;
       for (int64_t it = gtid; it < nblk; it += gsz) {
@@ -128,8 +162,30 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
         const int pa = 2 * ja, pb = 2 * jb;
         const int na[2] = {next_pos(pa, np), next_pos(pa + 1, np)};
         const int nb[2] = {next_pos(pb, np), next_pos(pb + 1, np)};
+        // entries (u, v) of this block that are the off-diagonal element of a
+        // next-step pair (decided from positions only, before any load)
+        unsigned mask = 0;
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            if (ja == jb && !(u == 0 && v == 1)) continue;
+            const int r = na[u], c = nb[v];
+            if ((r >> 1) == (c >> 1) && r != c) mask |= 1u << (2 * u + v);
+          }
+        // every load of the step is issued here, in one round trip: the block,
+        // and for a block that feeds a next rotation the diagonal blocks of
+        // pairs ja and jb (their new diagonal entries)
         const double2 r0 = *reinterpret_cast<const double2*>(A + (int64_t)pa * np + pb);
         const double2 r1 = *reinterpret_cast<const double2*>(A + (int64_t)(pa + 1) * np + pb);
+        double2 da = make_double2(0.0, 0.0), db = make_double2(0.0, 0.0);
+        double daq = 0.0, dbq = 0.0;
+        if (mask && ja != jb) {
+          da = *reinterpret_cast<const double2*>(A + (int64_t)pa * np + pa);        // app, apq
+          daq = A[(int64_t)(pa + 1) * np + pa + 1];                                 // aqq
+          db = *reinterpret_cast<const double2*>(A + (int64_t)pb * np + pb);
+          dbq = A[(int64_t)(pb + 1) * np + pb + 1];
+        }
         const double a00 = r0.x, a01 = r0.y, a10 = r1.x, a11 = r1.y;
         double nv[2][2];
         if (ja == jb) {
@@ -156,30 +212,37 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
               An[(int64_t)nb[v] * np + na[u]] = nv[u][v];
             }
         }
-        // next-step pairs whose off-diagonal entry this block produced
-#pragma unroll
-        for (int u = 0; u < 2; ++u)
-#pragma unroll
-          for (int v = 0; v < 2; ++v) {
-            if (ja == jb && !(u == 0 && v == 1)) continue;
-            const int r = na[u], c = nb[v];
-            if ((r >> 1) != (c >> 1) || r == c) continue;
-            const int jn = r >> 1;
-            const double dr = new_diag(A, R, np, pa + u);
-            const double dc = new_diag(A, R, np, pb + v);
-            const bool r_first = (r & 1) == 0;
-            double cn, sn, tn;
-            if (jacobi_rotation(r_first ? dr : dc, r_first ? dc : dr, nv[u][v], a.tol_rel,
-                                floor_abs, cn, sn, tn))
-              count_rotation(a.counts, next_sweep, a.max_sweeps);
-            Rn[3 * jn] = cn;
-            Rn[3 * jn + 1] = sn;
-            Rn[3 * jn + 2] = tn;
-            if (!last) {
-              a.log[((int64_t)(t + 1) * P + jn) * 2] = cn;
-              a.log[((int64_t)(t + 1) * P + jn) * 2 + 1] = sn;
-            }
+        // next-step pairs whose off-diagonal entry this block produced: only
+        // these threads run the rotation (a data-dependent loop, so the FP64
+        // chain is not executed predicated by every thread)
+        while (mask) {
+          const int k = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const int u = k >> 1, v = k & 1;
+          const int r = na[u];
+          const int jn = r >> 1;
+          double dr, dc;
+          if (ja == jb) {
+            dr = nv[0][0];
+            dc = nv[1][1];
+          } else {
+            dr = new_diag(da, daq, R[3 * ja + 1], R[3 * ja + 2], u);
+            dc = new_diag(db, dbq, R[3 * jb + 1], R[3 * jb + 2], v);
           }
+          const double off = (k == 0) ? nv[0][0] : (k == 1) ? nv[0][1] : (k == 2) ? nv[1][0] : nv[1][1];
+          const bool r_first = (r & 1) == 0;
+          double cn, sn, tn;
+          if (jacobi_rotation(r_first ? dr : dc, r_first ? dc : dr, off, a.tol_rel, floor_abs, cn,
+                              sn, tn))
+            count_rotation(a.counts, next_sweep, a.max_sweeps);
+          Rn[3 * jn] = cn;
+          Rn[3 * jn + 1] = sn;
+          Rn[3 * jn + 2] = tn;
+          if (!last) {
+            a.log[((int64_t)(t + 1) * P + jn) * 2] = cn;
+            a.log[((int64_t)(t + 1) * P + jn) * 2 + 1] = sn;
+          }
+        }
       }
       if (dpos >= 0) dpos = next_pos(dpos, np);
       cur ^= 1;
