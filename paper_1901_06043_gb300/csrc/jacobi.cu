@@ -23,77 +23,108 @@
 
 namespace tk {
 
-__device__ __forceinline__ int slot_of_pos(int pos, int np) {
-  int k = pos >> 1;
-  return (pos & 1) ? (np - 1 - k) : k;
-}
-__device__ __forceinline__ int pos_of_slot(int s, int np) {
-  return (s < (np >> 1)) ? (2 * s) : (2 * (np - 1 - s) + 1);
-}
-// Storage position at the next step of the element now at `pos`.
+// Storage position at the next step of the element now at `pos`.  Slots of
+// the round robin: position 2k holds slot k, position 2k+1 slot np-1-k; a
+// step keeps slot 0 and moves slot s to s+1 (slot np-1 to 1).  In positions:
+// 0 stays, an even position moves up by 2 (np-2 goes to np-1), position 1
+// goes to 2 and any other odd position moves down by 2.
 __device__ __forceinline__ int next_pos(int pos, int np) {
-  int s = slot_of_pos(pos, np);
-  int ns = (s == 0) ? 0 : (s % (np - 1)) + 1;
-  return pos_of_slot(ns, np);
+  if (pos & 1) return (pos == 1) ? (np > 2 ? 2 : 1) : pos - 2;
+  if (pos == 0) return 0;
+  return (pos == np - 2) ? np - 1 : pos + 2;
 }
 
-// FP64 reciprocal and reciprocal square root from an FP32 hardware seed
-// (~2^-22) and two Newton steps (quadratic: ~2^-44, then rounding-limited).
-// On this part a dependent FP64 FMA takes ~64 cycles while the IEEE FP64
-// divide takes ~440 and the square root ~670, and the rotation sits on the
-// critical path of every Jacobi step.  Outside the FP32 normal range the
-// IEEE operations are used.
-__device__ __forceinline__ double rcp64(double x) {
-  const double ax = fabs(x);
-  if (!(ax > 1e-36 && ax < 1e36)) return 1.0 / x;
-  double r = (double)__frcp_rn((float)x);
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
-}
-__device__ __forceinline__ double rsqrt64(double x) {   // x > 0
-  if (!(x > 1e-36 && x < 1e36)) return 1.0 / sqrt(x);
-  double y = (double)rsqrtf((float)x);
-  const double h = 0.5 * x;
-  y = y * fma(-h * y, y, 1.5);
-  return y * fma(-h * y, y, 1.5);
-}
-
-// Rotation that annihilates a_pq (sym.schur2 of Golub & Van Loan, Alg. 8.5.1).
-// Skipped (identity) when |a_pq| <= max(tol_rel sqrt(|a_pp a_qq|), floor_abs).
+// Rotation (c, s) for the 2x2 block [[app, apq], [apq, aqq]]: the smaller of
+// the two angles that annihilate apq (sym.schur2 of Golub & Van Loan,
+// Alg. 8.5.1: tau = (aqq - app) / (2 apq), t = sign(tau) / (|tau| +
+// sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c).  Skipped (c = 1, s = 0,
+// returns false) when |apq| <= max(tol_rel sqrt(|app aqq|), floor_abs).
+//
+// The angle is computed in FP32 after an exact power-of-two scaling of
+// (aqq - app, apq) into range; (c, s) are then made orthonormal to FP64
+// rounding by the second-order correction f = 1 - e/2 + 3e^2/8 of
+// 1/sqrt(1 + e), e = c^2 + s^2 - 1 (|e| ~ 1e-7, so the neglected term is
+// ~1e-21).  The transformation is therefore an exact similarity in FP64; only
+// the angle is FP32-accurate, which leaves ~1e-7 |apq| in the annihilated
+// entry (kept, and removed by a later sweep).  This keeps the dependent FP64
+// chain at ~6 operations (an FP64 operation takes ~64 cycles on this part,
+// and the rotation is on the critical path of every step).
 __device__ __forceinline__ bool jacobi_rotation(double app, double aqq, double apq, double tol_rel,
-                                                double floor_abs, double& c, double& s, double& t) {
+                                                double floor_abs, double& c, double& s) {
   c = 1.0;
   s = 0.0;
-  t = 0.0;
-  const double aapq = fabs(apq);
-  if (!(aapq > floor_abs) || !(apq * apq > tol_rel * tol_rel * fabs(app) * fabs(aqq))) return false;
+  if (!(fabs(apq) > floor_abs) || !(apq * apq > tol_rel * tol_rel * fabs(app) * fabs(aqq)))
+    return false;
   const double d = aqq - app;
-  if (fabs(d) > 1e15 * 2.0 * aapq) {
-    t = apq * rcp64(d);                       // tau huge: t = 1 / (2 tau) to O(tau^-3)
-  } else {
-    const double tau = d * rcp64(2.0 * apq);
-    const double q = fma(tau, tau, 1.0);
-    const double sq = q * rsqrt64(q);         // sqrt(1 + tau^2)
-    t = (tau >= 0.0) ? rcp64(tau + sq) : -rcp64(sq - tau);
-  }
-  c = rsqrt64(fma(t, t, 1.0));
-  s = t * c;
+  // 2^(1023 - E), E the larger biased exponent of d and apq (clamped so the
+  // scale is a normal FP64 number)
+  const int ed = (__double2hiint(d) >> 20) & 0x7ff, eb = (__double2hiint(apq) >> 20) & 0x7ff;
+  int sb = 2046 - (ed > eb ? ed : eb);
+  sb = sb < 1 ? 1 : (sb > 2046 ? 2046 : sb);
+  const double scale = __hiloint2double(sb << 20, 0);
+  const float df = (float)(d * scale), bf = (float)(apq * scale);
+  const float tau = __fdividef(df, 2.f * bf);
+  const float atau = fabsf(tau);
+  float t = (atau > 1e10f) ? __fdividef(0.5f, atau) : __fdividef(1.f, atau + sqrtf(fmaf(tau, tau, 1.f)));
+  t = copysignf(t, tau);
+  const float cf = rsqrtf(fmaf(t, t, 1.f));
+  const float sf = t * cf;
+  if (!(sf != 0.f) || !(cf == cf)) return false;   // angle below FP32 resolution (or NaN input)
+  const double c0 = cf, s0 = sf;
+  const double e = fma(c0, c0, fma(s0, s0, -1.0));
+  const double f = fma(e, fma(e, 0.375, -0.5), 1.0);
+  c = c0 * f;
+  s = s0 * f;
   return true;
 }
 
-// New diagonal entry of member `q` (0: p, 1: q) of a pair after its rotation
-// (s, t) of the pair's diagonal block (app, apq; aqq).
-__device__ __forceinline__ double new_diag(double2 pp_pq, double aqq, double s, double t, int q) {
-  if (s == 0.0) return q ? aqq : pp_pq.x;
-  return q ? aqq + t * pp_pq.y : pp_pq.x - t * pp_pq.y;
+// Entries of the pair's 2x2 diagonal block [[app, apq], [apq, aqq]] after
+// the rotation (c, s): A' = G^T A G with G = [[c, s], [-s, c]].
+__device__ __forceinline__ double rot_pp(double app, double apq, double aqq, double c, double s) {
+  return fma(c * c, app, fma(-2.0 * c * s, apq, (s * s) * aqq));
+}
+__device__ __forceinline__ double rot_qq(double app, double apq, double aqq, double c, double s) {
+  return fma(s * s, app, fma(2.0 * c * s, apq, (c * c) * aqq));
+}
+__device__ __forceinline__ double rot_pq(double app, double apq, double aqq, double c, double s) {
+  return fma(c * s, app - aqq, (c * c - s * s) * apq);
+}
+
+// Block `it` of the upper triangle of 2x2 blocks (column-major order: jb,
+// then ja <= jb), the next-step positions of its rows and columns, and the
+// entries (bit 2u+v) that become the off-diagonal element of a next-step
+// pair.  Depends on positions only, so it is the same at every step.
+struct BlockGeom {
+  int ja, jb, na0, na1, nb0, nb1;
+  unsigned mask;
+};
+__device__ __forceinline__ BlockGeom block_geom(int64_t it, int np) {
+  BlockGeom g;
+  int jb = (int)((sqrtf(8.f * (float)it + 1.f) - 1.f) * 0.5f);
+  while ((int64_t)(jb + 1) * (jb + 2) / 2 <= it) ++jb;
+  while ((int64_t)jb * (jb + 1) / 2 > it) --jb;
+  g.jb = jb;
+  g.ja = (int)(it - (int64_t)jb * (jb + 1) / 2);
+  const int na[2] = {next_pos(2 * g.ja, np), next_pos(2 * g.ja + 1, np)};
+  const int nb[2] = {next_pos(2 * jb, np), next_pos(2 * jb + 1, np)};
+  g.na0 = na[0]; g.na1 = na[1]; g.nb0 = nb[0]; g.nb1 = nb[1];
+  unsigned mask = 0;
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      if (g.ja == jb && !(u == 0 && v == 1)) continue;
+      const int r = na[u], c = nb[v];
+      if ((r >> 1) == (c >> 1) && r != c) mask |= 1u << (2 * u + v);
+    }
+  g.mask = mask;
+  return g;
 }
 
 struct JacobiArgs {
   double* A[2];       // np x np row-major, ping-pong
   double* V;          // n x np row-major (rows: coordinates, cols: storage positions)
-  double* rot[2];     // 3 * P: c, s, t of the current / next step
+  double* rot[2];     // 2 * P: c, s of the current / next step
   double* log;        // (np - 1) * P * 2: c, s of every step of the current sweep
   unsigned* counts;   // non-skipped rotations per sweep (max_sweeps + 1 entries, zeroed)
   int* info;          // [0] sweeps, [1] converged, [2] final A buffer, [3] dummy position
@@ -107,8 +138,11 @@ __device__ __forceinline__ void count_rotation(unsigned* counts, int idx, int ma
   if (idx <= max_sweeps) atomicAdd(&counts[idx], 1u);
 }
 
+constexpr int VGROUP = 8;   // log entries a lane loads at once in the V pass
+constexpr int VROWS = 2;    // target V rows per CTA
+
 __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
-  extern __shared__ double vsm[];
+  extern __shared__ __align__(16) double vsm[];
   const int n = a.n, np = a.np, P = np >> 1;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
@@ -123,18 +157,17 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
   int cur = 0, rc = 0;
   int dpos = (n & 1) ? n : -1;   // dummy index (odd n) sits at position n initially
   int sweeps = 0, converged = 0;
+  const BlockGeom g0 = block_geom(gtid < nblk ? gtid : 0, np);   // this thread's first block
 
   // prologue: rotations of step 0
   for (int64_t j = gtid; j < P; j += gsz) {
     const int p = 2 * (int)j;
     const double* A = A0;
-    double c, s, t;
+    double c, s;
     if (jacobi_rotation(A[(int64_t)p * np + p], A[(int64_t)(p + 1) * np + p + 1],
-                        A[(int64_t)p * np + p + 1], a.tol_rel, floor_abs, c, s, t))
+                        A[(int64_t)p * np + p + 1], a.tol_rel, floor_abs, c, s))
       count_rotation(a.counts, 0, a.max_sweeps);
-    rot0[3 * j] = c;
-    rot0[3 * j + 1] = s;
-    rot0[3 * j + 2] = t;
+    reinterpret_cast<double2*>(rot0)[j] = make_double2(c, s);
   }
   if (!grid_sync(a.bar, gen)) return;
 
@@ -142,8 +175,7 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
     // the sweep's step-0 rotations into the log
     for (int64_t j = gtid; j < P; j += gsz) {
       const double* Rc = rc ? rot1 : rot0;
-      a.log[2 * j] = Rc[3 * j];
-      a.log[2 * j + 1] = Rc[3 * j + 1];
+      reinterpret_cast<double2*>(a.log)[j] = reinterpret_cast<const double2*>(Rc)[j];
     }
     for (int t = 0; t < np - 1; ++t) {
       // pointer selects, not runtime-indexed parameter arrays (those would go
@@ -155,24 +187,11 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
       const bool last = (t == np - 2);
       const int next_sweep = last ? sweep + 1 : sweep;
       for (int64_t it = gtid; it < nblk; it += gsz) {
-        int jb = (int)((sqrtf(8.f * (float)it + 1.f) - 1.f) * 0.5f);
-        while ((int64_t)(jb + 1) * (jb + 2) / 2 <= it) ++jb;
-        while ((int64_t)jb * (jb + 1) / 2 > it) --jb;
-        const int ja = (int)(it - (int64_t)jb * (jb + 1) / 2);
-        const int pa = 2 * ja, pb = 2 * jb;
-        const int na[2] = {next_pos(pa, np), next_pos(pa + 1, np)};
-        const int nb[2] = {next_pos(pb, np), next_pos(pb + 1, np)};
-        // entries (u, v) of this block that are the off-diagonal element of a
-        // next-step pair (decided from positions only, before any load)
-        unsigned mask = 0;
-#pragma unroll
-        for (int u = 0; u < 2; ++u)
-#pragma unroll
-          for (int v = 0; v < 2; ++v) {
-            if (ja == jb && !(u == 0 && v == 1)) continue;
-            const int r = na[u], c = nb[v];
-            if ((r >> 1) == (c >> 1) && r != c) mask |= 1u << (2 * u + v);
-          }
+        const BlockGeom g = (it == gtid) ? g0 : block_geom(it, np);
+        const int ja = g.ja, jb = g.jb, pa = 2 * ja, pb = 2 * jb;
+        const int na[2] = {g.na0, g.na1};
+        const int nb[2] = {g.nb0, g.nb1};
+        unsigned mask = g.mask;
         // every load of the step is issued here, in one round trip: the block,
         // and for a block that feeds a next rotation the diagonal blocks of
         // pairs ja and jb (their new diagonal entries)
@@ -188,18 +207,20 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
         }
         const double a00 = r0.x, a01 = r0.y, a10 = r1.x, a11 = r1.y;
         double nv[2][2];
+        const double2 Ra = reinterpret_cast<const double2*>(R)[ja];
+        const double2 Rb = reinterpret_cast<const double2*>(R)[jb];
         if (ja == jb) {
-          const double s = R[3 * ja + 1], tt = R[3 * ja + 2];
-          double d0 = a00, d1 = a11, off = a01;
-          if (s != 0.0) { d0 = a00 - tt * a01; d1 = a11 + tt * a01; off = 0.0; }
+          const double c = Ra.x, s = Ra.y;
+          const double d0 = rot_pp(a00, a01, a11, c, s), d1 = rot_qq(a00, a01, a11, c, s);
+          const double off = rot_pq(a00, a01, a11, c, s);
           nv[0][0] = d0; nv[1][1] = d1; nv[0][1] = off; nv[1][0] = off;
           An[(int64_t)na[0] * np + na[0]] = d0;
           An[(int64_t)na[1] * np + na[1]] = d1;
           An[(int64_t)na[0] * np + na[1]] = off;
           An[(int64_t)na[1] * np + na[0]] = off;
         } else {
-          const double ca = R[3 * ja], sa = R[3 * ja + 1];
-          const double cb = R[3 * jb], sb = R[3 * jb + 1];
+          const double ca = Ra.x, sa = Ra.y;
+          const double cb = Rb.x, sb = Rb.y;
           const double q00 = ca * a00 - sa * a10, q01 = ca * a01 - sa * a11;
           const double q10 = sa * a00 + ca * a10, q11 = sa * a01 + ca * a11;
           nv[0][0] = q00 * cb - q01 * sb; nv[0][1] = q00 * sb + q01 * cb;
@@ -226,18 +247,16 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
             dr = nv[0][0];
             dc = nv[1][1];
           } else {
-            dr = new_diag(da, daq, R[3 * ja + 1], R[3 * ja + 2], u);
-            dc = new_diag(db, dbq, R[3 * jb + 1], R[3 * jb + 2], v);
+            dr = u ? rot_qq(da.x, da.y, daq, Ra.x, Ra.y) : rot_pp(da.x, da.y, daq, Ra.x, Ra.y);
+            dc = v ? rot_qq(db.x, db.y, dbq, Rb.x, Rb.y) : rot_pp(db.x, db.y, dbq, Rb.x, Rb.y);
           }
           const double off = (k == 0) ? nv[0][0] : (k == 1) ? nv[0][1] : (k == 2) ? nv[1][0] : nv[1][1];
           const bool r_first = (r & 1) == 0;
-          double cn, sn, tn;
+          double cn, sn;
           if (jacobi_rotation(r_first ? dr : dc, r_first ? dc : dr, off, a.tol_rel, floor_abs, cn,
-                              sn, tn))
+                              sn))
             count_rotation(a.counts, next_sweep, a.max_sweeps);
-          Rn[3 * jn] = cn;
-          Rn[3 * jn + 1] = sn;
-          Rn[3 * jn + 2] = tn;
+          reinterpret_cast<double2*>(Rn)[jn] = make_double2(cn, sn);
           if (!last) {
             a.log[((int64_t)(t + 1) * P + jn) * 2] = cn;
             a.log[((int64_t)(t + 1) * P + jn) * 2 + 1] = sn;
@@ -254,20 +273,51 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
     if (warp < a.vwarps) {
       double* b0 = vsm + (size_t)warp * 2 * np;
       double* b1 = b0 + np;
-      for (int row = blockIdx.x * a.vwarps + warp; row < n; row += gridDim.x * a.vwarps) {
+      // rows spread over all CTAs first (the pass is FP64-throughput bound:
+      // a row per warp on as many SMs as possible)
+      for (int row = blockIdx.x + gridDim.x * warp; row < n; row += gridDim.x * a.vwarps) {
         double* vr = a.V + (int64_t)row * np;
         for (int cidx = lane; cidx < np; cidx += 32) b0[cidx] = vr[cidx];
         __syncwarp();
-        for (int t = 0; t < np - 1; ++t) {
-          const double* lg = a.log + (int64_t)t * P * 2;
-          for (int j = lane; j < P; j += 32) {
-            const double2 cs = *reinterpret_cast<const double2*>(lg + 2 * j);
-            const double v0 = b0[2 * j], v1 = b0[2 * j + 1];
-            b1[next_pos(2 * j, np)] = cs.x * v0 - cs.y * v1;
-            b1[next_pos(2 * j + 1, np)] = cs.y * v0 + cs.x * v1;
+        // flattened (step, group) loop; the next group's (c, s) loads are in
+        // flight while the current group is applied
+        const int G = (P + 32 * VGROUP - 1) / (32 * VGROUP);
+        const int64_t total = (int64_t)(np - 1) * G;
+        const double2* lg = reinterpret_cast<const double2*>(a.log);
+        double2 cs[VGROUP], csn[VGROUP];
+#pragma unroll
+        for (int k = 0; k < VGROUP; ++k) {
+          const int j = 32 * k + lane;
+          cs[k] = (j < P) ? lg[j] : make_double2(1.0, 0.0);
+        }
+        int t1 = 0, g1 = 0;   // (step, group) of the prefetch
+        for (int64_t it = 0; it < total; ++it) {
+          const int j0 = g1 * 32 * VGROUP;
+          if (++g1 == G) { g1 = 0; ++t1; }
+          if (it + 1 < total) {
+            const int j1 = g1 * 32 * VGROUP;
+#pragma unroll
+            for (int k = 0; k < VGROUP; ++k) {
+              const int j = j1 + 32 * k + lane;
+              csn[k] = (j < P) ? lg[(int64_t)t1 * P + j] : make_double2(1.0, 0.0);
+            }
           }
-          __syncwarp();
-          double* tmp = b0; b0 = b1; b1 = tmp;
+#pragma unroll
+          for (int k = 0; k < VGROUP; ++k) {
+            const int j = j0 + 32 * k + lane;
+            if (j < P) {
+              const double2 v = reinterpret_cast<const double2*>(b0)[j];
+              const double v0 = v.x, v1 = v.y;
+              b1[next_pos(2 * j, np)] = cs[k].x * v0 - cs[k].y * v1;
+              b1[next_pos(2 * j + 1, np)] = cs[k].y * v0 + cs[k].x * v1;
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < VGROUP; ++k) cs[k] = csn[k];
+          if (j0 + 32 * VGROUP >= P) {   // last group of step t
+            __syncwarp();
+            double* tmp = b0; b0 = b1; b1 = tmp;
+          }
         }
         for (int cidx = lane; cidx < np; cidx += 32) vr[cidx] = b0[cidx];
         __syncwarp();
@@ -360,8 +410,8 @@ JacobiLayout jacobi_layout(int n, double* work) {
   L.A1 = L.A0 + np * np;
   L.V = L.A1 + np * np;
   L.rot0 = L.V + (size_t)n * np;
-  L.rot1 = L.rot0 + 3 * P;
-  L.log = L.rot1 + 3 * P;
+  L.rot1 = L.rot0 + 2 * P;
+  L.log = L.rot1 + 2 * P;
   L.rank = (int*)(L.log + 2 * P * (np > 1 ? np - 1 : 1));
   return L;
 }
@@ -376,7 +426,7 @@ int vpass_warps(int np) {
 
 size_t jacobi_work_bytes(int n) {
   const size_t np = n + (n & 1), P = np / 2;
-  return sizeof(double) * (2 * np * np + (size_t)n * np + 6 * P + 2 * P * (np > 1 ? np - 1 : 1)) +
+  return sizeof(double) * (2 * np * np + (size_t)n * np + 4 * P + 2 * P * (np > 1 ? np - 1 : 1)) +
          sizeof(int) * (np + 4);
 }
 
@@ -413,7 +463,9 @@ cudaError_t launch_jacobi(const double* S, int n, double* work, const double* fr
   const int64_t P = np / 2;
   const int64_t items = P * (P + 1) / 2;
   int64_t want = (items + 255) / 256;
-  if (want < (n + a.vwarps - 1) / a.vwarps) want = (n + a.vwarps - 1) / a.vwarps;
+  // the V pass is FP64-throughput bound: at most VROWS rows per CTA where
+  // the SM count allows
+  if (want < (n + VROWS - 1) / VROWS) want = (n + VROWS - 1) / VROWS;
   const int64_t cap = num_sms;   // one CTA per SM: fewer arrivals per barrier
   const int grid = (int)(want < 1 ? 1 : (want > cap ? cap : want));
   if (max_sweeps > 0) {
