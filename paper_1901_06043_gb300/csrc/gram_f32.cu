@@ -1,0 +1,261 @@
+// FP32-product Gram of a column-mode slab view (L == 1, the first mode of the
+// natural-descending layout): S = Y Y^T, Y the I x Rt matrix whose column r is
+// slab r, contiguous in i.  Section 5.1 (Alg. 2) forms the Gram of the mode-n
+// unfolding slab by slab; for the first mode every slab is one column of Y.
+//
+// Tile 128 x 128 of the lower triangle per CTA, 256 threads with 8 x 8
+// outputs each (float4 shared-memory operands: 4 loads per 64 FMAs), K staged
+// 16 slabs at a time by a 3-deep cp.async pipeline, split-K over CTAs with a
+// fixed-order FP64 reduction of the partial tiles.
+//
+// Summation (the rank cut compares a tail of ~1e-9 of the trace, so a biased
+// rounding in the diagonal would move the cut): the 16 products of a K-block
+// are summed into a fresh register, the block sums are added in FP32
+// (round-to-nearest, unbiased for these smoothly distributed terms) over a
+// chunk of CHUNK blocks, and every chunk sum enters an exact FP32 pair
+// (TwoSum: hi + lo) kept in shared memory.  Nothing on the FP64 pipe runs in
+// the main loop.
+#include <cstdio>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace tk {
+namespace {
+
+constexpr int BT = 128;     // output tile
+constexpr int BK = 16;      // slabs per stage (= the fresh-register K-block)
+constexpr int NST = 3;      // pipeline stages
+constexpr int CHUNK = 32;   // K-blocks per FP32 chunk sum
+constexpr int NTHR = 256;
+
+struct Smem {
+  float a[NST][BK][BT];
+  float b[NST][BK][BT];
+  float hi[BT * BT];
+  float lo[BT * BT];
+};
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Rows [i0, i0+128) of slabs [kb*BK, kb*BK+16) into dst[kk][ii]; zero outside.
+template <bool VEC>
+__device__ __forceinline__ void load_panel(float (*dst)[BT], const float* __restrict__ y, int64_t I,
+                                           int64_t Rt, int64_t i0, int64_t kb) {
+  const int tid = threadIdx.x;
+  if constexpr (VEC) {
+#pragma unroll
+    for (int e = 0; e < (BK * BT / 4) / NTHR; ++e) {
+      const int c = tid + NTHR * e;
+      const int kk = c >> 5, q = c & 31;
+      const int64_t r = kb * BK + kk, i = i0 + 4 * q;
+      const bool valid = (r < Rt) && (i < I);
+      cp_async16(&dst[kk][4 * q], valid ? y + i + I * r : y, valid);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < (BK * BT) / NTHR; ++e) {
+      const int c = tid + NTHR * e;
+      const int kk = c >> 7, q = c & 127;
+      const int64_t r = kb * BK + kk, i = i0 + q;
+      const bool valid = (r < Rt) && (i < I);
+      cp_async4(&dst[kk][q], valid ? y + i + I * r : y, valid);
+    }
+  }
+}
+
+// One CTA: tile (ta, tb), ta >= tb, over K-blocks [NKB*ks/ksplit, NKB*(ks+1)/ksplit).
+// Writes the FP64 partial tile part[(ks * ntiles + tile) * BT * BT + row * BT + col].
+template <bool VEC>
+__global__ void __launch_bounds__(NTHR, 1)
+    k_gram_f32_col(const float* __restrict__ y, int64_t I, int64_t Rt, int ntiles, int ksplit,
+                   double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+  const int tile = blockIdx.x, ks = blockIdx.y;
+  int ta = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);
+  while ((ta + 1) * (ta + 2) / 2 <= tile) ++ta;
+  while (ta * (ta + 1) / 2 > tile) --ta;
+  const int tb = tile - ta * (ta + 1) / 2;
+  const bool diag = (ta == tb);
+  const int64_t ia0 = (int64_t)ta * BT, ib0 = (int64_t)tb * BT;
+  const int64_t NKB = (Rt + BK - 1) / BK;
+  const int64_t kb0 = NKB * ks / ksplit;
+  const int64_t count = NKB * (ks + 1) / ksplit - kb0;
+
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // this thread's rows ty*4 + {0..3} and 64 + ty*4 + {0..3}; columns likewise with tx
+  for (int u = 0; u < 8; ++u) {
+    const int row = (u < 4) ? ty * 4 + u : 64 + ty * 4 + (u - 4);
+    *reinterpret_cast<float4*>(&sm.hi[row * BT + tx * 4]) = make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4*>(&sm.hi[row * BT + 64 + tx * 4]) = make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4*>(&sm.lo[row * BT + tx * 4]) = make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4*>(&sm.lo[row * BT + 64 + tx * 4]) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+
+#pragma unroll
+  for (int s = 0; s < NST - 1; ++s) {
+    if (s < count) {
+      load_panel<VEC>(sm.a[s], y, I, Rt, ia0, kb0 + s);
+      if (!diag) load_panel<VEC>(sm.b[s], y, I, Rt, ib0, kb0 + s);
+    }
+    cp_commit();
+  }
+
+  float acc[8][8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+
+  for (int64_t idx = 0; idx < count; ++idx) {
+    cp_wait<NST - 2>();
+    __syncthreads();
+    {
+      const int64_t nxt = idx + NST - 1;
+      const int sn = (int)(nxt % NST);
+      if (nxt < count) {
+        load_panel<VEC>(sm.a[sn], y, I, Rt, ia0, kb0 + nxt);
+        if (!diag) load_panel<VEC>(sm.b[sn], y, I, Rt, ib0, kb0 + nxt);
+      }
+      cp_commit();
+    }
+    const int st = (int)(idx % NST);
+    const float(*A)[BT] = sm.a[st];
+    const float(*B)[BT] = diag ? sm.a[st] : sm.b[st];
+    float t[8][8];
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&A[kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&A[kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&B[kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&B[kk][64 + tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) t[u][v] = (kk == 0) ? a[u] * b[v] : fmaf(a[u], b[v], t[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int v = 0; v < 8; ++v) acc[u][v] += t[u][v];
+
+    if (((idx + 1) % CHUNK) == 0 || idx + 1 == count) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int row = (u < 4) ? ty * 4 + u : 64 + ty * 4 + (u - 4);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float* ph = &sm.hi[row * BT + h * 64 + tx * 4];
+          float* pl = &sm.lo[row * BT + h * 64 + tx * 4];
+          float4 vh = *reinterpret_cast<float4*>(ph);
+          float4 vl = *reinterpret_cast<float4*>(pl);
+          float s, e;
+          two_sum_f(vh.x, acc[u][4 * h + 0], s, e); vh.x = s; vl.x += e;
+          two_sum_f(vh.y, acc[u][4 * h + 1], s, e); vh.y = s; vl.y += e;
+          two_sum_f(vh.z, acc[u][4 * h + 2], s, e); vh.z = s; vl.z += e;
+          two_sum_f(vh.w, acc[u][4 * h + 3], s, e); vh.w = s; vl.w += e;
+          *reinterpret_cast<float4*>(ph) = vh;
+          *reinterpret_cast<float4*>(pl) = vl;
+        }
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+      }
+    }
+  }
+  cp_wait<0>();
+
+  double* out = part + ((int64_t)ks * ntiles + tile) * BT * BT;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int row = (u < 4) ? ty * 4 + u : 64 + ty * 4 + (u - 4);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int col = h * 64 + tx * 4;
+      const float4 vh = *reinterpret_cast<const float4*>(&sm.hi[row * BT + col]);
+      const float4 vl = *reinterpret_cast<const float4*>(&sm.lo[row * BT + col]);
+      double2* o = reinterpret_cast<double2*>(out + row * BT + col);
+      o[0] = make_double2((double)vh.x + (double)vl.x, (double)vh.y + (double)vl.y);
+      o[1] = make_double2((double)vh.z + (double)vl.z, (double)vh.w + (double)vl.w);
+    }
+  }
+}
+
+// S[i][j] = S[j][i] = sum over ks (fixed order) of the partial tiles.
+__global__ void k_gram_f32_reduce(const double* __restrict__ part, int ntiles, int ksplit,
+                                  int64_t I, double* __restrict__ S) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)ntiles * BT * BT) return;
+  const int tile = (int)(idx / (BT * BT));
+  const int e = (int)(idx % (BT * BT));
+  int ta = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);
+  while ((ta + 1) * (ta + 2) / 2 <= tile) ++ta;
+  while (ta * (ta + 1) / 2 > tile) --ta;
+  const int tb = tile - ta * (ta + 1) / 2;
+  const int64_t i = (int64_t)ta * BT + e / BT, j = (int64_t)tb * BT + e % BT;
+  if (i >= I || j >= I) return;
+  if (ta == tb && j > i) return;   // diagonal tile: its lower half (mirrored below)
+  double s = 0.0;
+  for (int k = 0; k < ksplit; ++k) s += part[((int64_t)k * ntiles + tile) * BT * BT + e];
+  S[i * I + j] = s;
+  S[j * I + i] = s;
+}
+
+}  // namespace
+
+GramPlan plan_gram_f32_col(int64_t L, int64_t I, int64_t Rt, int num_sms) {
+  GramPlan p;
+  if (L != 1 || I < 64 || Rt < 1) return p;   // ntiles == 0: not applicable
+  const int64_t T = (I + BT - 1) / BT;
+  p.ntiles = (int)(T * (T + 1) / 2);
+  const int64_t NKB = (Rt + BK - 1) / BK;
+  int64_t want = ((int64_t)num_sms + p.ntiles - 1) / p.ntiles;   // one wave of one CTA per SM
+  if (want * p.ntiles > num_sms && want > 1) want -= 1;
+  const int64_t cap = (int64_t)(256ll << 20) / ((int64_t)p.ntiles * BT * BT * 8);
+  if (want > cap) want = cap;
+  if (want > NKB) want = NKB;
+  if (want < 1) want = 1;
+  p.ksplit = (int)want;
+  p.scratch_bytes = (size_t)p.ksplit * p.ntiles * BT * BT * sizeof(double);
+  return p;
+}
+
+cudaError_t launch_gram_f32_col(const float* y, int64_t I, int64_t Rt, const GramPlan& p,
+                                double* scratch, double* S, cudaStream_t st) {
+  const bool vec = (I % 4 == 0) && ((((uintptr_t)y) & 15) == 0);
+  const int smem = (int)sizeof(Smem);
+  cudaError_t e = cudaFuncSetAttribute(vec ? k_gram_f32_col<true> : k_gram_f32_col<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(p.ntiles, p.ksplit);
+  if (vec) k_gram_f32_col<true><<<grid, NTHR, smem, st>>>(y, I, Rt, p.ntiles, p.ksplit, scratch);
+  else k_gram_f32_col<false><<<grid, NTHR, smem, st>>>(y, I, Rt, p.ntiles, p.ksplit, scratch);
+  const int64_t tot = (int64_t)p.ntiles * BT * BT;
+  k_gram_f32_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(scratch, p.ntiles, p.ksplit, I, S);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+}  // namespace tk

@@ -78,6 +78,7 @@ def test_norm_nonfinite_is_reported(ctx):
 GRAM_SHAPES = [
     (7,), (1, 5), (130, 3), (3, 130), (65, 9, 4), (5, 64, 3), (4, 3, 70), (33, 1, 17, 2),
     (2, 3, 2, 3, 2), (200, 300), (17, 129, 5), (3, 2, 1000),
+    (500, 2000), (257, 1000), (1024, 90),
 ]
 
 
