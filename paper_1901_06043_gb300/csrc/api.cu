@@ -216,12 +216,12 @@ tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabV
     return TUCKER_OK;
   }
   if (kern == 1 && dt == TUCKER_F32) {
-    const GramPlan pc = plan_gram_f32_col(v.L, v.I, v.Rt, c->num_sms);
+    const GramPlan pc = plan_gram_f32(v.L, v.I, v.Rt, c->num_sms);
     if (pc.ntiles > 0) {
       DevBuf scratch;
       TK_TRY(dev_alloc(c, scratch, pc.scratch_bytes));
-      TK_CUDA(c, launch_gram_f32_col((const float*)y, v.I, v.Rt, pc, scratch.as<double>(), S,
-                                     c->stream));
+      TK_CUDA(c, launch_gram_f32((const float*)y, v.L, v.I, v.Rt, pc, scratch.as<double>(), S,
+                                 c->stream));
       return TUCKER_OK;
     }
   }

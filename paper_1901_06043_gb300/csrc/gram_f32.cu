@@ -1,7 +1,9 @@
-// FP32-product Gram of a column-mode slab view (L == 1, the first mode of the
-// natural-descending layout): S = Y Y^T, Y the I x Rt matrix whose column r is
-// slab r, contiguous in i.  Section 5.1 (Alg. 2) forms the Gram of the mode-n
-// unfolding slab by slab; for the first mode every slab is one column of Y.
+// FP32-product Gram of a slab view (Section 5.1, Alg. 2: S = sum over slabs r
+// of Y_r Y_r^T, Y_r the I x L slab r).  Column mode (L == 1, the first mode of
+// the natural-descending layout): every slab is one column, contiguous in i.
+// Row mode (L > 1): a K-block is 16 consecutive l of one slab (contiguous in
+// l), transposed into shared memory by 4-byte copies, and the blocks are
+// visited in the l-block-major order of gram_order.cuh.
 //
 // Tile 128 x 128 of the lower triangle per CTA, 256 threads with 8 x 8
 // outputs each (float4 shared-memory operands: 4 loads per 64 FMAs), K staged
@@ -18,6 +20,7 @@
 #include <cstdio>
 
 #include "common.cuh"
+#include "gram_order.cuh"
 #include "kernels.h"
 
 namespace tk {
@@ -29,9 +32,18 @@ constexpr int NST = 3;      // pipeline stages
 constexpr int CHUNK = 32;   // K-blocks per FP32 chunk sum
 constexpr int NTHR = 256;
 
+// Operand loaders: column mode with 16-byte copies (I % 4 == 0, aligned y),
+// column mode with 4-byte copies, row mode (4-byte copies, transposing).
+enum { LD_COL16 = 0, LD_COL4 = 1, LD_ROW = 2 };
+
+// Operand row stride in floats: padded in row mode, where 16 consecutive l of
+// one row i land in 16 different operand rows (bank spread for the copies).
+template <int LD> struct Stride { static constexpr int v = (LD == LD_ROW) ? BT + 4 : BT; };
+
+template <int LD>
 struct Smem {
-  float a[NST][BK][BT];
-  float b[NST][BK][BT];
+  float a[NST][BK][Stride<LD>::v];
+  float b[NST][BK][Stride<LD>::v];
   float hi[BT * BT];
   float lo[BT * BT];
 };
@@ -58,40 +70,57 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
   e = (a - (s - bb)) + (b - bb);
 }
 
-// Rows [i0, i0+128) of slabs [kb*BK, kb*BK+16) into dst[kk][ii]; zero outside.
-template <bool VEC>
-__device__ __forceinline__ void load_panel(float (*dst)[BT], const float* __restrict__ y, int64_t I,
-                                           int64_t Rt, int64_t i0, int64_t kb) {
+// Rows [i0, i0+128) of K-block kb into dst[kk][ii]; zero outside the view.
+// Column mode: slabs kb*16 .. kb*16+15.  Row mode: l = l0 .. l0+15 of slab r.
+template <int LD>
+__device__ __forceinline__ void load_panel(float (*dst)[Stride<LD>::v], const float* __restrict__ y,
+                                           const KGeom& g, int64_t i0, int64_t kb) {
   const int tid = threadIdx.x;
-  if constexpr (VEC) {
+  if constexpr (LD == LD_COL16) {
 #pragma unroll
     for (int e = 0; e < (BK * BT / 4) / NTHR; ++e) {
       const int c = tid + NTHR * e;
       const int kk = c >> 5, q = c & 31;
       const int64_t r = kb * BK + kk, i = i0 + 4 * q;
-      const bool valid = (r < Rt) && (i < I);
-      cp_async16(&dst[kk][4 * q], valid ? y + i + I * r : y, valid);
+      const bool valid = (r < g.Rt) && (i < g.I);
+      cp_async16(&dst[kk][4 * q], valid ? y + i + g.I * r : y, valid);
     }
-  } else {
+  } else if constexpr (LD == LD_COL4) {
 #pragma unroll
     for (int e = 0; e < (BK * BT) / NTHR; ++e) {
       const int c = tid + NTHR * e;
       const int kk = c >> 7, q = c & 127;
       const int64_t r = kb * BK + kk, i = i0 + q;
-      const bool valid = (r < Rt) && (i < I);
-      cp_async4(&dst[kk][q], valid ? y + i + I * r : y, valid);
+      const bool valid = (r < g.Rt) && (i < g.I);
+      cp_async4(&dst[kk][q], valid ? y + i + g.I * r : y, valid);
+    }
+  } else {
+    const int64_t r = kb / g.nLB;
+    const int64_t l0 = (kb - r * g.nLB) * BK;
+    const float* base = y + g.L * g.I * r;
+#pragma unroll
+    for (int e = 0; e < (BK * BT) / NTHR; ++e) {
+      const int c = tid + NTHR * e;
+      const int kk = c & 15, q = c >> 4;   // 16 threads read 16 consecutive l of row i
+      const int64_t l = l0 + kk, i = i0 + q;
+      const bool valid = (l < g.L) && (i < g.I);
+      cp_async4(&dst[kk][q], valid ? base + l + g.L * i : y, valid);
     }
   }
 }
 
-// One CTA: tile (ta, tb), ta >= tb, over K-blocks [NKB*ks/ksplit, NKB*(ks+1)/ksplit).
-// Writes the FP64 partial tile part[(ks * ntiles + tile) * BT * BT + row * BT + col].
-template <bool VEC>
+// One CTA: tile (ta, tb), ta >= tb, over the K-blocks of split ks in the
+// order of make_korder (column mode: a contiguous run, chunks of CHUNK
+// blocks; row mode: l-block-major over the split's slabs, chunk ends from
+// korder_block).  Writes the FP64 partial tile
+// part[(ks * ntiles + tile) * BT * BT + row * BT + col].
+template <int LD>
 __global__ void __launch_bounds__(NTHR, 1)
-    k_gram_f32_col(const float* __restrict__ y, int64_t I, int64_t Rt, int ntiles, int ksplit,
-                   double* __restrict__ part) {
+    k_gram_f32(const float* __restrict__ y, KGeom g, int ntiles, int ksplit,
+               double* __restrict__ part) {
+  constexpr int SA = Stride<LD>::v;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+  Smem<LD>& sm = *reinterpret_cast<Smem<LD>*>(smem_raw);
   const int tile = blockIdx.x, ks = blockIdx.y;
   int ta = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);
   while ((ta + 1) * (ta + 2) / 2 <= tile) ++ta;
@@ -99,9 +128,8 @@ __global__ void __launch_bounds__(NTHR, 1)
   const int tb = tile - ta * (ta + 1) / 2;
   const bool diag = (ta == tb);
   const int64_t ia0 = (int64_t)ta * BT, ib0 = (int64_t)tb * BT;
-  const int64_t NKB = (Rt + BK - 1) / BK;
-  const int64_t kb0 = NKB * ks / ksplit;
-  const int64_t count = NKB * (ks + 1) / ksplit - kb0;
+  const KOrder ord = make_korder(g, ks, ksplit);
+  const int64_t count = ord.count;
 
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   // this thread's rows ty*4 + {0..3} and 64 + ty*4 + {0..3}; columns likewise with tx
@@ -116,8 +144,10 @@ __global__ void __launch_bounds__(NTHR, 1)
 #pragma unroll
   for (int s = 0; s < NST - 1; ++s) {
     if (s < count) {
-      load_panel<VEC>(sm.a[s], y, I, Rt, ia0, kb0 + s);
-      if (!diag) load_panel<VEC>(sm.b[s], y, I, Rt, ib0, kb0 + s);
+      bool unused;
+      const int64_t kb = korder_block(g, ord, s, unused);
+      load_panel<LD>(sm.a[s], y, g, ia0, kb);
+      if (!diag) load_panel<LD>(sm.b[s], y, g, ib0, kb);
     }
     cp_commit();
   }
@@ -135,14 +165,16 @@ __global__ void __launch_bounds__(NTHR, 1)
       const int64_t nxt = idx + NST - 1;
       const int sn = (int)(nxt % NST);
       if (nxt < count) {
-        load_panel<VEC>(sm.a[sn], y, I, Rt, ia0, kb0 + nxt);
-        if (!diag) load_panel<VEC>(sm.b[sn], y, I, Rt, ib0, kb0 + nxt);
+        bool unused;
+        const int64_t kb = korder_block(g, ord, nxt, unused);
+        load_panel<LD>(sm.a[sn], y, g, ia0, kb);
+        if (!diag) load_panel<LD>(sm.b[sn], y, g, ib0, kb);
       }
       cp_commit();
     }
     const int st = (int)(idx % NST);
-    const float(*A)[BT] = sm.a[st];
-    const float(*B)[BT] = diag ? sm.a[st] : sm.b[st];
+    const float(*A)[SA] = sm.a[st];
+    const float(*B)[SA] = diag ? sm.a[st] : sm.b[st];
     float t[8][8];
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
@@ -162,7 +194,13 @@ __global__ void __launch_bounds__(NTHR, 1)
 #pragma unroll
       for (int v = 0; v < 8; ++v) acc[u][v] += t[u][v];
 
-    if (((idx + 1) % CHUNK) == 0 || idx + 1 == count) {
+    bool chunk_end;
+    if constexpr (LD == LD_ROW) {
+      korder_block(g, ord, idx, chunk_end);
+    } else {
+      chunk_end = ((idx + 1) % CHUNK) == 0;
+    }
+    if (chunk_end || idx + 1 == count) {
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int row = (u < 4) ? ty * 4 + u : 64 + ty * 4 + (u - 4);
@@ -225,33 +263,41 @@ __global__ void k_gram_f32_reduce(const double* __restrict__ part, int ntiles, i
 
 }  // namespace
 
-GramPlan plan_gram_f32_col(int64_t L, int64_t I, int64_t Rt, int num_sms) {
+GramPlan plan_gram_f32(int64_t L, int64_t I, int64_t Rt, int num_sms) {
   GramPlan p;
-  if (L != 1 || I < 64 || Rt < 1) return p;   // ntiles == 0: not applicable
+  if (I < 64 || Rt < 1 || L < 1) return p;   // ntiles == 0: not applicable
+  const KGeom g = make_kgeom(L, I, Rt, BK);
   const int64_t T = (I + BT - 1) / BT;
   p.ntiles = (int)(T * (T + 1) / 2);
-  const int64_t NKB = (Rt + BK - 1) / BK;
   int64_t want = ((int64_t)num_sms + p.ntiles - 1) / p.ntiles;   // one wave of one CTA per SM
   if (want * p.ntiles > num_sms && want > 1) want -= 1;
   const int64_t cap = (int64_t)(256ll << 20) / ((int64_t)p.ntiles * BT * BT * 8);
   if (want > cap) want = cap;
-  if (want > NKB) want = NKB;
+  if (want > g.NKB) want = g.NKB;
   if (want < 1) want = 1;
   p.ksplit = (int)want;
   p.scratch_bytes = (size_t)p.ksplit * p.ntiles * BT * BT * sizeof(double);
   return p;
 }
 
-cudaError_t launch_gram_f32_col(const float* y, int64_t I, int64_t Rt, const GramPlan& p,
-                                double* scratch, double* S, cudaStream_t st) {
-  const bool vec = (I % 4 == 0) && ((((uintptr_t)y) & 15) == 0);
-  const int smem = (int)sizeof(Smem);
-  cudaError_t e = cudaFuncSetAttribute(vec ? k_gram_f32_col<true> : k_gram_f32_col<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+template <int LD>
+static cudaError_t launch_ld(const float* y, const KGeom& g, const GramPlan& p, double* scratch,
+                             cudaStream_t st) {
+  const int smem = (int)sizeof(Smem<LD>);
+  cudaError_t e = cudaFuncSetAttribute(k_gram_f32<LD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(p.ntiles, p.ksplit);
-  if (vec) k_gram_f32_col<true><<<grid, NTHR, smem, st>>>(y, I, Rt, p.ntiles, p.ksplit, scratch);
-  else k_gram_f32_col<false><<<grid, NTHR, smem, st>>>(y, I, Rt, p.ntiles, p.ksplit, scratch);
+  k_gram_f32<LD><<<dim3(p.ntiles, p.ksplit), NTHR, smem, st>>>(y, g, p.ntiles, p.ksplit, scratch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_f32(const float* y, int64_t L, int64_t I, int64_t Rt, const GramPlan& p,
+                            double* scratch, double* S, cudaStream_t st) {
+  const KGeom g = make_kgeom(L, I, Rt, BK);
+  cudaError_t e;
+  if (L > 1) e = launch_ld<LD_ROW>(y, g, p, scratch, st);
+  else if ((I % 4 == 0) && ((((uintptr_t)y) & 15) == 0)) e = launch_ld<LD_COL16>(y, g, p, scratch, st);
+  else e = launch_ld<LD_COL4>(y, g, p, scratch, st);
+  if (e != cudaSuccess) return e;
   const int64_t tot = (int64_t)p.ntiles * BT * BT;
   k_gram_f32_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(scratch, p.ntiles, p.ksplit, I, S);
   count_launches(2);

@@ -24,11 +24,11 @@ cudaError_t launch_gram_simt(const void* y, tucker_dtype dt, bool fp64, int64_t 
                              int64_t Rt, const GramPlan& p, double* scratch, double* S,
                              cudaStream_t st);
 
-// ---- FP32-product Gram of a column-mode view (L == 1): 128 x 128 tiles,
-// cp.async pipeline; plan.ntiles == 0 when it does not apply
-GramPlan plan_gram_f32_col(int64_t L, int64_t I, int64_t Rt, int num_sms);
-cudaError_t launch_gram_f32_col(const float* y, int64_t I, int64_t Rt, const GramPlan& p,
-                                double* scratch, double* S, cudaStream_t st);
+// ---- FP32-product Gram of FP32 input, I >= 64: 128 x 128 tiles, cp.async
+// pipeline; plan.ntiles == 0 when it does not apply
+GramPlan plan_gram_f32(int64_t L, int64_t I, int64_t Rt, int num_sms);
+cudaError_t launch_gram_f32(const float* y, int64_t L, int64_t I, int64_t Rt, const GramPlan& p,
+                            double* scratch, double* S, cudaStream_t st);
 
 // ---- SIMT TTM
 cudaError_t launch_ttm_simt(const void* y, tucker_dtype ydt, bool fp64, int64_t L, int64_t I,

@@ -6,6 +6,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "gram_order.cuh"
 
 namespace tk {
 
@@ -161,29 +162,8 @@ cudaError_t launch_sumsq(const void* y, tucker_dtype dt, int64_t n, double* part
 
 // ------------------------------------------------------------------ Gram
 
-// Geometry of the K (contraction) dimension of a slab view.  K runs over
-// (r, l) pairs.  With L == 1 a K-block is BK consecutive slabs (column mode,
-// contiguous along i); otherwise a K-block is BK consecutive l of one slab
-// (row mode, contiguous along l), masked at l >= L.
-struct KGeom {
-  int64_t L, I, Rt;
-  int64_t nLB;   // K-blocks per slab in row mode
-  int64_t NKB;   // total K-blocks
-};
-
 constexpr int GT = 64;    // Gram output tile
 constexpr int GBK = 16;   // K-block
-
-__host__ __device__ inline KGeom make_kgeom(int64_t L, int64_t I, int64_t Rt, int bk) {
-  KGeom g{L, I, Rt, 1, 0};
-  if (L == 1) {
-    g.NKB = (Rt + bk - 1) / bk;
-  } else {
-    g.nLB = (L + bk - 1) / bk;
-    g.NKB = Rt * g.nLB;
-  }
-  return g;
-}
 
 // Loads the (GBK x GT) panel of rows [i0, i0+GT) for K-block kb into regs.
 template <typename TIn, typename TC>
@@ -223,56 +203,6 @@ __device__ __forceinline__ void gram_store(TC (*sm)[GT + 1], const KGeom& g, con
     else { kk = idx % GBK; ii = idx / GBK; }
     sm[kk][ii] = reg[e];
   }
-}
-
-// Order in which one CTA (split ks of ksplit) visits its K-blocks, and where
-// its FP32 chunks end.  FP32 rounding of a running sum only stays unbiased
-// when the terms added to it have comparable size; the l index of a row-mode
-// view runs over already-truncated modes, whose energy decays with the index
-// (their eigenvalues are in descending order), so summing one slab's l-run
-// into one FP32 accumulator drops the small terms systematically.
-//   column mode (L == 1):  blocks kb0..kb1-1 (BK slabs each, unordered
-//                          energies); a chunk is CHUNK blocks.
-//   row mode, Rt >= ksplit: the CTA owns slabs [r0, r0+nr) and visits l-block
-//                          lb of all of them before lb+1; a chunk never mixes
-//                          l-blocks.
-//   row mode, Rt < ksplit:  blocks kb0..kb1-1 (lb fastest); every block is
-//                          its own chunk.
-struct KOrder {
-  int mode;
-  int64_t kb0, r0, nr, count;
-};
-
-constexpr int GCHUNK = 16;
-
-__device__ __forceinline__ KOrder make_korder(const KGeom& g, int ks, int ksplit) {
-  KOrder o{0, 0, 0, 1, 0};
-  if (g.L == 1) {
-    o.mode = 0;
-    o.kb0 = g.NKB * ks / ksplit;
-    o.count = g.NKB * (ks + 1) / ksplit - o.kb0;
-  } else if (g.Rt >= ksplit) {
-    o.mode = 1;
-    o.r0 = g.Rt * ks / ksplit;
-    o.nr = g.Rt * (ks + 1) / ksplit - o.r0;
-    o.count = o.nr * g.nLB;
-  } else {
-    o.mode = 2;
-    o.kb0 = g.NKB * ks / ksplit;
-    o.count = g.NKB * (ks + 1) / ksplit - o.kb0;
-  }
-  return o;
-}
-
-__device__ __forceinline__ int64_t korder_block(const KGeom& g, const KOrder& o, int64_t idx,
-                                                bool& chunk_end) {
-  if (o.mode == 1) {
-    const int64_t lb = idx / o.nr, rr = idx - lb * o.nr;
-    chunk_end = (rr == o.nr - 1) || ((rr + 1) % GCHUNK == 0);
-    return (o.r0 + rr) * g.nLB + lb;
-  }
-  chunk_end = (o.mode == 2) || ((idx + 1) % GCHUNK == 0);
-  return o.kb0 + idx;
 }
 
 // One CTA: lower-triangle tile (ta >= tb) of S over its K-blocks.  TC is the
