@@ -223,7 +223,7 @@ def main():
     torch.cuda.synchronize()
     in_bytes = x.numel() * x.element_size()
     N = len(w["dims"])
-    cpu_slices = args.cpu_slices or (40 if args.workload == "large" else None)
+    cpu_slices = args.cpu_slices or (500 if args.workload == "large" else None)
 
     if args.impl == "reference":
         if rank != 0:
@@ -343,6 +343,17 @@ def tucker_mixed_available():
 FP64_PEAK_TFLOPS = 1.19   # measured FP64 FMA throughput on this part (in-register probe)
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one ncu
+# capture per kernel, with the input elements (I x K) that launch processed;
+# a launch of the same kernel streams its input once, so its traffic scales
+# with I x K.  Only kernels whose source has not changed since the capture.
+CAPTURED_TRAFFIC = {
+    # k_gram_f32<LD_COL16>, mode-0 Gram of 500x500x40x11x2 FP32
+    ("gram", "simt-fp32", "col"): dict(bytes=912.2e6, elems=500 * 440000,
+                                        src="profiles/k_gram_f32_col_prof_500x500x40x11x2.md"),
+}
+
+
 def step_rooflines(res, w, pk):
     """Roofline of every Gram / TTM / eigensolve step of one ST-HOSVD, from
     the library's own CUDA events on its stream (algorithmic work: Gram
@@ -364,7 +375,12 @@ def step_rooflines(res, w, pk):
             ("ttm", ms["ttm"][n], 2 * R * I * K, I * K * esz + R * K * wk_esz, res.ttm_kernel[n]),
             ("eig", ms["eig"][n], 6.0 * I ** 3 * max(res.sweeps[n], 1), 0, "fp64-jacobi")]:
             t = max(t_ms, 1e-6) / 1e3
-            if kern == "tcgen05" or (kind == "ttm" and kern != "simt-fp64" and False):
+            traffic, tsrc = None, None
+            cap = CAPTURED_TRAFFIC.get((kind, kern, "col" if L == 1 else "row"))
+            if cap is not None and I >= 64:
+                traffic = cap["bytes"] * (I * K) / cap["elems"]
+                tsrc = "ncu capture scaled by I*K: " + cap["src"]
+            if kern == "tcgen05":
                 bound, ach, peak, unit = "hbm", nbytes / t / 1e9, pk["hbm_gbs"], "GB/s"
                 src = "measured HBM copy"
             elif kern == "simt-fp32":
@@ -373,9 +389,13 @@ def step_rooflines(res, w, pk):
             else:
                 bound, ach, peak, unit = "alu", flops / t / 1e12, FP64_PEAK_TFLOPS, "TFLOP/s"
                 src = "measured FP64 FMA probe"
-            out.append({"kernel": f"{kind} mode {n} ({kern})", "bound": bound, "achieved": ach,
-                        "peak": peak, "unit": unit, "frac": ach / peak, "traffic": None,
-                        "ms": t_ms, "hbm_gbs_achieved": nbytes / t / 1e9, "peak_src": src})
+            row = {"kernel": f"{kind} mode {n} ({kern})", "bound": bound, "achieved": ach,
+                   "peak": peak, "unit": unit, "frac": ach / peak, "traffic": traffic,
+                   "ms": t_ms, "hbm_gbs_achieved": nbytes / t / 1e9, "peak_src": src}
+            if tsrc:
+                row["traffic_src"] = tsrc
+                row["algorithmic_bytes"] = nbytes
+            out.append(row)
         cur[n] = R
     return out
 
