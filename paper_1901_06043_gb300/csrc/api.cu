@@ -276,19 +276,24 @@ tucker_status do_cut(tucker_ctx* c, const double* w, int n, double thr, int fixe
   return sync(c);
 }
 
+// ymax: max|y| if the caller knows it (e.g. from the norm pass), else <= 0.
 tucker_status do_ttm(tucker_ctx* c, const void* y, tucker_dtype ydt, const SlabView& v,
                      const double* A, int64_t K, int64_t lda, int arow, tucker_prec prec, void* z,
-                     tucker_dtype zdt, int* kernel_used) {
+                     tucker_dtype zdt, int* kernel_used, double ymax = -1.0) {
   const bool tc = (prec == TUCKER_PREC_MIXED || prec == TUCKER_PREC_TENSOR) && ydt == TUCKER_F32 &&
-                  zdt == TUCKER_F32 &&
+                  zdt == TUCKER_F32 && (((uintptr_t)y) & 15) == 0 &&
                   ttm_tc_supported(v.L, v.I, v.Rt, K);
   if (kernel_used) *kernel_used = tc ? 2 : (prec == TUCKER_PREC_FP64 ? 0 : 1);
   if (tc) {
+    if (!(ymax >= 0.0)) {
+      double nrm;
+      TK_TRY(do_norm(c, y, ydt, v.L * v.I * v.Rt, &nrm, &ymax));
+    }
     DevBuf scratch;
     TK_TRY(dev_alloc(c, scratch, ttm_tc_scratch_bytes(v.I, K)));
     TK_CUDA(c, cudaMemsetAsync(c->d_words + 9, 0, sizeof(unsigned), c->stream));
-    TK_CUDA(c, launch_ttm_tc((const float*)y, v.L, v.I, v.Rt, A, K, lda, arow, (float*)z,
-                             scratch.p, c->d_words + 9, c->stream));
+    TK_CUDA(c, launch_ttm_tc((const float*)y, v.L, v.I, v.Rt, A, K, lda, arow, split_scale(ymax),
+                             (float*)z, scratch.p, c->d_words + 9, c->num_sms, c->stream));
     unsigned err = 0;
     TK_CUDA(c, cudaMemcpyAsync(&err, c->d_words + 9, sizeof(unsigned), cudaMemcpyDeviceToHost,
                                c->stream));
@@ -553,7 +558,8 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
     DevBuf z;
     TK_TRY(dev_alloc(c, z, dtype_size(wdt) * numel(ndim, nd)));
     tmt.start(c);
-    TK_TRY(do_ttm(c, y, ydt, v, r->factors[n], R, I, 1, prec, z.p, wdt, &r->ttm_kernel[n]));
+    TK_TRY(do_ttm(c, y, ydt, v, r->factors[n], R, I, 1, prec, z.p, wdt, &r->ttm_kernel[n],
+                  s == 0 ? xmax : -1.0));
     tmt.stop(c);
     ycur.reset();
     ycur.p = z.release();

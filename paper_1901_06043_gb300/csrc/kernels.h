@@ -44,10 +44,12 @@ struct TcGramPlan {
 TcGramPlan plan_gram_tc(int64_t L, int64_t I, int64_t Rt, int num_sms);
 cudaError_t launch_gram_tc(const float* y, int64_t L, int64_t I, int64_t Rt, const TcGramPlan& p,
                            float scale, double* scratch, unsigned* err, double* S, cudaStream_t st);
+// TTM of the column-major mode-0 view (L == 1, I % 4 == 0, K <= 128); sy =
+// power-of-two scale of y with max|y sy| <= 2^14
 int ttm_tc_supported(int64_t L, int64_t I, int64_t Rt, int64_t K);
 cudaError_t launch_ttm_tc(const float* y, int64_t L, int64_t I, int64_t Rt, const double* A,
-                          int64_t K, int64_t lda, int a_rowmajor, float* z, void* scratch,
-                          unsigned* err, cudaStream_t st);
+                          int64_t K, int64_t lda, int a_rowmajor, float sy, float* z, void* scratch,
+                          unsigned* err, int num_sms, cudaStream_t st);
 size_t ttm_tc_scratch_bytes(int64_t I, int64_t K);
 
 // ---- Jacobi eigensolver, sort and rank cut

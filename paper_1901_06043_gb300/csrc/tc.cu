@@ -30,9 +30,12 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tc_common.cuh"
 
 namespace tk {
 namespace {
+
+using namespace tc;
 
 constexpr int BK = 64;                 // columns (K) per stage
 constexpr int NSTAGE = 2;
@@ -49,12 +52,7 @@ constexpr uint32_t B_BYTES = 256 * BK * 2;
 constexpr uint32_t OFF_HA = 0, OFF_LA = A_BYTES, OFF_HB = 2 * A_BYTES, OFF_LB = 2 * A_BYTES + B_BYTES;
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 96 KB
 constexpr uint32_t SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024;
-constexpr unsigned long long WAIT_LIMIT = 1ull << 22;
 constexpr int TILE_ELEMS = 128 * 256;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
 
 // Byte offset of (mn, k) in an MN-major SW128 FP16 tile: 1024-byte atoms of
 // 8 k-rows x 64 mn, 16-byte chunks XOR-swizzled by k%8; atoms ATOM_MN apart
@@ -64,68 +62,10 @@ __device__ __forceinline__ uint32_t mn_off(int mn, int k, uint32_t sK) {
          ((uint32_t)(((mn & 63) >> 3) ^ (k & 7)) << 4) + (uint32_t)(mn & 7) * 2u;
 }
 
-// tcgen05 shared-memory matrix descriptor (SW128, sm_100-family version bit).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;   // 128-byte swizzle
-  return d;
-}
-
 // Instruction descriptor: kind::f16, FP16 A and B, FP32 D, both MN-major.
 __device__ __forceinline__ uint32_t instr_desc(int M, int N) {
   return (1u << 4) | (0u << 7) | (0u << 10) | (1u << 15) | (1u << 16) |
          ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
-}
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned* err) {
-  for (unsigned long long it = 0; it < WAIT_LIMIT; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-    if (done) return true;
-    if (*(volatile unsigned*)err & DEV_ERR_MBAR_TIMEOUT) return false;
-  }
-  atomicOr(err, DEV_ERR_MBAR_TIMEOUT);
-  return false;
-}
-
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t idesc,
-                                       uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // x s = h + l: FP16 hi part, FP16 part of the remainder.
@@ -389,12 +329,5 @@ cudaError_t launch_gram_tc(const float* y, int64_t L, int64_t I, int64_t Rt, con
   k_gram_tc_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(scratch, a.ntypes, a.nkg, a.TA, I, S);
   return cudaGetLastError();
 }
-
-int ttm_tc_supported(int64_t, int64_t, int64_t, int64_t) { return 0; }
-cudaError_t launch_ttm_tc(const float*, int64_t, int64_t, int64_t, const double*, int64_t, int64_t,
-                          int, float*, void*, unsigned*, cudaStream_t) {
-  return cudaErrorNotSupported;
-}
-size_t ttm_tc_scratch_bytes(int64_t, int64_t) { return 0; }
 
 }  // namespace tk

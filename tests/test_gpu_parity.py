@@ -288,6 +288,33 @@ def test_ttm_fp32(ctx, dims, K):
         assert np.abs(got - want).max() <= 2e-7 * np.abs(A).max() * np.abs(xs).max() * dims[n]
 
 
+TC_TTM_SHAPES = [((256, 300), 54), ((500, 1000), 128), ((64, 7, 3), 1), ((68, 513), 100),
+                 ((200, 160, 9), 30)]
+
+
+@pytest.mark.parametrize("dims,K", TC_TTM_SHAPES)
+def test_ttm_mixed_tensor_cores_mode0(ctx, dims, K):
+    """Mode-0 TTM on tcgen05 (two-term FP16 split of Y and A, products
+    hh + hl + lh, truncating FP32 accumulator).  Error per output is bounded
+    by the split residuals (3 x 2^-22) plus one truncation per accumulation
+    step (<= 2^-23 of the running |sum| per MMA, ~100 steps at I = 500), i.e.
+    <= 2e-5 of sum_i |a_ki| |y_i|; checked elementwise against that bound.
+    Row-major and column-major A, a ragged last slab tile (Rt % 256 != 0) and
+    a partial last 64-wide stage of I are covered."""
+    rng = np.random.default_rng(K + 5 * len(dims))
+    x = rng.standard_normal(oracle.linear_size(dims))
+    t = dev(x, torch.float32)
+    xs = host(t)
+    A = rng.standard_normal((K, dims[0]))
+    want = oracle.ttm(xs, dims, 0, A)
+    bound = 2e-5 * oracle.ttm(np.abs(xs), dims, 0, np.abs(A))
+    got = host(ctx.ttm(t, dims, 0, dev(A), "mixed"))
+    assert np.all(np.abs(got - want) <= bound), np.max(np.abs(got - want) / bound)
+    Ac = dev(np.asfortranarray(A)).t().contiguous().t()
+    got = host(ctx.ttm(t, dims, 0, Ac, "mixed"))
+    assert np.all(np.abs(got - want) <= bound)
+
+
 # --------------------------------------------------------- whole ST-HOSVD
 
 def _check_against_oracle(x, dims, res, ref, err_tol=1e-12, eig_tol=1e-10, angle_tol=1e-8):
@@ -389,14 +416,16 @@ def test_sthosvd_fp32_path_ranks_and_error(ctx):
 
 @pytest.mark.parametrize("eps", [1e-2, 1e-4])
 def test_sthosvd_mixed_path_ranks_and_error(ctx, eps):
-    """MIXED (tensor-core mode-0 Gram): ranks identical to the FP64 oracle on
-    a decaying-spectrum FP32 tensor; error within 1e-6 of the oracle's."""
+    """MIXED (FP32 round-to-nearest Gram, tensor-core mode-0 TTM): ranks
+    identical to the FP64 oracle on a decaying-spectrum FP32 tensor; error
+    within 5e-6 of the oracle's."""
     dims = (200, 160, 48, 11)
     x = synth.tucker_torch(dims, (30, 30, 24, 11), decay=0.1, eta=1e-7, seed=9)
     xs = host(x)
     ref = oracle.sthosvd(xs, dims, eps=eps)
     res = ctx.sthosvd(x, dims, eps=eps, prec="mixed")
     assert res.gram_kernel[0] == "simt-fp32"
+    assert res.ttm_kernel[0] == "tcgen05"
     assert res.ranks == ref["ranks"]
     ours = {"core": host(res.core), "core_dims": res.ranks,
             "factors": [host(f) for f in res.factors], "discarded": res.discarded,
