@@ -40,10 +40,42 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done) : "r"(bar), "r"(parity) : "memory");
     if (done) return true;
-    if (*(volatile unsigned*)err & DEV_ERR_MBAR_TIMEOUT) return false;
+    // another role's timeout ends this wait too; the error word is a global
+    // read (an L2 round trip), so it is looked at only every 256 polls
+    if ((it & 255) == 255 && (*(volatile unsigned*)err & DEV_ERR_MBAR_TIMEOUT)) return false;
   }
   atomicOr(err, DEV_ERR_MBAR_TIMEOUT);
   return false;
+}
+
+// Arrive on the barrier and raise its expected transaction bytes by `bytes`.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+// Raise the barrier's expected transaction bytes without arriving.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+// Bulk copy global -> this CTA's shared memory (16-byte aligned addresses,
+// size a multiple of 16); completion is counted in bytes on `bar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// 2D tiled TMA load of the box at (x, y) (x innermost; x * element size a
+// multiple of 16 bytes) into this CTA's shared memory; completion is counted
+// in bytes on `bar`.  Out-of-range elements are filled with zeros.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(bar)
+      : "memory");
 }
 
 __device__ __forceinline__ void tc_commit(uint32_t bar) {

@@ -13,14 +13,21 @@
 // I ~ 500 products) perturb the data of the next mode far below eps; unlike
 // the Gram, no tail sum accumulates them.
 //
-// Work split.  A tile is 256 consecutive slabs (MMA N = 256) over all of I;
+// Work split.  A tile is 128 consecutive slabs (MMA N = 128) over all of I;
 // one persistent CTA per SM walks tiles blockIdx.x, blockIdx.x + gridDim.x,
-// ...  Stages of 64 i flow through a two-slot ring.  Roles (13 warps): warps
-// 0-7 load Y with 16-byte streaming loads, split it into the K-major SW128 B
-// operand, and copy the stage's pre-split A chunk; warp 8 issues the MMAs;
-// warps 9-12 drain the double-buffered accumulators (2 x 256 tensor-memory
-// columns) and write Z.  Every wait is bounded: a wait that gives up sets
-// DEV_ERR_MBAR_TIMEOUT and the kernel winds down.
+// ...; a stage is 64 i of the tile.  The kernel is bound by reading Y, a
+// stream of 256-byte pieces (64 i of one slab) at the slab pitch, which needs
+// ~100 KB of reads in flight per SM to approach the HBM rate.  So Y goes
+// through its own ring: one loader thread issues a 2D tiled TMA load of the
+// stage's box (64 i x 128 slabs, 32 KB, zero-filled outside the view) into
+// one of three raw FP32 slots (96 KB in flight), completing on an mbarrier by
+// byte count; eight converter warps split a raw slot into the
+// K-major SW128 FP16 hi/lo B operand of one of two operand slots, and one of
+// them bulk-copies the stage's pre-split A chunk next to it; warp 9 issues the
+// MMAs; warps 10-13 drain the double-buffered accumulators (2 x 128
+// tensor-memory columns) and write Z.  Every wait is bounded: a wait that
+// gives up sets DEV_ERR_MBAR_TIMEOUT and the kernel winds down.
+#include <cuda.h>
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -32,19 +39,24 @@ namespace {
 
 using namespace tc;
 
-constexpr int TN = 256;                        // slabs per tile (MMA N)
+constexpr int TN = 128;                        // slabs per tile (MMA N)
+constexpr uint32_t TMEM_COLS = 2 * TN;         // two accumulator buffers
 constexpr int TM = 128;                        // MMA M (rows of A; K <= TM)
 constexpr int SK = 64;                         // i per stage
-constexpr int NSTAGE = 2;
-constexpr int NPROD = 8;
-constexpr int MMA_WARP = 8;
-constexpr int NTHREADS = 13 * 32;
-constexpr uint32_t A_BYTES = TM * SK * 2;      // 16 KB
-constexpr uint32_t B_BYTES = TN * SK * 2;      // 32 KB
+constexpr int NOP = 2;                         // operand slots
+constexpr int NRAW = 3;                        // raw Y slots
+constexpr int LOAD_WARP = 0;
+constexpr int NCONV = 8;                       // converter warps 1..8
+constexpr int MMA_WARP = 9;
+constexpr int NTHREADS = 14 * 32;              // + epilogue warps 10..13
+constexpr uint32_t A_BYTES = TM * SK * 2;      // 16 KB (one of hi / lo)
+constexpr uint32_t B_BYTES = TN * SK * 2;      // 16 KB
 constexpr uint32_t OFF_AH = 0, OFF_AL = A_BYTES, OFF_BH = 2 * A_BYTES,
                    OFF_BL = 2 * A_BYTES + B_BYTES;
-constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 96 KB
-constexpr uint32_t SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024;
+constexpr uint32_t OP_BYTES = 2 * A_BYTES + 2 * B_BYTES;     // 64 KB
+constexpr uint32_t RAW_BYTES = TN * SK * 4;                  // 32 KB
+constexpr uint32_t SMEM_BYTES = NOP * OP_BYTES + NRAW * RAW_BYTES + 1024;
+constexpr int CV4 = (TN * SK / 4) / (NCONV * 32);            // float4 per converter thread (8)
 
 // Byte offset of (row, k) in a K-major SW128 FP16 tile with 64 k per row:
 // 1024-byte atoms of 8 rows x 128 bytes, 16-byte chunks XOR-swizzled by
@@ -59,12 +71,15 @@ __device__ __forceinline__ uint32_t instr_desc_kk(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// (a, b) = (h_a + l_a, h_b + l_b): FP16 pairs of the round-to-nearest hi part
+// and of the remainder.  Pair conversions (two values per instruction) keep
+// the split off the scalar conversion pipe, which bounded the kernel.
 __device__ __forceinline__ void split_pack(float a, float b, uint32_t& h, uint32_t& l) {
-  const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
-  const __half la = __float2half_rn(a - __half2float(ha));
-  const __half lb = __float2half_rn(b - __half2float(hb));
-  h = (uint32_t)__half_as_ushort(ha) | ((uint32_t)__half_as_ushort(hb) << 16);
-  l = (uint32_t)__half_as_ushort(la) | ((uint32_t)__half_as_ushort(lb) << 16);
+  const __half2 h2 = __float22half2_rn(make_float2(a, b));
+  const float2 hf = __half22float2(h2);
+  const __half2 l2 = __float22half2_rn(make_float2(a - hf.x, b - hf.y));
+  h = *reinterpret_cast<const uint32_t*>(&h2);
+  l = *reinterpret_cast<const uint32_t*>(&l2);
 }
 
 // A (K x I, FP64: element (k, i) at A[k*lda + i] if arow else A[k + lda*i])
@@ -127,7 +142,7 @@ struct TtmTcArgs {
   int64_t I, Rt;
   int K;                 // rows of A = outputs per slab (<= 128)
   int nks;               // stages per tile = ceil(I / 64)
-  int64_t ntiles;        // ceil(Rt / 256)
+  int64_t ntiles;        // ceil(Rt / 128)
   float sy;              // power of two
   const uint8_t* aprep;  // nks x [A_h | A_l] images
   const float* sa;       // the power-of-two scale of A (device)
@@ -135,17 +150,24 @@ struct TtmTcArgs {
   unsigned* err;
 };
 
-__global__ void __launch_bounds__(NTHREADS, 1) k_ttm_tc_col(TtmTcArgs g) {
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_ttm_tc_col(TtmTcArgs g, const __grid_constant__ CUtensorMap ymap) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t bar_full[NSTAGE], bar_empty[NSTAGE], bar_accf[2], bar_acce[2], bar_done;
+  uint8_t* raw = smem + NOP * OP_BYTES;
+  __shared__ uint64_t raw_full[NRAW], raw_empty[NRAW], op_full[NOP], op_empty[NOP];
+  __shared__ uint64_t bar_accf[2], bar_acce[2], bar_done;
   __shared__ uint32_t tmem_base_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NSTAGE; ++s) {
-      mbar_init(smem_u32(&bar_full[s]), NPROD);
-      mbar_init(smem_u32(&bar_empty[s]), 1);
+    for (int s = 0; s < NRAW; ++s) {
+      mbar_init(smem_u32(&raw_full[s]), 1);
+      mbar_init(smem_u32(&raw_empty[s]), NCONV);
+    }
+    for (int s = 0; s < NOP; ++s) {
+      mbar_init(smem_u32(&op_full[s]), NCONV);
+      mbar_init(smem_u32(&op_empty[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&bar_accf[b]), 1);
@@ -154,9 +176,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_ttm_tc_col(TtmTcArgs g) {
     mbar_init(smem_u32(&bar_done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-        smem_u32(&tmem_base_sh)));
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+        smem_u32(&tmem_base_sh)), "n"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -165,54 +187,69 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_ttm_tc_col(TtmTcArgs g) {
   const uint32_t tmem = tmem_base_sh;
   const int64_t my_tiles =
       (g.ntiles > (int64_t)blockIdx.x) ? (g.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t nstages = my_tiles * g.nks;
 
-  if (warp < NPROD) {
-    // ---------------- producers: Y -> FP16 hi/lo B operand; A chunk copy
-    const int ptid = threadIdx.x;   // 0..255
-    bool ok = true;
-    for (int64_t j = 0; j < my_tiles && ok; ++j) {
-      const int64_t m0 = ((int64_t)blockIdx.x + j * gridDim.x) * TN;
-      for (int ks = 0; ks < g.nks; ++ks) {
-        const int64_t gs = j * g.nks + ks;
-        const int slot = (int)(gs % NSTAGE);
-        float4 v[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int c = ptid + 256 * e;
-          const int m = c >> 4, q = c & 15;
-          const int64_t slab = m0 + m, i = (int64_t)ks * SK + 4 * q;
-          v[e] = (slab < g.Rt && i < g.I)
-                     ? __ldcs(reinterpret_cast<const float4*>(g.y + slab * g.I + i))
-                     : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        uint4 av[8];
-        const uint4* asrc = reinterpret_cast<const uint4*>(g.aprep + (size_t)ks * 2 * A_BYTES);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) av[e] = asrc[ptid + 256 * e];
-        if (gs >= NSTAGE) {
-          if (!mbar_wait(smem_u32(&bar_empty[slot]), (uint32_t)(((gs / NSTAGE) - 1) & 1), g.err)) {
-            ok = false;
-            break;
-          }
-        }
-        uint8_t* st = smem + (size_t)slot * STAGE_BYTES;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) reinterpret_cast<uint4*>(st + OFF_AH)[ptid + 256 * e] = av[e];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int c = ptid + 256 * e;
-          const int m = c >> 4, q = c & 15;
-          uint2 hp, lp;
-          split_pack(v[e].x * g.sy, v[e].y * g.sy, hp.x, lp.x);
-          split_pack(v[e].z * g.sy, v[e].w * g.sy, hp.y, lp.y);
-          const uint32_t o = kmaj_off(m, 4 * q);
-          *reinterpret_cast<uint2*>(st + OFF_BH + o) = hp;
-          *reinterpret_cast<uint2*>(st + OFF_BL + o) = lp;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&bar_full[slot]));
+  if (warp == LOAD_WARP) {
+    // ---------------- loader: Y boxes -> raw slots (TMA)
+    if (lane == 0) {
+      for (int64_t gs = 0; gs < nstages; ++gs) {
+        const int r = (int)(gs % NRAW);
+        if (gs >= NRAW &&
+            !mbar_wait(smem_u32(&raw_empty[r]), (uint32_t)(((gs / NRAW) - 1) & 1), g.err))
+          break;
+        const int64_t j = gs / g.nks;
+        const int ks = (int)(gs - j * g.nks);
+        const int64_t m0 = ((int64_t)blockIdx.x + j * gridDim.x) * TN;
+        mbar_arrive_expect_tx(smem_u32(&raw_full[r]), RAW_BYTES);
+        tma_load_2d(smem_u32(raw + (size_t)r * RAW_BYTES), &ymap, ks * SK, (int)m0,
+                    smem_u32(&raw_full[r]));
       }
+    }
+    __syncwarp();
+  } else if (warp <= NCONV) {
+    // ---------------- converters: raw FP32 -> FP16 hi/lo B operand; A chunk
+    const int ct = threadIdx.x - 32;   // 0..255
+    for (int64_t gs = 0; gs < nstages; ++gs) {
+      const int r = (int)(gs % NRAW), o = (int)(gs % NOP);
+      const int64_t j = gs / g.nks;
+      const int ks = (int)(gs - j * g.nks);
+      const int64_t m0 = ((int64_t)blockIdx.x + j * gridDim.x) * TN;
+      if (!mbar_wait(smem_u32(&raw_full[r]), (uint32_t)((gs / NRAW) & 1), g.err)) break;
+      if (gs >= NOP &&
+          !mbar_wait(smem_u32(&op_empty[o]), (uint32_t)(((gs / NOP) - 1) & 1), g.err))
+        break;
+      uint8_t* st = smem + (size_t)o * OP_BYTES;
+      if (ct == 0) {
+        mbar_expect_tx(smem_u32(&op_full[o]), 2 * A_BYTES);
+        bulk_g2s(smem_u32(st + OFF_AH), g.aprep + (size_t)ks * 2 * A_BYTES, 2 * A_BYTES,
+                 smem_u32(&op_full[o]));
+      }
+      const uint8_t* src = raw + (size_t)r * RAW_BYTES;
+      float4 v[CV4];
+#pragma unroll
+      for (int e = 0; e < CV4; ++e) {
+        const int c = ct + NCONV * 32 * e;
+        const int m = c >> 4, q = c & 15;
+        const bool ok = (m0 + m < g.Rt) && ((int64_t)ks * SK + 4 * q < g.I);
+        v[e] = ok ? *reinterpret_cast<const float4*>(src + (size_t)m * (SK * 4) + 16 * q)
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&raw_empty[r]));   // raw slot read
+#pragma unroll
+      for (int e = 0; e < CV4; ++e) {
+        const int c = ct + NCONV * 32 * e;
+        const int m = c >> 4, q = c & 15;
+        uint2 hp, lp;
+        split_pack(v[e].x * g.sy, v[e].y * g.sy, hp.x, lp.x);
+        split_pack(v[e].z * g.sy, v[e].w * g.sy, hp.y, lp.y);
+        const uint32_t off = kmaj_off(m, 4 * q);
+        *reinterpret_cast<uint2*>(st + OFF_BH + off) = hp;
+        *reinterpret_cast<uint2*>(st + OFF_BL + off) = lp;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&op_full[o]));
     }
   } else if (warp == MMA_WARP) {
     // ---------------- MMA issue (one thread)
@@ -225,24 +262,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_ttm_tc_col(TtmTcArgs g) {
         if (j >= 2) ok = mbar_wait(smem_u32(&bar_acce[buf]), (uint32_t)(((j / 2) - 1) & 1), g.err);
         for (int ks = 0; ks < g.nks && ok; ++ks) {
           const int64_t gs = j * g.nks + ks;
-          const int slot = (int)(gs % NSTAGE);
-          ok = mbar_wait(smem_u32(&bar_full[slot]), (uint32_t)((gs / NSTAGE) & 1), g.err);
+          const int o = (int)(gs % NOP);
+          ok = mbar_wait(smem_u32(&op_full[o]), (uint32_t)((gs / NOP) & 1), g.err);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t st = sbase + (uint32_t)slot * STAGE_BYTES;
-          const uint32_t d = tmem + (uint32_t)buf * 256u;
+          const uint32_t st = sbase + (uint32_t)o * OP_BYTES;
+          const uint32_t d = tmem + (uint32_t)buf * (uint32_t)TN;
+          // a K step of 16 FP16 is 32 bytes along the swizzled row: +2 in the
+          // descriptor's address field (addr >> 4)
+          const uint64_t ah0 = smem_desc(st + OFF_AH, 16, 1024), al0 = smem_desc(st + OFF_AL, 16, 1024);
+          const uint64_t bh0 = smem_desc(st + OFF_BH, 16, 1024), bl0 = smem_desc(st + OFF_BL, 16, 1024);
 #pragma unroll
           for (int kk = 0; kk < SK / 16; ++kk) {
-            const uint64_t ah = smem_desc(st + OFF_AH + 32u * kk, 16, 1024);
-            const uint64_t al = smem_desc(st + OFF_AL + 32u * kk, 16, 1024);
-            const uint64_t bh = smem_desc(st + OFF_BH + 32u * kk, 16, 1024);
-            const uint64_t bl = smem_desc(st + OFF_BL + 32u * kk, 16, 1024);
+            const uint64_t ah = ah0 + 2u * kk, al = al0 + 2u * kk;
+            const uint64_t bh = bh0 + 2u * kk, bl = bl0 + 2u * kk;
             const uint32_t acc0 = (ks > 0 || kk > 0) ? 1u : 0u;
             tc_mma(d, ah, bh, idesc, acc0);
             tc_mma(d, ah, bl, idesc, 1u);
             tc_mma(d, al, bh, idesc, 1u);
           }
-          tc_commit(smem_u32(&bar_empty[slot]));
+          tc_commit(smem_u32(&op_empty[o]));
         }
         if (ok) tc_commit(smem_u32(&bar_accf[buf]));
       }
@@ -262,7 +301,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_ttm_tc_col(TtmTcArgs g) {
       if (32 * q < g.K) {
         for (int c0 = 0; c0 < TN; c0 += 32) {
           uint32_t rr[32];
-          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * 256u + (uint32_t)c0, rr);
+          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * (uint32_t)TN + (uint32_t)c0, rr);
           if (r < g.K) {
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) {
@@ -281,16 +320,37 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_ttm_tc_col(TtmTcArgs g) {
   mbar_wait(smem_u32(&bar_done), 0, g.err);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) {
+  if (warp == MMA_WARP) {
     asm volatile("tcgen05.fence::after_thread_sync;");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TMEM_COLS));
   }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime (no
+// link-time dependency on the driver library).
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
 }
 
 }  // namespace
 
 int ttm_tc_supported(int64_t L, int64_t I, int64_t Rt, int64_t K) {
-  return L == 1 && I >= 64 && I <= 65536 && (I % 4) == 0 && K >= 1 && K <= TM && Rt >= 1;
+  return L == 1 && I >= 64 && I <= 65536 && (I % 4) == 0 && K >= 1 && K <= TM && Rt >= 1 &&
+         Rt < (1ll << 31);
 }
 
 size_t ttm_tc_scratch_bytes(int64_t I, int64_t K) {
@@ -326,8 +386,20 @@ cudaError_t launch_ttm_tc(const float* y, int64_t L, int64_t I, int64_t Rt, cons
   a.sa = sa;
   a.z = z;
   a.err = err;
+  // Y as a 2D tensor: x = i (contiguous), y = slab; boxes of 64 i x 128 slabs
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  alignas(64) CUtensorMap ymap;
+  const cuuint64_t gdim[2] = {(cuuint64_t)I, (cuuint64_t)Rt};
+  const cuuint64_t gstride[1] = {(cuuint64_t)I * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)SK, (cuuint32_t)TN};
+  const cuuint32_t estride[2] = {1, 1};
+  if (enc(&ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)y, gdim, gstride, box, estride,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
   const int grid = (int)(a.ntiles < num_sms ? a.ntiles : num_sms);
-  k_ttm_tc_col<<<grid, NTHREADS, SMEM_BYTES, st>>>(a);
+  k_ttm_tc_col<<<grid, NTHREADS, SMEM_BYTES, st>>>(a, ymap);
   count_launches(2);
   return cudaGetLastError();
 }
