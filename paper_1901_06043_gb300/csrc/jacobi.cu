@@ -49,28 +49,67 @@ __device__ __forceinline__ int next_pos(int pos, int np) {
 // entry (kept, and removed by a later sweep).  This keeps the dependent FP64
 // chain at ~6 operations (an FP64 operation takes ~64 cycles on this part,
 // and the rotation is on the critical path of every step).
-__device__ __forceinline__ bool jacobi_rotation(double app, double aqq, double apq, double tol_rel,
-                                                double floor_abs, double& c, double& s) {
+// FP64 values seen through their bits: on this part every FP64 instruction,
+// a compare or a conversion included, goes through a narrow pipe, so the
+// per-step decisions and the FP32 <-> FP64 moves of the rotation use integer
+// operations.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+// log2|x| to ~1e-7 (exponent plus the FP32 log2 of the top 23 mantissa bits);
+// zero and subnormals come out <= -1023.
+__device__ __forceinline__ float log2_abs(double x) {
+  const unsigned long long b = abs_bits(x);
+  const float m = __int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffff));
+  return (float)((int)(b >> 52) - 1023) + __log2f(m);
+}
+// x * 2^sh as FP32 by moving the exponent (mantissa truncated to 23 bits);
+// results below the FP32 normal range become 0.
+__device__ __forceinline__ float f64_to_f32_shifted(double x, int sh) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127 + sh;
+  if (e <= 0) return 0.f;
+  const unsigned u = (unsigned)(b >> 63) << 31 | (unsigned)(e > 254 ? 254 : e) << 23 |
+                     (unsigned)((b >> 29) & 0x7fffff);
+  return __uint_as_float(u);
+}
+// A normal FP32 value as FP64 (exact).
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned long long b = (unsigned long long)(u >> 31) << 63 |
+                               (unsigned long long)(((u >> 23) & 0xff) - 127 + 1023) << 52 |
+                               (unsigned long long)(u & 0x7fffff) << 29;
+  return __longlong_as_double((long long)b);
+}
+
+// The rotation test |apq| > max(tol_rel sqrt(|app aqq|), floor_abs): the
+// floor exactly (integer compare of magnitudes), the relative part in the
+// log2 domain to ~1e-6 (either decision is valid that close to the bound).
+__device__ __forceinline__ bool rotation_needed(double app, double aqq, double apq,
+                                                float log2_tol_rel, unsigned long long floor_bits) {
+  if (!(abs_bits(apq) > floor_bits)) return false;
+  return log2_abs(apq) > log2_tol_rel + 0.5f * (log2_abs(app) + log2_abs(aqq));
+}
+
+__device__ __forceinline__ bool jacobi_rotation(double app, double aqq, double apq,
+                                                float log2_tol_rel, unsigned long long floor_bits,
+                                                double& c, double& s) {
   c = 1.0;
   s = 0.0;
-  if (!(fabs(apq) > floor_abs) || !(apq * apq > tol_rel * tol_rel * fabs(app) * fabs(aqq)))
-    return false;
+  if (!rotation_needed(app, aqq, apq, log2_tol_rel, floor_bits)) return false;
   const double d = aqq - app;
-  // 2^(1023 - E), E the larger biased exponent of d and apq (clamped so the
-  // scale is a normal FP64 number)
-  const int ed = (__double2hiint(d) >> 20) & 0x7ff, eb = (__double2hiint(apq) >> 20) & 0x7ff;
-  int sb = 2046 - (ed > eb ? ed : eb);
-  sb = sb < 1 ? 1 : (sb > 2046 ? 2046 : sb);
-  const double scale = __hiloint2double(sb << 20, 0);
-  const float df = (float)(d * scale), bf = (float)(apq * scale);
+  // scale d and apq by 2^(1023 - E), E the larger biased exponent of the two
+  const int ed = (int)(abs_bits(d) >> 52), eb = (int)(abs_bits(apq) >> 52);
+  const int sh = 1023 - (ed > eb ? ed : eb);
+  const float df = f64_to_f32_shifted(d, sh), bf = f64_to_f32_shifted(apq, sh);
   const float tau = __fdividef(df, 2.f * bf);
   const float atau = fabsf(tau);
   float t = (atau > 1e10f) ? __fdividef(0.5f, atau) : __fdividef(1.f, atau + sqrtf(fmaf(tau, tau, 1.f)));
   t = copysignf(t, tau);
   const float cf = rsqrtf(fmaf(t, t, 1.f));
   const float sf = t * cf;
-  if (!(sf != 0.f) || !(cf == cf)) return false;   // angle below FP32 resolution (or NaN input)
-  const double c0 = cf, s0 = sf;
+  if (!(sf != 0.f) || !(cf == cf) || !(bf != 0.f)) return false;   // below FP32 resolution, or NaN
+  const double c0 = f32_to_f64(cf), s0 = f32_to_f64(sf);
   const double e = fma(c0, c0, fma(s0, s0, -1.0));
   const double f = fma(e, fma(e, 0.375, -0.5), 1.0);
   c = c0 * f;
@@ -147,6 +186,8 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
   const double floor_abs = a.tol_abs * sqrt(*a.fro2);
+  const unsigned long long floor_bits = abs_bits(floor_abs);
+  const float log2_tol = (a.tol_rel > 0.0) ? log2f((float)a.tol_rel) : -INFINITY;
   const int64_t nblk = (int64_t)P * (P + 1) / 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* const A0 = a.A[0];
@@ -165,7 +206,7 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
     const double* A = A0;
     double c, s;
     if (jacobi_rotation(A[(int64_t)p * np + p], A[(int64_t)(p + 1) * np + p + 1],
-                        A[(int64_t)p * np + p + 1], a.tol_rel, floor_abs, c, s))
+                        A[(int64_t)p * np + p + 1], log2_tol, floor_bits, c, s))
       count_rotation(a.counts, 0, a.max_sweeps);
     reinterpret_cast<double2*>(rot0)[j] = make_double2(c, s);
   }
@@ -209,10 +250,20 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
         double nv[2][2];
         const double2 Ra = reinterpret_cast<const double2*>(R)[ja];
         const double2 Rb = reinterpret_cast<const double2*>(R)[jb];
+        // a skipped rotation is exactly (c, s) = (1, 0), which the update
+        // formulas reproduce exactly; a warp whose blocks all have skipped
+        // rotations (most warps of the later sweeps) copies and issues no
+        // FP64 instruction.  The test is an integer compare of s's bits.
+        const bool rot_a = __double_as_longlong(Ra.y) != 0, rot_b = __double_as_longlong(Rb.y) != 0;
+        const bool any_rot = __any_sync(__activemask(), rot_a || rot_b);
         if (ja == jb) {
           const double c = Ra.x, s = Ra.y;
-          const double d0 = rot_pp(a00, a01, a11, c, s), d1 = rot_qq(a00, a01, a11, c, s);
-          const double off = rot_pq(a00, a01, a11, c, s);
+          double d0 = a00, d1 = a11, off = a01;
+          if (any_rot) {
+            d0 = rot_pp(a00, a01, a11, c, s);
+            d1 = rot_qq(a00, a01, a11, c, s);
+            off = rot_pq(a00, a01, a11, c, s);
+          }
           nv[0][0] = d0; nv[1][1] = d1; nv[0][1] = off; nv[1][0] = off;
           An[(int64_t)na[0] * np + na[0]] = d0;
           An[(int64_t)na[1] * np + na[1]] = d1;
@@ -221,10 +272,14 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
         } else {
           const double ca = Ra.x, sa = Ra.y;
           const double cb = Rb.x, sb = Rb.y;
-          const double q00 = ca * a00 - sa * a10, q01 = ca * a01 - sa * a11;
-          const double q10 = sa * a00 + ca * a10, q11 = sa * a01 + ca * a11;
-          nv[0][0] = q00 * cb - q01 * sb; nv[0][1] = q00 * sb + q01 * cb;
-          nv[1][0] = q10 * cb - q11 * sb; nv[1][1] = q10 * sb + q11 * cb;
+          if (any_rot) {
+            const double q00 = ca * a00 - sa * a10, q01 = ca * a01 - sa * a11;
+            const double q10 = sa * a00 + ca * a10, q11 = sa * a01 + ca * a11;
+            nv[0][0] = q00 * cb - q01 * sb; nv[0][1] = q00 * sb + q01 * cb;
+            nv[1][0] = q10 * cb - q11 * sb; nv[1][1] = q10 * sb + q11 * cb;
+          } else {
+            nv[0][0] = a00; nv[0][1] = a01; nv[1][0] = a10; nv[1][1] = a11;
+          }
 #pragma unroll
           for (int u = 0; u < 2; ++u)
 #pragma unroll
@@ -247,13 +302,15 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
             dr = nv[0][0];
             dc = nv[1][1];
           } else {
-            dr = u ? rot_qq(da.x, da.y, daq, Ra.x, Ra.y) : rot_pp(da.x, da.y, daq, Ra.x, Ra.y);
-            dc = v ? rot_qq(db.x, db.y, dbq, Rb.x, Rb.y) : rot_pp(db.x, db.y, dbq, Rb.x, Rb.y);
+            dr = !rot_a ? (u ? daq : da.x)
+                        : (u ? rot_qq(da.x, da.y, daq, Ra.x, Ra.y) : rot_pp(da.x, da.y, daq, Ra.x, Ra.y));
+            dc = !rot_b ? (v ? dbq : db.x)
+                        : (v ? rot_qq(db.x, db.y, dbq, Rb.x, Rb.y) : rot_pp(db.x, db.y, dbq, Rb.x, Rb.y));
           }
           const double off = (k == 0) ? nv[0][0] : (k == 1) ? nv[0][1] : (k == 2) ? nv[1][0] : nv[1][1];
           const bool r_first = (r & 1) == 0;
           double cn, sn;
-          if (jacobi_rotation(r_first ? dr : dc, r_first ? dc : dr, off, a.tol_rel, floor_abs, cn,
+          if (jacobi_rotation(r_first ? dr : dc, r_first ? dc : dr, off, log2_tol, floor_bits, cn,
                               sn))
             count_rotation(a.counts, next_sweep, a.max_sweeps);
           reinterpret_cast<double2*>(Rn)[jn] = make_double2(cn, sn);
@@ -305,11 +362,18 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
 #pragma unroll
           for (int k = 0; k < VGROUP; ++k) {
             const int j = j0 + 32 * k + lane;
+            // identity rotations (most of the later sweeps) are copies; the
+            // FP64 arithmetic is issued only if a lane of the group rotates
+            const bool rot = __any_sync(0xffffffffu, __double_as_longlong(cs[k].y) != 0);
             if (j < P) {
               const double2 v = reinterpret_cast<const double2*>(b0)[j];
-              const double v0 = v.x, v1 = v.y;
-              b1[next_pos(2 * j, np)] = cs[k].x * v0 - cs[k].y * v1;
-              b1[next_pos(2 * j + 1, np)] = cs[k].y * v0 + cs[k].x * v1;
+              double n0 = v.x, n1 = v.y;
+              if (rot) {
+                n0 = cs[k].x * v.x - cs[k].y * v.y;
+                n1 = cs[k].y * v.x + cs[k].x * v.y;
+              }
+              b1[next_pos(2 * j, np)] = n0;
+              b1[next_pos(2 * j + 1, np)] = n1;
             }
           }
 #pragma unroll
