@@ -109,24 +109,97 @@ __device__ __forceinline__ void load_panel(float (*dst)[Stride<LD>::v], const fl
   }
 }
 
-// One CTA: tile (ta, tb), ta >= tb, over the K-blocks of split ks in the
+// Column mode, 16-byte copies, with the per-thread address arithmetic hoisted
+// out of the K loop: thread chunk e covers kk = c >> 5, i = i0 + 4 (c & 31)
+// (c = tid + 256 e); off[e] = i + I kk, iok[e] = i < I.  Only the last
+// K-block of the view can run past Rt.
+struct ColPanel {
+  int64_t off[2];
+  bool iok[2];
+};
+__device__ __forceinline__ ColPanel col_panel(const KGeom& g, int64_t i0) {
+  ColPanel p;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int c = threadIdx.x + NTHR * e;
+    const int kk = c >> 5, q = c & 31;
+    p.off[e] = i0 + 4 * q + g.I * kk;
+    p.iok[e] = i0 + 4 * q < g.I;
+  }
+  return p;
+}
+__device__ __forceinline__ void load_col16(float (*dst)[BT], const float* __restrict__ y,
+                                           const KGeom& g, const ColPanel& p, int64_t kb) {
+  const float* base = y + kb * BK * g.I;
+  const bool full = (kb + 1) * BK <= g.Rt;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int c = threadIdx.x + NTHR * e;
+    const int kk = c >> 5, q = c & 31;
+    const bool valid = p.iok[e] && (full || kb * BK + kk < g.Rt);
+    cp_async16(&dst[kk][4 * q], valid ? base + p.off[e] : y, valid);
+  }
+}
+
+// The 16 K-steps of one stage into the fresh per-block sums, then into acc.
+// UPPER == false leaves out the thread's (rows 0-63, columns 64-127)
+// quadrant, which lies above the diagonal of a diagonal tile.
+template <int SA, bool UPPER>
+__device__ __forceinline__ void stage_fma(const float (*A)[SA], const float (*B)[SA], int tx, int ty,
+                                          float (&acc)[8][8]) {
+  float t[8][8];
+#pragma unroll
+  for (int kk = 0; kk < BK; ++kk) {
+    const float4 a0 = *reinterpret_cast<const float4*>(&A[kk][ty * 4]);
+    const float4 a1 = *reinterpret_cast<const float4*>(&A[kk][64 + ty * 4]);
+    const float4 b0 = *reinterpret_cast<const float4*>(&B[kk][tx * 4]);
+    const float4 b1 = *reinterpret_cast<const float4*>(&B[kk][64 + tx * 4]);
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        if (!UPPER && u < 4 && v >= 4) continue;
+        t[u][v] = (kk == 0) ? a[u] * b[v] : fmaf(a[u], b[v], t[u][v]);
+      }
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      if (!UPPER && u < 4 && v >= 4) continue;
+      acc[u][v] += t[u][v];
+    }
+}
+
+// CTAs are laid out tile-major over the lower triangle of tiles (row ta,
+// then tb <= ta); an off-diagonal tile has ko K-splits, a diagonal tile kd
+// (its upper quadrants are skipped, so it gets fewer, longer splits and all
+// CTAs finish together).  First CTA of tile row ta:
+__host__ __device__ __forceinline__ int64_t row_start(int ta, int ko, int kd) {
+  return (int64_t)ko * ta * (ta - 1) / 2 + (int64_t)kd * ta;
+}
+
+// One CTA: tile (ta, tb), ta >= tb, over the K-blocks of its split ks in the
 // order of make_korder (column mode: a contiguous run, chunks of CHUNK
 // blocks; row mode: l-block-major over the split's slabs, chunk ends from
-// korder_block).  Writes the FP64 partial tile
-// part[(ks * ntiles + tile) * BT * BT + row * BT + col].
+// korder_block).  Writes its FP64 partial tile
+// part[blockIdx.x * BT * BT + row * BT + col].
 template <int LD>
 __global__ void __launch_bounds__(NTHR, 1)
-    k_gram_f32(const float* __restrict__ y, KGeom g, int ntiles, int ksplit,
+    k_gram_f32(const float* __restrict__ y, KGeom g, int T, int ko, int kd,
                double* __restrict__ part) {
   constexpr int SA = Stride<LD>::v;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<LD>& sm = *reinterpret_cast<Smem<LD>*>(smem_raw);
-  const int tile = blockIdx.x, ks = blockIdx.y;
-  int ta = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);
-  while ((ta + 1) * (ta + 2) / 2 <= tile) ++ta;
-  while (ta * (ta + 1) / 2 > tile) --ta;
-  const int tb = tile - ta * (ta + 1) / 2;
-  const bool diag = (ta == tb);
+  int ta = 0;
+  while (ta + 1 < T && row_start(ta + 1, ko, kd) <= (int64_t)blockIdx.x) ++ta;
+  const int off = (int)((int64_t)blockIdx.x - row_start(ta, ko, kd));
+  const bool diag = off >= ta * ko;
+  const int tb = diag ? ta : off / ko;
+  const int ks = diag ? off - ta * ko : off % ko;
+  const int ksplit = diag ? kd : ko;
   const int64_t ia0 = (int64_t)ta * BT, ib0 = (int64_t)tb * BT;
   const KOrder ord = make_korder(g, ks, ksplit);
   const int64_t count = ord.count;
@@ -141,14 +214,32 @@ __global__ void __launch_bounds__(NTHR, 1)
     *reinterpret_cast<float4*>(&sm.lo[row * BT + 64 + tx * 4]) = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 
+  ColPanel cpa, cpb;
+  if constexpr (LD == LD_COL16) {
+    cpa = col_panel(g, ia0);
+    cpb = col_panel(g, ib0);
+  }
+  // K-block of position idx in this split's order
+  auto block_at = [&](int64_t idx) -> int64_t {
+    if constexpr (LD == LD_ROW) {
+      bool unused;
+      return korder_block(g, ord, idx, unused);
+    } else {
+      return ord.kb0 + idx;
+    }
+  };
+  auto load_stage = [&](int slot, int64_t kb) {
+    if constexpr (LD == LD_COL16) {
+      load_col16(sm.a[slot], y, g, cpa, kb);
+      if (!diag) load_col16(sm.b[slot], y, g, cpb, kb);
+    } else {
+      load_panel<LD>(sm.a[slot], y, g, ia0, kb);
+      if (!diag) load_panel<LD>(sm.b[slot], y, g, ib0, kb);
+    }
+  };
 #pragma unroll
   for (int s = 0; s < NST - 1; ++s) {
-    if (s < count) {
-      bool unused;
-      const int64_t kb = korder_block(g, ord, s, unused);
-      load_panel<LD>(sm.a[s], y, g, ia0, kb);
-      if (!diag) load_panel<LD>(sm.b[s], y, g, ib0, kb);
-    }
+    if (s < count) load_stage(s, block_at(s));
     cp_commit();
   }
 
@@ -158,41 +249,20 @@ __global__ void __launch_bounds__(NTHR, 1)
 #pragma unroll
     for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
 
+  int st = 0, sn = NST - 1;   // stage slot of idx, and of idx + NST - 1
   for (int64_t idx = 0; idx < count; ++idx) {
     cp_wait<NST - 2>();
     __syncthreads();
     {
       const int64_t nxt = idx + NST - 1;
-      const int sn = (int)(nxt % NST);
-      if (nxt < count) {
-        bool unused;
-        const int64_t kb = korder_block(g, ord, nxt, unused);
-        load_panel<LD>(sm.a[sn], y, g, ia0, kb);
-        if (!diag) load_panel<LD>(sm.b[sn], y, g, ib0, kb);
-      }
+      if (nxt < count) load_stage(sn, block_at(nxt));
       cp_commit();
     }
-    const int st = (int)(idx % NST);
     const float(*A)[SA] = sm.a[st];
-    const float(*B)[SA] = diag ? sm.a[st] : sm.b[st];
-    float t[8][8];
-#pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&A[kk][ty * 4]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&A[kk][64 + ty * 4]);
-      const float4 b0 = *reinterpret_cast<const float4*>(&B[kk][tx * 4]);
-      const float4 b1 = *reinterpret_cast<const float4*>(&B[kk][64 + tx * 4]);
-      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-#pragma unroll
-        for (int v = 0; v < 8; ++v) t[u][v] = (kk == 0) ? a[u] * b[v] : fmaf(a[u], b[v], t[u][v]);
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-#pragma unroll
-      for (int v = 0; v < 8; ++v) acc[u][v] += t[u][v];
+    if (diag) stage_fma<SA, false>(A, A, tx, ty, acc);
+    else stage_fma<SA, true>(A, sm.b[st], tx, ty, acc);
+    st = (st + 1 == NST) ? 0 : st + 1;
+    sn = (sn + 1 == NST) ? 0 : sn + 1;
 
     bool chunk_end;
     if constexpr (LD == LD_ROW) {
@@ -225,7 +295,7 @@ __global__ void __launch_bounds__(NTHR, 1)
   }
   cp_wait<0>();
 
-  double* out = part + ((int64_t)ks * ntiles + tile) * BT * BT;
+  double* out = part + (int64_t)blockIdx.x * BT * BT;
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int row = (u < 4) ? ty * 4 + u : 64 + ty * 4 + (u - 4);
@@ -241,11 +311,13 @@ __global__ void __launch_bounds__(NTHR, 1)
   }
 }
 
-// S[i][j] = S[j][i] = sum over ks (fixed order) of the partial tiles.
-__global__ void k_gram_f32_reduce(const double* __restrict__ part, int ntiles, int ksplit,
+// S[i][j] = S[j][i] = sum over the tile's K-splits (fixed order) of its
+// partial tiles.
+__global__ void k_gram_f32_reduce(const double* __restrict__ part, int T, int ko, int kd,
                                   int64_t I, double* __restrict__ S) {
+  const int64_t ntiles = (int64_t)T * (T + 1) / 2;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)ntiles * BT * BT) return;
+  if (idx >= ntiles * BT * BT) return;
   const int tile = (int)(idx / (BT * BT));
   const int e = (int)(idx % (BT * BT));
   int ta = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);
@@ -255,8 +327,10 @@ __global__ void k_gram_f32_reduce(const double* __restrict__ part, int ntiles, i
   const int64_t i = (int64_t)ta * BT + e / BT, j = (int64_t)tb * BT + e % BT;
   if (i >= I || j >= I) return;
   if (ta == tb && j > i) return;   // diagonal tile: its lower half (mirrored below)
+  const int64_t first = row_start(ta, ko, kd) + (int64_t)tb * ko;
+  const int nk = (ta == tb) ? kd : ko;
   double s = 0.0;
-  for (int k = 0; k < ksplit; ++k) s += part[((int64_t)k * ntiles + tile) * BT * BT + e];
+  for (int k = 0; k < nk; ++k) s += part[(first + k) * BT * BT + e];
   S[i * I + j] = s;
   S[j * I + i] = s;
 }
@@ -269,14 +343,28 @@ GramPlan plan_gram_f32(int64_t L, int64_t I, int64_t Rt, int num_sms) {
   const KGeom g = make_kgeom(L, I, Rt, BK);
   const int64_t T = (I + BT - 1) / BT;
   p.ntiles = (int)(T * (T + 1) / 2);
-  int64_t want = ((int64_t)num_sms + p.ntiles - 1) / p.ntiles;   // one wave of one CTA per SM
-  if (want * p.ntiles > num_sms && want > 1) want -= 1;
-  const int64_t cap = (int64_t)(256ll << 20) / ((int64_t)p.ntiles * BT * BT * 8);
-  if (want > cap) want = cap;
-  if (want > g.NKB) want = g.NKB;
-  if (want < 1) want = 1;
-  p.ksplit = (int)want;
-  p.scratch_bytes = (size_t)p.ksplit * p.ntiles * BT * BT * sizeof(double);
+  const int64_t noff = T * (T - 1) / 2;
+  // one wave of one CTA per SM; a diagonal tile costs ~3/4 of an
+  // off-diagonal one per K-block (one quadrant skipped, one panel loaded)
+  int64_t ko = 1, kd = 1;
+  for (int64_t k = 1; k <= num_sms; ++k) {
+    const int64_t d = (3 * k + 2) / 4 > 0 ? (3 * k + 2) / 4 : 1;
+    if (noff * k + T * d > num_sms) break;
+    ko = k;
+    kd = d;
+  }
+  if (noff == 0) kd = num_sms;   // a single diagonal tile
+  const int64_t cap = (int64_t)(256ll << 20) / ((int64_t)BT * BT * 8);
+  while (noff * ko + T * kd > cap && (ko > 1 || kd > 1)) {
+    if (ko > 1) --ko;
+    if (kd > 1) --kd;
+  }
+  if (ko > g.NKB) ko = g.NKB;
+  if (kd > g.NKB) kd = g.NKB;
+  p.ksplit = (int)ko;
+  p.ksplit_diag = (int)kd;
+  p.nctas = (int)(noff * ko + T * kd);
+  p.scratch_bytes = (size_t)p.nctas * BT * BT * sizeof(double);
   return p;
 }
 
@@ -286,7 +374,8 @@ static cudaError_t launch_ld(const float* y, const KGeom& g, const GramPlan& p, 
   const int smem = (int)sizeof(Smem<LD>);
   cudaError_t e = cudaFuncSetAttribute(k_gram_f32<LD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  k_gram_f32<LD><<<dim3(p.ntiles, p.ksplit), NTHR, smem, st>>>(y, g, p.ntiles, p.ksplit, scratch);
+  const int T = (int)((g.I + BT - 1) / BT);
+  k_gram_f32<LD><<<p.nctas, NTHR, smem, st>>>(y, g, T, p.ksplit, p.ksplit_diag, scratch);
   return cudaGetLastError();
 }
 
@@ -299,7 +388,8 @@ cudaError_t launch_gram_f32(const float* y, int64_t L, int64_t I, int64_t Rt, co
   else e = launch_ld<LD_COL4>(y, g, p, scratch, st);
   if (e != cudaSuccess) return e;
   const int64_t tot = (int64_t)p.ntiles * BT * BT;
-  k_gram_f32_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(scratch, p.ntiles, p.ksplit, I, S);
+  k_gram_f32_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+      scratch, (int)((I + BT - 1) / BT), p.ksplit, p.ksplit_diag, I, S);
   count_launches(2);
   return cudaGetLastError();
 }

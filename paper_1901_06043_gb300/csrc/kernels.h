@@ -15,6 +15,8 @@ cudaError_t launch_sumsq(const void* y, tucker_dtype dt, int64_t n, double* part
 // ---- SIMT Gram (FP64 or FP32 products), split-K partial tiles + reduction
 struct GramPlan {
   int ntiles = 0, ksplit = 0;
+  int ksplit_diag = 0;   // plan_gram_f32: K splits of a diagonal tile (ksplit: off-diagonal)
+  int nctas = 0;         // plan_gram_f32: CTAs (= partial tiles)
   size_t scratch_bytes = 0;
 };
 GramPlan plan_gram_simt(int64_t L, int64_t I, int64_t Rt, int num_sms);
