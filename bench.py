@@ -383,7 +383,7 @@ def step_rooflines(res, w, pk):
             if kern == "tcgen05":
                 bound, ach, peak, unit = "hbm", nbytes / t / 1e9, pk["hbm_gbs"], "GB/s"
                 src = "measured HBM copy"
-            elif kern == "simt-fp32":
+            elif kern in ("simt-fp32", "simt-fp32c"):
                 bound, ach, peak, unit = "alu", flops / t / 1e12, FP32_PEAK_TFLOPS, "TFLOP/s"
                 src = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
             else:

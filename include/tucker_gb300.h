@@ -53,7 +53,13 @@ typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
 
 /* Arithmetic of the Gram and TTM steps.  The eigensolve and the rank cut
  * are FP64 in every mode, and the Gram is always reduced across slabs in
- * FP64.
+ * FP64.  In every precision a mode with I_n < 64 gets an FP64 Gram (the
+ * energy of the later, small modes sits in a few components, where FP32
+ * block sums do not average out), and an eps-driven tucker_sthosvd with
+ * eps^2 / N < 1e-9 computes all its Grams in FP64: FP32-product Grams leave
+ * up to ~1.5e-10 ||X||^2 on the discarded subspace, too close to the
+ * threshold eps^2 ||X||^2 / N below that.  The result reports the kernel of
+ * every step.
  *   FP64   : products and sums in FP64 (any input dtype); core in FP64.
  *   FP32   : FP32 products, round-to-nearest FP32 sums over short chunks
  *            combined exactly (TwoSum) and in FP64; working tensor and core

@@ -180,8 +180,15 @@ float split_scale(double maxabs) {
   return std::ldexp(1.0f, e);
 }
 
-// Which kernel serves a Gram / TTM step: 0 SIMT FP64, 1 SIMT FP32, 2 tcgen05.
+// Smallest eps^2 / N at which an eps-driven ST-HOSVD keeps a reduced-precision
+// Gram (see tucker_sthosvd).
+constexpr double kMinFp32GramThreshold = 1e-9;
+
+// Which kernel serves a Gram / TTM step: 0 SIMT FP64, 1 SIMT FP32, 2 tcgen05,
+// 3 small-mode FP64 (I < 64, every precision), 4 FP32 with exact
+// (compensated) block sums (row modes with few slabs).
 int gram_kernel_for(tucker_prec prec, tucker_dtype dt, const SlabView& v, int sms) {
+  if (plan_gram_small(v.L, v.I, v.Rt, sms, v.L0).nctas > 0) return 3;
   if (prec == TUCKER_PREC_FP64) return 0;
   if (prec == TUCKER_PREC_TENSOR && dt == TUCKER_F32 && plan_gram_tc(v.L, v.I, v.Rt, sms).ok) return 2;
   return 1;
@@ -215,20 +222,29 @@ tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabV
     }
     return TUCKER_OK;
   }
+  if (kern == 3) {
+    const GramPlan ps = plan_gram_small(v.L, v.I, v.Rt, c->num_sms, v.L0);
+    DevBuf scratch;
+    TK_TRY(dev_alloc(c, scratch, ps.scratch_bytes));
+    TK_CUDA(c, launch_gram_small(y, dt, v.L, v.I, v.Rt, v.L0, ps, scratch.as<double>(), S,
+                                 c->stream));
+    return TUCKER_OK;
+  }
   if (kern == 1 && dt == TUCKER_F32) {
-    const GramPlan pc = plan_gram_f32(v.L, v.I, v.Rt, c->num_sms);
+    const GramPlan pc = plan_gram_f32(v.L, v.I, v.Rt, c->num_sms, v.L0);
     if (pc.ntiles > 0) {
+      if (kernel_used && gram_f32_compensated(v.L, v.Rt)) *kernel_used = 4;
       DevBuf scratch;
       TK_TRY(dev_alloc(c, scratch, pc.scratch_bytes));
-      TK_CUDA(c, launch_gram_f32((const float*)y, v.L, v.I, v.Rt, pc, scratch.as<double>(), S,
-                                 c->stream));
+      TK_CUDA(c, launch_gram_f32((const float*)y, v.L, v.I, v.Rt, v.L0, pc, scratch.as<double>(),
+                                 S, c->stream));
       return TUCKER_OK;
     }
   }
-  GramPlan p = plan_gram_simt(v.L, v.I, v.Rt, c->num_sms);
+  GramPlan p = plan_gram_simt(v.L, v.I, v.Rt, c->num_sms, v.L0);
   DevBuf scratch;
   TK_TRY(dev_alloc(c, scratch, p.scratch_bytes));
-  TK_CUDA(c, launch_gram_simt(y, dt, kern == 0, v.L, v.I, v.Rt, p, scratch.as<double>(), S,
+  TK_CUDA(c, launch_gram_simt(y, dt, kern == 0, v.L, v.I, v.Rt, v.L0, p, scratch.as<double>(), S,
                               c->stream));
   return TUCKER_OK;
 }
@@ -513,6 +529,15 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
   r->norm_x_sq = nrm2;
   const double thr = ranks ? 0.0 : eps * eps * nrm2 / ndim;
   r->threshold = thr;
+  // Gram precision.  The rank cut compares a tail sum with eps^2 ||X||^2 / N.
+  // An FP32-product Gram (unbiased rounding, split and ordered as in the
+  // kernels) leaves up to ~1.5e-10 ||X||^2 on the discarded subspace of the
+  // later modes, whose energy sits in a few components; below
+  // eps^2 / N = 1e-9 that is no longer far below the threshold, so the
+  // Grams are computed in FP64 there (the TTMs keep their precision).
+  tucker_prec gram_prec = prec;
+  if (!ranks && prec != TUCKER_PREC_FP64 && eps * eps / ndim < kMinFp32GramThreshold)
+    gram_prec = TUCKER_PREC_FP64;
 
   DevBuf S, V, ycur;
   TK_TRY(dev_alloc(c, S, sizeof(double) * imax * imax));
@@ -528,7 +553,8 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
     const int I = (int)v.I;
     Timer tmg, tme, tmt;
     tmg.start(c);
-    TK_TRY(do_gram(c, y, ydt, v, prec, S.as<double>(), &r->gram_kernel[n], s == 0 ? xmax : -1.0));
+    TK_TRY(do_gram(c, y, ydt, v, gram_prec, S.as<double>(), &r->gram_kernel[n],
+                   s == 0 ? xmax : -1.0));
     tmg.stop(c);
     DevBuf w;
     TK_TRY(dev_alloc(c, w, sizeof(double) * I));

@@ -25,14 +25,16 @@ void count_launches(int n);
 
 // Slab view of mode n of a tensor with dims J: element (l, i, r) at
 // l + L*(i + I*r) with L = prod_{k<n} J_k, I = J_n, Rt = prod_{k>n} J_k.
+// L0 = J_0 (n > 0) is the fastest sub-index of l.
 struct SlabView {
-  int64_t L, I, Rt;
+  int64_t L, I, Rt, L0;
 };
 
 inline SlabView slab_view(int ndim, const int64_t* dims, int n) {
-  SlabView v{1, dims[n], 1};
+  SlabView v{1, dims[n], 1, 1};
   for (int k = 0; k < n; ++k) v.L *= dims[k];
   for (int k = n + 1; k < ndim; ++k) v.Rt *= dims[k];
+  if (n > 0) v.L0 = dims[0];
   return v;
 }
 

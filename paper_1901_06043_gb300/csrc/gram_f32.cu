@@ -96,14 +96,15 @@ __device__ __forceinline__ void load_panel(float (*dst)[Stride<LD>::v], const fl
     }
   } else {
     const int64_t r = kb / g.nLB;
-    const int64_t l0 = (kb - r * g.nLB) * BK;
+    int64_t lbeg, lend;
+    lblock_range(g, kb - r * g.nLB, BK, lbeg, lend);
     const float* base = y + g.L * g.I * r;
 #pragma unroll
     for (int e = 0; e < (BK * BT) / NTHR; ++e) {
       const int c = tid + NTHR * e;
       const int kk = c & 15, q = c >> 4;   // 16 threads read 16 consecutive l of row i
-      const int64_t l = l0 + kk, i = i0 + q;
-      const bool valid = (l < g.L) && (i < g.I);
+      const int64_t l = lbeg + kk, i = i0 + q;
+      const bool valid = (l < lend) && (i < g.I);
       cp_async4(&dst[kk][q], valid ? base + l + g.L * i : y, valid);
     }
   }
@@ -144,12 +145,19 @@ __device__ __forceinline__ void load_col16(float (*dst)[BT], const float* __rest
 // The 16 K-steps of one stage into the fresh per-block sums, then into acc.
 // UPPER == false leaves out the thread's (rows 0-63, columns 64-127)
 // quadrant, which lies above the diagonal of a diagonal tile.
+// The steps run from the last K of the block to the first: in row mode the
+// 16 l of a block are consecutive indices of an already-truncated mode,
+// whose energy falls with l, so this adds the products in increasing size
+// and no square is added to a sum that dwarfs it (round-to-nearest drops
+// the small part of such a square one-sidedly: a negative bias of ~5e-10 of
+// the trace with the ascending order).  Column-mode blocks have no order.
 template <int SA, bool UPPER>
 __device__ __forceinline__ void stage_fma(const float (*A)[SA], const float (*B)[SA], int tx, int ty,
                                           float (&acc)[8][8]) {
   float t[8][8];
 #pragma unroll
-  for (int kk = 0; kk < BK; ++kk) {
+  for (int kq = 0; kq < BK; ++kq) {
+    const int kk = BK - 1 - kq;
     const float4 a0 = *reinterpret_cast<const float4*>(&A[kk][ty * 4]);
     const float4 a1 = *reinterpret_cast<const float4*>(&A[kk][64 + ty * 4]);
     const float4 b0 = *reinterpret_cast<const float4*>(&B[kk][tx * 4]);
@@ -161,7 +169,7 @@ __device__ __forceinline__ void stage_fma(const float (*A)[SA], const float (*B)
 #pragma unroll
       for (int v = 0; v < 8; ++v) {
         if (!UPPER && u < 4 && v >= 4) continue;
-        t[u][v] = (kk == 0) ? a[u] * b[v] : fmaf(a[u], b[v], t[u][v]);
+        t[u][v] = (kq == 0) ? a[u] * b[v] : fmaf(a[u], b[v], t[u][v]);
       }
   }
 #pragma unroll
@@ -181,12 +189,54 @@ __host__ __device__ __forceinline__ int64_t row_start(int ta, int ko, int kd) {
   return (int64_t)ko * ta * (ta - 1) / 2 + (int64_t)kd * ta;
 }
 
+// Compensated form of stage_fma: t + c is the block's sum of products to
+// ~2^-48 relative (t and c are overwritten).  Each product's rounding error is exact (p + ep = a b,
+// ep = fma(a, b, -p)) and each addition's is exact (TwoSum); the
+// round-to-nearest intrinsics keep the compiler from fusing them.  Used for
+// row-mode views with few slabs: after the earlier modes are truncated the
+// energy sits in a few l, a few block sums dominate every entry, and their
+// FP32 rounding (~6e-8 each) does not average out -- 0.3 of the eps = 1e-4
+// threshold on the discarded subspace of a 500x500x500x11x8 tensor's third
+// mode.  About 10 FP32 operations per product.
+template <int SA, bool UPPER>
+__device__ __forceinline__ void stage_fma_comp(const float (*A)[SA], const float (*B)[SA], int tx,
+                                               int ty, float (&t)[8][8], float (&c)[8][8]) {
+#pragma unroll
+  for (int kq = 0; kq < BK; ++kq) {
+    const int kk = BK - 1 - kq;
+    const float4 a0 = *reinterpret_cast<const float4*>(&A[kk][ty * 4]);
+    const float4 a1 = *reinterpret_cast<const float4*>(&A[kk][64 + ty * 4]);
+    const float4 b0 = *reinterpret_cast<const float4*>(&B[kk][tx * 4]);
+    const float4 b1 = *reinterpret_cast<const float4*>(&B[kk][64 + tx * 4]);
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        if (!UPPER && u < 4 && v >= 4) continue;
+        const float p = __fmul_rn(a[u], b[v]);
+        const float ep = fmaf(a[u], b[v], -p);
+        if (kq == 0) {
+          t[u][v] = p;
+          c[u][v] = ep;
+        } else {
+          const float sum = __fadd_rn(t[u][v], p);
+          const float bb = __fsub_rn(sum, t[u][v]);
+          const float es = __fadd_rn(__fsub_rn(t[u][v], __fsub_rn(sum, bb)), __fsub_rn(p, bb));
+          t[u][v] = sum;
+          c[u][v] = __fadd_rn(c[u][v], __fadd_rn(ep, es));
+        }
+      }
+  }
+}
+
 // One CTA: tile (ta, tb), ta >= tb, over the K-blocks of its split ks in the
 // order of make_korder (column mode: a contiguous run, chunks of CHUNK
 // blocks; row mode: l-block-major over the split's slabs, chunk ends from
 // korder_block).  Writes its FP64 partial tile
 // part[blockIdx.x * BT * BT + row * BT + col].
-template <int LD>
+template <int LD, bool COMP>
 __global__ void __launch_bounds__(NTHR, 1)
     k_gram_f32(const float* __restrict__ y, KGeom g, int T, int ko, int kd,
                double* __restrict__ part) {
@@ -259,6 +309,47 @@ __global__ void __launch_bounds__(NTHR, 1)
       cp_commit();
     }
     const float(*A)[SA] = sm.a[st];
+    if constexpr (COMP) {
+      // every block goes straight into the exact (hi, lo) pair; the first
+      // l-block of each run of L0 (l0 < 16: where the energy of the earlier,
+      // truncated modes sits) is summed exactly, the others plainly
+      float t[8][8], c[8][8];
+      const int64_t kbc = block_at(idx);
+      const bool exact = ((kbc % g.nLB) % g.nL0B) == 0;
+      if (exact) {
+        if (diag) stage_fma_comp<SA, false>(A, A, tx, ty, t, c);
+        else stage_fma_comp<SA, true>(A, sm.b[st], tx, ty, t, c);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) { t[u][v] = 0.f; c[u][v] = 0.f; }
+        if (diag) stage_fma<SA, false>(A, A, tx, ty, t);
+        else stage_fma<SA, true>(A, sm.b[st], tx, ty, t);
+      }
+      st = (st + 1 == NST) ? 0 : st + 1;
+      sn = (sn + 1 == NST) ? 0 : sn + 1;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int row = (u < 4) ? ty * 4 + u : 64 + ty * 4 + (u - 4);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (diag && u < 4 && h == 1) continue;   // above the diagonal: not computed
+          float* ph = &sm.hi[row * BT + h * 64 + tx * 4];
+          float* pl = &sm.lo[row * BT + h * 64 + tx * 4];
+          float4 vh = *reinterpret_cast<float4*>(ph);
+          float4 vl = *reinterpret_cast<float4*>(pl);
+          float s2, e2;
+          two_sum_f(vh.x, t[u][4 * h + 0], s2, e2); vh.x = s2; vl.x += e2 + c[u][4 * h + 0];
+          two_sum_f(vh.y, t[u][4 * h + 1], s2, e2); vh.y = s2; vl.y += e2 + c[u][4 * h + 1];
+          two_sum_f(vh.z, t[u][4 * h + 2], s2, e2); vh.z = s2; vl.z += e2 + c[u][4 * h + 2];
+          two_sum_f(vh.w, t[u][4 * h + 3], s2, e2); vh.w = s2; vl.w += e2 + c[u][4 * h + 3];
+          *reinterpret_cast<float4*>(ph) = vh;
+          *reinterpret_cast<float4*>(pl) = vl;
+        }
+      }
+      continue;
+    }
     if (diag) stage_fma<SA, false>(A, A, tx, ty, acc);
     else stage_fma<SA, true>(A, sm.b[st], tx, ty, acc);
     st = (st + 1 == NST) ? 0 : st + 1;
@@ -337,10 +428,10 @@ __global__ void k_gram_f32_reduce(const double* __restrict__ part, int T, int ko
 
 }  // namespace
 
-GramPlan plan_gram_f32(int64_t L, int64_t I, int64_t Rt, int num_sms) {
+GramPlan plan_gram_f32(int64_t L, int64_t I, int64_t Rt, int num_sms, int64_t L0) {
   GramPlan p;
   if (I < 64 || Rt < 1 || L < 1) return p;   // ntiles == 0: not applicable
-  const KGeom g = make_kgeom(L, I, Rt, BK);
+  const KGeom g = make_kgeom(L, I, Rt, BK, L0);
   const int64_t T = (I + BT - 1) / BT;
   p.ntiles = (int)(T * (T + 1) / 2);
   const int64_t noff = T * (T - 1) / 2;
@@ -368,24 +459,32 @@ GramPlan plan_gram_f32(int64_t L, int64_t I, int64_t Rt, int num_sms) {
   return p;
 }
 
-template <int LD>
+template <int LD, bool COMP>
 static cudaError_t launch_ld(const float* y, const KGeom& g, const GramPlan& p, double* scratch,
                              cudaStream_t st) {
   const int smem = (int)sizeof(Smem<LD>);
-  cudaError_t e = cudaFuncSetAttribute(k_gram_f32<LD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_gram_f32<LD, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const int T = (int)((g.I + BT - 1) / BT);
-  k_gram_f32<LD><<<p.nctas, NTHR, smem, st>>>(y, g, T, p.ksplit, p.ksplit_diag, scratch);
+  k_gram_f32<LD, COMP><<<p.nctas, NTHR, smem, st>>>(y, g, T, p.ksplit, p.ksplit_diag, scratch);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gram_f32(const float* y, int64_t L, int64_t I, int64_t Rt, const GramPlan& p,
-                            double* scratch, double* S, cudaStream_t st) {
-  const KGeom g = make_kgeom(L, I, Rt, BK);
+int gram_f32_compensated(int64_t L, int64_t Rt) { return L > 1 && Rt < 4096; }
+
+cudaError_t launch_gram_f32(const float* y, int64_t L, int64_t I, int64_t Rt, int64_t L0,
+                            const GramPlan& p, double* scratch, double* S, cudaStream_t st) {
+  const KGeom g = make_kgeom(L, I, Rt, BK, L0);
   cudaError_t e;
-  if (L > 1) e = launch_ld<LD_ROW>(y, g, p, scratch, st);
-  else if ((I % 4 == 0) && ((((uintptr_t)y) & 15) == 0)) e = launch_ld<LD_COL16>(y, g, p, scratch, st);
-  else e = launch_ld<LD_COL4>(y, g, p, scratch, st);
+  if (L > 1) {
+    e = gram_f32_compensated(L, Rt) ? launch_ld<LD_ROW, true>(y, g, p, scratch, st)
+                                    : launch_ld<LD_ROW, false>(y, g, p, scratch, st);
+  } else if ((I % 4 == 0) && ((((uintptr_t)y) & 15) == 0)) {
+    e = launch_ld<LD_COL16, false>(y, g, p, scratch, st);
+  } else {
+    e = launch_ld<LD_COL4, false>(y, g, p, scratch, st);
+  }
   if (e != cudaSuccess) return e;
   const int64_t tot = (int64_t)p.ntiles * BT * BT;
   k_gram_f32_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(

@@ -7,24 +7,42 @@ namespace tk {
 
 // Geometry of the K (contraction) dimension of a slab view.  K runs over
 // (r, l) pairs.  With L == 1 a K-block is BK consecutive slabs (column mode,
-// contiguous along i); otherwise a K-block is BK consecutive l of one slab
-// (row mode, contiguous along l), masked at l >= L.
+// contiguous along i).  Otherwise a K-block is up to BK consecutive l of one
+// slab (row mode, contiguous along l) that never cross a multiple of L0, the
+// fastest sub-index of l: when the modes below n are already truncated, l0
+// is an eigen-sorted index whose energy falls along it, and a block confined
+// to one run of l0 can be summed smallest-first (see the Gram kernels).  A
+// row of L0 l holds nL0B blocks (the last one partial); a slab holds
+// nLB = (L / L0) nL0B blocks.
 struct KGeom {
   int64_t L, I, Rt;
+  int64_t L0;    // block alignment of l (divides L)
+  int64_t nL0B;  // K-blocks per run of L0 l
   int64_t nLB;   // K-blocks per slab in row mode
   int64_t NKB;   // total K-blocks
 };
 
-
-__host__ __device__ inline KGeom make_kgeom(int64_t L, int64_t I, int64_t Rt, int bk) {
-  KGeom g{L, I, Rt, 1, 0};
+__host__ __device__ inline KGeom make_kgeom(int64_t L, int64_t I, int64_t Rt, int bk,
+                                             int64_t L0 = 0) {
+  KGeom g{L, I, Rt, L, 1, 1, 0};
   if (L == 1) {
     g.NKB = (Rt + bk - 1) / bk;
   } else {
-    g.nLB = (L + bk - 1) / bk;
+    if (L0 >= 1 && L0 <= L && L % L0 == 0) g.L0 = L0;
+    g.nL0B = (g.L0 + bk - 1) / bk;
+    g.nLB = (L / g.L0) * g.nL0B;
     g.NKB = Rt * g.nLB;
   }
   return g;
+}
+
+// Row mode: the l range [l_begin, l_end) of l-block lb of a slab.
+__host__ __device__ inline void lblock_range(const KGeom& g, int64_t lb, int bk, int64_t& l_begin,
+                                             int64_t& l_end) {
+  const int64_t row = lb / g.nL0B, sub = lb - row * g.nL0B;
+  l_begin = row * g.L0 + sub * bk;
+  const int64_t e = row * g.L0 + g.L0;
+  l_end = (l_begin + bk < e) ? l_begin + bk : e;
 }
 
 // Order in which one CTA (split ks of ksplit) visits its K-blocks, and where

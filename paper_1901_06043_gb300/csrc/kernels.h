@@ -19,18 +19,30 @@ struct GramPlan {
   int nctas = 0;         // plan_gram_f32: CTAs (= partial tiles)
   size_t scratch_bytes = 0;
 };
-GramPlan plan_gram_simt(int64_t L, int64_t I, int64_t Rt, int num_sms);
+// L0: the fastest sub-index of l (the first dim of the tensor for a mode
+// n > 0); row-mode K-blocks never cross a multiple of it
+GramPlan plan_gram_simt(int64_t L, int64_t I, int64_t Rt, int num_sms, int64_t L0);
 GramPlan plan_gram_simt_capped(int64_t L, int64_t I, int64_t Rt, int num_sms, size_t max_bytes,
-                               int* ok);
+                               int* ok, int64_t L0);
 cudaError_t launch_gram_simt(const void* y, tucker_dtype dt, bool fp64, int64_t L, int64_t I,
-                             int64_t Rt, const GramPlan& p, double* scratch, double* S,
+                             int64_t Rt, int64_t L0, const GramPlan& p, double* scratch, double* S,
                              cudaStream_t st);
 
 // ---- FP32-product Gram of FP32 input, I >= 64: 128 x 128 tiles, cp.async
 // pipeline; plan.ntiles == 0 when it does not apply
-GramPlan plan_gram_f32(int64_t L, int64_t I, int64_t Rt, int num_sms);
-cudaError_t launch_gram_f32(const float* y, int64_t L, int64_t I, int64_t Rt, const GramPlan& p,
-                            double* scratch, double* S, cudaStream_t st);
+GramPlan plan_gram_f32(int64_t L, int64_t I, int64_t Rt, int num_sms, int64_t L0);
+// Whether launch_gram_f32 runs its compensated (exact block sums) variant:
+// row-mode views with fewer than 4096 slabs
+int gram_f32_compensated(int64_t L, int64_t Rt);
+cudaError_t launch_gram_f32(const float* y, int64_t L, int64_t I, int64_t Rt, int64_t L0,
+                            const GramPlan& p, double* scratch, double* S, cudaStream_t st);
+
+// ---- Gram of a small mode (I < 64) in FP64 (products of FP32 inputs are
+// exact), for every precision; plan.nctas == 0 when it does not apply
+GramPlan plan_gram_small(int64_t L, int64_t I, int64_t Rt, int num_sms, int64_t L0);
+cudaError_t launch_gram_small(const void* y, tucker_dtype dt, int64_t L, int64_t I, int64_t Rt,
+                              int64_t L0, const GramPlan& p, double* scratch, double* S,
+                              cudaStream_t st);
 
 // ---- SIMT TTM
 cudaError_t launch_ttm_simt(const void* y, tucker_dtype ydt, bool fp64, int64_t L, int64_t I,

@@ -59,9 +59,10 @@ extern "C" tucker_status tucker_gram_noalloc(const void* y_dev, tucker_dtype dty
   if (s != TUCKER_OK) return s;
   const tk::SlabView v = tk::slab_view(ndim, dims, mode);
   int fits = 0;
-  tk::GramPlan p = tk::plan_gram_simt_capped(v.L, v.I, v.Rt, g_num_sms[dev], kScratchBytes, &fits);
+  tk::GramPlan p =
+      tk::plan_gram_simt_capped(v.L, v.I, v.Rt, g_num_sms[dev], kScratchBytes, &fits, v.L0);
   if (!fits) return TUCKER_ERR_INVALID;   // I_n above 1984: partial tiles exceed the scratch
-  cudaError_t e = tk::launch_gram_simt(y_dev, dtype, prec == TUCKER_PREC_FP64, v.L, v.I, v.Rt, p,
+  cudaError_t e = tk::launch_gram_simt(y_dev, dtype, prec == TUCKER_PREC_FP64, v.L, v.I, v.Rt, v.L0, p,
                                        g_scratch_ptr[dev], S_dev, (cudaStream_t)stream);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -180,14 +180,15 @@ __device__ __forceinline__ void gram_load(const TIn* __restrict__ y, const KGeom
     }
   } else {
     int64_t r = kb / g.nLB;
-    int64_t l0 = (kb - r * g.nLB) * GBK;
+    int64_t lbeg, lend;
+    lblock_range(g, kb - r * g.nLB, GBK, lbeg, lend);
     const TIn* base = y + g.L * g.I * r;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       int idx = tid + 256 * e;
       int kk = idx % GBK, ii = idx / GBK;
-      int64_t l = l0 + kk, i = i0 + ii;
-      reg[e] = (l < g.L && i < g.I) ? (TC)base[l + g.L * i] : (TC)0;
+      int64_t l = lbeg + kk, i = i0 + ii;
+      reg[e] = (l < lend && i < g.I) ? (TC)base[l + g.L * i] : (TC)0;
     }
   }
 }
@@ -257,10 +258,14 @@ __global__ void __launch_bounds__(256) k_gram_simt(const TIn* __restrict__ y, KG
     // first and only that block sum enters the chunk accumulator.  Squares
     // x^2 pile up near zero (chi-square), and adding them one by one to a
     // large FP32 sum rounds with a negative bias ~ (terms in the sum)^1.5;
-    // 16-term block sums have a smooth density and round without bias.
+    // 16-term block sums have a smooth density and round without bias.  The
+    // block runs from its last K to its first: in row mode its 16 l are
+    // consecutive indices of a truncated mode whose energy falls with l, so
+    // the products are added in increasing size.
     TC t[4][4];
 #pragma unroll
-    for (int kk = 0; kk < GBK; ++kk) {
+    for (int kq = 0; kq < GBK; ++kq) {
+      const int kk = GBK - 1 - kq;
       TC a[4], b[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) a[u] = As[kk][ty + 16 * u];
@@ -271,7 +276,7 @@ __global__ void __launch_bounds__(256) k_gram_simt(const TIn* __restrict__ y, KG
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           if constexpr (sizeof(TC) == 4)
-            t[u][v] = (kk == 0) ? a[u] * b[v] : fma(a[u], b[v], t[u][v]);
+            t[u][v] = (kq == 0) ? a[u] * b[v] : fma(a[u], b[v], t[u][v]);
           else
             acc[u][v] = fma(a[u], b[v], acc[u][v]);
         }
@@ -328,9 +333,9 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int ntiles, int k
   S[j * I + i] = s;
 }
 
-GramPlan plan_gram_simt(int64_t L, int64_t I, int64_t Rt, int num_sms) {
+GramPlan plan_gram_simt(int64_t L, int64_t I, int64_t Rt, int num_sms, int64_t L0) {
   GramPlan p;
-  KGeom g = make_kgeom(L, I, Rt, GBK);
+  KGeom g = make_kgeom(L, I, Rt, GBK, L0);
   int T = (int)((I + GT - 1) / GT);
   p.ntiles = T * (T + 1) / 2;
   int64_t want = ((int64_t)num_sms * 4 + p.ntiles - 1) / p.ntiles;
@@ -346,8 +351,8 @@ GramPlan plan_gram_simt(int64_t L, int64_t I, int64_t Rt, int num_sms) {
 // Same split as plan_gram_simt, with the partial-tile scratch held to at most
 // max_bytes (fewer K-splits).  ok == 0 when even one split does not fit.
 GramPlan plan_gram_simt_capped(int64_t L, int64_t I, int64_t Rt, int num_sms, size_t max_bytes,
-                               int* ok) {
-  GramPlan p = plan_gram_simt(L, I, Rt, num_sms);
+                               int* ok, int64_t L0) {
+  GramPlan p = plan_gram_simt(L, I, Rt, num_sms, L0);
   const size_t per_split = (size_t)p.ntiles * GT * GT * sizeof(double);
   *ok = per_split <= max_bytes;
   if (!*ok) return p;
@@ -359,9 +364,9 @@ GramPlan plan_gram_simt_capped(int64_t L, int64_t I, int64_t Rt, int num_sms, si
 }
 
 cudaError_t launch_gram_simt(const void* y, tucker_dtype dt, bool fp64, int64_t L, int64_t I,
-                             int64_t Rt, const GramPlan& p, double* scratch, double* S,
+                             int64_t Rt, int64_t L0, const GramPlan& p, double* scratch, double* S,
                              cudaStream_t st) {
-  KGeom g = make_kgeom(L, I, Rt, GBK);
+  KGeom g = make_kgeom(L, I, Rt, GBK, L0);
   dim3 grid(p.ntiles, p.ksplit);
   count_launches(2);
   if (dt == TUCKER_F64) {

@@ -158,7 +158,7 @@ class Result:
         self.threshold = r.threshold
         self.discarded = [r.discarded_sq[k] for k in range(N)]
         self.sweeps = [r.jacobi_sweeps[k] for k in range(N)]
-        names = {0: "simt-fp64", 1: "simt-fp32", 2: "tcgen05"}
+        names = {0: "simt-fp64", 1: "simt-fp32", 2: "tcgen05", 3: "small-fp64", 4: "simt-fp32c"}
         self.gram_kernel = [names.get(r.gram_kernel[k], "?") for k in range(N)]
         self.ttm_kernel = [names.get(r.ttm_kernel[k], "?") for k in range(N)]
         self.core_dtype = r.core_dtype

@@ -131,6 +131,50 @@ def test_gram_fp32_trace_unbiased(ctx, mode, decay):
     assert abs(got - want) <= (1e-9 if decay else 3e-10) * want, (got - want) / want
 
 
+@pytest.mark.parametrize("mode", [2, 3])
+def test_gram_fp32_trace_unbiased_two_decaying_modes(ctx, mode):
+    """Entries decaying geometrically along modes 0 and 1, as after two
+    truncated modes: the l index of modes 2 and 3 runs over (l0, l1) with
+    energy falling along each, so a K-block that crossed a multiple of J_0
+    would add the small tail of one l0 run after the large head of the next.
+    Blocks aligned to J_0 and summed smallest-first keep the trace within
+    1e-9 of the FP64 sum of squares, the bound of the one-mode decay case
+    (few rows carry the trace, so fewer rounding errors average out)."""
+    dims = (40, 40, 512, 200)
+    g = torch.Generator(device="cuda").manual_seed(5 + mode)
+    t = torch.randn(dims[::-1], generator=g, device="cuda", dtype=torch.float32)
+    t *= (0.8 ** torch.arange(40, device="cuda", dtype=torch.float32))
+    t *= (0.8 ** torch.arange(40, device="cuda", dtype=torch.float32)).view(40, 1)
+    t = t.reshape(-1)
+    want = float((t.double() ** 2).sum())
+    got = float(torch.trace(ctx.gram(t, dims, mode, "fp32")))
+    assert abs(got - want) <= 1e-9 * want, (got - want) / want
+
+
+def test_sharded_gram_sums_to_unsharded(ctx):
+    """A tensor split along its last mode over 2 ranks: the CUDA path's Grams
+    of the two shards, summed in rank order (the sharded design's only
+    exchange), equal the unsharded Gram and the oracle's, for every mode
+    n < N-1, with FP64 and with FP32 products."""
+    from paper_1901_06043_gb300 import shard
+    dims = (130, 40, 9, 6)
+    x = np.random.default_rng(11).standard_normal(oracle.linear_size(dims))
+    for dtype, prec, tol in [(torch.float64, "fp64", 1e-13), (torch.float32, "fp32", 1e-6)]:
+        t = dev(x, dtype)
+        xs = host(t)
+        for n in range(len(dims) - 1):
+            full = host(ctx.gram(t, dims, n, prec))
+            acc = None
+            for r in range(2):
+                a, b = shard.shard_slice(dims, 2, r)
+                part = host(ctx.gram(t[a:b], shard.shard_dims(dims, 2, r), n, prec))
+                acc = part if acc is None else acc + part
+            want = oracle.gram(xs, dims, n)
+            scale = np.abs(want).max() * math.log2(x.size)
+            assert np.abs(acc - want).max() <= tol * scale, (prec, n)
+            assert np.abs(acc - full).max() <= tol * scale, (prec, n)
+
+
 MIXED_GRAM_SHAPES = [(64, 300), (128, 2000), (500, 700), (256, 33, 7), (132, 100), (1024, 90),
                      (96, 64)]
 
