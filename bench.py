@@ -349,8 +349,11 @@ FP64_PEAK_TFLOPS = 1.19   # measured FP64 FMA throughput on this part (in-regist
 # with I x K.  Only kernels whose source has not changed since the capture.
 CAPTURED_TRAFFIC = {
     # k_gram_f32<LD_COL16>, mode-0 Gram of 500x500x40x11x2 FP32
-    ("gram", "simt-fp32", "col"): dict(bytes=912.2e6, elems=500 * 440000,
+    ("gram", "simt-fp32", "col"): dict(bytes=1700.2e6, elems=500 * 440000,
                                         src="profiles/k_gram_f32_col_prof_500x500x40x11x2.md"),
+    # k_ttm_tc_col, mode-0 TTM of 500x500x40x11x2 FP32 to 54 rows
+    ("ttm", "tcgen05", "col"): dict(bytes=964.7e6, elems=500 * 440000,
+                                    src="profiles/k_ttm_tc_col_prof_500x500x40x11x2.md"),
 }
 
 
