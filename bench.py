@@ -34,17 +34,19 @@ if ROOT not in sys.path:
 METRIC = "ST-HOSVD input GB/s at eps=1e-4, mixed vs FP64 path; Gram/TTM % of roofline"
 
 WORKLOADS = {
+    # recon: the subtensor [0, end) rebuilt by multi-TTM in every step
     "large": dict(dims=(500, 500, 500, 11, 8), core=(60, 60, 60, 11, 6), decay=0.08, eta=1e-7,
-                  eps=1e-4, dtype="f32"),
+                  eps=1e-4, dtype="f32", recon=(500, 500, 500, 11, 1)),
     "c256": dict(dims=(256, 256, 256, 11, 32), core=(40, 40, 40, 11, 16), decay=0.1, eta=1e-7,
-                 eps=1e-4, dtype="f32"),
+                 eps=1e-4, dtype="f32", recon=(256, 256, 256, 11, 1)),
     "c200": dict(dims=(200, 200, 200, 50), core=(30, 30, 30, 12), decay=0.15, eta=1e-6,
-                 eps=1e-4, dtype="f64"),
-    "small": dict(dims=(40, 50, 30), core=(5, 6, 4), decay=0.0, eta=1e-4, eps=1e-3, dtype="f64"),
+                 eps=1e-4, dtype="f64", recon=(200, 200, 200, 1)),
+    "small": dict(dims=(40, 50, 30), core=(5, 6, 4), decay=0.0, eta=1e-4, eps=1e-3, dtype="f64",
+                  recon=(40, 50, 30)),
     # the large workload's first two time steps and 40 of its 500 mode-2
     # slices: a 0.9 GB case of the same kernels for profiler captures
     "prof": dict(dims=(500, 500, 40, 11, 2), core=(60, 60, 40, 11, 2), decay=0.08, eta=1e-7,
-                 eps=1e-4, dtype="f32"),
+                 eps=1e-4, dtype="f32", recon=(500, 500, 40, 11, 1)),
 }
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 x max clock
@@ -170,11 +172,34 @@ def cpu_sample(x_dev, w, frac_slices):
     return sub.reshape(-1).double().cpu().numpy(), sdims
 
 
-def run_cpu_oracle(xs, sdims, eps):
+def run_cpu_oracle(xs, sdims, eps, recon_frac=None):
+    """The oracle's step on the sample: ST-HOSVD, then the multi-TTM of a
+    subtensor of the same relative size as the GPU step's (recon_frac: the
+    fraction of the tensor the GPU step rebuilds, taken along mode 2 of the
+    sample)."""
     import oracle
     t0 = time.perf_counter()
     res = oracle.sthosvd(xs, sdims, eps=eps)
+    if recon_frac is not None:
+        end = list(sdims)
+        k = 2 if len(sdims) > 2 else 0
+        end[k] = max(1, int(round(sdims[k] * recon_frac)))
+        oracle.reconstruct(res["core"], res["core_dims"], res["factors"], (0,) * len(sdims), tuple(end))
     return time.perf_counter() - t0, res
+
+
+def recon_frac(w):
+    return float(np.prod(w["recon"])) / float(np.prod(w["dims"]))
+
+
+def step(ctx, x, w, prec):
+    """One pass of the hot path: ST-HOSVD (Algorithm 1) and the multi-TTM
+    reconstruction (Section 7) of the workload's subtensor; returns the
+    result (the reconstructed subtensor stays on the device)."""
+    r = ctx.sthosvd(x, w["dims"], eps=w["eps"], prec=prec)
+    rec = r.reconstruct((0,) * len(w["dims"]), w["recon"], prec=prec)
+    del rec
+    return r
 
 
 def blas_threads():
@@ -193,7 +218,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large")
-    ap.add_argument("--prec", choices=["mixed", "fp32", "fp64"], default=None)
+    ap.add_argument("--prec", choices=["mixed", "fp32", "fp64", "tensor"], default=None)
     ap.add_argument("--no-fp64", action="store_true", help="skip the one-step FP64-path leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -232,9 +257,9 @@ def main():
         xs, sdims = cpu_sample(x, w, cpu_slices or (w["dims"][2] if N >= 3 else None))
         del x
         for _ in range(args.warmup):
-            run_cpu_oracle(xs, sdims, w["eps"])
+            run_cpu_oracle(xs, sdims, w["eps"], recon_frac(w))
         for _ in range(args.steps):
-            t, _ = run_cpu_oracle(xs, sdims, w["eps"])
+            t, _ = run_cpu_oracle(xs, sdims, w["eps"], recon_frac(w))
             ref_ms.append(t * 1e3)
         ms = statistics.mean(ref_ms)
         sbytes = xs.size * (4 if w["dtype"] == "f32" else 8)
@@ -261,7 +286,17 @@ def main():
             last.close()
         last = ctx_t.sthosvd(x, w["dims"], eps=w["eps"], prec=prec)
     ranks = last.ranks
-    ms_detail = last.ms
+    ms_detail = dict(last.ms)
+    # the reconstruction's own time (CUDA events on the library's stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    rec = last.reconstruct((0,) * len(w["dims"]), w["recon"], prec=prec)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_detail["recon"] = e0.elapsed_time(e1)
+    rec_bytes = rec.numel() * rec.element_size()
+    del rec
     pk = peaks()
     dom, step_rows = dominant(last, w, pk)
     last.close()
@@ -275,7 +310,7 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     for _ in range(args.steps):
-        r = ctx.sthosvd(x, w["dims"], eps=w["eps"], prec=prec)
+        r = step(ctx, x, w, prec)
         r.close()
     ev1.record()
     torch.cuda.synchronize()
@@ -294,11 +329,14 @@ def main():
                    "l2": "input larger than L2 (no flush)", "ranks": list(ranks),
                    "parallelism": f"replicas x{ws}"},
         "roofline": dom,
+        "step": "ST-HOSVD (norm, Gram, eigensolve, rank cut, TTM per mode) + multi-TTM "
+                f"reconstruction of the [0, {'x'.join(map(str, w['recon']))}) subtensor",
         "gpu_launches": int(launches),
         "clocks": clk,
         "per_mode_ms": {k: v for k, v in ms_detail.items()},
         "steps_roofline": [{k: r[k] for k in ("kernel", "ms", "bound", "achieved", "unit", "frac")}
-                           for r in step_rows],
+                           for r in step_rows] +
+                          [recon_roofline(ranks, w, ms_detail["recon"], rec_bytes, prec, pk)],
     }
 
     if rank == 0 and not args.no_e2e:
@@ -307,7 +345,7 @@ def main():
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record()
-        r64 = ctx_t.sthosvd(x, w["dims"], eps=w["eps"], prec="fp64")
+        r64 = step(ctx_t, x, w, "fp64")
         t1.record()
         torch.cuda.synchronize()
         ms64 = t0.elapsed_time(t1)
@@ -318,14 +356,15 @@ def main():
         r64.close()
     if rank == 0 and not args.no_cpu:
         xs, sdims = cpu_sample(x, w, cpu_slices if N >= 3 else None)
-        t, _ = run_cpu_oracle(xs, sdims, w["eps"])
+        t, _ = run_cpu_oracle(xs, sdims, w["eps"], recon_frac(w))
         sbytes = xs.size * (4 if w["dtype"] == "f32" else 8)
         out["cpu_baseline"] = {
             "value": sbytes / 1e9 / t, "unit": "GB/s", "cores": len(os.sched_getaffinity(0)),
             "blas_threads": blas_threads(), "kind": "oracle",
             "sample": (f"FP64 numpy oracle ST-HOSVD (Algorithm 1-3, eps {w['eps']:g}) of the "
                        f"{'x'.join(map(str, sdims))} sub-tensor of the workload "
-                       f"({sbytes / 1e9:.2f} GB as {w['dtype']}), {t:.1f} s")}
+                       f"({sbytes / 1e9:.2f} GB as {w['dtype']}) and the multi-TTM of "
+                       f"{recon_frac(w):.3g} of it, {t:.1f} s")}
     if rank == 0:
         print(json.dumps(out))
     ctx.close()
@@ -403,6 +442,24 @@ def step_rooflines(res, w, pk):
     return out
 
 
+def recon_roofline(ranks, w, ms, out_bytes, prec, pk):
+    """The multi-TTM reconstruction of the step: its flops under the chain
+    order the library picks (sum over the chain of 2 x output elements x
+    contracted rank), against the FP32 (or FP64) SIMT peak."""
+    from paper_1901_06043_gb300 import tucker
+    order = tucker.ttm_order(ranks, w["recon"], "flops")
+    cur = list(ranks)
+    flops = 0.0
+    for n in order:
+        cur[n] = w["recon"][n]
+        flops += 2.0 * float(np.prod(cur)) * ranks[n]
+    peak = FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS
+    ach = flops / (ms / 1e3) / 1e12
+    return {"kernel": f"multi-TTM reconstruction (order {list(order)})", "ms": ms, "bound": "alu",
+            "achieved": ach, "unit": "TFLOP/s", "frac": ach / peak,
+            "hbm_gbs_achieved": out_bytes / (ms / 1e3) / 1e9}
+
+
 def dominant(res, w, pk):
     """The longest step's roofline entry."""
     rows = step_rooflines(res, w, pk)
@@ -410,8 +467,9 @@ def dominant(res, w, pk):
 
 
 def e2e_leg(ctx, x, w, prec, args):
-    """Same metric end to end: pinned host input -> device copy -> ST-HOSVD
-    through the C ABI -> core and factors back to the host, per step."""
+    """Same metric end to end: pinned host input -> device copy -> the step
+    through the C ABI (ST-HOSVD and the subtensor reconstruction, which stays
+    on the device) -> core and factors back to the host, per step."""
     import torch
     try:
         xh = torch.empty(x.numel(), dtype=x.dtype, pin_memory=True)
@@ -427,7 +485,7 @@ def e2e_leg(ctx, x, w, prec, args):
     t0 = time.perf_counter()
     for _ in range(steps):
         xd.copy_(xh, non_blocking=True)
-        r = ctx.sthosvd(xd, w["dims"], eps=w["eps"], prec=prec)
+        r = step(ctx, xd, w, prec)
         core, fac = r.to_host()
         d2h = core.nbytes + sum(f.nbytes for f in fac)
         r.close()
