@@ -101,6 +101,7 @@ typedef struct tucker_result {
   int jacobi_sweeps[TUCKER_MAX_MODES];
   int gram_kernel[TUCKER_MAX_MODES]; /* kernel that ran: 0 SIMT FP64, 1 SIMT FP32, 2 tcgen05 */
   int ttm_kernel[TUCKER_MAX_MODES];
+  int eig_kernel[TUCKER_MAX_MODES];  /* 0 Jacobi, 1 tridiagonal + inverse iteration          */
   float ms_norm;                     /* device time per step (CUDA events), ms         */
   float ms_gram[TUCKER_MAX_MODES];
   float ms_eig[TUCKER_MAX_MODES];
@@ -118,10 +119,15 @@ const char* tucker_last_error(const tucker_ctx* ctx);
 /* Options (key, value):
  *   TUCKER_OPT_TIMING      1 = record per-step CUDA-event times into results
  *   TUCKER_OPT_MAX_SWEEPS  Jacobi sweep cap (default 40; 0 = no sweep)
- *   TUCKER_OPT_JACOBI_TOL  relative off-diagonal tolerance (default 1e-15) */
+ *   TUCKER_OPT_JACOBI_TOL  relative off-diagonal tolerance (default 1e-15)
+ *   TUCKER_OPT_EIG_SOLVER  eigensolver of the truncation step (tucker_sthosvd,
+ *                          tucker_eig_trunc): 0 auto (tridiagonal for
+ *                          64 <= I <= 4096, Jacobi otherwise), 1 Jacobi,
+ *                          2 tridiagonal for every I <= 4096 */
 #define TUCKER_OPT_TIMING 1
 #define TUCKER_OPT_MAX_SWEEPS 2
 #define TUCKER_OPT_JACOBI_TOL 3
+#define TUCKER_OPT_EIG_SOLVER 4
 tucker_status tucker_set_option(tucker_ctx* ctx, int key, double value);
 
 /* Diagnostics: number of device kernels this library has launched in the
@@ -198,6 +204,21 @@ tucker_status tucker_gram(tucker_ctx* ctx, const void* y_dev, tucker_dtype dtype
  * Synchronises.  EIG_NOCONV if the sweep cap was reached. */
 tucker_status tucker_eig(tucker_ctx* ctx, const double* S_dev, int64_t I,
                          double* eigvals_dev, double* V_dev, int* sweeps_host);
+
+/* Truncated eigensolve, the eigenvalue step of Algorithm 1 (Section 5.2;
+ * rank cut of Eq. Un): all eigenvalues of the symmetric I x I FP64 matrix S
+ * into eigvals_dev (I, descending), then R = the cut at thr (as in
+ * tucker_rank_cut) or R = fixed_R when fixed_R > 0, and the R leading
+ * orthonormal eigenvectors into U_dev (caller-owned, capacity I x I doubles;
+ * the first I x R hold them, column-major).  Solver per
+ * TUCKER_OPT_EIG_SOLVER: the tridiagonal one is Householder reduction,
+ * bisection, inverse iteration and a Cholesky QR, with Jacobi taken instead
+ * if that QR finds the vectors nearly dependent.  1 <= I <= 8192,
+ * 0 <= fixed_R <= I, thr >= 0.  Synchronises; *R_host and *discarded_host =
+ * tail(R).  EIG_NOCONV as tucker_eig when Jacobi ran and hit its cap. */
+tucker_status tucker_eig_trunc(tucker_ctx* ctx, const double* S_dev, int64_t I, double thr,
+                               int64_t fixed_R, double* eigvals_dev, double* U_dev,
+                               int64_t* R_host, double* discarded_host);
 
 /* Rank cut of Eq. Un on descending eigenvalues: R = min{R in 1..I :
  * sum_{i>=R} lambda_i <= thr}, the signed computed eigenvalues accumulated

@@ -26,6 +26,7 @@ struct tucker_ctx {
   int max_sweeps = 40;
   double tol_rel = 1e-15;
   double tol_abs = 1e-15;
+  int eig_solver = 0;            // 0 auto, 1 Jacobi, 2 tridiagonal
   std::string err;
   // small device scratch
   unsigned* d_words = nullptr;   // 256 words
@@ -280,6 +281,89 @@ tucker_status do_eig(tucker_ctx* c, const double* S, int n, double* w, double* V
   return TUCKER_OK;
 }
 
+// Whether the truncated eigensolve of an n x n Gram takes the tridiagonal
+// solver: from n = 64 up (below that a Jacobi sweep costs little), up to the
+// size whose three work vectors fit in shared memory.
+bool use_tridiag(const tucker_ctx* c, int n) {
+  if (c->eig_solver == 1) return false;
+  if (c->eig_solver == 2) return n >= 1 && n <= 4096;
+  return n >= 64 && n <= 4096;
+}
+
+// All eigenvalues (descending, into w) and the leading R eigenvectors of S by
+// the tridiagonal solver (tridiag.cu); R from the cut at thr, or fixed_R > 0.
+// U is allocated here (I x R, column-major).  *failed: the Cholesky QR
+// rejected the inverse-iteration vectors (the caller then takes Jacobi); w,
+// R and the discarded sum are valid either way.
+tucker_status do_eig_tri(tucker_ctx* c, const double* S, int n, double thr, int fixed_R,
+                         double* w, DevBuf& U, int64_t* R_out, double* disc, bool* failed) {
+  const int G = tridiag_team_size(n, c->num_sms);
+  const size_t nn = (size_t)n * n;
+  const size_t ndbl = nn + 3 * (size_t)n + 4 * (size_t)n + 2 * (size_t)G + (size_t)n + 1;
+  DevBuf work;
+  TK_TRY(dev_alloc(c, work, sizeof(double) * ndbl + sizeof(EigProblem) + 16));
+  EigProblem h{};
+  h.A = work.as<double>();
+  h.d = h.A + nn;
+  h.e = h.d + n;
+  h.tau = h.e + n;
+  h.xch = h.tau + n;
+  double* tail = h.xch + 4 * (size_t)n + 2 * (size_t)G;
+  EigProblem* pd = reinterpret_cast<EigProblem*>(tail + n + 1);
+  int* info = reinterpret_cast<int*>(pd + 1);
+  h.w = w;
+  h.info = info;
+  h.n = n;
+  cudaStream_t st = c->stream;
+  TK_CUDA(c, cudaMemcpyAsync(h.A, S, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
+  TK_CUDA(c, cudaMemsetAsync(c->d_words + 32, 0, sizeof(unsigned) * 3, st));
+  TK_CUDA(c, cudaMemsetAsync(info, 0, sizeof(int), st));
+  TK_CUDA(c, cudaMemcpyAsync(pd, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+  const GridBarrier bar{c->d_words + 32, c->d_words + 33, c->d_words + 34};
+  TK_CUDA(c, launch_tridiag(pd, 1, n, true, c->num_sms, bar, st));
+  TK_CUDA(c, launch_bisect(pd, 1, n, st));
+  TK_CUDA(c, launch_rank_cut(w, n, thr, fixed_R, c->d_i64, c->d_small + 2, tail, st));
+  int64_t R = 0;
+  unsigned werr = 0;
+  TK_CUDA(c, cudaMemcpyAsync(&R, c->d_i64, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  TK_CUDA(c, cudaMemcpyAsync(disc, c->d_small + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+  TK_CUDA(c, cudaMemcpyAsync(&werr, c->d_words + 34, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  TK_TRY(sync(c));
+  if (werr & DEV_ERR_BARRIER_TIMEOUT)
+    return set_err(c, TUCKER_ERR_CUDA, "tridiagonalization grid barrier gave up waiting");
+  if (R < 1 || R > n) return set_err(c, TUCKER_ERR_CUDA, "rank cut returned an invalid rank");
+  *R_out = R;
+  const int Ri = (int)R;
+  TK_TRY(dev_alloc(c, U, sizeof(double) * (size_t)n * Ri));
+  DevBuf vec;
+  const size_t zb = sizeof(double) * (size_t)n * Ri, gb = sizeof(double) * (size_t)Ri * Ri;
+  TK_TRY(dev_alloc(c, vec, zb + gb + eig_lu_bytes(n, Ri)));
+  h.z = vec.as<double>();
+  h.gram = h.z + (size_t)n * Ri;
+  h.lu = h.gram + (size_t)Ri * Ri;
+  h.U = U.as<double>();
+  h.R = Ri;
+  h.zoff = 0;
+  h.roff = 0;
+  TK_CUDA(c, cudaMemcpyAsync(pd, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+  TK_CUDA(c, launch_invit(pd, 1, Ri, st));
+  // Cholesky QR, twice (the second pass restores orthogonality to rounding
+  // when eigenvalues are clustered and the vectors are far from orthogonal).
+  // Z^T Z is the Gram of the column-major view of Z (L = 1, I = R, Rt = n).
+  const SlabView zv{1, (int64_t)Ri, (int64_t)n, 1};
+  for (int pass = 0; pass < 2; ++pass) {
+    TK_TRY(do_gram(c, h.z, TUCKER_F64, zv, TUCKER_PREC_FP64, h.gram, nullptr));
+    TK_CUDA(c, launch_chol(pd, 1, st));
+    TK_CUDA(c, launch_trsm_rows(pd, 1, n, st));
+  }
+  TK_CUDA(c, launch_backtransform(pd, 1, Ri, n, st));
+  int hinfo = 0;
+  TK_CUDA(c, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TK_TRY(sync(c));
+  *failed = hinfo != 0;
+  return TUCKER_OK;
+}
+
 tucker_status do_cut(tucker_ctx* c, const double* w, int n, double thr, int fixed_R, int64_t* R,
                      double* disc) {
   DevBuf tail;
@@ -411,6 +495,11 @@ tucker_status tucker_set_option(tucker_ctx* c, int key, double value) {
       if (value < 0 || value > 200) return set_err(c, TUCKER_ERR_INVALID, "sweep cap out of [0, 200]");
       c->max_sweeps = (int)value;
       return TUCKER_OK;
+    case TUCKER_OPT_EIG_SOLVER:
+      if (value != 0.0 && value != 1.0 && value != 2.0)
+        return set_err(c, TUCKER_ERR_INVALID, "eigensolver must be 0 (auto), 1 or 2");
+      c->eig_solver = (int)value;
+      return TUCKER_OK;
     case TUCKER_OPT_JACOBI_TOL:
       if (!(value > 0.0 && value < 1e-3)) return set_err(c, TUCKER_ERR_INVALID, "tolerance out of (0, 1e-3)");
       c->tol_rel = value;
@@ -447,6 +536,34 @@ tucker_status tucker_eig(tucker_ctx* c, const double* S, int64_t I, double* w, d
   if (!S || !w || !V || I < 1 || I > 8192)
     return set_err(c, TUCKER_ERR_INVALID, "tucker_eig: bad argument");
   return do_eig(c, S, (int)I, w, V, sweeps);
+}
+
+tucker_status tucker_eig_trunc(tucker_ctx* c, const double* S, int64_t I, double thr,
+                               int64_t fixed_R, double* w, double* U, int64_t* R, double* disc) {
+  if (!c) return TUCKER_ERR_INVALID;
+  if (!S || !w || !U || !R || !disc || I < 1 || I > 8192 || !(thr >= 0.0) || fixed_R < 0 ||
+      fixed_R > I)
+    return set_err(c, TUCKER_ERR_INVALID, "tucker_eig_trunc: bad argument");
+  const int n = (int)I;
+  if (use_tridiag(c, n)) {
+    DevBuf Ub;
+    bool failed = false;
+    TK_TRY(do_eig_tri(c, S, n, thr, (int)fixed_R, w, Ub, R, disc, &failed));
+    if (!failed) {
+      TK_CUDA(c, cudaMemcpyAsync(U, Ub.p, sizeof(double) * n * (*R), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+      return sync(c);
+    }
+  }
+  DevBuf V;
+  TK_TRY(dev_alloc(c, V, sizeof(double) * (size_t)n * n));
+  tucker_status es = do_eig(c, S, n, w, V.as<double>(), nullptr);
+  if (es != TUCKER_OK && es != TUCKER_ERR_EIG_NOCONV) return es;
+  TK_TRY(do_cut(c, w, n, thr, (int)fixed_R, R, disc));
+  TK_CUDA(c, cudaMemcpyAsync(U, V.p, sizeof(double) * n * (*R), cudaMemcpyDeviceToDevice,
+                             c->stream));
+  TK_TRY(sync(c));
+  return es;
 }
 
 tucker_status tucker_rank_cut(tucker_ctx* c, const double* w, int64_t I, double thr, int64_t* R,
@@ -556,25 +673,36 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
     TK_TRY(do_gram(c, y, ydt, v, gram_prec, S.as<double>(), &r->gram_kernel[n],
                    s == 0 ? xmax : -1.0));
     tmg.stop(c);
-    DevBuf w;
+    DevBuf w, U;
     TK_TRY(dev_alloc(c, w, sizeof(double) * I));
     tme.start(c);
     int sweeps = 0;
-    tucker_status es = do_eig(c, S.as<double>(), I, w.as<double>(), V.as<double>(), &sweeps);
-    tme.stop(c);
-    if (es != TUCKER_OK && es != TUCKER_ERR_EIG_NOCONV) return es;
-    r->jacobi_sweeps[n] = sweeps;
     int64_t R = 0;
     double disc = 0.0;
-    TK_TRY(do_cut(c, w.as<double>(), I, thr, ranks ? (int)ranks[n] : 0, &R, &disc));
+    tucker_status es = TUCKER_OK;
+    bool have = false;
+    const int fixed_R = ranks ? (int)ranks[n] : 0;
+    if (use_tridiag(c, I)) {
+      bool failed = false;
+      TK_TRY(do_eig_tri(c, S.as<double>(), I, thr, fixed_R, w.as<double>(), U, &R, &disc, &failed));
+      have = !failed;
+      r->eig_kernel[n] = 1;
+    }
+    if (!have) {
+      es = do_eig(c, S.as<double>(), I, w.as<double>(), V.as<double>(), &sweeps);
+      if (es != TUCKER_OK && es != TUCKER_ERR_EIG_NOCONV) return es;
+      TK_TRY(do_cut(c, w.as<double>(), I, thr, fixed_R, &R, &disc));
+      TK_TRY(dev_alloc(c, U, sizeof(double) * I * R));
+      TK_CUDA(c, cudaMemcpyAsync(U.p, V.p, sizeof(double) * I * R, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+      r->eig_kernel[n] = 0;
+    }
+    tme.stop(c);
+    r->jacobi_sweeps[n] = sweeps;
     r->ranks[n] = R;
     r->discarded_sq[n] = disc;
     r->eigvals[n] = w.as<double>();
     w.release();
-    DevBuf U;
-    TK_TRY(dev_alloc(c, U, sizeof(double) * I * R));
-    TK_CUDA(c, cudaMemcpyAsync(U.p, V.p, sizeof(double) * I * R, cudaMemcpyDeviceToDevice,
-                               c->stream));
     r->factors[n] = U.as<double>();
     U.release();
     // Y <- Y x_n U_n^T : A = U^T is U's column-major storage read row-major

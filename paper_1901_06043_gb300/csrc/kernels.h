@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "tucker_gb300.h"
+#include "common.cuh"
 
 namespace tk {
 
@@ -75,5 +76,37 @@ cudaError_t launch_eig_finish(int n, double* work, const int* info_host, int* in
                               double* w_out, double* V_out, cudaStream_t st);
 cudaError_t launch_rank_cut(const double* w, int n, double thr, int fixed_R, int64_t* out_R,
                             double* out_d, double* tail, cudaStream_t st);
+
+// ---- tridiagonal eigensolver (tridiag.cu): all eigenvalues, the leading R
+// eigenvectors.  One descriptor per matrix (device array of descriptors).
+struct EigProblem {
+  double* A;      // n x n row-major symmetric input copy; overwritten with the reflectors
+  double* d;      // n: diagonal of T
+  double* e;      // n: off-diagonal of T (e[k] = T[k+1][k])
+  double* tau;    // n: reflector scalars
+  double* xch;    // 4 n + 2 G: exchange buffers of the team reduction (G CTAs)
+  double* w;      // n: eigenvalues, descending
+  double* z;      // n x R row-major: eigenvectors of T, then their QR factor
+  double* lu;     // inverse-iteration factors: 4 n R doubles + 2 n R bytes
+  double* gram;   // R x R
+  double* U;      // n x R column-major output
+  int* info;      // 0 ok; 1 / 2 the Cholesky QR failed (see k_chol)
+  int n, R;
+  int zoff;       // first flattened vector index of this problem
+  int roff;       // first flattened row index of this problem
+};
+size_t tridiag_smem_bytes(int n);
+int tridiag_team_size(int n, int num_sms);
+inline size_t eig_lu_bytes(int n, int R) { return (size_t)n * R * (4 * sizeof(double) + 2); }
+// grid = true: one problem on a cooperative grid of tridiag_team_size CTAs;
+// false: `count` problems, one CTA each
+cudaError_t launch_tridiag(const EigProblem* probs_dev, int count, int nmax, bool grid,
+                           int num_sms, GridBarrier bar, cudaStream_t st);
+cudaError_t launch_bisect(const EigProblem* probs_dev, int count, int nmax, cudaStream_t st);
+cudaError_t launch_invit(const EigProblem* probs_dev, int count, int total_vectors, cudaStream_t st);
+cudaError_t launch_chol(const EigProblem* probs_dev, int count, cudaStream_t st);
+cudaError_t launch_trsm_rows(const EigProblem* probs_dev, int count, int total_rows, cudaStream_t st);
+cudaError_t launch_backtransform(const EigProblem* probs_dev, int count, int total_vectors,
+                                 int nmax, cudaStream_t st);
 
 }  // namespace tk

@@ -20,13 +20,14 @@ STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "NONFINITE", 4: "EIG_NOCONV", 5: "
           6: "UNSUPPORTED"}
 F32, F64 = 0, 1
 PREC = {"fp64": 0, "fp32": 1, "mixed": 2, "tensor": 3}
-OPT_TIMING, OPT_MAX_SWEEPS, OPT_JACOBI_TOL = 1, 2, 3
+OPT_TIMING, OPT_MAX_SWEEPS, OPT_JACOBI_TOL, OPT_EIG_SOLVER = 1, 2, 3, 4
+EIG_SOLVER = {"auto": 0, "jacobi": 1, "tridiag": 2}
 
 EXPORTS = ["tucker_create", "tucker_destroy", "tucker_last_error", "tucker_set_option",
            "tucker_sthosvd", "tucker_result_destroy", "tucker_reconstruct",
            "tucker_multi_ttm", "tucker_ttm_order", "tucker_norm_sq", "tucker_gram",
-           "tucker_eig", "tucker_rank_cut", "tucker_ttm", "tucker_kernel_launches",
-           "tucker_gram_noalloc"]
+           "tucker_eig", "tucker_eig_trunc", "tucker_rank_cut", "tucker_ttm",
+           "tucker_kernel_launches", "tucker_gram_noalloc"]
 
 
 class TuckerError(RuntimeError):
@@ -52,6 +53,7 @@ class CResult(ctypes.Structure):
         ("jacobi_sweeps", ctypes.c_int * MAX_MODES),
         ("gram_kernel", ctypes.c_int * MAX_MODES),
         ("ttm_kernel", ctypes.c_int * MAX_MODES),
+        ("eig_kernel", ctypes.c_int * MAX_MODES),
         ("ms_norm", ctypes.c_float),
         ("ms_gram", ctypes.c_float * MAX_MODES),
         ("ms_eig", ctypes.c_float * MAX_MODES),
@@ -87,6 +89,8 @@ def lib():
         L.tucker_norm_sq.argtypes = [vp, vp, c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]
         L.tucker_gram.argtypes = [vp, vp, c_int, c_int, i64p, c_int, c_int, vp]
         L.tucker_eig.argtypes = [vp, vp, ctypes.c_int64, vp, vp, ctypes.POINTER(c_int)]
+        L.tucker_eig_trunc.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_double, ctypes.c_int64,
+                                       vp, vp, i64p, ctypes.POINTER(ctypes.c_double)]
         L.tucker_rank_cut.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_double, i64p,
                                       ctypes.POINTER(ctypes.c_double)]
         L.tucker_ttm.argtypes = [vp, vp, c_int, c_int, i64p, c_int, vp, ctypes.c_int64,
@@ -161,6 +165,7 @@ class Result:
         names = {0: "simt-fp64", 1: "simt-fp32", 2: "tcgen05", 3: "small-fp64", 4: "simt-fp32c"}
         self.gram_kernel = [names.get(r.gram_kernel[k], "?") for k in range(N)]
         self.ttm_kernel = [names.get(r.ttm_kernel[k], "?") for k in range(N)]
+        self.eig_kernel = [{0: "jacobi", 1: "tridiag"}.get(r.eig_kernel[k], "?") for k in range(N)]
         self.core_dtype = r.core_dtype
         self.ms = {"norm": r.ms_norm, "total": r.ms_total,
                    "gram": [r.ms_gram[k] for k in range(N)],
@@ -334,6 +339,24 @@ class Context:
                                      ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(Vt.data_ptr()),
                                      ctypes.byref(sw)))
         return w, Vt.t(), sw.value
+
+    def eig_trunc(self, S, thr=0.0, R=0):
+        """All eigenvalues (descending) and the leading R eigenvectors (torch
+        (I, R)) of S; R from the cut at thr, or given.  Returns (w, U, R,
+        discarded)."""
+        import torch
+        _check_dev(S, "S")
+        I = S.shape[0]
+        w = torch.empty(I, dtype=torch.float64, device="cuda")
+        Ut = torch.empty((I, I), dtype=torch.float64, device="cuda")
+        Rv, d = ctypes.c_int64(), ctypes.c_double()
+        self._check(lib().tucker_eig_trunc(self._c, ctypes.c_void_p(S.data_ptr()), I, float(thr),
+                                           int(R), ctypes.c_void_p(w.data_ptr()),
+                                           ctypes.c_void_p(Ut.data_ptr()), ctypes.byref(Rv),
+                                           ctypes.byref(d)))
+        k = Rv.value
+        U = Ut.view(-1)[:I * k].view(k, I).t()
+        return w, U, k, d.value
 
     def rank_cut(self, w, thr):
         R, d = ctypes.c_int64(), ctypes.c_double()
