@@ -299,7 +299,8 @@ tucker_status do_eig_tri(tucker_ctx* c, const double* S, int n, double thr, int 
                          double* w, DevBuf& U, int64_t* R_out, double* disc, bool* failed) {
   const int G = tridiag_team_size(n, c->num_sms);
   const size_t nn = (size_t)n * n;
-  const size_t ndbl = nn + 3 * (size_t)n + 4 * (size_t)n + 2 * (size_t)G + (size_t)n + 1;
+  const size_t nwy = eig_wy_doubles(n);
+  const size_t ndbl = nn + 3 * (size_t)n + 4 * (size_t)n + 2 * (size_t)G + (size_t)n + 1 + nwy;
   DevBuf work;
   TK_TRY(dev_alloc(c, work, sizeof(double) * ndbl + sizeof(EigProblem) + 16));
   EigProblem h{};
@@ -309,7 +310,8 @@ tucker_status do_eig_tri(tucker_ctx* c, const double* S, int n, double thr, int 
   h.tau = h.e + n;
   h.xch = h.tau + n;
   double* tail = h.xch + 4 * (size_t)n + 2 * (size_t)G;
-  EigProblem* pd = reinterpret_cast<EigProblem*>(tail + n + 1);
+  h.wyT = tail + n + 1;
+  EigProblem* pd = reinterpret_cast<EigProblem*>(h.wyT + nwy);
   int* info = reinterpret_cast<int*>(pd + 1);
   h.w = w;
   h.info = info;

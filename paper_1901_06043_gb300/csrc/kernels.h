@@ -90,6 +90,7 @@ struct EigProblem {
   double* lu;     // inverse-iteration factors: 4 n R doubles + 2 n R bytes
   double* gram;   // R x R
   double* U;      // n x R column-major output
+  double* wyT;    // eig_wy_doubles(n): T factors of the blocked back-transformation
   int* info;      // 0 ok; 1 / 2 the Cholesky QR failed (see k_chol)
   int n, R;
   int zoff;       // first flattened vector index of this problem
@@ -98,6 +99,7 @@ struct EigProblem {
 size_t tridiag_smem_bytes(int n);
 int tridiag_team_size(int n, int num_sms);
 inline size_t eig_lu_bytes(int n, int R) { return (size_t)n * R * (4 * sizeof(double) + 2); }
+size_t eig_wy_doubles(int n);
 // grid = true: one problem on a cooperative grid of tridiag_team_size CTAs;
 // false: `count` problems, one CTA each
 cudaError_t launch_tridiag(const EigProblem* probs_dev, int count, int nmax, bool grid,

@@ -51,50 +51,71 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Sum over the CTA, returned to every thread, in a fixed order.  `red` holds
-// TNW doubles; consecutive calls must alternate between two buffers.
+// FP64 instructions occupy a sub-partition's FP64 pipe for ~64 cycles per
+// warp whatever they compute, so scalar work that every thread needs is done
+// by warp 0 and broadcast through shared memory.
+
+// Sum over the CTA, in a fixed order, returned to every thread.  `red` holds
+// TNW + 1 doubles; consecutive calls must alternate between two buffers.
 __device__ __forceinline__ double block_sum(double v, double* red) {
   v = warp_sum(v);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double s = red[0];
+  if (threadIdx.x < 32) {
+    double t = (threadIdx.x < TNW) ? red[threadIdx.x] : 0.0;
 #pragma unroll
-  for (int i = 1; i < TNW; ++i) s += red[i];
-  return s;
+    for (int o = TNW / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) red[TNW] = t;
+  }
+  __syncthreads();
+  return red[TNW];
 }
 
 // Householder reflector (Golub & Van Loan Alg. 5.1.1, with the sign of beta
 // opposite to alpha): for x = vx[k2..n-1] (alpha = x[k2]) find v (v[k2] = 1),
 // tau and beta with (I - tau v v^T) x = beta e_1.  Written in place into vx.
-// All threads of the CTA call it and return the same tau and beta.
+// All threads of the CTA call it and return the same tau and beta.  `red`
+// holds TNW + 4 doubles.
 __device__ void house(double* vx, int k2, int n, double* red, double& tau, double& beta) {
-  const double alpha = vx[k2];
   double s = 0.0;
   for (int j = k2 + 1 + threadIdx.x; j < n; j += TNT) s = fma(vx[j], vx[j], s);
-  const double sigma2 = block_sum(s, red);
-  if (sigma2 == 0.0) {
-    tau = 0.0;
-    beta = alpha;
-    __syncthreads();
-    if (threadIdx.x == 0) vx[k2] = 1.0;
-    for (int j = k2 + 1 + threadIdx.x; j < n; j += TNT) vx[j] = 0.0;
-  } else {
-    const double mu = sqrt(fma(alpha, alpha, sigma2));
-    beta = (alpha > 0.0) ? -mu : mu;
-    tau = (beta - alpha) / beta;
-    const double sc = 1.0 / (alpha - beta);
-    __syncthreads();
-    if (threadIdx.x == 0) vx[k2] = 1.0;
-    for (int j = k2 + 1 + threadIdx.x; j < n; j += TNT) vx[j] *= sc;
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = (threadIdx.x < TNW) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = TNW / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) {
+      const double alpha = vx[k2];
+      double ta = 0.0, be = alpha, sc = 0.0;
+      if (t != 0.0) {
+        const double mu = sqrt(fma(alpha, alpha, t));
+        be = (alpha > 0.0) ? -mu : mu;
+        ta = (be - alpha) / be;
+        sc = 1.0 / (alpha - be);
+      }
+      red[TNW + 1] = ta;
+      red[TNW + 2] = be;
+      red[TNW + 3] = sc;
+      vx[k2] = 1.0;
+    }
   }
+  __syncthreads();
+  tau = red[TNW + 1];
+  beta = red[TNW + 2];
+  const double sc = red[TNW + 3];
+  for (int j = k2 + 1 + threadIdx.x; j < n; j += TNT) vx[j] *= sc;
   __syncthreads();
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------- stage 1
-template <bool GRID>
-__global__ void __launch_bounds__(TNT) k_tridiag(const EigProblem* probs, GridBarrier bar) {
+// SROWS: the CTA's own rows live in shared memory (grid team, when they
+// fit); otherwise they are read and written in place in A (L2-resident).
+template <bool GRID, bool SROWS>
+__global__ void __launch_bounds__(TNT, 1) k_tridiag(const EigProblem* probs, GridBarrier bar) {
   extern __shared__ __align__(16) double tsm[];
   const EigProblem P = probs[GRID ? 0 : blockIdx.x];
   const int n = P.n;
@@ -108,9 +129,13 @@ __global__ void __launch_bounds__(TNT) k_tridiag(const EigProblem* probs, GridBa
   double* vk = tsm;                       // v_k by global index
   double* vn = tsm + n;                   // v_{k+1}
   double* const w = tsm + 2 * n;          // w_k
-  double* const red0 = tsm + 3 * n;
-  double* const red1 = red0 + TNW;
+  double* const red0 = tsm + 3 * n;       // TNW + 4 each
+  double* const red1 = red0 + TNW + 4;
+  double* const srows = red1 + TNW + 4;   // own rows t = 0, 1, ... (row c + G t) when SROWS
   unsigned gen = 0;
+  auto row = [&](int i) -> double* {
+    return SROWS ? srows + (size_t)((i - c) / G) * n : A + (int64_t)i * n;
+  };
 
   if (n <= 2) {
     if (c == 0 && threadIdx.x == 0) {
@@ -118,6 +143,13 @@ __global__ void __launch_bounds__(TNT) k_tridiag(const EigProblem* probs, GridBa
       if (n == 2) { P.e[0] = A[1]; P.d[1] = A[3]; }
     }
     return;
+  }
+  if (SROWS) {
+    for (int i = c; i < n; i += G) {
+      const double* src = A + (int64_t)i * n;
+      double* dst = row(i);
+      for (int j = threadIdx.x; j < n; j += TNT) dst[j] = src[j];
+    }
   }
   // ---- phase -1: v_0 from row 0, p_0 over own rows
   for (int j = threadIdx.x; j < n; j += TNT) vn[j] = (j >= 1) ? A[j] : 0.0;
@@ -132,7 +164,7 @@ __global__ void __launch_bounds__(TNT) k_tridiag(const EigProblem* probs, GridBa
     double pv = 0.0;
     const int i0 = 1 + ((c - 1) % G + G) % G;   // smallest own row >= 1
     for (int i = i0 + G * warp; i < n; i += G * TNW) {
-      const double* Ai = A + (int64_t)i * n;
+      const double* Ai = row(i);
       double acc = 0.0;
       for (int j = 1 + lane; j < n; j += 32) {
         const double a = Ai[j];
@@ -155,29 +187,53 @@ __global__ void __launch_bounds__(TNT) k_tridiag(const EigProblem* probs, GridBa
     const int b = k & 1, nb = b ^ 1;
     const double* pk = xp + b * n;
     const double* rk = xr + b * n;
-    // p_k . v_k from the CTAs' partials, fixed order (every warp alike)
-    double s = 0.0;
-    for (int q = lane; q < G; q += 32) s += __ldcg(xv + b * G + q);
-    s = warp_sum(s);
-    const double K = 0.5 * tau_k * s;
-    const double wk1 = __ldcg(pk + k + 1) - K;          // w_k at k+1 (v_k[k+1] = 1)
+    double* const red = (k & 1) ? red1 : red0;
+    double* const redo = (k & 1) ? red0 : red1;
+    // this thread's entries of p_k and of the pivot row (issued first), and
+    // p_k . v_k from the CTAs' partials in a fixed order (warp 0)
+    constexpr int JPT = 4;                  // j values per thread kept in registers
+    double pj[JPT], rj[JPT];
+#pragma unroll
+    for (int q = 0; q < JPT; ++q) {
+      const int j = k + 1 + threadIdx.x + q * TNT;
+      pj[q] = (j < n) ? __ldcg(pk + j) : 0.0;
+      rj[q] = (j < n) ? __ldcg(rk + j) : 0.0;
+    }
+    if (warp == 0) {
+      double s = 0.0;
+      for (int q = lane; q < G; q += 32) s += __ldcg(xv + b * G + q);
+      s = warp_sum(s);
+      if (lane == 0) {
+        const double K = 0.5 * tau_k * s;
+        redo[TNW + 1] = K;
+        redo[TNW + 2] = __ldcg(pk + k + 1) - K;   // w_k at k+1 (v_k[k+1] = 1)
+      }
+    }
+    __syncthreads();
+    const double K = redo[TNW + 1], wk1 = redo[TNW + 2];
     const bool owner = ((k + 1) % G) == c;
-    for (int j = k + 1 + threadIdx.x; j < n; j += TNT) {
-      const double wj = fma(-K, vk[j], __ldcg(pk + j));
+    auto wr = [&](int j, double pjq, double rjq) {
+      const double wj = fma(-K, vk[j], pjq);
       w[j] = wj;
       // row k+1 of the updated matrix: r_j = a_j - w_j - w_{k+1} v_j
-      const double r = fma(-wk1, vk[j], __ldcg(rk + j) - wj);
+      const double r = fma(-wk1, vk[j], rjq - wj);
       if (j == k + 1) {
         if (owner) P.d[k + 1] = r;
       } else {
         vn[j] = r;
       }
+    };
+#pragma unroll
+    for (int q = 0; q < JPT; ++q) {
+      const int j = k + 1 + threadIdx.x + q * TNT;
+      if (j < n) wr(j, pj[q], rj[q]);
     }
+    for (int j = k + 1 + threadIdx.x + JPT * TNT; j < n; j += TNT) wr(j, __ldcg(pk + j), __ldcg(rk + j));
     __syncthreads();
     const bool more = (k + 1 <= n - 3);
     double tau_n = 0.0;
     if (more) {
-      house(vn, k + 2, n, (k & 1) ? red1 : red0, tau_n, beta);
+      house(vn, k + 2, n, red, tau_n, beta);
       if (owner) {
         if (threadIdx.x == 0) { P.e[k + 1] = beta; P.tau[k + 1] = tau_n; }
         double* Ar = A + (int64_t)(k + 1) * n;
@@ -192,9 +248,10 @@ __global__ void __launch_bounds__(TNT) k_tridiag(const EigProblem* probs, GridBa
       const int lo = k + 2;
       const int i0 = lo + ((c - lo) % G + G) % G;
       for (int i = i0 + G * warp; i < n; i += G * TNW) {
-        double* Ai = A + (int64_t)i * n;
+        double* Ai = row(i);
         const double vi = vk[i], wi = w[i];
         double acc = 0.0;
+#pragma unroll 4
         for (int j = lo + lane; j < n; j += 32) {
           const double a = fma(-wi, vk[j], fma(-vi, w[j], Ai[j]));
           Ai[j] = a;
@@ -210,7 +267,7 @@ __global__ void __launch_bounds__(TNT) k_tridiag(const EigProblem* probs, GridBa
       }
     }
     if (!more) break;
-    const double sp = block_sum(lane == 0 ? pv : 0.0, (k & 1) ? red0 : red1);
+    const double sp = block_sum(lane == 0 ? pv : 0.0, redo);
     if (threadIdx.x == 0) xv[nb * G + c] = sp;
     { double* t = vk; vk = vn; vn = t; }
     tau_k = tau_n;
@@ -219,29 +276,46 @@ __global__ void __launch_bounds__(TNT) k_tridiag(const EigProblem* probs, GridBa
 }
 
 // ---------------------------------------------------------------- stage 2
-// Sturm count: the number of eigenvalues of T below x, from the signs of the
-// pivots of the LDL^T factorization of T - x I (q_0 = d_0 - x,
-// q_i = d_i - x - e_{i-1}^2 / q_{i-1}); a pivot smaller than pivmin in
-// magnitude is replaced by -pivmin (Kahan's safeguard).
-__device__ __forceinline__ int sturm_count(const double* d, const double* e2, int n, double x,
-                                           double pivmin) {
-  int cnt = 0;
-  double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  cnt += (q < 0.0);
+// Sturm count: the number of eigenvalues of T below x = the number of sign
+// changes in the leading principal minors p_0 = 1, p_1, ..., p_n of T - x I,
+// from the three-term recurrence p_i = (d_{i-1} - x) p_{i-1} -
+// e_{i-2}^2 p_{i-2} (Wilkinson, The Algebraic Eigenvalue Problem, Ch. 5: the
+// computed signs are exact for a matrix within a few ulps of T).  No
+// division: two FP64 operations and one product per step (a division costs
+// ~7 times an FMA here).  Both minors are rescaled by a power of two when
+// their exponents leave [-256, 256] (integer tests on the bits); an exact
+// zero minor is replaced by -2^-600 times the previous one, the counterpart
+// of the -pivmin safeguard of the ratio form.
+__device__ __forceinline__ int exp_bits(double v) {
+  return (int)((__double_as_longlong(v) >> 52) & 0x7ff);
+}
+__device__ __forceinline__ int sturm_count(const double* d, const double* e2, int n, double x) {
+  double pm = 1.0;          // p_{i-1}
+  double pc = d[0] - x;     // p_i
+  if ((__double_as_longlong(pc) << 1) == 0) pc = -0x1p-600;
+  int cnt = (int)((unsigned long long)__double_as_longlong(pc) >> 63);
   for (int i = 1; i < n; ++i) {
-    q = (d[i] - x) - e2[i - 1] / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += (q < 0.0);
+    double pn = fma(d[i] - x, pc, -e2[i - 1] * pm);
+    if ((__double_as_longlong(pn) << 1) == 0) pn = -0x1p-600 * pc;
+    cnt += (int)(((unsigned long long)(__double_as_longlong(pn) ^ __double_as_longlong(pc))) >> 63);
+    pm = pc;
+    pc = pn;
+    const int em = max(exp_bits(pc), exp_bits(pm));
+    if (em > 1023 + 256 || em < 1023 - 256) {
+      const double f = __longlong_as_double((long long)(2046 - em) << 52);   // 2^(1023 - em)
+      pc *= f;
+      pm *= f;
+    }
   }
   return cnt;
 }
 
-// One warp per eigenvalue.  Multisection: each round the 32 lanes count at
-// 32 interior points of [lo, hi] and the interval shrinks to the sub-interval
-// that holds eigenvalue number a (ascending), ~5 bits a round, until its width
-// is below 2 eps ||T|| (the accuracy of the counts).
-constexpr int BNW = 8;   // warps (eigenvalues) per CTA
+// One warp per eigenvalue, one warp per SM sub-partition (the FP64 pipe of a
+// sub-partition is the limit).  Multisection: each round the 32 lanes count
+// at 32 interior points of [lo, hi] and the interval shrinks to the
+// sub-interval that holds eigenvalue number a (ascending), ~5 bits a round,
+// until its width is below 2 eps ||T|| (the accuracy of the counts).
+constexpr int BNW = 4;   // warps (eigenvalues) per CTA
 __global__ void __launch_bounds__(BNW * 32) k_bisect(const EigProblem* probs) {
   extern __shared__ __align__(16) double bsm[];
   const EigProblem P = probs[blockIdx.y];
@@ -249,8 +323,8 @@ __global__ void __launch_bounds__(BNW * 32) k_bisect(const EigProblem* probs) {
   if ((int)blockIdx.x * BNW >= n) return;
   double* d = bsm;
   double* e2 = bsm + n;
-  __shared__ double s_lo[BNW * 32], s_hi[BNW * 32], s_piv[BNW * 32];
-  double glo = INFINITY, ghi = -INFINITY, emax = 0.0;
+  __shared__ double s_lo[BNW * 32], s_hi[BNW * 32];
+  double glo = INFINITY, ghi = -INFINITY;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double di = P.d[i];
     const double el = (i > 0) ? fabs(P.e[i - 1]) : 0.0;
@@ -259,22 +333,18 @@ __global__ void __launch_bounds__(BNW * 32) k_bisect(const EigProblem* probs) {
     if (i < n - 1) e2[i] = er * er;
     glo = fmin(glo, di - el - er);
     ghi = fmax(ghi, di + el + er);
-    emax = fmax(emax, er * er);
   }
   s_lo[threadIdx.x] = glo;
   s_hi[threadIdx.x] = ghi;
-  s_piv[threadIdx.x] = emax;
   __syncthreads();
   for (int i = 0; i < BNW * 32; ++i) {
     glo = fmin(glo, s_lo[i]);
     ghi = fmax(ghi, s_hi[i]);
-    emax = fmax(emax, s_piv[i]);
   }
   const double tnorm = fmax(fabs(glo), fabs(ghi));
-  const double pivmin = DBL_MIN * fmax(1.0, emax);
-  const double atol = 2.0 * DBL_EPSILON * tnorm;
-  glo -= 2.0 * DBL_EPSILON * tnorm * n + pivmin;
-  ghi += 2.0 * DBL_EPSILON * tnorm * n + pivmin;
+  const double atol = 2.0 * DBL_EPSILON * tnorm + DBL_MIN;
+  glo -= 2.0 * DBL_EPSILON * tnorm * n + DBL_MIN;
+  ghi += 2.0 * DBL_EPSILON * tnorm * n + DBL_MIN;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int j = blockIdx.x * BNW + warp;          // descending index
   if (j >= n) return;
@@ -282,7 +352,7 @@ __global__ void __launch_bounds__(BNW * 32) k_bisect(const EigProblem* probs) {
   double lo = glo, hi = ghi;
   for (int round = 0; round < 16 && hi - lo > atol; ++round) {
     const double x = lo + (hi - lo) * ((double)(lane + 1) / 33.0);
-    const int cnt = sturm_count(d, e2, n, x, pivmin);
+    const int cnt = sturm_count(d, e2, n, x);
     const unsigned above = __ballot_sync(0xffffffffu, cnt > a);
     const int m = above ? (__ffs(above) - 1) : 32;
     const double xm = __shfl_sync(0xffffffffu, x, m < 32 ? m : 31);
@@ -299,12 +369,43 @@ __global__ void __launch_bounds__(BNW * 32) k_bisect(const EigProblem* probs) {
 // superdiagonal from the row swaps), then two solves, the first from a
 // pseudo-random right-hand side, each followed by normalization.  Pivots
 // below eps ||T|| are raised to that size (the shift is an eigenvalue, so
-// one pivot is ~0); a running power-of-two rescale keeps the back
-// substitution finite.  Output column j of Z (n x R, row-major: Z[i*R + j]).
-__device__ __forceinline__ double hash_unit(uint32_t i, uint32_t j) {
+// one pivot is ~0); a running power-of-two rescale (|z| <= 2^400, so the
+// sum of squares stays finite) keeps the back substitution finite.  Output
+// column j of Z (n x R, row-major: Z[i*R + j]).
+//
+// The factorization runs fused with the first forward elimination, and the
+// pivots are stored as reciprocals, so the only reciprocal on the dependent
+// chain is the factorization's; it is an FP32 seed refined by two
+// Newton-Raphson steps r <- r (2 - x r) in FP64 (quadratic convergence:
+// 2^-23 -> 2^-46 -> below FP64 rounding), ~5 dependent FP64 operations
+// against ~7 for a full division.
+__device__ __forceinline__ uint32_t hash_u32(uint32_t i, uint32_t j) {
   uint32_t h = i * 0x9E3779B1u ^ (j + 0x7F4A7C15u) * 0x85EBCA77u;
   h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
-  return (double)h * (2.0 / 4294967296.0) - 1.0;
+  return h;
+}
+__device__ __forceinline__ double hash_unit(uint32_t i, uint32_t j) {
+  return (double)hash_u32(i, j) * (2.0 / 4294967296.0) - 1.0;
+}
+
+// 1/x for a normal x with |x| in [2^-1000, 2^1000]: the FP32 reciprocal of
+// x's mantissa (moved into FP32 by integer operations), rescaled by the
+// exponent, then two Newton-Raphson steps.
+__device__ __forceinline__ double rcp64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex < 24 || ex > 2022) return 1.0 / x;
+  const float mf = __uint_as_float(0x3f800000u | (unsigned)((b >> 29) & 0x7fffff));   // [1, 2)
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(mf));                              // (0.5, 1]
+  const unsigned rb = __float_as_uint(rf);
+  const int re = (int)((rb >> 23) & 0xff) - 127 + 1023 - (ex - 1023);
+  double r = __longlong_as_double((long long)((b >> 63) << 63 | (unsigned long long)re << 52 |
+                                              (unsigned long long)(rb & 0x7fffff) << 29));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
 }
 
 __global__ void k_invit(const EigProblem* probs, int nprob) {
@@ -317,84 +418,160 @@ __global__ void k_invit(const EigProblem* probs, int nprob) {
   if (j < 0 || j >= P.R) return;
   const int n = P.n, R = P.R;
   const double lam = P.w[j];
-  double* U0 = P.lu;
-  double* U1 = U0 + (int64_t)n * R;
-  double* U2 = U1 + (int64_t)n * R;
-  double* M = U2 + (int64_t)n * R;
-  unsigned char* flag = reinterpret_cast<unsigned char*>(M + (int64_t)n * R);
-  unsigned char* scnt = flag + (int64_t)n * R;
-  double* Z = P.z;
+  const double* __restrict__ d = P.d;
+  const double* __restrict__ e = P.e;
+  double* __restrict__ RI = P.lu;                        // 1 / pivot
+  double* __restrict__ U1 = RI + (int64_t)n * R;
+  double* __restrict__ U2 = U1 + (int64_t)n * R;
+  double* __restrict__ M = U2 + (int64_t)n * R;
+  unsigned char* __restrict__ flag = reinterpret_cast<unsigned char*>(M + (int64_t)n * R);
+  unsigned char* __restrict__ scnt = flag + (int64_t)n * R;
+  double* __restrict__ Z = P.z;
   auto at = [&](int k) { return (int64_t)k * R + j; };
   // ||T||_1 bound for the pivot floor
   double tn = 0.0;
   for (int i = 0; i < n; ++i) {
-    const double r = fabs(P.d[i]) + (i > 0 ? fabs(P.e[i - 1]) : 0.0) + (i < n - 1 ? fabs(P.e[i]) : 0.0);
+    const double r = fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
     tn = fmax(tn, r);
   }
-  const double ptol = fmax(DBL_EPSILON * tn, DBL_MIN);
-  // factor
-  double p0 = P.d[0] - lam, p1 = (n > 1) ? P.e[0] : 0.0;
+  const double ptol = fmax(DBL_EPSILON * tn, 0x1p-990);
+  const unsigned long long ptol_bits = (unsigned long long)__double_as_longlong(ptol);
+  auto absb = [](double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+  };
+  // factorization fused with the forward elimination of b (random); y -> Z
+  double p0 = d[0] - lam, p1 = (n > 1) ? e[0] : 0.0;
+  double pb = hash_unit(0, j);
   for (int k = 0; k + 1 < n; ++k) {
-    const double ek = P.e[k];
-    const double a1 = P.d[k + 1] - lam;
-    const double e1 = (k + 2 < n) ? P.e[k + 1] : 0.0;
-    if (fabs(p0) >= fabs(ek)) {
-      if (fabs(p0) < ptol) p0 = (p0 < 0.0) ? -ptol : ptol;
-      const double m = ek / p0;
-      U0[at(k)] = p0; U1[at(k)] = p1; U2[at(k)] = 0.0; M[at(k)] = m; flag[at(k)] = 0;
-      p0 = fma(-m, p1, a1);
-      p1 = e1;
-    } else {
-      const double m = p0 / ek;
-      U0[at(k)] = ek; U1[at(k)] = a1; U2[at(k)] = e1; M[at(k)] = m; flag[at(k)] = 1;
+    const double ek = e[k];
+    const double a1 = d[k + 1] - lam;
+    const double e1 = (k + 2 < n) ? e[k + 1] : 0.0;
+    const double bk1 = hash_unit(k + 1, j);
+    const bool swap = absb(ek) > absb(p0);
+    if (!swap && absb(p0) < ptol_bits) p0 = (p0 < 0.0) ? -ptol : ptol;
+    const double piv = swap ? ek : p0;
+    const double r = rcp64(piv);
+    const double m = (swap ? p0 : ek) * r;
+    RI[at(k)] = r;
+    U1[at(k)] = swap ? a1 : p1;
+    U2[at(k)] = swap ? e1 : 0.0;
+    M[at(k)] = m;
+    flag[at(k)] = swap ? 1 : 0;
+    double yk;
+    if (swap) {
+      yk = bk1;
+      pb = fma(-m, bk1, pb);
       p0 = fma(-m, a1, p1);
       p1 = -m * e1;
+    } else {
+      yk = pb;
+      pb = fma(-m, pb, bk1);
+      p0 = fma(-m, p1, a1);
+      p1 = e1;
     }
+    Z[at(k)] = yk;
   }
-  if (fabs(p0) < ptol) p0 = (p0 < 0.0) ? -ptol : ptol;
-  U0[at(n - 1)] = p0;
-  const double BIG = 0x1p+600, SMALL = 0x1p-600;
+  if (absb(p0) < ptol_bits) p0 = (p0 < 0.0) ? -ptol : ptol;
+  RI[at(n - 1)] = rcp64(p0);
+  U1[at(n - 1)] = 0.0;
+  U2[at(n - 1)] = 0.0;
+  Z[at(n - 1)] = pb;
+  const double SMALL = 0x1p-400;
   double bscale = 1.0;
+  // the passes below prefetch the operands of the next PF steps into
+  // registers before working through the current ones, which keeps the L2
+  // latency off the dependent chain (each step stores into Z, so the
+  // compiler cannot move the next loads ahead by itself)
+  constexpr int PF = 8;
   for (int it = 0; it < 2; ++it) {
-    // forward elimination of the right-hand side b (random, then the
-    // previous solution times bscale), y into Z
-    double pb = (it == 0) ? hash_unit(0, j) : Z[at(0)] * bscale;
-    for (int k = 0; k + 1 < n; ++k) {
-      const double bk1 = (it == 0) ? hash_unit(k + 1, j) : Z[at(k + 1)] * bscale;
-      const double m = M[at(k)];
-      double yk;
-      if (flag[at(k)] == 0) { yk = pb; pb = fma(-m, pb, bk1); }
-      else { yk = bk1; pb = fma(-m, bk1, pb); }
-      Z[at(k)] = yk;
-    }
-    Z[at(n - 1)] = pb;
-    // back substitution with rescaling; scnt[i] = rescales before z_i was stored
-    int nres = 0;
-    double sc = 1.0;             // 2^(-600 nres): the scale of z1, z2 and zk
-    double z1 = 0.0, z2 = 0.0;   // z_{k+1}, z_{k+2} at the current scale
-    for (int k = n - 1; k >= 0; --k) {
-      double r = Z[at(k)] * sc;
-      if (k + 1 < n) r = fma(-U1[at(k)], z1, r);
-      if (k + 2 < n) r = fma(-U2[at(k)], z2, r);
-      double zk = r / U0[at(k)];
-      if (fabs(zk) > BIG) {   // scale everything from here on down by 2^-600
-        zk *= SMALL; z1 *= SMALL; z2 *= SMALL; sc *= SMALL;
-        ++nres;
+    if (it == 1) {
+      // forward elimination of the previous solution (times bscale)
+      double pv = Z[at(0)] * bscale;
+      double nb_[PF], nm_[PF];
+      unsigned char nf_[PF];
+      auto load_f = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < PF; ++q) {
+          const int k = k0 + q;
+          const bool ok = k + 1 < n;
+          nb_[q] = ok ? Z[at(k + 1)] : 0.0;
+          nm_[q] = ok ? M[at(k)] : 0.0;
+          nf_[q] = ok ? flag[at(k)] : 0;
+        }
+      };
+      load_f(0);
+      for (int k0 = 0; k0 + 1 < n; k0 += PF) {
+        double cb[PF], cm[PF];
+        unsigned char cf[PF];
+#pragma unroll
+        for (int q = 0; q < PF; ++q) { cb[q] = nb_[q]; cm[q] = nm_[q]; cf[q] = nf_[q]; }
+        if (k0 + PF + 1 < n) load_f(k0 + PF);
+#pragma unroll
+        for (int q = 0; q < PF; ++q) {
+          const int k = k0 + q;
+          if (k + 1 < n) {
+            const double bk1 = cb[q] * bscale;
+            double yk;
+            if (cf[q] == 0) { yk = pv; pv = fma(-cm[q], pv, bk1); }
+            else { yk = bk1; pv = fma(-cm[q], bk1, pv); }
+            Z[at(k)] = yk;
+          }
+        }
       }
-      Z[at(k)] = zk;
-      scnt[at(k)] = (unsigned char)(nres > 255 ? 255 : nres);
-      z2 = z1;
-      z1 = zk;
+      Z[at(n - 1)] = pv;
     }
-    // bring all entries to the final scale and normalize
+    // back substitution with rescaling; scnt[i] = rescales before z_i was
+    // stored; the sum of squares is kept at the running scale
+    int nres = 0;
+    double sc = 1.0;             // 2^(-400 nres): the scale of z1, z2 and zk
+    double z1 = 0.0, z2 = 0.0;   // z_{k+1}, z_{k+2} at the current scale
     double ss = 0.0;
-    for (int k = 0; k < n; ++k) {
-      double zk = Z[at(k)];
-      for (int q = scnt[at(k)]; q < nres; ++q) zk *= SMALL;
-      Z[at(k)] = zk;
-      ss = fma(zk, zk, ss);
+    double ny[PF], n1[PF], n2[PF], nr[PF];
+    auto load_b = [&](int k0) {   // steps k0, k0 - 1, ..., k0 - PF + 1
+#pragma unroll
+      for (int q = 0; q < PF; ++q) {
+        const int k = k0 - q;
+        const bool ok = k >= 0;
+        ny[q] = ok ? Z[at(k)] : 0.0;
+        n1[q] = ok ? U1[at(k)] : 0.0;
+        n2[q] = ok ? U2[at(k)] : 0.0;
+        nr[q] = ok ? RI[at(k)] : 0.0;
+      }
+    };
+    load_b(n - 1);
+    for (int k0 = n - 1; k0 >= 0; k0 -= PF) {
+      double cy[PF], c1[PF], c2[PF], cr[PF];
+#pragma unroll
+      for (int q = 0; q < PF; ++q) { cy[q] = ny[q]; c1[q] = n1[q]; c2[q] = n2[q]; cr[q] = nr[q]; }
+      if (k0 - PF >= 0) load_b(k0 - PF);
+#pragma unroll
+      for (int q = 0; q < PF; ++q) {
+        const int k = k0 - q;
+        if (k >= 0) {
+          double rr = cy[q] * sc;
+          rr = fma(-c2[q], z2, rr);     // U2 and U1 are 0 past the end
+          rr = fma(-c1[q], z1, rr);
+          double zk = rr * cr[q];
+          if (absb(zk) > 0x58F0000000000000ull) {   // |zk| > 2^400: rescale by 2^-400
+            zk *= SMALL; z1 *= SMALL; z2 *= SMALL; sc *= SMALL; ss *= 0x1p-800;
+            ++nres;
+          }
+          Z[at(k)] = zk;
+          scnt[at(k)] = (unsigned char)(nres > 255 ? 255 : nres);
+          ss = fma(zk, zk, ss);
+          z2 = z1;
+          z1 = zk;
+        }
+      }
     }
-    bscale = (ss > 0.0) ? 1.0 / sqrt(ss) : 1.0;
+    if (nres > 0) {
+      for (int k = 0; k < n; ++k) {
+        double zk = Z[at(k)];
+        for (int q = scnt[at(k)]; q < nres; ++q) zk *= SMALL;
+        Z[at(k)] = zk;
+      }
+    }
+    bscale = (ss > 0.0) ? rcp64(sqrt(ss)) : 1.0;
   }
   for (int k = 0; k < n; ++k) Z[at(k)] *= bscale;
 }
@@ -456,72 +633,153 @@ __global__ void k_trsm_rows(const EigProblem* probs, int nprob) {
 }
 
 // ---------------------------------------------------------------- stage 6
-// U = Q_H Z with Q_H = H_0 H_1 ... H_{n-3}: the reflectors applied from the
-// last to the first; one warp per vector, the vector in shared memory.
-// U is I x R column-major.
-__global__ void k_backtransform(const EigProblem* probs, int nprob, int warps_per_cta,
-                                int zstride) {
-  extern __shared__ __align__(16) double zsm[];
+// U = Q_H Z with Q_H = H_0 H_1 ... H_{n-3}, in blocks of WYB reflectors: a
+// block H_k0 ... H_{k0+m-1} equals I - V T V^T with V = [v_k0 ... v_{k0+m-1}]
+// and T upper triangular (the compact WY form, Schreiber & Van Loan 1989:
+// T_jj = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] (V[:, 0:j]^T v_j)).  The blocks
+// are applied from the last to the first: z <- z - V (T (V^T z)).  U is
+// I x R column-major.
+constexpr int WYB = 32;
+__host__ __device__ __forceinline__ int wy_blocks(int n) { return n > 2 ? (n - 2 + WYB - 1) / WYB : 0; }
+
+// One CTA per block of reflectors: the T factor into wyT (WYB x WYB, row-major).
+__global__ void __launch_bounds__(256) k_wy_t(const EigProblem* probs) {
+  const EigProblem P = probs[blockIdx.y];
+  const int n = P.n, b = blockIdx.x;
+  if (b >= wy_blocks(n)) return;
+  const int k0 = b * WYB, m = min(WYB, n - 2 - k0);
+  __shared__ double W[WYB][WYB + 1];
+  __shared__ double T[WYB][WYB + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.x * warps_per_cta + warp;   // flattened (problem, vector)
+  // W[i][j] = v_{k0+i} . v_{k0+j} for i < j; v_{k0+j} is 1 at k0+j+1 and
+  // A[k0+j][c] beyond, and v_{k0+i} is A[k0+i][c] there
+  for (int q = warp; q < m * m; q += 8) {
+    const int i = q / m, jj = q % m;
+    if (i >= jj) continue;
+    const double* vi = P.A + (int64_t)(k0 + i) * n;
+    const double* vj = P.A + (int64_t)(k0 + jj) * n;
+    const int s0 = k0 + jj + 1;
+    double acc = 0.0;
+    for (int c = s0 + 1 + lane; c < n; c += 32) acc = fma(vi[c], vj[c], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) W[i][jj] = acc + vi[s0];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int jj = 0; jj < m; ++jj) {
+      const double tj = P.tau[k0 + jj];
+      if (lane < jj) {
+        double s = 0.0;
+        for (int l = lane; l < jj; ++l) s = fma(T[lane][l], W[l][jj], s);
+        T[lane][jj] = -tj * s;
+      } else if (lane == jj) {
+        T[lane][jj] = tj;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  double* To = P.wyT + (size_t)b * WYB * WYB;
+  for (int q = threadIdx.x; q < WYB * WYB; q += 256) {
+    const int i = q / WYB, jj = q % WYB;
+    To[q] = (i < m && jj < m && i <= jj) ? T[i][jj] : 0.0;
+  }
+}
+
+// One CTA per eigenvector (flattened over problems), the vector in shared memory.
+__global__ void __launch_bounds__(256) k_backtransform(const EigProblem* probs, int nprob) {
+  extern __shared__ __align__(16) double zs[];
+  __shared__ double y[WYB], y2[WYB];
+  const int t = blockIdx.x;
   int p = 0;
   while (p + 1 < nprob && probs[p + 1].zoff <= t) ++p;
   const EigProblem P = probs[p];
   const int j = t - P.zoff;
   if (j < 0 || j >= P.R || *P.info) return;
   const int n = P.n, R = P.R;
-  double* z = zsm + (size_t)warp * zstride;
-  for (int i = lane; i < n; i += 32) z[i] = P.z[(int64_t)i * R + j];
-  __syncwarp();
-  for (int k = n - 3; k >= 0; --k) {
-    const double tau = P.tau[k];
-    if (tau == 0.0) continue;
-    const double* vrow = P.A + (int64_t)k * n;   // v_k[k+1] = 1, v_k[i] = A[k][i] for i >= k+2
-    double s = 0.0;
-    for (int i = k + 2 + lane; i < n; i += 32) s = fma(vrow[i], z[i], s);
-    s = warp_sum(s);
-    const double f = tau * (z[k + 1] + s);
-    __syncwarp();
-    if (lane == 0) z[k + 1] -= f;
-    for (int i = k + 2 + lane; i < n; i += 32) z[i] = fma(-f, vrow[i], z[i]);
-    __syncwarp();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double* A = P.A;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) zs[i] = P.z[(int64_t)i * R + j];
+  __syncthreads();
+  for (int b = wy_blocks(n) - 1; b >= 0; --b) {
+    const int k0 = b * WYB, m = min(WYB, n - 2 - k0);
+    // y = V^T z
+    for (int q = warp; q < m; q += 8) {
+      const double* v = A + (int64_t)(k0 + q) * n;
+      const int s0 = k0 + q + 1;
+      double acc = 0.0;
+      for (int c = s0 + 1 + lane; c < n; c += 32) acc = fma(v[c], zs[c], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) y[q] = acc + zs[s0];
+    }
+    __syncthreads();
+    // y2 = T y
+    if (warp == 0 && lane < m) {
+      const double* Tb = P.wyT + (size_t)b * WYB * WYB + (size_t)lane * WYB;
+      double s = 0.0;
+      for (int l = lane; l < m; ++l) s = fma(Tb[l], y[l], s);
+      y2[lane] = s;
+    }
+    __syncthreads();
+    // z <- z - V y2 (entry i gets the reflectors q with k0 + q + 1 <= i)
+    for (int i = k0 + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      const int qmax = min(m, i - k0);
+      double s = 0.0;
+      for (int q = 0; q < qmax; ++q) {
+        const double coef = (i == k0 + q + 1) ? 1.0 : A[(int64_t)(k0 + q) * n + i];
+        s = fma(coef, y2[q], s);
+      }
+      zs[i] -= s;
+    }
+    __syncthreads();
   }
-  for (int i = lane; i < n; i += 32) P.U[(int64_t)j * n + i] = z[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) P.U[(int64_t)j * n + i] = zs[i];
 }
 
 // ---------------------------------------------------------------- launchers
-size_t tridiag_smem_bytes(int n) { return sizeof(double) * (3 * (size_t)n + 2 * TNW); }
+namespace {
+int tridiag_rows_per_cta(int n, int G) { return (n + G - 1) / G; }
+size_t tridiag_base_smem(int n) { return sizeof(double) * (3 * (size_t)n + 2 * (TNW + 4)); }
+constexpr size_t kTridiagSmemRowsCap = 160 * 1024;
+}  // namespace
+
+size_t tridiag_smem_bytes(int n) { return tridiag_base_smem(n); }
+
+// ~6 rows per CTA at the first step (the step time is latency-bound: 2 to 8
+// rows per CTA measured within 8% of each other at n = 500), at most one CTA
+// per SM
+int tridiag_team_size(int n, int num_sms) {
+  int G = (n + 5) / 6;
+  return G > num_sms ? num_sms : (G < 1 ? 1 : G);
+}
 
 cudaError_t launch_tridiag(const EigProblem* probs_dev, int count, int nmax, bool grid,
                            int num_sms, GridBarrier bar, cudaStream_t st) {
-  const size_t smem = tridiag_smem_bytes(nmax);
   cudaError_t e;
   if (grid) {
-    e = cudaFuncSetAttribute(k_tridiag<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int G = tridiag_team_size(nmax, num_sms);
+    const size_t srow = sizeof(double) * (size_t)tridiag_rows_per_cta(nmax, G) * nmax;
+    const bool sr = tridiag_base_smem(nmax) + srow <= kTridiagSmemRowsCap;
+    const size_t smem = tridiag_base_smem(nmax) + (sr ? srow : 0);
+    void* fn = sr ? (void*)k_tridiag<true, true> : (void*)k_tridiag<true, false>;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag<true>, TNT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TNT, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-    // ~4 rows per CTA at the first step, at most one CTA per SM
-    int G = (nmax + 3) / 4;
-    if (G > num_sms) G = num_sms;
-    if (G < 1) G = 1;
     void* args[] = {(void*)&probs_dev, (void*)&bar};
-    e = cudaLaunchCooperativeKernel((void*)k_tridiag<true>, dim3(G), dim3(TNT), args, smem, st);
+    e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(TNT), args, smem, st);
     count_launches(1);
     return e;
   }
-  e = cudaFuncSetAttribute(k_tridiag<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = tridiag_base_smem(nmax);
+  e = cudaFuncSetAttribute(k_tridiag<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
   if (e != cudaSuccess) return e;
-  k_tridiag<false><<<count, TNT, smem, st>>>(probs_dev, bar);
+  k_tridiag<false, false><<<count, TNT, smem, st>>>(probs_dev, bar);
   count_launches(1);
   return cudaGetLastError();
-}
-
-int tridiag_team_size(int n, int num_sms) {
-  int G = (n + 3) / 4;
-  return G > num_sms ? num_sms : (G < 1 ? 1 : G);
 }
 
 cudaError_t launch_bisect(const EigProblem* probs_dev, int count, int nmax, cudaStream_t st) {
@@ -553,18 +811,21 @@ cudaError_t launch_trsm_rows(const EigProblem* probs_dev, int count, int total_r
   return cudaGetLastError();
 }
 
+size_t eig_wy_doubles(int n) { return (size_t)wy_blocks(n) * WYB * WYB; }
+
 cudaError_t launch_backtransform(const EigProblem* probs_dev, int count, int total_vectors,
                                  int nmax, cudaStream_t st) {
   if (total_vectors < 1) return cudaSuccess;
-  int wpc = (int)((96 * 1024) / (sizeof(double) * (size_t)nmax));
-  if (wpc > 8) wpc = 8;
-  if (wpc < 1) wpc = 1;
-  const size_t smem = sizeof(double) * (size_t)nmax * wpc;
+  const int nb = wy_blocks(nmax);
+  if (nb > 0) {
+    k_wy_t<<<dim3(nb, count), 256, 0, st>>>(probs_dev);
+    count_launches(1);
+  }
+  const size_t smem = sizeof(double) * (size_t)nmax;
   cudaError_t e = cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_backtransform<<<(total_vectors + wpc - 1) / wpc, wpc * 32, smem, st>>>(probs_dev, count, wpc,
-                                                                          nmax);
+  k_backtransform<<<total_vectors, 256, smem, st>>>(probs_dev, count);
   count_launches(1);
   return cudaGetLastError();
 }
