@@ -152,6 +152,24 @@ tucker_status tucker_sthosvd(tucker_ctx* ctx, const void* x_dev, tucker_dtype dt
                              tucker_prec prec, tucker_result** out);
 tucker_status tucker_result_destroy(tucker_result* res);
 
+/* Batched ST-HOSVD: Algorithm 1, eps-driven, mode order 0..N_i-1, for each of
+ * `count` independent tensors of any orders and shapes (x_dev[i], ndims[i],
+ * dims[i][0..ndims[i]-1], all of one dtype; every mode size <= 4096).  Each
+ * result is exactly what tucker_sthosvd would compute with the tridiagonal
+ * eigensolver.  The tensors advance through their modes together: step s
+ * takes mode s of every tensor with more than s modes, issues their Gram
+ * kernels, then one reduction, eigenvalue, rank-cut, eigenvector and
+ * back-transformation launch for all of them (one CTA per matrix where the
+ * eigensolver is sequential), then their TTMs; the host synchronises twice
+ * per step (to size the factors from the ranks, and to check the Cholesky QR
+ * of the eigenvectors, which falls back to Jacobi for a matrix it rejects).
+ * out[0..count-1] receive results to release with tucker_result_destroy
+ * (all NULL on failure).  Errors as tucker_sthosvd. */
+tucker_status tucker_sthosvd_batched(tucker_ctx* ctx, int count, const void* const* x_dev,
+                                     tucker_dtype dtype, const int* ndims,
+                                     const int64_t* const* dims, double eps, tucker_prec prec,
+                                     tucker_result** out);
+
 /* (Partial) reconstruction, Section 7: Z = G x_n A_n over the modes in
  * `mode_order_or_null` (NULL = the flop-minimal order by exhaustive
  * search), with A_n = rows begin_n..end_n-1 of U_n.  NULL begin/end = the

@@ -196,8 +196,12 @@ int gram_kernel_for(tucker_prec prec, tucker_dtype dt, const SlabView& v, int sm
 }
 
 // maxabs: max|y| if the caller knows it (e.g. from the norm pass), else <= 0.
+// check = false: the tensor-core kernel's error word (d_words[8]) is neither
+// cleared nor read here; the caller clears it before and reads it after a
+// batch of calls.
 tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabView& v,
-                      tucker_prec prec, double* S, int* kernel_used, double maxabs = -1.0) {
+                      tucker_prec prec, double* S, int* kernel_used, double maxabs = -1.0,
+                      bool check = true) {
   int kern = gram_kernel_for(prec, dt, v, c->num_sms);
   if (kern == 2 && (((uintptr_t)y) & 15) != 0) kern = 1;
   if (kernel_used) *kernel_used = kern;
@@ -209,9 +213,10 @@ tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabV
     TcGramPlan p = plan_gram_tc(v.L, v.I, v.Rt, c->num_sms);
     DevBuf scratch;
     TK_TRY(dev_alloc(c, scratch, p.scratch_bytes));
-    TK_CUDA(c, cudaMemsetAsync(c->d_words + 8, 0, sizeof(unsigned), c->stream));
+    if (check) TK_CUDA(c, cudaMemsetAsync(c->d_words + 8, 0, sizeof(unsigned), c->stream));
     TK_CUDA(c, launch_gram_tc((const float*)y, v.L, v.I, v.Rt, p, split_scale(maxabs),
                               scratch.as<double>(), c->d_words + 8, S, c->stream));
+    if (!check) return TUCKER_OK;
     unsigned err = 0;
     TK_CUDA(c, cudaMemcpyAsync(&err, c->d_words + 8, sizeof(unsigned), cudaMemcpyDeviceToHost,
                                c->stream));
@@ -379,9 +384,10 @@ tucker_status do_cut(tucker_ctx* c, const double* w, int n, double thr, int fixe
 }
 
 // ymax: max|y| if the caller knows it (e.g. from the norm pass), else <= 0.
+// check = false: as do_gram, for the tensor-core TTM's error word (d_words[9]).
 tucker_status do_ttm(tucker_ctx* c, const void* y, tucker_dtype ydt, const SlabView& v,
                      const double* A, int64_t K, int64_t lda, int arow, tucker_prec prec, void* z,
-                     tucker_dtype zdt, int* kernel_used, double ymax = -1.0) {
+                     tucker_dtype zdt, int* kernel_used, double ymax = -1.0, bool check = true) {
   const bool tc = (prec == TUCKER_PREC_MIXED || prec == TUCKER_PREC_TENSOR) && ydt == TUCKER_F32 &&
                   zdt == TUCKER_F32 && (((uintptr_t)y) & 15) == 0 &&
                   ttm_tc_supported(v.L, v.I, v.Rt, K);
@@ -393,9 +399,10 @@ tucker_status do_ttm(tucker_ctx* c, const void* y, tucker_dtype ydt, const SlabV
     }
     DevBuf scratch;
     TK_TRY(dev_alloc(c, scratch, ttm_tc_scratch_bytes(v.I, K)));
-    TK_CUDA(c, cudaMemsetAsync(c->d_words + 9, 0, sizeof(unsigned), c->stream));
+    if (check) TK_CUDA(c, cudaMemsetAsync(c->d_words + 9, 0, sizeof(unsigned), c->stream));
     TK_CUDA(c, launch_ttm_tc((const float*)y, v.L, v.I, v.Rt, A, K, lda, arow, split_scale(ymax),
                              (float*)z, scratch.p, c->d_words + 9, c->num_sms, c->stream));
+    if (!check) return TUCKER_OK;
     unsigned err = 0;
     TK_CUDA(c, cudaMemcpyAsync(&err, c->d_words + 9, sizeof(unsigned), cudaMemcpyDeviceToHost,
                                c->stream));
@@ -741,6 +748,253 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
   *out = r;
   r = nullptr;  // disarm guard
   if (noconv) return set_err(c, TUCKER_ERR_EIG_NOCONV, "Jacobi reached the sweep cap in some mode");
+  return TUCKER_OK;
+}
+
+tucker_status tucker_sthosvd_batched(tucker_ctx* c, int count, const void* const* xs,
+                                     tucker_dtype dt, const int* ndims,
+                                     const int64_t* const* dimss, double eps, tucker_prec prec,
+                                     tucker_result** out) {
+  if (!c) return TUCKER_ERR_INVALID;
+  if (!out || !xs || !ndims || !dimss || count < 1 || (dt != TUCKER_F32 && dt != TUCKER_F64) ||
+      prec < 0 || prec > 3 || !(eps >= 0.0 && std::isfinite(eps)))
+    return set_err(c, TUCKER_ERR_INVALID, "tucker_sthosvd_batched: bad argument");
+  for (int i = 0; i < count; ++i) out[i] = nullptr;
+  if ((prec == TUCKER_PREC_MIXED || prec == TUCKER_PREC_TENSOR) && dt != TUCKER_F32)
+    return set_err(c, TUCKER_ERR_UNSUPPORTED, "MIXED/TENSOR precision needs FP32 input");
+  int maxN = 0;
+  for (int i = 0; i < count; ++i) {
+    if (!xs[i] || !check_dims(ndims[i], dimss[i]))
+      return set_err(c, TUCKER_ERR_INVALID, "tucker_sthosvd_batched: bad tensor");
+    for (int k = 0; k < ndims[i]; ++k)
+      if (dimss[i][k] > 4096)
+        return set_err(c, TUCKER_ERR_INVALID, "tucker_sthosvd_batched: mode size above 4096");
+    maxN = std::max(maxN, ndims[i]);
+  }
+  cudaStream_t st = c->stream;
+  const tucker_dtype wdt = (prec == TUCKER_PREC_FP64) ? TUCKER_F64 : dt;
+  std::vector<tucker_result*> res(count, nullptr);
+  struct Guard {
+    std::vector<tucker_result*>& r;
+    ~Guard() { for (auto* p : r) if (p) tucker_result_destroy(p); }
+  } guard{res};
+  for (int i = 0; i < count; ++i) {
+    res[i] = new tucker_result();
+    memset(res[i], 0, sizeof(tucker_result));
+    res[i]->ndim = ndims[i];
+    res[i]->core_dtype = wdt;
+    for (int k = 0; k < ndims[i]; ++k) { res[i]->dims[k] = dimss[i][k]; res[i]->mode_order[k] = k; }
+  }
+  Timer t_total;
+  t_total.start(c);
+  // ---- norms of all tensors, one synchronization
+  std::vector<double> nrm2(count), xmax(count);
+  {
+    std::vector<int> nb(count);
+    size_t off = 0;
+    for (int i = 0; i < count; ++i) {
+      const int64_t ne = numel(ndims[i], dimss[i]);
+      nb[i] = (int)std::max<int64_t>(1, std::min<int64_t>((ne + 255) / 256, (int64_t)c->num_sms * 8));
+      off += 2 * (size_t)nb[i];
+    }
+    DevBuf part, outb;
+    TK_TRY(dev_alloc(c, part, sizeof(double) * off));
+    TK_TRY(dev_alloc(c, outb, sizeof(double) * 2 * count + sizeof(unsigned) * count));
+    unsigned* bad_d = reinterpret_cast<unsigned*>(outb.as<double>() + 2 * count);
+    TK_CUDA(c, cudaMemsetAsync(bad_d, 0, sizeof(unsigned) * count, st));
+    off = 0;
+    for (int i = 0; i < count; ++i) {
+      TK_CUDA(c, launch_sumsq(xs[i], dt, numel(ndims[i], dimss[i]), part.as<double>() + off, nb[i],
+                              bad_d + i, outb.as<double>() + 2 * i, st));
+      off += 2 * (size_t)nb[i];
+    }
+    std::vector<double> h(2 * count);
+    std::vector<unsigned> bad(count);
+    TK_CUDA(c, cudaMemcpyAsync(h.data(), outb.p, sizeof(double) * 2 * count, cudaMemcpyDeviceToHost, st));
+    TK_CUDA(c, cudaMemcpyAsync(bad.data(), bad_d, sizeof(unsigned) * count, cudaMemcpyDeviceToHost, st));
+    TK_TRY(sync(c));
+    for (int i = 0; i < count; ++i) {
+      if (bad[i]) return set_err(c, TUCKER_ERR_NONFINITE, "a tensor of the batch holds NaN or Inf");
+      nrm2[i] = h[2 * i];
+      xmax[i] = h[2 * i + 1];
+      res[i]->norm_x_sq = nrm2[i];
+      res[i]->threshold = eps * eps * nrm2[i] / ndims[i];
+    }
+  }
+  // FP64 Grams below eps^2 / N = 1e-9, as in tucker_sthosvd
+  std::vector<tucker_prec> gprec(count, prec);
+  for (int i = 0; i < count; ++i)
+    if (prec != TUCKER_PREC_FP64 && eps * eps / ndims[i] < kMinFp32GramThreshold)
+      gprec[i] = TUCKER_PREC_FP64;
+  std::vector<std::vector<int64_t>> cur(count);
+  std::vector<const void*> y(count);
+  std::vector<DevBuf> ycur(count);
+  std::vector<tucker_dtype> ydt(count, dt);
+  for (int i = 0; i < count; ++i) {
+    cur[i].assign(dimss[i], dimss[i] + ndims[i]);
+    y[i] = xs[i];
+  }
+  TK_CUDA(c, cudaMemsetAsync(c->d_words + 8, 0, 2 * sizeof(unsigned), st));
+  for (int s = 0; s < maxN; ++s) {
+    std::vector<int> act;
+    for (int i = 0; i < count; ++i)
+      if (ndims[i] > s) act.push_back(i);
+    const int m = (int)act.size();
+    // ---- per-problem workspace: A (Gram, reduced in place), d, e, tau, xch, wyT
+    std::vector<size_t> wo(m);
+    size_t wtot = 0;
+    int nmax = 0;
+    for (int q = 0; q < m; ++q) {
+      const int n = (int)cur[act[q]][s];
+      nmax = std::max(nmax, n);
+      wo[q] = wtot;
+      wtot += (size_t)n * n + 3 * (size_t)n + 4 * (size_t)n + 2 + eig_wy_doubles(n);
+    }
+    DevBuf work, meta;
+    TK_TRY(dev_alloc(c, work, sizeof(double) * wtot));
+    TK_TRY(dev_alloc(c, meta, sizeof(EigProblem) * m + sizeof(double) * m + sizeof(int64_t) * m +
+                                  sizeof(double) * m + sizeof(int) * m));
+    EigProblem* pd = meta.as<EigProblem>();
+    double* thr_d = reinterpret_cast<double*>(pd + m);
+    int64_t* R_d = reinterpret_cast<int64_t*>(thr_d + m);
+    double* disc_d = reinterpret_cast<double*>(R_d + m);
+    int* info_d = reinterpret_cast<int*>(disc_d + m);
+    std::vector<EigProblem> h(m);
+    std::vector<DevBuf> wbuf(m);
+    std::vector<double> thr(m);
+    for (int q = 0; q < m; ++q) {
+      const int i = act[q], n = (int)cur[i][s];
+      EigProblem& P = h[q];
+      P = EigProblem{};
+      P.A = work.as<double>() + wo[q];
+      P.d = P.A + (size_t)n * n;
+      P.e = P.d + n;
+      P.tau = P.e + n;
+      P.xch = P.tau + n;
+      P.wyT = P.xch + 4 * (size_t)n + 2;
+      P.info = info_d + q;
+      P.n = n;
+      TK_TRY(dev_alloc(c, wbuf[q], sizeof(double) * n));
+      P.w = wbuf[q].as<double>();
+      thr[q] = res[i]->threshold;
+      const SlabView v = slab_view(ndims[i], cur[i].data(), s);
+      TK_TRY(do_gram(c, y[i], ydt[i], v, gprec[i], P.A, &res[i]->gram_kernel[s],
+                     s == 0 ? xmax[i] : -1.0, false));
+    }
+    TK_CUDA(c, cudaMemsetAsync(info_d, 0, sizeof(int) * m, st));
+    TK_CUDA(c, cudaMemcpyAsync(pd, h.data(), sizeof(EigProblem) * m, cudaMemcpyHostToDevice, st));
+    TK_CUDA(c, cudaMemcpyAsync(thr_d, thr.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+    const GridBarrier nobar{nullptr, nullptr, nullptr};
+    TK_CUDA(c, launch_tridiag(pd, m, nmax, false, c->num_sms, nobar, st));
+    TK_CUDA(c, launch_bisect(pd, m, nmax, st));
+    TK_CUDA(c, launch_rank_cut_batched(pd, m, thr_d, nullptr, R_d, disc_d, st));
+    std::vector<int64_t> R(m);
+    std::vector<double> disc(m);
+    TK_CUDA(c, cudaMemcpyAsync(R.data(), R_d, sizeof(int64_t) * m, cudaMemcpyDeviceToHost, st));
+    TK_CUDA(c, cudaMemcpyAsync(disc.data(), disc_d, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    TK_TRY(sync(c));
+    // ---- leading eigenvectors of all problems
+    size_t vtot = 0;
+    int zoff = 0, roff = 0;
+    std::vector<size_t> vo(m);
+    std::vector<DevBuf> ubuf(m);
+    for (int q = 0; q < m; ++q) {
+      const int n = h[q].n, Rq = (int)R[q];
+      if (Rq < 1 || Rq > n) return set_err(c, TUCKER_ERR_CUDA, "rank cut returned an invalid rank");
+      vo[q] = vtot;
+      vtot += (size_t)n * Rq + (size_t)Rq * Rq + (eig_lu_bytes(n, Rq) + 7) / 8;
+      TK_TRY(dev_alloc(c, ubuf[q], sizeof(double) * (size_t)n * Rq));
+    }
+    DevBuf vec;
+    TK_TRY(dev_alloc(c, vec, sizeof(double) * vtot));
+    for (int q = 0; q < m; ++q) {
+      EigProblem& P = h[q];
+      P.R = (int)R[q];
+      P.z = vec.as<double>() + vo[q];
+      P.gram = P.z + (size_t)P.n * P.R;
+      P.lu = P.gram + (size_t)P.R * P.R;
+      P.U = ubuf[q].as<double>();
+      P.zoff = zoff;
+      P.roff = roff;
+      zoff += P.R;
+      roff += P.n;
+    }
+    TK_CUDA(c, cudaMemcpyAsync(pd, h.data(), sizeof(EigProblem) * m, cudaMemcpyHostToDevice, st));
+    TK_CUDA(c, launch_invit(pd, m, zoff, st));
+    for (int pass = 0; pass < 2; ++pass) {
+      TK_CUDA(c, launch_zgram_batched(pd, m, st));   // problems with R <= 64
+      for (int q = 0; q < m; ++q)
+        if (h[q].R > zgram_batched_max_r()) {
+          const SlabView zv{1, (int64_t)h[q].R, (int64_t)h[q].n, 1};
+          TK_TRY(do_gram(c, h[q].z, TUCKER_F64, zv, TUCKER_PREC_FP64, h[q].gram, nullptr));
+        }
+      TK_CUDA(c, launch_chol(pd, m, st));
+      TK_CUDA(c, launch_trsm_rows(pd, m, roff, st));
+    }
+    TK_CUDA(c, launch_backtransform(pd, m, zoff, nmax, st));
+    std::vector<int> info(m);
+    TK_CUDA(c, cudaMemcpyAsync(info.data(), info_d, sizeof(int) * m, cudaMemcpyDeviceToHost, st));
+    TK_TRY(sync(c));
+    // ---- results of the step, Jacobi where the Cholesky QR refused, TTMs
+    for (int q = 0; q < m; ++q) {
+      const int i = act[q], n = h[q].n;
+      int64_t Rq = R[q];
+      double dq = disc[q];
+      res[i]->eig_kernel[s] = 1;
+      if (info[q]) {
+        DevBuf S2, V2, U2;
+        TK_TRY(dev_alloc(c, S2, sizeof(double) * (size_t)n * n));
+        TK_TRY(dev_alloc(c, V2, sizeof(double) * (size_t)n * n));
+        const SlabView v = slab_view(ndims[i], cur[i].data(), s);
+        TK_TRY(do_gram(c, y[i], ydt[i], v, gprec[i], S2.as<double>(), nullptr, -1.0, false));
+        int sweeps = 0;
+        tucker_status es = do_eig(c, S2.as<double>(), n, h[q].w, V2.as<double>(), &sweeps);
+        if (es != TUCKER_OK && es != TUCKER_ERR_EIG_NOCONV) return es;
+        TK_TRY(do_cut(c, h[q].w, n, thr[q], 0, &Rq, &dq));
+        TK_TRY(dev_alloc(c, U2, sizeof(double) * (size_t)n * Rq));
+        TK_CUDA(c, cudaMemcpyAsync(U2.p, V2.p, sizeof(double) * n * Rq, cudaMemcpyDeviceToDevice, st));
+        ubuf[q].reset();
+        ubuf[q].p = U2.release();
+        ubuf[q].st = st;
+        res[i]->eig_kernel[s] = 0;
+        res[i]->jacobi_sweeps[s] = sweeps;
+      }
+      res[i]->ranks[s] = Rq;
+      res[i]->discarded_sq[s] = dq;
+      res[i]->eigvals[s] = static_cast<double*>(wbuf[q].release());
+      res[i]->factors[s] = ubuf[q].as<double>();
+      ubuf[q].release();
+      const SlabView v = slab_view(ndims[i], cur[i].data(), s);
+      std::vector<int64_t> nd = cur[i];
+      nd[s] = Rq;
+      DevBuf z;
+      TK_TRY(dev_alloc(c, z, dtype_size(wdt) * numel(ndims[i], nd.data())));
+      TK_TRY(do_ttm(c, y[i], ydt[i], v, res[i]->factors[s], Rq, n, 1, prec, z.p, wdt,
+                    &res[i]->ttm_kernel[s], s == 0 ? xmax[i] : -1.0, false));
+      ycur[i].reset();
+      ycur[i].p = z.release();
+      ycur[i].st = st;
+      y[i] = ycur[i].p;
+      ydt[i] = wdt;
+      cur[i][s] = Rq;
+    }
+  }
+  unsigned werr[2] = {0, 0};
+  TK_CUDA(c, cudaMemcpyAsync(werr, c->d_words + 8, sizeof(werr), cudaMemcpyDeviceToHost, st));
+  t_total.stop(c);
+  TK_TRY(sync(c));
+  if (werr[0] | werr[1]) {
+    char msg[96];
+    snprintf(msg, sizeof msg, "tensor-core kernel reported device error words 0x%x 0x%x", werr[0], werr[1]);
+    return set_err(c, TUCKER_ERR_CUDA, msg);
+  }
+  const float ms = c->timing ? t_total.ms() : 0.f;
+  for (int i = 0; i < count; ++i) {
+    res[i]->core = ycur[i].release();
+    res[i]->ms_total = ms;
+    out[i] = res[i];
+    res[i] = nullptr;
+  }
   return TUCKER_OK;
 }
 

@@ -110,5 +110,11 @@ cudaError_t launch_chol(const EigProblem* probs_dev, int count, cudaStream_t st)
 cudaError_t launch_trsm_rows(const EigProblem* probs_dev, int count, int total_rows, cudaStream_t st);
 cudaError_t launch_backtransform(const EigProblem* probs_dev, int count, int total_vectors,
                                  int nmax, cudaStream_t st);
+// batched rank cut (thr[p], fixed[p] > 0 or NULL) and Z^T Z for problems with R <= 64
+cudaError_t launch_rank_cut_batched(const EigProblem* probs_dev, int count, const double* thr,
+                                    const int* fixed, int64_t* R_out, double* disc_out,
+                                    cudaStream_t st);
+int zgram_batched_max_r();
+cudaError_t launch_zgram_batched(const EigProblem* probs_dev, int count, cudaStream_t st);
 
 }  // namespace tk

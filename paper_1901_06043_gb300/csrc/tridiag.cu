@@ -736,7 +736,92 @@ __global__ void __launch_bounds__(256) k_backtransform(const EigProblem* probs, 
   for (int i = threadIdx.x; i < n; i += blockDim.x) P.U[(int64_t)j * n + i] = zs[i];
 }
 
+// ---------------------------------------------------------------- batched helpers
+// Rank cut of Eq. Un for each problem (one thread each): R = min{R in 1..n :
+// tail(R) <= thr}, tail accumulated from the smallest eigenvalue up (the same
+// order as k_rank_cut), or R = fixed when fixed > 0; disc = tail(R).
+__global__ void k_rank_cut_batched(const EigProblem* probs, int count, const double* thr,
+                                   const int* fixed, int64_t* R_out, double* disc_out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  const EigProblem P = probs[p];
+  const int n = P.n;
+  const int fr = fixed ? fixed[p] : 0;
+  double tail = 0.0, best_tail = 0.0;
+  int best = n;
+  for (int R = n - 1; R >= 1; --R) {
+    tail += P.w[R];
+    if (fr > 0 ? (R == fr) : (tail <= thr[p])) { best = R; best_tail = tail; }
+  }
+  if (fr > 0 && fr == n) { best = n; best_tail = 0.0; }
+  R_out[p] = best;
+  disc_out[p] = best_tail;
+}
+
+// G = Z^T Z (R x R, full) for each problem with R <= 64, one CTA each: rows of
+// Z staged 16 at a time in shared memory, one thread per lower-triangle entry
+// (several when R(R+1)/2 > 256), FP64 sums in row order.
+constexpr int ZG_MAXR = 64, ZG_ROWS = 16, ZG_PPT = (ZG_MAXR * (ZG_MAXR + 1) / 2 + TNT - 1) / TNT;
+__global__ void __launch_bounds__(TNT) k_zgram_batched(const EigProblem* probs) {
+  const EigProblem P = probs[blockIdx.x];
+  const int n = P.n, R = P.R;
+  if (R > ZG_MAXR || *P.info) return;
+  __shared__ double zs[ZG_ROWS][ZG_MAXR + 1];
+  const int npair = R * (R + 1) / 2;
+  int pa[ZG_PPT], pb[ZG_PPT];
+  double acc[ZG_PPT];
+#pragma unroll
+  for (int q = 0; q < ZG_PPT; ++q) {
+    const int t = threadIdx.x + TNT * q;
+    int a = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+    while ((a + 1) * (a + 2) / 2 <= t) ++a;
+    while (a * (a + 1) / 2 > t) --a;
+    pa[q] = (t < npair) ? a : 0;
+    pb[q] = (t < npair) ? t - a * (a + 1) / 2 : 0;
+    acc[q] = 0.0;
+  }
+  for (int i0 = 0; i0 < n; i0 += ZG_ROWS) {
+    __syncthreads();
+    for (int c = threadIdx.x; c < ZG_ROWS * R; c += TNT) {
+      const int r = c / R, a = c - r * R;
+      zs[r][a] = (i0 + r < n) ? P.z[(int64_t)(i0 + r) * R + a] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < ZG_PPT; ++q) {
+      if (threadIdx.x + TNT * q >= npair) break;
+      double s = acc[q];
+#pragma unroll
+      for (int r = 0; r < ZG_ROWS; ++r) s = fma(zs[r][pa[q]], zs[r][pb[q]], s);
+      acc[q] = s;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < ZG_PPT; ++q) {
+    if (threadIdx.x + TNT * q >= npair) break;
+    P.gram[(int64_t)pa[q] * R + pb[q]] = acc[q];
+    P.gram[(int64_t)pb[q] * R + pa[q]] = acc[q];
+  }
+}
+
 // ---------------------------------------------------------------- launchers
+cudaError_t launch_rank_cut_batched(const EigProblem* probs_dev, int count, const double* thr,
+                                    const int* fixed, int64_t* R_out, double* disc_out,
+                                    cudaStream_t st) {
+  k_rank_cut_batched<<<(count + 127) / 128, 128, 0, st>>>(probs_dev, count, thr, fixed, R_out,
+                                                           disc_out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+int zgram_batched_max_r() { return ZG_MAXR; }
+
+cudaError_t launch_zgram_batched(const EigProblem* probs_dev, int count, cudaStream_t st) {
+  k_zgram_batched<<<count, TNT, 0, st>>>(probs_dev);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 namespace {
 int tridiag_rows_per_cta(int n, int G) { return (n + G - 1) / G; }
 size_t tridiag_base_smem(int n) { return sizeof(double) * (3 * (size_t)n + 2 * (TNW + 4)); }

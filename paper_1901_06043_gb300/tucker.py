@@ -24,7 +24,8 @@ OPT_TIMING, OPT_MAX_SWEEPS, OPT_JACOBI_TOL, OPT_EIG_SOLVER = 1, 2, 3, 4
 EIG_SOLVER = {"auto": 0, "jacobi": 1, "tridiag": 2}
 
 EXPORTS = ["tucker_create", "tucker_destroy", "tucker_last_error", "tucker_set_option",
-           "tucker_sthosvd", "tucker_result_destroy", "tucker_reconstruct",
+           "tucker_sthosvd", "tucker_sthosvd_batched", "tucker_result_destroy",
+           "tucker_reconstruct",
            "tucker_multi_ttm", "tucker_ttm_order", "tucker_norm_sq", "tucker_gram",
            "tucker_eig", "tucker_eig_trunc", "tucker_rank_cut", "tucker_ttm",
            "tucker_kernel_launches", "tucker_gram_noalloc"]
@@ -80,6 +81,10 @@ def lib():
         L.tucker_set_option.argtypes = [vp, c_int, ctypes.c_double]
         L.tucker_sthosvd.argtypes = [vp, vp, c_int, c_int, i64p, ctypes.c_double, i64p,
                                      ctypes.POINTER(c_int), c_int, ctypes.POINTER(ctypes.POINTER(CResult))]
+        L.tucker_sthosvd_batched.argtypes = [vp, c_int, ctypes.POINTER(vp), c_int,
+                                             ctypes.POINTER(c_int), ctypes.POINTER(i64p),
+                                             ctypes.c_double, c_int,
+                                             ctypes.POINTER(ctypes.POINTER(CResult))]
         L.tucker_result_destroy.argtypes = [ctypes.POINTER(CResult)]
         L.tucker_reconstruct.argtypes = [vp, ctypes.POINTER(CResult), i64p, i64p,
                                          ctypes.POINTER(c_int), c_int, vp, c_int]
@@ -272,6 +277,27 @@ class Context:
             lib().tucker_result_destroy(out)   # EIG_NOCONV still returns a result
         self._check(st)
         return Result(self, out)
+
+    def sthosvd_batched(self, xs, dims_list, eps, prec="fp64"):
+        """ST-HOSVD of several tensors at once (tucker_sthosvd_batched);
+        xs: contiguous CUDA tensors of one dtype, dims_list: their dims."""
+        n = len(xs)
+        if n != len(dims_list) or n < 1:
+            raise ValueError("xs and dims_list must have the same, nonzero length")
+        for t in xs:
+            _check_dev(t, "x")
+        codes = {_dtype_code(t) for t in xs}
+        if len(codes) != 1:
+            raise TypeError("all tensors of a batch must have one dtype")
+        ptrs = (ctypes.c_void_p * n)(*[t.data_ptr() for t in xs])
+        nd = (ctypes.c_int * n)(*[len(d) for d in dims_list])
+        dim_arrs = [(ctypes.c_int64 * len(d))(*[int(v) for v in d]) for d in dims_list]
+        dptrs = (ctypes.POINTER(ctypes.c_int64) * n)(
+            *[ctypes.cast(a, ctypes.POINTER(ctypes.c_int64)) for a in dim_arrs])
+        outs = (ctypes.POINTER(CResult) * n)()
+        self._check(lib().tucker_sthosvd_batched(self._c, n, ptrs, codes.pop(), nd, dptrs,
+                                                 float(eps), PREC[prec], outs))
+        return [Result(self, outs[i]) for i in range(n)]
 
     def reconstruct(self, res, begin=None, end=None, mode_order=None, prec="fp64", out_dtype=None):
         import torch
