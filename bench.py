@@ -43,6 +43,11 @@ WORKLOADS = {
                  eps=1e-4, dtype="f64", recon=(200, 200, 200, 1)),
     "small": dict(dims=(40, 50, 30), core=(5, 6, 4), decay=0.0, eta=1e-4, eps=1e-3, dtype="f64",
                   recon=(40, 50, 30)),
+    # 64 tensors of uneven shapes compressed by one batched call per step:
+    # 3-way cubes with sides uniform in [48, 256] and 4-way tensors
+    # [32..160]^3 x [4..16], FP32, core sides 8-32, decay 10^(-0.2 sum idx),
+    # relative noise 1e-6
+    "batch64": dict(batch=64, decay=0.2, eta=1e-6, eps=1e-4, dtype="f32"),
     # the large workload's first two time steps and 40 of its 500 mode-2
     # slices: a 0.9 GB case of the same kernels for profiler captures
     "prof": dict(dims=(500, 500, 40, 11, 2), core=(60, 60, 40, 11, 2), decay=0.08, eta=1e-7,
@@ -64,7 +69,26 @@ def peaks():
     return p
 
 
+def batch_shapes(w, seed):
+    """(dims, core) of every tensor of a batched workload (seeded)."""
+    rng = np.random.default_rng(1000 + seed)
+    out = []
+    for k in range(w["batch"]):
+        if k % 2 == 0:
+            a = int(rng.integers(48, 257))
+            dims = (a, a, a)
+        else:
+            dims = tuple(int(v) for v in rng.integers(32, 161, size=3)) + (int(rng.integers(4, 17)),)
+        core = tuple(min(d, int(rng.integers(8, 33))) for d in dims)
+        out.append((dims, core))
+    return out
+
+
 def describe(w):
+    if "batch" in w:
+        return (f"{w['batch']} {w['dtype']} tensors: 3-way cubes, sides uniform in [48, 256], and "
+                f"4-way [32..160]^3 x [4..16], cores 8-32 per side, decay 10^(-{w['decay']}*sum idx), "
+                f"noise {w['eta']:g}, eps {w['eps']:g}")
     d = "x".join(map(str, w["dims"]))
     c = "x".join(map(str, w["core"]))
     gb = np.prod(w["dims"]) * (4 if w["dtype"] == "f32" else 8) / 1e9
@@ -239,6 +263,8 @@ def main():
     from paper_1901_06043_gb300 import synth, tucker
 
     w = WORKLOADS[args.workload]
+    if "batch" in w:
+        return main_batch(args, w, ws, rank)
     prec = args.prec or ("mixed" if tucker_mixed_available() else "fp32")
     if w["dtype"] == "f64" and prec == "mixed":
         prec = "fp32"
@@ -369,6 +395,119 @@ def main():
         print(json.dumps(out))
     ctx.close()
     ctx_t.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main_batch(args, w, ws, rank):
+    """The batched workload: one step = one tucker_sthosvd_batched call over
+    all tensors (Algorithm 1 for each, lock-step by mode)."""
+    import torch
+    from paper_1901_06043_gb300 import synth, tucker
+    prec = args.prec or ("mixed" if tucker_mixed_available() else "fp32")
+    shapes = batch_shapes(w, args.seed + rank)
+    xs = [synth.tucker_torch(d, c, decay=w["decay"], eta=w["eta"], seed=args.seed + rank + 7 * k)
+          for k, (d, c) in enumerate(shapes)]
+    dims_list = [d for d, _ in shapes]
+    torch.cuda.synchronize()
+    in_bytes = sum(t.numel() * t.element_size() for t in xs)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # a bounded sample: the first tensors of the batch, on the host
+        k = max(1, min(len(xs), args.cpu_slices or 8))
+        hx = [t.double().cpu().numpy() for t in xs[:k]]
+        del xs
+        import oracle
+        ref_ms = []
+        for it in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            for xh, d in zip(hx, dims_list[:k]):
+                oracle.sthosvd(xh, d, eps=w["eps"])
+            if it >= args.warmup:
+                ref_ms.append((time.perf_counter() - t0) * 1e3)
+        ms = statistics.mean(ref_ms)
+        sbytes = sum(a.size * 4 for a in hx)
+        val = sbytes / 1e9 / (ms / 1e3)
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {describe(w)}", "prec": "fp64-cpu-oracle"},
+            "cpu_baseline": {"value": val, "unit": "GB/s", "cores": len(os.sched_getaffinity(0)),
+                             "kind": "oracle",
+                             "sample": f"oracle ST-HOSVD of the first {k} tensors of the batch"},
+            "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+    ctx = tucker.Context()
+    ranks = None
+    for _ in range(args.warmup):
+        rs = ctx.sthosvd_batched(xs, dims_list, w["eps"], prec=prec)
+        ranks = [r.ranks for r in rs]
+        for r in rs:
+            r.close()
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device())
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = tucker.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        rs = ctx.sthosvd_batched(xs, dims_list, w["eps"], prec=prec)
+        for r in rs:
+            r.close()
+    ev1.record()
+    torch.cuda.synchronize()
+    launches = (tucker.kernel_launches() - l0) // args.steps
+    barrier(ws)
+    clk = clocks.stop()
+    ms_local = ev0.elapsed_time(ev1) / args.steps
+    ms = reduce_max(ms_local, ws)
+    value = ws * in_bytes / 1e9 / (ms / 1e3)
+    pk = peaks()
+    out = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {describe(w)}", "prec": prec,
+                   "total_bytes": in_bytes, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{ws}"},
+        # the whole step against HBM: every input byte is read at least once
+        "roofline": {"bound": "hbm", "achieved": value, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": value / pk["hbm_gbs"], "traffic": None,
+                     "kernel": "whole batched step (input bytes / step time)"},
+        "step": "tucker_sthosvd_batched over all tensors",
+        "gpu_launches": int(launches), "clocks": clk,
+        "ranks_first": [list(r) for r in ranks[:4]],
+    }
+    if rank == 0 and not args.no_e2e:
+        # host-resident inputs: pinned copies in, every core and factor out
+        hx = [t.cpu().pin_memory() for t in xs]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = max(1, args.steps)
+        d2h = 0
+        e0.record()
+        for _ in range(steps):
+            dx = [h.to("cuda", non_blocking=True) for h in hx]
+            rs = ctx.sthosvd_batched(dx, dims_list, w["eps"], prec=prec)
+            d2h = 0
+            for r in rs:
+                core, fac = r.to_host()
+                d2h += core.nbytes + sum(f.nbytes for f in fac)
+                r.close()
+            del dx
+        e1.record()
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1) / steps
+        out["e2e"] = {"value": in_bytes / 1e9 / (ems / 1e3), "unit": "GB/s",
+                      "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": d2h}
+    print(json.dumps(out)) if rank == 0 else None
+    ctx.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -321,14 +321,14 @@ tucker_status do_eig_tri(tucker_ctx* c, const double* S, int n, double thr, int 
   h.w = w;
   h.info = info;
   h.n = n;
+  h.team_off = 0;
+  h.team_size = G;
   cudaStream_t st = c->stream;
   TK_CUDA(c, cudaMemcpyAsync(h.A, S, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
   TK_CUDA(c, cudaMemsetAsync(c->d_words + 32, 0, sizeof(unsigned) * 3, st));
   TK_CUDA(c, cudaMemsetAsync(info, 0, sizeof(int), st));
-  TK_CUDA(c, cudaMemcpyAsync(pd, &h, sizeof(h), cudaMemcpyHostToDevice, st));
-  const GridBarrier bar{c->d_words + 32, c->d_words + 33, c->d_words + 34};
-  TK_CUDA(c, launch_tridiag(pd, 1, n, true, c->num_sms, bar, st));
-  TK_CUDA(c, launch_bisect(pd, 1, n, st));
+  TK_CUDA(c, launch_tridiag(pd, &h, 1, c->d_words + 32, c->d_words + 34, st));
+  TK_CUDA(c, launch_bisect(pd, 1, n, n, c->num_sms, st));
   TK_CUDA(c, launch_rank_cut(w, n, thr, fixed_R, c->d_i64, c->d_small + 2, tail, st));
   int64_t R = 0;
   unsigned werr = 0;
@@ -842,23 +842,27 @@ tucker_status tucker_sthosvd_batched(tucker_ctx* c, int count, const void* const
     const int m = (int)act.size();
     // ---- per-problem workspace: A (Gram, reduced in place), d, e, tau, xch, wyT
     std::vector<size_t> wo(m);
+    std::vector<int> nq(m), team(m);
     size_t wtot = 0;
     int nmax = 0;
+    for (int q = 0; q < m; ++q) nq[q] = (int)cur[act[q]][s];
+    tridiag_batch_teams(nq.data(), m, c->num_sms, team.data());
     for (int q = 0; q < m; ++q) {
-      const int n = (int)cur[act[q]][s];
+      const int n = nq[q];
       nmax = std::max(nmax, n);
       wo[q] = wtot;
-      wtot += (size_t)n * n + 3 * (size_t)n + 4 * (size_t)n + 2 + eig_wy_doubles(n);
+      wtot += (size_t)n * n + 3 * (size_t)n + 4 * (size_t)n + 2 * (size_t)team[q] + eig_wy_doubles(n);
     }
     DevBuf work, meta;
     TK_TRY(dev_alloc(c, work, sizeof(double) * wtot));
     TK_TRY(dev_alloc(c, meta, sizeof(EigProblem) * m + sizeof(double) * m + sizeof(int64_t) * m +
-                                  sizeof(double) * m + sizeof(int) * m));
+                                  sizeof(double) * m + sizeof(int) * m + sizeof(unsigned) * (m + 1)));
     EigProblem* pd = meta.as<EigProblem>();
     double* thr_d = reinterpret_cast<double*>(pd + m);
     int64_t* R_d = reinterpret_cast<int64_t*>(thr_d + m);
     double* disc_d = reinterpret_cast<double*>(R_d + m);
     int* info_d = reinterpret_cast<int*>(disc_d + m);
+    unsigned* bars_d = reinterpret_cast<unsigned*>(info_d + m);   // m team barriers + error word
     std::vector<EigProblem> h(m);
     std::vector<DevBuf> wbuf(m);
     std::vector<double> thr(m);
@@ -871,9 +875,11 @@ tucker_status tucker_sthosvd_batched(tucker_ctx* c, int count, const void* const
       P.e = P.d + n;
       P.tau = P.e + n;
       P.xch = P.tau + n;
-      P.wyT = P.xch + 4 * (size_t)n + 2;
+      P.wyT = P.xch + 4 * (size_t)n + 2 * (size_t)team[q];
       P.info = info_d + q;
       P.n = n;
+      P.team_size = team[q];
+      P.team_off = q == 0 ? 0 : h[q - 1].team_off + h[q - 1].team_size;
       TK_TRY(dev_alloc(c, wbuf[q], sizeof(double) * n));
       P.w = wbuf[q].as<double>();
       thr[q] = res[i]->threshold;
@@ -881,12 +887,12 @@ tucker_status tucker_sthosvd_batched(tucker_ctx* c, int count, const void* const
       TK_TRY(do_gram(c, y[i], ydt[i], v, gprec[i], P.A, &res[i]->gram_kernel[s],
                      s == 0 ? xmax[i] : -1.0, false));
     }
-    TK_CUDA(c, cudaMemsetAsync(info_d, 0, sizeof(int) * m, st));
-    TK_CUDA(c, cudaMemcpyAsync(pd, h.data(), sizeof(EigProblem) * m, cudaMemcpyHostToDevice, st));
+    TK_CUDA(c, cudaMemsetAsync(info_d, 0, sizeof(int) * m + sizeof(unsigned) * (m + 1), st));
     TK_CUDA(c, cudaMemcpyAsync(thr_d, thr.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
-    const GridBarrier nobar{nullptr, nullptr, nullptr};
-    TK_CUDA(c, launch_tridiag(pd, m, nmax, false, c->num_sms, nobar, st));
-    TK_CUDA(c, launch_bisect(pd, m, nmax, st));
+    TK_CUDA(c, launch_tridiag(pd, h.data(), m, bars_d, bars_d + m, st));
+    int neig = 0;
+    for (int q = 0; q < m; ++q) neig += h[q].n;
+    TK_CUDA(c, launch_bisect(pd, m, nmax, neig, c->num_sms, st));
     TK_CUDA(c, launch_rank_cut_batched(pd, m, thr_d, nullptr, R_d, disc_d, st));
     std::vector<int64_t> R(m);
     std::vector<double> disc(m);
@@ -933,8 +939,12 @@ tucker_status tucker_sthosvd_batched(tucker_ctx* c, int count, const void* const
     }
     TK_CUDA(c, launch_backtransform(pd, m, zoff, nmax, st));
     std::vector<int> info(m);
+    unsigned berr = 0;
     TK_CUDA(c, cudaMemcpyAsync(info.data(), info_d, sizeof(int) * m, cudaMemcpyDeviceToHost, st));
+    TK_CUDA(c, cudaMemcpyAsync(&berr, bars_d + m, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     TK_TRY(sync(c));
+    if (berr & DEV_ERR_BARRIER_TIMEOUT)
+      return set_err(c, TUCKER_ERR_CUDA, "tridiagonalization team barrier gave up waiting");
     // ---- results of the step, Jacobi where the Cholesky QR refused, TTMs
     for (int q = 0; q < m; ++q) {
       const int i = act[q], n = h[q].n;

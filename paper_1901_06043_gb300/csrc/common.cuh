@@ -57,13 +57,16 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 // completes when it reaches k * gridDim.x); departure: acquire polling.  The
 // CTA's writes are ordered before thread 0's release by the preceding
 // __syncthreads.  The counter starts at 0 (memset by the host).
+// team > 0: the barrier spans `team` CTAs that share b.count (a team of a
+// larger cooperative grid) instead of the whole grid.
 __device__ __forceinline__ bool grid_sync(const GridBarrier& b, unsigned& my_gen,
-                                          unsigned long long limit = (1ull << 24)) {
+                                          unsigned long long limit = (1ull << 24),
+                                          unsigned team = 0) {
   __syncthreads();
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned target = (my_gen + 1) * gridDim.x;
+    const unsigned target = (my_gen + 1) * (team ? team : gridDim.x);
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(b.count), "r"(1u) : "memory");
     unsigned long long it = 0;
     while (ld_acquire_u32(b.count) < target) {

@@ -95,16 +95,25 @@ struct EigProblem {
   int n, R;
   int zoff;       // first flattened vector index of this problem
   int roff;       // first flattened row index of this problem
+  int team_off;   // k_tridiag: first CTA of this problem's team
+  int team_size;  // k_tridiag: CTAs of the team (xch holds 4 n + 2 team_size)
+  int srows;      // k_tridiag: the team's rows live in shared memory
 };
-size_t tridiag_smem_bytes(int n);
 int tridiag_team_size(int n, int num_sms);
+// Team sizes for a batch: 1 CTA each plus the remaining SMs shared in
+// proportion to n^3; all 1 when count >= num_sms.
+void tridiag_batch_teams(const int* n, int count, int num_sms, int* team);
 inline size_t eig_lu_bytes(int n, int R) { return (size_t)n * R * (4 * sizeof(double) + 2); }
 size_t eig_wy_doubles(int n);
-// grid = true: one problem on a cooperative grid of tridiag_team_size CTAs;
-// false: `count` problems, one CTA each
-cudaError_t launch_tridiag(const EigProblem* probs_dev, int count, int nmax, bool grid,
-                           int num_sms, GridBarrier bar, cudaStream_t st);
-cudaError_t launch_bisect(const EigProblem* probs_dev, int count, int nmax, cudaStream_t st);
+// Problems with their team_off / team_size set (teams back to back) and
+// team_size * n / ... as planned; probs_host is the host copy of the
+// descriptors (it sets the launch shape and each team's shared-memory rows).
+// bar_counts: `count` zeroed words (one barrier per team), err: error word.
+cudaError_t launch_tridiag(const EigProblem* probs_dev, EigProblem* probs_host, int count,
+                           unsigned* bar_counts, unsigned* err, cudaStream_t st);
+// total_eigs: the sum of n over the problems (sets the lanes per eigenvalue)
+cudaError_t launch_bisect(const EigProblem* probs_dev, int count, int nmax, int total_eigs,
+                          int num_sms, cudaStream_t st);
 cudaError_t launch_invit(const EigProblem* probs_dev, int count, int total_vectors, cudaStream_t st);
 cudaError_t launch_chol(const EigProblem* probs_dev, int count, cudaStream_t st);
 cudaError_t launch_trsm_rows(const EigProblem* probs_dev, int count, int total_rows, cudaStream_t st);

@@ -112,15 +112,22 @@ __device__ void house(double* vx, int k2, int n, double* red, double& tau, doubl
 }  // namespace
 
 // ---------------------------------------------------------------- stage 1
-// SROWS: the CTA's own rows live in shared memory (grid team, when they
-// fit); otherwise they are read and written in place in A (L2-resident).
-template <bool GRID, bool SROWS>
-__global__ void __launch_bounds__(TNT, 1) k_tridiag(const EigProblem* probs, GridBarrier bar) {
+// One team of P.team_size CTAs per problem (teams back to back in the grid);
+// a team of one synchronizes with __syncthreads, a larger one with its own
+// bounded barrier.  P.srows: the CTA's own rows live in shared memory;
+// otherwise they are read and written in place in A (L2-resident).
+__global__ void __launch_bounds__(TNT, 1) k_tridiag(const EigProblem* probs, int count,
+                                                    unsigned* bar_counts, unsigned* err) {
   extern __shared__ __align__(16) double tsm[];
-  const EigProblem P = probs[GRID ? 0 : blockIdx.x];
+  int pidx = 0;
+  while (pidx + 1 < count && probs[pidx + 1].team_off <= (int)blockIdx.x) ++pidx;
+  const EigProblem P = probs[pidx];
   const int n = P.n;
-  const int G = GRID ? (int)gridDim.x : 1;
-  const int c = GRID ? (int)blockIdx.x : 0;
+  const int G = P.team_size;
+  const int c = (int)blockIdx.x - P.team_off;
+  if (c < 0 || c >= G) return;
+  const bool SROWS = P.srows != 0;
+  const GridBarrier bar{bar_counts + pidx, nullptr, err};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* A = P.A;
   double* const xp = P.xch;               // p_k: 2 x n
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(TNT, 1) k_tridiag(const EigProblem* probs, Gri
     if (threadIdx.x == 0) xv[c] = s;
   }
   { double* t = vk; vk = vn; vn = t; }
-  if (GRID) { if (!grid_sync(bar, gen)) return; } else __syncthreads();
+  if (G > 1) { if (!grid_sync(bar, gen, 1ull << 24, (unsigned)G)) return; } else __syncthreads();
 
   // ---- phases 0 .. n-3
   for (int k = 0; k <= n - 3; ++k) {
@@ -271,7 +278,7 @@ __global__ void __launch_bounds__(TNT, 1) k_tridiag(const EigProblem* probs, Gri
     if (threadIdx.x == 0) xv[nb * G + c] = sp;
     { double* t = vk; vk = vn; vn = t; }
     tau_k = tau_n;
-    if (GRID) { if (!grid_sync(bar, gen)) return; } else __syncthreads();
+    if (G > 1) { if (!grid_sync(bar, gen, 1ull << 24, (unsigned)G)) return; } else __syncthreads();
   }
 }
 
@@ -281,25 +288,38 @@ __global__ void __launch_bounds__(TNT, 1) k_tridiag(const EigProblem* probs, Gri
 // from the three-term recurrence p_i = (d_{i-1} - x) p_{i-1} -
 // e_{i-2}^2 p_{i-2} (Wilkinson, The Algebraic Eigenvalue Problem, Ch. 5: the
 // computed signs are exact for a matrix within a few ulps of T).  No
-// division: two FP64 operations and one product per step (a division costs
-// ~7 times an FMA here).  Both minors are rescaled by a power of two when
-// their exponents leave [-256, 256] (integer tests on the bits); an exact
-// zero minor is replaced by -2^-600 times the previous one, the counterpart
-// of the -pivmin safeguard of the ratio form.
+// division: three FP64 operations a step (a division costs ~7 FMAs here).
+// T arrives scaled by a power of two to entries of magnitude <= 1, so the
+// minors grow by at most ~3 per step: both are rescaled by a power of two
+// when their exponents leave [-256, 256], tested every 8 steps.  An exact
+// zero minor becomes -sign(previous) 2^-600 (integer operations only), the
+// counterpart of the -pivmin safeguard of the ratio form; with e_i != 0 the
+// count is then the same as with the zero counted either way.
 __device__ __forceinline__ int exp_bits(double v) {
   return (int)((__double_as_longlong(v) >> 52) & 0x7ff);
 }
+__device__ __forceinline__ double nonzero_or_tiny(double pn, double pc) {
+  const long long b = __double_as_longlong(pn);
+  if ((b << 1) != 0) return pn;
+  // -sign(pc) * 2^-600
+  const long long t = (~__double_as_longlong(pc) & (long long)0x8000000000000000ull) |
+                      ((long long)(1023 - 600) << 52);
+  return __longlong_as_double(t);
+}
 __device__ __forceinline__ int sturm_count(const double* d, const double* e2, int n, double x) {
   double pm = 1.0;          // p_{i-1}
-  double pc = d[0] - x;     // p_i
-  if ((__double_as_longlong(pc) << 1) == 0) pc = -0x1p-600;
+  double pc = nonzero_or_tiny(d[0] - x, 1.0);
   int cnt = (int)((unsigned long long)__double_as_longlong(pc) >> 63);
-  for (int i = 1; i < n; ++i) {
-    double pn = fma(d[i] - x, pc, -e2[i - 1] * pm);
-    if ((__double_as_longlong(pn) << 1) == 0) pn = -0x1p-600 * pc;
-    cnt += (int)(((unsigned long long)(__double_as_longlong(pn) ^ __double_as_longlong(pc))) >> 63);
-    pm = pc;
-    pc = pn;
+  int i = 1;
+  while (i < n) {
+    const int iend = min(n, i + 8);
+#pragma unroll 8
+    for (; i < iend; ++i) {
+      const double pn = nonzero_or_tiny(fma(d[i] - x, pc, -e2[i - 1] * pm), pc);
+      cnt += (int)(((unsigned long long)(__double_as_longlong(pn) ^ __double_as_longlong(pc))) >> 63);
+      pm = pc;
+      pc = pn;
+    }
     const int em = max(exp_bits(pc), exp_bits(pm));
     if (em > 1023 + 256 || em < 1023 - 256) {
       const double f = __longlong_as_double((long long)(2046 - em) << 52);   // 2^(1023 - em)
@@ -310,17 +330,21 @@ __device__ __forceinline__ int sturm_count(const double* d, const double* e2, in
   return cnt;
 }
 
-// One warp per eigenvalue, one warp per SM sub-partition (the FP64 pipe of a
-// sub-partition is the limit).  Multisection: each round the 32 lanes count
-// at 32 interior points of [lo, hi] and the interval shrinks to the
-// sub-interval that holds eigenvalue number a (ascending), ~5 bits a round,
-// until its width is below 2 eps ||T|| (the accuracy of the counts).
-constexpr int BNW = 4;   // warps (eigenvalues) per CTA
-__global__ void __launch_bounds__(BNW * 32) k_bisect(const EigProblem* probs) {
+// Bisection by multisection: L lanes (1 <= L <= 32, a power of two) work on
+// one eigenvalue, each round counting at L interior points of [lo, hi] and
+// keeping the sub-interval that holds eigenvalue number a (ascending), until
+// its width is below 2 eps ||T|| (the accuracy of the counts).  A warp issues
+// one FP64 instruction per step whatever its lanes do, so L trades rounds
+// (53 / log2(L + 1)) against warps: wide L for a few eigenvalues, narrow L for
+// many.  CTA = BNW warps of one problem.
+constexpr int BNW = 4;
+__global__ void __launch_bounds__(BNW * 32) k_bisect(const EigProblem* probs, int L) {
   extern __shared__ __align__(16) double bsm[];
   const EigProblem P = probs[blockIdx.y];
   const int n = P.n;
-  if ((int)blockIdx.x * BNW >= n) return;
+  const int per_warp = 32 / L;
+  const int per_cta = BNW * per_warp;
+  if ((int)blockIdx.x * per_cta >= n) return;
   double* d = bsm;
   double* e2 = bsm + n;
   __shared__ double s_lo[BNW * 32], s_hi[BNW * 32];
@@ -329,8 +353,6 @@ __global__ void __launch_bounds__(BNW * 32) k_bisect(const EigProblem* probs) {
     const double di = P.d[i];
     const double el = (i > 0) ? fabs(P.e[i - 1]) : 0.0;
     const double er = (i < n - 1) ? fabs(P.e[i]) : 0.0;
-    d[i] = di;
-    if (i < n - 1) e2[i] = er * er;
     glo = fmin(glo, di - el - er);
     ghi = fmax(ghi, di + el + er);
   }
@@ -342,25 +364,41 @@ __global__ void __launch_bounds__(BNW * 32) k_bisect(const EigProblem* probs) {
     ghi = fmax(ghi, s_hi[i]);
   }
   const double tnorm = fmax(fabs(glo), fabs(ghi));
-  const double atol = 2.0 * DBL_EPSILON * tnorm + DBL_MIN;
-  glo -= 2.0 * DBL_EPSILON * tnorm * n + DBL_MIN;
-  ghi += 2.0 * DBL_EPSILON * tnorm * n + DBL_MIN;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = blockIdx.x * BNW + warp;          // descending index
-  if (j >= n) return;
-  const int a = n - 1 - j;                        // ascending index
-  double lo = glo, hi = ghi;
-  for (int round = 0; round < 16 && hi - lo > atol; ++round) {
-    const double x = lo + (hi - lo) * ((double)(lane + 1) / 33.0);
-    const int cnt = sturm_count(d, e2, n, x);
-    const unsigned above = __ballot_sync(0xffffffffu, cnt > a);
-    const int m = above ? (__ffs(above) - 1) : 32;
-    const double xm = __shfl_sync(0xffffffffu, x, m < 32 ? m : 31);
-    const double xl = __shfl_sync(0xffffffffu, x, m > 0 ? m - 1 : 0);
-    if (m < 32) hi = xm;
-    if (m > 0) lo = xl;
+  // scale by 2^-ex (exact) so that ||T|| / 2^ex is in [0.5, 1)
+  const int ex = (tnorm > 0.0) ? exp_bits(tnorm) - 1022 : 0;
+  const double sc = __longlong_as_double((long long)(1023 - ex) << 52);
+  const double isc = __longlong_as_double((long long)(1023 + ex) << 52);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    d[i] = P.d[i] * sc;
+    if (i < n - 1) { const double ei = P.e[i] * sc; e2[i] = ei * ei; }
   }
-  if (lane == 0) P.w[j] = 0.5 * (lo + hi);
+  __syncthreads();
+  const double tn = tnorm * sc;
+  const double atol = 2.0 * DBL_EPSILON * tn + DBL_MIN;
+  glo = glo * sc - (2.0 * DBL_EPSILON * tn * n + DBL_MIN);
+  ghi = ghi * sc + (2.0 * DBL_EPSILON * tn * n + DBL_MIN);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / L, l = lane % L;                         // group, lane in group
+  const int j = blockIdx.x * per_cta + warp * per_warp + g;     // descending index
+  const bool valid = j < n;
+  const int a = n - 1 - (valid ? j : n - 1);                    // ascending index
+  const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (g * L));
+  double lo = glo, hi = ghi;
+  for (int round = 0; round < 64; ++round) {
+    const bool active = valid && (hi - lo > atol);
+    if (!__any_sync(0xffffffffu, active)) break;
+    const double x = lo + (hi - lo) * ((double)(l + 1) / (double)(L + 1));
+    const int cnt = active ? sturm_count(d, e2, n, x) : 0;
+    const unsigned above = __ballot_sync(0xffffffffu, active && cnt > a) & gmask;
+    const int m = above ? (__ffs(above) - 1 - g * L) : L;      // first point above, in group
+    const double xm = __shfl_sync(0xffffffffu, x, g * L + (m < L ? m : L - 1));
+    const double xl = __shfl_sync(0xffffffffu, x, g * L + (m > 0 ? m - 1 : 0));
+    if (active) {
+      if (m < L) hi = xm;
+      if (m > 0) lo = xl;
+    }
+  }
+  if (valid && l == 0) P.w[j] = 0.5 * (lo + hi) * isc;
 }
 
 // ---------------------------------------------------------------- stage 4
@@ -825,10 +863,8 @@ cudaError_t launch_zgram_batched(const EigProblem* probs_dev, int count, cudaStr
 namespace {
 int tridiag_rows_per_cta(int n, int G) { return (n + G - 1) / G; }
 size_t tridiag_base_smem(int n) { return sizeof(double) * (3 * (size_t)n + 2 * (TNW + 4)); }
-constexpr size_t kTridiagSmemRowsCap = 160 * 1024;
+constexpr size_t kTridiagSmemRowsCap = 120 * 1024;
 }  // namespace
-
-size_t tridiag_smem_bytes(int n) { return tridiag_base_smem(n); }
 
 // ~6 rows per CTA at the first step (the step time is latency-bound: 2 to 8
 // rows per CTA measured within 8% of each other at n = 500), at most one CTA
@@ -838,40 +874,62 @@ int tridiag_team_size(int n, int num_sms) {
   return G > num_sms ? num_sms : (G < 1 ? 1 : G);
 }
 
-cudaError_t launch_tridiag(const EigProblem* probs_dev, int count, int nmax, bool grid,
-                           int num_sms, GridBarrier bar, cudaStream_t st) {
-  cudaError_t e;
-  if (grid) {
-    const int G = tridiag_team_size(nmax, num_sms);
-    const size_t srow = sizeof(double) * (size_t)tridiag_rows_per_cta(nmax, G) * nmax;
-    const bool sr = tridiag_base_smem(nmax) + srow <= kTridiagSmemRowsCap;
-    const size_t smem = tridiag_base_smem(nmax) + (sr ? srow : 0);
-    void* fn = sr ? (void*)k_tridiag<true, true> : (void*)k_tridiag<true, false>;
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+void tridiag_batch_teams(const int* n, int count, int num_sms, int* team) {
+  for (int p = 0; p < count; ++p) team[p] = 1;
+  if (count >= num_sms) return;
+  double tot = 0.0;
+  for (int p = 0; p < count; ++p) tot += (double)n[p] * n[p] * n[p];
+  const int extra = num_sms - count;
+  for (int p = 0; p < count; ++p) {
+    int g = 1 + (int)(extra * ((double)n[p] * n[p] * n[p]) / (tot > 0.0 ? tot : 1.0));
+    const int cap = tridiag_team_size(n[p], num_sms);
+    team[p] = g < cap ? g : cap;
+  }
+}
+
+cudaError_t launch_tridiag(const EigProblem* probs_dev, EigProblem* probs_host, int count,
+                           unsigned* bar_counts, unsigned* err, cudaStream_t st) {
+  int nmax = 0, grid = 0, multi = 0;
+  size_t rows_max = 0;
+  for (int p = 0; p < count; ++p) {
+    EigProblem& P = probs_host[p];
+    nmax = P.n > nmax ? P.n : nmax;
+    const size_t rb = sizeof(double) * (size_t)tridiag_rows_per_cta(P.n, P.team_size) * P.n;
+    P.srows = rb <= kTridiagSmemRowsCap;
+    if (P.srows && rb > rows_max) rows_max = rb;
+    grid += P.team_size;
+    multi |= P.team_size > 1;
+  }
+  const size_t smem = tridiag_base_smem(nmax) + rows_max;
+  cudaError_t e = cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(const_cast<EigProblem*>(probs_dev), probs_host, sizeof(EigProblem) * count,
+                      cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
+  if (multi) {
+    // teams of several CTAs spin on each other: all CTAs must be resident
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TNT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag, TNT, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-    void* args[] = {(void*)&probs_dev, (void*)&bar};
-    e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(TNT), args, smem, st);
-    count_launches(1);
-    return e;
+    void* args[] = {(void*)&probs_dev, (void*)&count, (void*)&bar_counts, (void*)&err};
+    return cudaLaunchCooperativeKernel((void*)k_tridiag, dim3(grid), dim3(TNT), args, smem, st);
   }
-  const size_t smem = tridiag_base_smem(nmax);
-  e = cudaFuncSetAttribute(k_tridiag<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-  if (e != cudaSuccess) return e;
-  k_tridiag<false, false><<<count, TNT, smem, st>>>(probs_dev, bar);
-  count_launches(1);
+  k_tridiag<<<grid, TNT, smem, st>>>(probs_dev, count, bar_counts, err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_bisect(const EigProblem* probs_dev, int count, int nmax, cudaStream_t st) {
+cudaError_t launch_bisect(const EigProblem* probs_dev, int count, int nmax, int total_eigs,
+                          int num_sms, cudaStream_t st) {
+  // lanes per eigenvalue: about one warp per SM sub-partition in total
+  int L = 32;
+  while (L > 1 && (int64_t)total_eigs * L > (int64_t)num_sms * 4 * 32) L >>= 1;
   const size_t smem = sizeof(double) * 2 * (size_t)nmax;
   cudaError_t e = cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_bisect<<<dim3((nmax + BNW - 1) / BNW, count), BNW * 32, smem, st>>>(probs_dev);
+  const int per_cta = BNW * (32 / L);
+  k_bisect<<<dim3((nmax + per_cta - 1) / per_cta, count), BNW * 32, smem, st>>>(probs_dev, L);
   count_launches(1);
   return cudaGetLastError();
 }
