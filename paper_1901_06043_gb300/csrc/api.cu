@@ -33,6 +33,11 @@ struct tucker_ctx {
   double* d_small = nullptr;     // 64 doubles
   int* d_info = nullptr;         // 16 ints
   int64_t* d_i64 = nullptr;      // 16 int64
+  // side streams for independent work of a batch (fork / join by events)
+  static constexpr int kSide = 8;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t side_ev[kSide] = {};
+  cudaEvent_t fork_ev = nullptr;
 };
 
 namespace {
@@ -122,6 +127,31 @@ tucker_status sync(tucker_ctx* c) {
   TK_CUDA(c, cudaStreamSynchronize(c->stream));
   return TUCKER_OK;
 }
+
+// Side streams start after everything enqueued so far on the context stream
+// (fork) and the context stream continues after all of them (join).  Work
+// issued while c->stream is switched to a side stream keeps its scratch
+// allocations stream-ordered on that side stream.
+tucker_status fork_side(tucker_ctx* c) {
+  TK_CUDA(c, cudaEventRecord(c->fork_ev, c->stream));
+  for (int k = 0; k < tucker_ctx::kSide; ++k)
+    TK_CUDA(c, cudaStreamWaitEvent(c->side[k], c->fork_ev, 0));
+  return TUCKER_OK;
+}
+tucker_status join_side(tucker_ctx* c) {
+  for (int k = 0; k < tucker_ctx::kSide; ++k) {
+    TK_CUDA(c, cudaEventRecord(c->side_ev[k], c->side[k]));
+    TK_CUDA(c, cudaStreamWaitEvent(c->stream, c->side_ev[k], 0));
+  }
+  return TUCKER_OK;
+}
+struct StreamSwap {
+  tucker_ctx* c;
+  cudaStream_t main;
+  explicit StreamSwap(tucker_ctx* cc) : c(cc), main(cc->stream) {}
+  void to(int k) { c->stream = c->side[k % tucker_ctx::kSide]; }
+  ~StreamSwap() { c->stream = main; }
+};
 
 struct Timer {
   cudaEvent_t a = nullptr, b = nullptr;
@@ -471,9 +501,19 @@ tucker_status tucker_create(tucker_ctx** out, void* stream) {
   if (e == cudaSuccess) e = cudaMalloc(&c->d_small, sizeof(double) * 64);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_info, sizeof(int) * 16);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_i64, sizeof(int64_t) * 16);
+  for (int k = 0; k < tucker_ctx::kSide && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->side_ev[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaGetLastError();
     cudaFree(c->d_words); cudaFree(c->d_small); cudaFree(c->d_info); cudaFree(c->d_i64);
+    for (int k = 0; k < tucker_ctx::kSide; ++k) {
+      if (c->side[k]) cudaStreamDestroy(c->side[k]);
+      if (c->side_ev[k]) cudaEventDestroy(c->side_ev[k]);
+    }
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
     delete c;
     return e == cudaErrorMemoryAllocation ? TUCKER_ERR_OOM : TUCKER_ERR_CUDA;
   }
@@ -488,6 +528,12 @@ tucker_status tucker_destroy(tucker_ctx* c) {
   cudaFree(c->d_small);
   cudaFree(c->d_info);
   cudaFree(c->d_i64);
+  for (int k = 0; k < tucker_ctx::kSide; ++k) {
+    cudaStreamSynchronize(c->side[k]);
+    cudaStreamDestroy(c->side[k]);
+    cudaEventDestroy(c->side_ev[k]);
+  }
+  cudaEventDestroy(c->fork_ev);
   delete c;
   return TUCKER_OK;
 }
@@ -866,6 +912,10 @@ tucker_status tucker_sthosvd_batched(tucker_ctx* c, int count, const void* const
     std::vector<EigProblem> h(m);
     std::vector<DevBuf> wbuf(m);
     std::vector<double> thr(m);
+    for (int q = 0; q < m; ++q) TK_TRY(dev_alloc(c, wbuf[q], sizeof(double) * nq[q]));
+    Timer tg, te, tt;
+    tg.start(c);
+    TK_TRY(fork_side(c));
     for (int q = 0; q < m; ++q) {
       const int i = act[q], n = (int)cur[i][s];
       EigProblem& P = h[q];
@@ -880,13 +930,17 @@ tucker_status tucker_sthosvd_batched(tucker_ctx* c, int count, const void* const
       P.n = n;
       P.team_size = team[q];
       P.team_off = q == 0 ? 0 : h[q - 1].team_off + h[q - 1].team_size;
-      TK_TRY(dev_alloc(c, wbuf[q], sizeof(double) * n));
       P.w = wbuf[q].as<double>();
       thr[q] = res[i]->threshold;
       const SlabView v = slab_view(ndims[i], cur[i].data(), s);
+      StreamSwap sw(c);
+      sw.to(q);
       TK_TRY(do_gram(c, y[i], ydt[i], v, gprec[i], P.A, &res[i]->gram_kernel[s],
                      s == 0 ? xmax[i] : -1.0, false));
     }
+    TK_TRY(join_side(c));
+    tg.stop(c);
+    te.start(c);
     TK_CUDA(c, cudaMemsetAsync(info_d, 0, sizeof(int) * m + sizeof(unsigned) * (m + 1), st));
     TK_CUDA(c, cudaMemcpyAsync(thr_d, thr.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
     TK_CUDA(c, launch_tridiag(pd, h.data(), m, bars_d, bars_d + m, st));
@@ -945,7 +999,7 @@ tucker_status tucker_sthosvd_batched(tucker_ctx* c, int count, const void* const
     TK_TRY(sync(c));
     if (berr & DEV_ERR_BARRIER_TIMEOUT)
       return set_err(c, TUCKER_ERR_CUDA, "tridiagonalization team barrier gave up waiting");
-    // ---- results of the step, Jacobi where the Cholesky QR refused, TTMs
+    // ---- results of the step, Jacobi where the Cholesky QR refused
     for (int q = 0; q < m; ++q) {
       const int i = act[q], n = h[q].n;
       int64_t Rq = R[q];
@@ -974,19 +1028,46 @@ tucker_status tucker_sthosvd_batched(tucker_ctx* c, int count, const void* const
       res[i]->eigvals[s] = static_cast<double*>(wbuf[q].release());
       res[i]->factors[s] = ubuf[q].as<double>();
       ubuf[q].release();
-      const SlabView v = slab_view(ndims[i], cur[i].data(), s);
+    }
+    te.stop(c);
+    tt.start(c);
+    // ---- TTMs of all tensors on the side streams; outputs allocated (and the
+    // inputs released, after the join) on the context stream
+    std::vector<DevBuf> znew(m);
+    for (int q = 0; q < m; ++q) {
+      const int i = act[q];
       std::vector<int64_t> nd = cur[i];
-      nd[s] = Rq;
-      DevBuf z;
-      TK_TRY(dev_alloc(c, z, dtype_size(wdt) * numel(ndims[i], nd.data())));
-      TK_TRY(do_ttm(c, y[i], ydt[i], v, res[i]->factors[s], Rq, n, 1, prec, z.p, wdt,
-                    &res[i]->ttm_kernel[s], s == 0 ? xmax[i] : -1.0, false));
+      nd[s] = res[i]->ranks[s];
+      TK_TRY(dev_alloc(c, znew[q], dtype_size(wdt) * numel(ndims[i], nd.data())));
+    }
+    TK_TRY(fork_side(c));
+    for (int q = 0; q < m; ++q) {
+      const int i = act[q];
+      const SlabView v = slab_view(ndims[i], cur[i].data(), s);
+      StreamSwap sw(c);
+      sw.to(q);
+      TK_TRY(do_ttm(c, y[i], ydt[i], v, res[i]->factors[s], res[i]->ranks[s], h[q].n, 1, prec,
+                    znew[q].p, wdt, &res[i]->ttm_kernel[s], s == 0 ? xmax[i] : -1.0, false));
+    }
+    TK_TRY(join_side(c));
+    for (int q = 0; q < m; ++q) {
+      const int i = act[q];
       ycur[i].reset();
-      ycur[i].p = z.release();
+      ycur[i].p = znew[q].release();
       ycur[i].st = st;
       y[i] = ycur[i].p;
       ydt[i] = wdt;
-      cur[i][s] = Rq;
+      cur[i][s] = res[i]->ranks[s];
+    }
+    tt.stop(c);
+    if (c->timing) {
+      // phases are shared by the whole batch: every result gets their times
+      const float g = tg.ms(), e = te.ms(), t = tt.ms();
+      for (int q = 0; q < m; ++q) {
+        res[act[q]]->ms_gram[s] = g;
+        res[act[q]]->ms_eig[s] = e;
+        res[act[q]]->ms_ttm[s] = t;
+      }
     }
   }
   unsigned werr[2] = {0, 0};

@@ -16,7 +16,7 @@
 // thread when I(I+1)/2 > 256); a CTA stages K-blocks of 16 (the K geometry of
 // gram_order.cuh) in shared memory as FP64 and walks K-blocks blockIdx.x,
 // blockIdx.x + gridDim.x, ...; each CTA writes its partial triangle and a
-// second kernel sums the partials in CTA order.
+// second kernel sums the partials (a fixed order, see k_gram_small_reduce).
 #include "common.cuh"
 #include "gram_order.cuh"
 #include "kernels.h"
@@ -90,20 +90,27 @@ __global__ void __launch_bounds__(SNT) k_gram_small(const TIn* __restrict__ y, K
   }
 }
 
-// S[i][j] = S[j][i] = sum over CTAs (in order) of the partial triangles.
+// S[i][j] = S[j][i] = sum over CTAs of the partial triangles: one warp per
+// entry, lane l summing parts l, l + 32, ... in order, then a fixed butterfly
+// across the lanes (a chain of ~nparts / 32 FP64 additions instead of nparts).
 __global__ void k_gram_small_reduce(const double* __restrict__ part, int nparts, int I,
                                     double* __restrict__ S) {
   const int npair = I * (I + 1) / 2;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (p >= npair) return;
   int i = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
   while ((i + 1) * (i + 2) / 2 <= p) ++i;
   while (i * (i + 1) / 2 > p) --i;
   const int j = p - i * (i + 1) / 2;
   double s = 0.0;
-  for (int k = 0; k < nparts; ++k) s += part[(int64_t)k * npair + p];
-  S[(int64_t)i * I + j] = s;
-  S[(int64_t)j * I + i] = s;
+  for (int k = lane; k < nparts; k += 32) s += part[(int64_t)k * npair + p];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    S[(int64_t)i * I + j] = s;
+    S[(int64_t)j * I + i] = s;
+  }
 }
 
 }  // namespace
@@ -130,7 +137,7 @@ cudaError_t launch_gram_small(const void* y, tucker_dtype dt, int64_t L, int64_t
   else
     k_gram_small<float><<<p.nctas, SNT, 0, st>>>((const float*)y, g, scratch);
   const int npair = (int)(I * (I + 1) / 2);
-  k_gram_small_reduce<<<(npair + 255) / 256, 256, 0, st>>>(scratch, p.nctas, (int)I, S);
+  k_gram_small_reduce<<<(npair + 7) / 8, 256, 0, st>>>(scratch, p.nctas, (int)I, S);
   count_launches(2);
   return cudaGetLastError();
 }
