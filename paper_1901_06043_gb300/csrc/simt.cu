@@ -92,29 +92,46 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 // FP32 input: x^2 = p + e exactly (p = fl(x*x), e = fma(x, x, -p)); the p
-// are summed as an FP32 pair (hi, lo) with TwoSum, flushed into FP64 every
-// 64 elements, so the result matches an FP64 sum of the exact squares to
-// ~1e-15 while the kernel stays on the FP32 pipe and the HBM roofline.
+// are summed as an FP32 pair (hi, lo) with TwoSum and the pair is moved into
+// the FP64 sum every 128 elements, so the result matches an FP64 sum of the
+// exact squares to ~1e-15 while the kernel stays on the FP32 pipe and the
+// HBM roofline.  Every FP64 instruction costs a sub-partition's FP64 pipe 64
+// cycles per warp, so the per-element path has none: the moves into FP64
+// convert on integer bits, max |x| and the non-finite test are integer
+// maxima of the bit patterns, and a group of 16 whose largest |x| is at
+// least 2^64 (an FP32 square could overflow) or nonzero and below 2^-60 (its
+// squares would underflow FP32) is squared in FP64 on a warp-uniform branch
+// (in a group with a larger value, squares below 2^-120 are ~2^-96 of it).
+__device__ __forceinline__ double f32_bits_to_f64(float x) {
+  // exact for normal x; zero and subnormals (below 1.2e-38) become 0
+  const unsigned u = __float_as_uint(x);
+  const unsigned ex = (u >> 23) & 0xffu;
+  const unsigned long long b = (unsigned long long)(u >> 31) << 63 |
+                               (unsigned long long)(ex + 1023u - 127u) << 52 |
+                               (unsigned long long)(u & 0x7fffffu) << 29;
+  return ex == 0u ? 0.0 : __longlong_as_double((long long)b);
+}
+
 struct SumSqF32 {
   double acc = 0.0;
-  float hi = 0.f, lo = 0.f, mx = 0.f;
-  bool bad = false;
-  __device__ __forceinline__ void add(float x) {
-    bad |= !isfinite(x);
-    mx = fmaxf(mx, fabsf(x));
+  float hi = 0.f, lo = 0.f;
+  unsigned mxb = 0;     // max |x| as bits; >= 0x7f800000: NaN or Inf seen
+  __device__ __forceinline__ void add_fast(float x) {
     const float p = x * x;
-    if (!isfinite(p)) {            // |x| > ~1.8e19: square in FP64 instead
-      acc = fma((double)x, (double)x, acc);
-      return;
-    }
     const float e = fmaf(x, x, -p);
     float s, err;
     two_sum(hi, p, s, err);
     hi = s;
     lo += err + e;
   }
+  __device__ __forceinline__ void add(float x) {   // tails: per-element test
+    const unsigned b = __float_as_uint(x) & 0x7fffffffu;
+    mxb = max(mxb, b);
+    if (b >= 0x5f800000u || (b != 0u && b < 0x21800000u)) acc = fma((double)x, (double)x, acc);
+    else add_fast(x);
+  }
   __device__ __forceinline__ void flush() {
-    acc += (double)hi + (double)lo;
+    acc += f32_bits_to_f64(hi) + f32_bits_to_f64(lo);
     hi = lo = 0.f;
   }
 };
@@ -131,13 +148,30 @@ __global__ void __launch_bounds__(256) k_sumsq_f32(const float* __restrict__ y, 
   const float4* yv = reinterpret_cast<const float4*>(y + head);
   // four independent 16-byte loads in flight per thread per iteration
   int64_t v = tid;
+  int groups = 0;
   for (; v + 3 * stride < nv; v += 4 * stride) {
     float4 q[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) q[u] = __ldcs(yv + v + u * stride);
+    unsigned gm = 0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) { s.add(q[u].x); s.add(q[u].y); s.add(q[u].z); s.add(q[u].w); }
-    s.flush();
+    for (int u = 0; u < 4; ++u) {
+      gm = max(gm, __float_as_uint(q[u].x) & 0x7fffffffu);
+      gm = max(gm, __float_as_uint(q[u].y) & 0x7fffffffu);
+      gm = max(gm, __float_as_uint(q[u].z) & 0x7fffffffu);
+      gm = max(gm, __float_as_uint(q[u].w) & 0x7fffffffu);
+    }
+    s.mxb = max(s.mxb, gm);
+    if (__any_sync(__activemask(), gm >= 0x5f800000u || (gm != 0u && gm < 0x21800000u))) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { s.add(q[u].x); s.add(q[u].y); s.add(q[u].z); s.add(q[u].w); }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        s.add_fast(q[u].x); s.add_fast(q[u].y); s.add_fast(q[u].z); s.add_fast(q[u].w);
+      }
+    }
+    if (++groups == 8) { s.flush(); groups = 0; }
   }
   for (; v < nv; v += stride) {
     const float4 q = __ldcs(yv + v);
@@ -146,7 +180,8 @@ __global__ void __launch_bounds__(256) k_sumsq_f32(const float* __restrict__ y, 
   for (int64_t i = tid; i < head; i += stride) s.add(y[i]);
   for (int64_t i = head + 4 * nv + tid; i < n; i += stride) s.add(y[i]);
   s.flush();
-  block_store_sum_max(s.acc, (double)s.mx, partial, nonfinite, s.bad);
+  const bool bad = s.mxb >= 0x7f800000u;
+  block_store_sum_max(s.acc, bad ? 0.0 : (double)__uint_as_float(s.mxb), partial, nonfinite, bad);
 }
 
 cudaError_t launch_sumsq(const void* y, tucker_dtype dt, int64_t n, double* partial, int nblocks,

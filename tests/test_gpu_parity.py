@@ -61,6 +61,25 @@ def test_norm_sq(ctx, n, dt):
     assert abs(got - want) <= 1e-13 * want
 
 
+@pytest.mark.parametrize("scale", ["huge", "tiny", "mixed"])
+def test_norm_sq_extreme_magnitudes_fp32(ctx, scale):
+    """FP32 inputs whose squares overflow (|x| >= 2^64) or underflow FP32:
+    the FP64 sum of the exact squares either way."""
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(100003)
+    if scale == "huge":
+        x *= 1e25
+    elif scale == "tiny":
+        x *= 1e-25
+    else:
+        x *= 10.0 ** rng.uniform(-30, 30, x.size)
+    t = dev(x, torch.float32)
+    xs = host(t)
+    want = oracle.norm_sq(xs)
+    got = ctx.norm_sq(t)
+    assert abs(got - want) <= 1e-13 * want
+
+
 def test_norm_nonfinite_is_reported(ctx):
     from paper_1901_06043_gb300.tucker import TuckerError
     x = np.ones(1000)
