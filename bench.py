@@ -52,6 +52,10 @@ WORKLOADS = {
     # slices: a 0.9 GB case of the same kernels for profiler captures
     "prof": dict(dims=(500, 500, 40, 11, 2), core=(60, 60, 40, 11, 2), decay=0.08, eta=1e-7,
                  eps=1e-4, dtype="f32", recon=(500, 500, 40, 11, 1)),
+    # a 2.2 GB case whose mode-1 view has the large workload's row-mode shape
+    # (L = R_0 ~ 54, I = 500, more than 4096 slabs: the uncompensated kernel)
+    "prof_row": dict(dims=(256, 500, 32, 11, 12), core=(60, 60, 32, 11, 12), decay=0.08, eta=1e-7,
+                     eps=1e-4, dtype="f32", recon=(256, 500, 32, 11, 1)),
 }
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 x max clock

@@ -142,6 +142,75 @@ __device__ __forceinline__ void load_col16(float (*dst)[BT], const float* __rest
   }
 }
 
+// Row mode, with the block sequence of make_korder / korder_block produced
+// incrementally (no divisions in the K loop; the same blocks in the same
+// order): the slab r, the l-block lb = run * nL0B + sub of the slab, and the
+// split-local slab index rr (order mode 1: lb-major over the split's slabs;
+// mode 2: lb fastest).
+struct RowPos {
+  int64_t r;
+  int64_t rr;
+  int64_t lb, run, sub;
+};
+__device__ __forceinline__ RowPos row_pos(const KGeom& g, const KOrder& o, int64_t idx) {
+  bool unused;
+  const int64_t kb = korder_block(g, o, idx, unused);
+  RowPos p;
+  p.r = kb / g.nLB;
+  p.lb = kb - p.r * g.nLB;
+  p.run = p.lb / g.nL0B;
+  p.sub = p.lb - p.run * g.nL0B;
+  p.rr = p.r - o.r0;
+  return p;
+}
+__device__ __forceinline__ void row_advance(const KGeom& g, const KOrder& o, RowPos& p) {
+  auto next_lb = [&]() {
+    ++p.lb;
+    if (++p.sub == g.nL0B) { p.sub = 0; ++p.run; }
+  };
+  if (o.mode == 1) {
+    if (++p.rr == o.nr) {
+      p.rr = 0;
+      next_lb();
+    }
+    p.r = o.r0 + p.rr;
+  } else {
+    next_lb();
+    if (p.lb == g.nLB) { p.lb = 0; p.run = 0; p.sub = 0; ++p.r; }
+  }
+}
+// this thread's fixed part of the row-mode copy addresses: element c = tid +
+// 256 e goes to dst[c & 15][c >> 4] from l = lbeg + (c & 15), i = i0 + (c >> 4)
+struct RowPanel {
+  int64_t off[(BK * BT) / NTHR];
+  bool iok[(BK * BT) / NTHR];
+};
+__device__ __forceinline__ RowPanel row_panel(const KGeom& g, int64_t i0) {
+  RowPanel p;
+#pragma unroll
+  for (int e = 0; e < (BK * BT) / NTHR; ++e) {
+    const int c = threadIdx.x + NTHR * e;
+    const int kk = c & 15, q = c >> 4;
+    p.off[e] = kk + g.L * (i0 + q);
+    p.iok[e] = i0 + q < g.I;
+  }
+  return p;
+}
+__device__ __forceinline__ void load_row(float (*dst)[Stride<LD_ROW>::v], const float* __restrict__ y,
+                                         const KGeom& g, const RowPanel& pp, const RowPos& pos) {
+  const int64_t lbeg = pos.run * g.L0 + pos.sub * BK;
+  const int64_t rem = (pos.run + 1) * g.L0 - lbeg;   // l left in this run of L0
+  const float* base = y + g.L * g.I * pos.r + lbeg;
+  const int kk = threadIdx.x & 15;
+  const bool lok = kk < rem;
+#pragma unroll
+  for (int e = 0; e < (BK * BT) / NTHR; ++e) {
+    const int c = threadIdx.x + NTHR * e;
+    const bool valid = lok && pp.iok[e];
+    cp_async4(&dst[kk][c >> 4], valid ? base + pp.off[e] : y, valid);
+  }
+}
+
 // The 16 K-steps of one stage into the fresh per-block sums, then into acc.
 // UPPER == false leaves out the thread's (rows 0-63, columns 64-127)
 // quadrant, which lies above the diagonal of a diagonal tile.
@@ -269,6 +338,14 @@ __global__ void __launch_bounds__(NTHR, 1)
     cpa = col_panel(g, ia0);
     cpb = col_panel(g, ib0);
   }
+  RowPanel rpa, rpb;
+  RowPos pre{}, cur{};   // row mode: the block to prefetch next, the block being summed
+  if constexpr (LD == LD_ROW) {
+    rpa = row_panel(g, ia0);
+    rpb = row_panel(g, ib0);
+    cur = row_pos(g, ord, 0);
+    pre = cur;
+  }
   // K-block of position idx in this split's order
   auto block_at = [&](int64_t idx) -> int64_t {
     if constexpr (LD == LD_ROW) {
@@ -287,9 +364,22 @@ __global__ void __launch_bounds__(NTHR, 1)
       if (!diag) load_panel<LD>(sm.b[slot], y, g, ib0, kb);
     }
   };
+  auto load_row_stage = [&](int slot, const RowPos& p) {
+    if constexpr (LD == LD_ROW) {
+      load_row(sm.a[slot], y, g, rpa, p);
+      if (!diag) load_row(sm.b[slot], y, g, rpb, p);
+    }
+  };
 #pragma unroll
   for (int s = 0; s < NST - 1; ++s) {
-    if (s < count) load_stage(s, block_at(s));
+    if (s < count) {
+      if constexpr (LD == LD_ROW) {
+        load_row_stage(s, pre);
+        row_advance(g, ord, pre);
+      } else {
+        load_stage(s, block_at(s));
+      }
+    }
     cp_commit();
   }
 
@@ -305,7 +395,14 @@ __global__ void __launch_bounds__(NTHR, 1)
     __syncthreads();
     {
       const int64_t nxt = idx + NST - 1;
-      if (nxt < count) load_stage(sn, block_at(nxt));
+      if (nxt < count) {
+        if constexpr (LD == LD_ROW) {
+          load_row_stage(sn, pre);
+          row_advance(g, ord, pre);
+        } else {
+          load_stage(sn, block_at(nxt));
+        }
+      }
       cp_commit();
     }
     const float(*A)[SA] = sm.a[st];
@@ -314,8 +411,14 @@ __global__ void __launch_bounds__(NTHR, 1)
       // l-block of each run of L0 (l0 < 16: where the energy of the earlier,
       // truncated modes sits) is summed exactly, the others plainly
       float t[8][8], c[8][8];
-      const int64_t kbc = block_at(idx);
-      const bool exact = ((kbc % g.nLB) % g.nL0B) == 0;
+      bool exact;
+      if constexpr (LD == LD_ROW) {
+        exact = cur.sub == 0;
+        row_advance(g, ord, cur);
+      } else {
+        const int64_t kbc = block_at(idx);
+        exact = ((kbc % g.nLB) % g.nL0B) == 0;
+      }
       if (exact) {
         if (diag) stage_fma_comp<SA, false>(A, A, tx, ty, t, c);
         else stage_fma_comp<SA, true>(A, sm.b[st], tx, ty, t, c);
@@ -357,7 +460,9 @@ __global__ void __launch_bounds__(NTHR, 1)
 
     bool chunk_end;
     if constexpr (LD == LD_ROW) {
-      korder_block(g, ord, idx, chunk_end);
+      // korder_block's chunk ends, from the position of block idx
+      chunk_end = (ord.mode == 2) || (cur.rr == ord.nr - 1) || (((cur.rr + 1) % GCHUNK) == 0);
+      row_advance(g, ord, cur);
     } else {
       chunk_end = ((idx + 1) % CHUNK) == 0;
     }
