@@ -444,8 +444,12 @@ tucker_status do_ttm(tucker_ctx* c, const void* y, tucker_dtype ydt, const SlabV
     }
     return TUCKER_OK;
   }
-  TK_CUDA(c, launch_ttm_simt(y, ydt, prec == TUCKER_PREC_FP64, v.L, v.I, v.Rt, A, K, lda, arow, z,
-                             zdt, c->stream));
+  // the FP32 copy of the operator pays off once the TTM spans several waves
+  DevBuf a32;
+  if (prec != TUCKER_PREC_FP64 && (double)v.L * (double)v.Rt * (double)K >= 16777216.0)
+    TK_TRY(dev_alloc(c, a32, sizeof(float) * (size_t)K * v.I));
+  TK_CUDA(c, launch_ttm_simt(y, ydt, prec == TUCKER_PREC_FP64, v.L, v.I, v.Rt, A, K, lda, arow,
+                             a32.as<float>(), z, zdt, c->stream));
   return TUCKER_OK;
 }
 

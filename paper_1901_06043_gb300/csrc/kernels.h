@@ -46,9 +46,10 @@ cudaError_t launch_gram_small(const void* y, tucker_dtype dt, int64_t L, int64_t
                               cudaStream_t st);
 
 // ---- SIMT TTM
+// a32_scratch: K * I floats for the FP32 copy of A (FP32 arithmetic), or NULL
 cudaError_t launch_ttm_simt(const void* y, tucker_dtype ydt, bool fp64, int64_t L, int64_t I,
                             int64_t Rt, const double* A, int64_t K, int64_t lda, int a_rowmajor,
-                            void* z, tucker_dtype zdt, cudaStream_t st);
+                            float* a32_scratch, void* z, tucker_dtype zdt, cudaStream_t st);
 
 // ---- tensor-core (tcgen05) Gram and TTM on the FP16 hi/lo split
 struct TcGramPlan {

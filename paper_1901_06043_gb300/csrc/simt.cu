@@ -429,11 +429,15 @@ __global__ void __launch_bounds__(256) k_ttm_simt(const TIn* __restrict__ y, int
                                                   int64_t Rt, int64_t nLT,
                                                   const double* __restrict__ A, int64_t K,
                                                   int64_t lda, int a_rowmajor,
+                                                  const float* __restrict__ A32,
                                                   TOut* __restrict__ z) {
   __shared__ TC As[TBI][TT + 1];   // As[i][k]
   __shared__ TC Ys[TBI][TT + 1];   // Ys[i][m]
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
+  // output coordinates of this thread: the index that is contiguous in Z goes
+  // to consecutive threads (k in column mode, l in row mode)
+  const int kq = (L == 1) ? tx : ty, mq = (L == 1) ? ty : tx;
   const int64_t mt = blockIdx.x;
   const int64_t k0 = (int64_t)blockIdx.y * TT;
   int64_t r0, l0;
@@ -457,7 +461,10 @@ __global__ void __launch_bounds__(256) k_ttm_simt(const TIn* __restrict__ y, int
       else { kk = idx % TT; ii = idx / TT; }
       int64_t k = k0 + kk, i = i0 + ii;
       TC v = (TC)0;
-      if (k < K && i < I) v = (TC)(a_rowmajor ? A[k * lda + i] : A[k + lda * i]);
+      if (k < K && i < I) {
+        if (A32) v = (TC)A32[k * I + i];   // FP32 operator converted once (k_ttm_a32)
+        else v = (TC)(a_rowmajor ? A[k * lda + i] : A[k + lda * i]);
+      }
       As[ii][kk] = v;
     }
     // Y tile: 16 i x 64 m
@@ -482,9 +489,9 @@ __global__ void __launch_bounds__(256) k_ttm_simt(const TIn* __restrict__ y, int
     for (int ii = 0; ii < TBI; ++ii) {
       TC a[4], b[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = As[ii][ty + 16 * u];
+      for (int u = 0; u < 4; ++u) a[u] = As[ii][kq + 16 * u];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) b[v] = Ys[ii][tx + 16 * v];
+      for (int v = 0; v < 4; ++v) b[v] = Ys[ii][mq + 16 * v];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -495,11 +502,11 @@ __global__ void __launch_bounds__(256) k_ttm_simt(const TIn* __restrict__ y, int
   // write Z: (k, m) -> l + L*(k + K*r)
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    int64_t k = k0 + ty + 16 * u;
+    int64_t k = k0 + kq + 16 * u;
     if (k >= K) continue;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      int mm = tx + 16 * v;
+      int mm = mq + 16 * v;
       if (L == 1) {
         int64_t r = r0 + mm;
         if (r < Rt) z[k + K * r] = (TOut)acc[u][v];
@@ -511,32 +518,55 @@ __global__ void __launch_bounds__(256) k_ttm_simt(const TIn* __restrict__ y, int
   }
 }
 
+// A (K x I, FP64, either layout) -> FP32 row-major K x I.  An FP64 -> FP32
+// conversion runs on the FP64 pipe (64 cycles per warp instruction), so the
+// FP32 TTM converts its operator once here instead of in every tile.
+__global__ void k_ttm_a32(const double* __restrict__ A, int64_t K, int64_t I, int64_t lda,
+                          int a_rowmajor, float* __restrict__ A32) {
+  const int64_t n = K * I;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e / I, i = e - k * I;
+    A32[e] = (float)(a_rowmajor ? A[k * lda + i] : A[k + lda * i]);
+  }
+}
+
 template <typename TIn, typename TOut>
 static void ttm_dispatch_c(bool fp64, dim3 grid, cudaStream_t st, const void* y, int64_t L, int64_t I,
                            int64_t Rt, int64_t nLT, const double* A, int64_t K, int64_t lda,
-                           int arow, void* z) {
+                           int arow, const float* A32, void* z) {
   if (fp64)
-    k_ttm_simt<TIn, TOut, double><<<grid, 256, 0, st>>>((const TIn*)y, L, I, Rt, nLT, A, K, lda, arow, (TOut*)z);
+    k_ttm_simt<TIn, TOut, double><<<grid, 256, 0, st>>>((const TIn*)y, L, I, Rt, nLT, A, K, lda, arow,
+                                                        nullptr, (TOut*)z);
   else
-    k_ttm_simt<TIn, TOut, float><<<grid, 256, 0, st>>>((const TIn*)y, L, I, Rt, nLT, A, K, lda, arow, (TOut*)z);
+    k_ttm_simt<TIn, TOut, float><<<grid, 256, 0, st>>>((const TIn*)y, L, I, Rt, nLT, A, K, lda, arow,
+                                                       A32, (TOut*)z);
 }
 
 cudaError_t launch_ttm_simt(const void* y, tucker_dtype ydt, bool fp64, int64_t L, int64_t I,
                             int64_t Rt, const double* A, int64_t K, int64_t lda, int a_rowmajor,
-                            void* z, tucker_dtype zdt, cudaStream_t st) {
+                            float* a32_scratch, void* z, tucker_dtype zdt, cudaStream_t st) {
   int64_t nLT = 1, nMT;
   if (L == 1) nMT = (Rt + TT - 1) / TT;
   else { nLT = (L + TT - 1) / TT; nMT = Rt * nLT; }
   if (nMT <= 0 || K <= 0) return cudaSuccess;
   if (nMT > 0x7fffffffll) return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)nMT, (unsigned)((K + TT - 1) / TT));
+  const float* A32 = nullptr;
+  if (!fp64 && a32_scratch) {
+    const int64_t n = K * I;
+    k_ttm_a32<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(
+        A, K, I, lda, a_rowmajor, a32_scratch);
+    count_launches(1);
+    A32 = a32_scratch;
+  }
   count_launches(1);
   if (ydt == TUCKER_F64) {
-    if (zdt == TUCKER_F64) ttm_dispatch_c<double, double>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, z);
-    else ttm_dispatch_c<double, float>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, z);
+    if (zdt == TUCKER_F64) ttm_dispatch_c<double, double>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, A32, z);
+    else ttm_dispatch_c<double, float>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, A32, z);
   } else {
-    if (zdt == TUCKER_F64) ttm_dispatch_c<float, double>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, z);
-    else ttm_dispatch_c<float, float>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, z);
+    if (zdt == TUCKER_F64) ttm_dispatch_c<float, double>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, A32, z);
+    else ttm_dispatch_c<float, float>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, A32, z);
   }
   return cudaGetLastError();
 }
