@@ -555,17 +555,30 @@ def step_rooflines(res, w, pk):
         Rt = int(np.prod(cur[n + 1:])) if n + 1 < len(cur) else 1
         K = L * Rt
         esz = in_esz if s == 0 else wk_esz
+        eig_k = "fp64-" + res.eig_kernel[n]
+        eig_flops = (4.0 / 3.0) * I ** 3 if res.eig_kernel[n] == "tridiag" else \
+            6.0 * I ** 3 * max(res.sweeps[n], 1)
         for kind, t_ms, flops, nbytes, kern in [
             ("gram", ms["gram"][n], I * (I + 1) * K, I * K * esz, res.gram_kernel[n]),
             ("ttm", ms["ttm"][n], 2 * R * I * K, I * K * esz + R * K * wk_esz, res.ttm_kernel[n]),
-            ("eig", ms["eig"][n], 6.0 * I ** 3 * max(res.sweeps[n], 1), 0, "fp64-jacobi")]:
+            ("eig", ms["eig"][n], eig_flops, 0, eig_k)]:
             t = max(t_ms, 1e-6) / 1e3
             traffic, tsrc = None, None
             cap = CAPTURED_TRAFFIC.get((kind, kern, "col" if L == 1 else "row"))
             if cap is not None and I >= 64:
                 traffic = cap["bytes"] * (I * K) / cap["elems"]
                 tsrc = "ncu capture scaled by I*K: " + cap["src"]
-            if kern == "tcgen05":
+            extra = {}
+            if kern == "tcgen05-x3":
+                # FP32-exact products from three FP16 digits each: 9 FP16
+                # tensor-core products per product of the method
+                bound, ach, unit = "tensor", flops / t / 1e12, "TFLOP/s"
+                peak = pk["bf16_tflops"] / 9.0
+                src = "measured dense BF16/FP16 burst / 9 (3-digit FP16 split, all 9 products)"
+                T = (I + 127) // 128
+                mma = 9 * 2 * 128 * 128 * K * (T * (T + 1) // 2)
+                extra = {"mma_tflops": mma / t / 1e12, "mma_frac": mma / t / 1e12 / pk["bf16_tflops"]}
+            elif kern == "tcgen05":
                 bound, ach, peak, unit = "hbm", nbytes / t / 1e9, pk["hbm_gbs"], "GB/s"
                 src = "measured HBM copy"
             elif kern in ("simt-fp32", "simt-fp32c"):
@@ -577,6 +590,7 @@ def step_rooflines(res, w, pk):
             row = {"kernel": f"{kind} mode {n} ({kern})", "bound": bound, "achieved": ach,
                    "peak": peak, "unit": unit, "frac": ach / peak, "traffic": traffic,
                    "ms": t_ms, "hbm_gbs_achieved": nbytes / t / 1e9, "peak_src": src}
+            row.update(extra)
             if tsrc:
                 row["traffic_src"] = tsrc
                 row["algorithmic_bytes"] = nbytes

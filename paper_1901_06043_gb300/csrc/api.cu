@@ -181,14 +181,23 @@ struct Timer {
 
 // ---------------------------------------------------------------- steps
 
+// rowmax != NULL: y is FP32 with a mode-0 size I0 (n = I0 * ncols) and the
+// column-major pass also records the row maxima (for the digit scales of the
+// exact tensor-core Gram) into rowmax[I0].
 tucker_status do_norm(tucker_ctx* c, const void* y, tucker_dtype dt, int64_t n, double* out,
-                      double* maxabs = nullptr) {
+                      double* maxabs = nullptr, unsigned* rowmax = nullptr, int64_t I0 = 0) {
   int nb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8);
   if (nb < 1) nb = 1;
   DevBuf part;
   TK_TRY(dev_alloc(c, part, sizeof(double) * 2 * nb));
   TK_CUDA(c, cudaMemsetAsync(c->d_words, 0, sizeof(unsigned), c->stream));
-  TK_CUDA(c, launch_sumsq(y, dt, n, part.as<double>(), nb, c->d_words, c->d_small, c->stream));
+  if (rowmax) {
+    TK_CUDA(c, cudaMemsetAsync(rowmax, 0, sizeof(unsigned) * I0, c->stream));
+    TK_CUDA(c, launch_sumsq_rowmax((const float*)y, I0, n / I0, part.as<double>(), nb, c->d_words,
+                                   rowmax, c->d_small, c->stream));
+  } else {
+    TK_CUDA(c, launch_sumsq(y, dt, n, part.as<double>(), nb, c->d_words, c->d_small, c->stream));
+  }
   double h[2] = {0.0, 0.0};
   unsigned bad = 0;
   TK_CUDA(c, cudaMemcpyAsync(h, c->d_small, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -215,14 +224,34 @@ float split_scale(double maxabs) {
 // Gram (see tucker_sthosvd).
 constexpr double kMinFp32GramThreshold = 1e-9;
 
-// Which kernel serves a Gram / TTM step: 0 SIMT FP64, 1 SIMT FP32, 2 tcgen05,
-// 3 small-mode FP64 (I < 64, every precision), 4 FP32 with exact
-// (compensated) block sums (row modes with few slabs).
+// Which kernel serves a Gram / TTM step: 0 SIMT FP64, 1 SIMT FP32, 2 tcgen05
+// (rounded FP16 split products), 3 small-mode FP64 (I < 64, every
+// precision), 4 FP32 with exact (compensated) block sums (row modes with few
+// slabs), 5 tcgen05 on exact integer digit products (MIXED, mode-0 view).
 int gram_kernel_for(tucker_prec prec, tucker_dtype dt, const SlabView& v, int sms) {
   if (plan_gram_small(v.L, v.I, v.Rt, sms, v.L0).nctas > 0) return 3;
   if (prec == TUCKER_PREC_FP64) return 0;
   if (prec == TUCKER_PREC_TENSOR && dt == TUCKER_F32 && plan_gram_tc(v.L, v.I, v.Rt, sms).ok) return 2;
+  if (prec == TUCKER_PREC_MIXED && dt == TUCKER_F32 && plan_gram_tcx(v.L, v.I, v.Rt, sms).nctas > 0)
+    return 5;
   return 1;
+}
+
+// Row maxima of the column-major mode-0 view (as FP32 bits) for the digit
+// scales of the exact tensor-core Gram; own scratch, so it may run on a side
+// stream.  Also gives the sum of squares, unused here.
+tucker_status rowmax_pass(tucker_ctx* c, const float* y, int64_t I0, int64_t ncols,
+                          unsigned* rowmax) {
+  const int nb = c->num_sms * 4;
+  DevBuf scr;
+  TK_TRY(dev_alloc(c, scr, sizeof(double) * (2 * (size_t)nb + 2) + sizeof(unsigned)));
+  double* part = scr.as<double>();
+  double* out = part + 2 * nb;
+  unsigned* bad = reinterpret_cast<unsigned*>(out + 2);
+  TK_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(unsigned), c->stream));
+  TK_CUDA(c, cudaMemsetAsync(rowmax, 0, sizeof(unsigned) * I0, c->stream));
+  TK_CUDA(c, launch_sumsq_rowmax(y, I0, ncols, part, nb, bad, rowmax, out, c->stream));
+  return TUCKER_OK;
 }
 
 // maxabs: max|y| if the caller knows it (e.g. from the norm pass), else <= 0.
@@ -231,10 +260,34 @@ int gram_kernel_for(tucker_prec prec, tucker_dtype dt, const SlabView& v, int sm
 // batch of calls.
 tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabView& v,
                       tucker_prec prec, double* S, int* kernel_used, double maxabs = -1.0,
-                      bool check = true) {
+                      bool check = true, const unsigned* rowmax = nullptr) {
   int kern = gram_kernel_for(prec, dt, v, c->num_sms);
-  if (kern == 2 && (((uintptr_t)y) & 15) != 0) kern = 1;
+  if ((kern == 2 || kern == 5) && (((uintptr_t)y) & 15) != 0) kern = 1;
   if (kernel_used) *kernel_used = kern;
+  if (kern == 5) {
+    const GramPlan p = plan_gram_tcx(v.L, v.I, v.Rt, c->num_sms);
+    DevBuf scratch, rm;
+    TK_TRY(dev_alloc(c, scratch, p.scratch_bytes));
+    if (!rowmax) {
+      TK_TRY(dev_alloc(c, rm, sizeof(unsigned) * v.I));
+      TK_TRY(rowmax_pass(c, (const float*)y, v.I, v.Rt, rm.as<unsigned>()));
+      rowmax = rm.as<unsigned>();
+    }
+    if (check) TK_CUDA(c, cudaMemsetAsync(c->d_words + 8, 0, sizeof(unsigned), c->stream));
+    TK_CUDA(c, launch_gram_tcx((const float*)y, v.I, v.Rt, p, rowmax, scratch.p, c->d_words + 8, S,
+                               c->stream));
+    if (!check) return TUCKER_OK;
+    unsigned err = 0;
+    TK_CUDA(c, cudaMemcpyAsync(&err, c->d_words + 8, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                               c->stream));
+    TK_TRY(sync(c));
+    if (err) {
+      char m[96];
+      snprintf(m, sizeof m, "tensor-core Gram reported device error word 0x%x", err);
+      return set_err(c, TUCKER_ERR_CUDA, m);
+    }
+    return TUCKER_OK;
+  }
   if (kern == 2) {
     if (!(maxabs > 0.0)) {
       double nrm;
@@ -700,7 +753,17 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
   t_norm.start(c);
   const int64_t nx = numel(ndim, dims);
   double nrm2 = 0.0, xmax = 0.0;
-  TK_TRY(do_norm(c, x, dt, nx, &nrm2, &xmax));
+  // the exact tensor-core Gram of a first mode 0 takes its digit scales from
+  // row maxima that the norm pass records on the way
+  DevBuf rowmax;
+  {
+    const SlabView v0 = slab_view(ndim, dims, 0);
+    const bool tcx = order[0] == 0 && !(!ranks && prec != TUCKER_PREC_FP64 &&
+                                        eps * eps / ndim < kMinFp32GramThreshold) &&
+                     gram_kernel_for(prec, dt, v0, c->num_sms) == 5 && (((uintptr_t)x) & 15) == 0;
+    if (tcx) TK_TRY(dev_alloc(c, rowmax, sizeof(unsigned) * v0.I));
+  }
+  TK_TRY(do_norm(c, x, dt, nx, &nrm2, &xmax, rowmax.as<unsigned>(), dims[0]));
   t_norm.stop(c);
   r->norm_x_sq = nrm2;
   const double thr = ranks ? 0.0 : eps * eps * nrm2 / ndim;
@@ -730,7 +793,7 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
     Timer tmg, tme, tmt;
     tmg.start(c);
     TK_TRY(do_gram(c, y, ydt, v, gram_prec, S.as<double>(), &r->gram_kernel[n],
-                   s == 0 ? xmax : -1.0));
+                   s == 0 ? xmax : -1.0, true, s == 0 ? rowmax.as<unsigned>() : nullptr));
     tmg.stop(c);
     DevBuf w, U;
     TK_TRY(dev_alloc(c, w, sizeof(double) * I));

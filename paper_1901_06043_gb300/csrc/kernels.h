@@ -13,6 +13,13 @@ namespace tk {
 cudaError_t launch_sumsq(const void* y, tucker_dtype dt, int64_t n, double* partial, int nblocks,
                          unsigned* nonfinite, double* out, cudaStream_t st);
 
+// The same over the column-major I0 x ncols mode-0 view, also recording each
+// row's max |x| as FP32 bits (atomicMax into the zeroed rowmax_bits[I0]);
+// I0 % 4 == 0, I0 <= 2048, 16-byte aligned y
+cudaError_t launch_sumsq_rowmax(const float* y, int64_t I0, int64_t ncols, double* partial,
+                                int nblocks, unsigned* nonfinite, unsigned* rowmax_bits, double* out,
+                                cudaStream_t st);
+
 // ---- SIMT Gram (FP64 or FP32 products), split-K partial tiles + reduction
 struct GramPlan {
   int ntiles = 0, ksplit = 0;
@@ -20,6 +27,14 @@ struct GramPlan {
   int nctas = 0;         // plan_gram_f32: CTAs (= partial tiles)
   size_t scratch_bytes = 0;
 };
+// ---- tensor-core Gram of the mode-0 view on exact digit products
+// (gram_tcx.cu): plan.nctas == 0 when it does not apply (L == 1, 128 <= I <=
+// 2048, I % 4 == 0); rowmax_bits from launch_sumsq_rowmax
+GramPlan plan_gram_tcx(int64_t L, int64_t I, int64_t Rt, int num_sms);
+cudaError_t launch_gram_tcx(const float* y, int64_t I, int64_t Rt, const GramPlan& p,
+                            const unsigned* rowmax_bits, void* scratch, unsigned* err, double* S,
+                            cudaStream_t st);
+
 // L0: the fastest sub-index of l (the first dim of the tensor for a mode
 // n > 0); row-mode K-blocks never cross a multiple of it
 GramPlan plan_gram_simt(int64_t L, int64_t I, int64_t Rt, int num_sms, int64_t L0);

@@ -167,7 +167,8 @@ class Result:
         self.threshold = r.threshold
         self.discarded = [r.discarded_sq[k] for k in range(N)]
         self.sweeps = [r.jacobi_sweeps[k] for k in range(N)]
-        names = {0: "simt-fp64", 1: "simt-fp32", 2: "tcgen05", 3: "small-fp64", 4: "simt-fp32c"}
+        names = {0: "simt-fp64", 1: "simt-fp32", 2: "tcgen05", 3: "small-fp64", 4: "simt-fp32c",
+                 5: "tcgen05-x3"}
         self.gram_kernel = [names.get(r.gram_kernel[k], "?") for k in range(N)]
         self.ttm_kernel = [names.get(r.ttm_kernel[k], "?") for k in range(N)]
         self.eig_kernel = [{0: "jacobi", 1: "tridiag"}.get(r.eig_kernel[k], "?") for k in range(N)]

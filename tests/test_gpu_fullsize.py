@@ -135,7 +135,7 @@ def test_large_mixed_path_full_size(ctx):
     r64 = ctx.sthosvd(x, dims, eps=1e-4, prec="fp64")
     rmx = ctx.sthosvd(x, dims, eps=1e-4, prec="mixed")
     assert rmx.ranks == r64.ranks
-    assert rmx.gram_kernel[0] == "simt-fp32" and rmx.ttm_kernel[0] == "tcgen05"
+    assert rmx.gram_kernel[0] == "tcgen05-x3" and rmx.ttm_kernel[0] == "tcgen05"
     err = math.sqrt(sum(rmx.discarded) / rmx.norm_sq)
     assert err <= 1e-4
     # Cor. 1: ||X - Xhat||^2 = sum of the discarded eigenvalues (relative to

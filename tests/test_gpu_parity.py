@@ -241,6 +241,67 @@ def test_gram_tensor_error_on_discarded_subspace(ctx):
     assert abs(proj) <= 0.05 * thr, (proj / thr, c)
 
 
+MIXED_X3_SHAPES = [(128, 3000), (500, 2000), (256, 33, 70), (132, 700), (1024, 300), (2048, 64),
+                   (500, 257)]
+
+
+@pytest.mark.parametrize("dims", MIXED_X3_SHAPES)
+def test_gram_mixed_mode0_exact_digits(ctx, dims):
+    """Mode-0 Gram of MIXED precision: tensor cores on exact integer digit
+    products (three 8-bit digits of each value under a per-row power-of-two
+    scale; window sums below 2^24 are exact in the FP32 accumulator).  Rows
+    of very different magnitude (10^-3 .. 10^3), one zero row, a few exact
+    zeros and a ragged K: every entry within 1e-6 of sqrt(S_ii S_jj) of the
+    oracle's FP64 Gram (representation error 2^-24 of each row's maximum)."""
+    rng = np.random.default_rng(dims[0] * 7 + dims[-1])
+    n = oracle.linear_size(dims)
+    rows = np.arange(n) % dims[0]
+    rs = 10.0 ** rng.uniform(-3, 3, dims[0])
+    rs[dims[0] // 3] = 0.0
+    x = rng.standard_normal(n) * rs[rows]
+    x[rng.integers(0, n, size=n // 50)] = 0.0
+    t = dev(x, torch.float32)
+    xs = host(t)
+    want = oracle.gram(xs, dims, 0)
+    got = host(ctx.gram(t, dims, 0, "mixed"))
+    d = np.sqrt(np.outer(np.diag(want), np.diag(want)))
+    assert np.all(np.abs(got - want) <= 1e-6 * d + 1e-300), np.nanmax(np.abs(got - want) / d)
+    assert np.array_equal(got, got.T)
+
+
+def test_gram_mixed_mode0_trace_unbiased(ctx):
+    """trace(S) = ||Y||^2 on 1.3e8 Gaussian entries: the exact-digit
+    tensor-core Gram rounds only unbiasedly (digit rounding, window
+    combination), so its trace matches the FP64 sum of squares to 3e-10,
+    the bound of the FP32 round-to-nearest Gram (a truncating accumulator
+    is off by ~1e-6)."""
+    dims = (256, 64, 8000)
+    g = torch.Generator(device="cuda").manual_seed(77)
+    t = torch.randn(dims[::-1], generator=g, device="cuda", dtype=torch.float32).reshape(-1)
+    want = float((t.double() ** 2).sum())
+    got = float(torch.trace(ctx.gram(t, dims, 0, "mixed")))
+    assert abs(got - want) <= 3e-10 * want, (got - want) / want
+
+
+def test_gram_mixed_mode0_error_on_discarded_subspace(ctx):
+    """What the eps cut sees, at eps = 1e-4 (the regime MIXED is meant for):
+    the exact-digit Gram's error projected on the discarded eigenvectors of a
+    Tucker tensor's mode-0 Gram stays below 2 % of the threshold."""
+    dims = (256, 64, 40, 11)
+    x = synth.tucker_torch(dims, (40, 20, 20, 11), decay=0.1, eta=1e-7, seed=3)
+    want = host(ctx.gram(x, dims, 0, "fp64"))
+    got = host(ctx.gram(x, dims, 0, "mixed"))
+    w, V = oracle.eig_desc(want)
+    nrm2 = float(np.trace(want))
+    thr = 1e-8 * nrm2 / 4                         # eps = 1e-4, N = 4
+    R, tail = oracle.rank_cut(w, thr)
+    P = V[:, R:]
+    E = got - want
+    proj = np.trace(P.T @ E @ P)
+    assert abs(np.trace(E)) <= 1e-9 * nrm2, np.trace(E) / nrm2
+    assert abs(proj) <= 0.02 * thr, proj / thr
+
+
 # ---------------------------------------------------------------- eigen
 
 def _spd(n, seed, spectrum=None):
@@ -617,15 +678,16 @@ def test_sthosvd_fp32_path_ranks_and_error(ctx):
 
 @pytest.mark.parametrize("eps", [1e-2, 1e-4])
 def test_sthosvd_mixed_path_ranks_and_error(ctx, eps):
-    """MIXED (FP32 round-to-nearest Gram, tensor-core mode-0 TTM): ranks
-    identical to the FP64 oracle on a decaying-spectrum FP32 tensor; error
-    within 5e-6 of the oracle's."""
+    """MIXED (mode-0 Gram on exact-digit tensor-core products, other modes
+    FP32 round-to-nearest; tensor-core mode-0 TTM): ranks identical to the
+    FP64 oracle on a decaying-spectrum FP32 tensor; error within 5e-6 of the
+    oracle's."""
     dims = (200, 160, 48, 11)
     x = synth.tucker_torch(dims, (30, 30, 24, 11), decay=0.1, eta=1e-7, seed=9)
     xs = host(x)
     ref = oracle.sthosvd(xs, dims, eps=eps)
     res = ctx.sthosvd(x, dims, eps=eps, prec="mixed")
-    assert res.gram_kernel[0] == "simt-fp32"
+    assert res.gram_kernel[0] == "tcgen05-x3"
     assert res.ttm_kernel[0] == "tcgen05"
     assert res.ranks == ref["ranks"]
     ours = {"core": host(res.core), "core_dims": res.ranks,
