@@ -34,10 +34,10 @@
 // splits sized to one wave of the SMs; the CTAs of a split are adjacent in
 // launch order so their shared columns are served from L2.
 //
-// Roles (17 warps): warps 0-7 load X with 16-byte loads, split it into the
+// Roles (25 warps): warps 0-15 load X with 16-byte loads, split it into the
 // digit planes of the A (rows 128 ta..) and B (rows 128 tb..) operands,
-// MN-major SW128 (three-stage ring); warp 8 issues the MMAs (one thread); warps
-// 9-16 drain tensor memory, two per lane quarter, 64 columns each.  Every wait
+// MN-major SW128 (three-stage ring); warp 16 issues the MMAs (one thread);
+// warps 17-24 drain tensor memory, two per lane quarter, 64 columns each.  Every wait
 // is bounded: one that gives up sets DEV_ERR_MBAR_TIMEOUT and the kernel winds
 // down; tensor memory is always released.
 #include <cuda_fp16.h>
@@ -54,11 +54,11 @@ using namespace tc;
 constexpr int BK = 16;                          // columns (K) per stage: one MMA step
 constexpr int NSTAGE = 3;
 constexpr int WIN = 16;                         // stages per exact window (256 columns)
-constexpr int NPROD = 8;
-constexpr int MMA_WARP = 8;
-constexpr int EPI_WARP0 = 9;
+constexpr int NPROD = 16;                       // one column of the stage each
+constexpr int MMA_WARP = 16;
+constexpr int EPI_WARP0 = 17;
 constexpr int NEPI = 8;
-constexpr int NTHREADS = (EPI_WARP0 + NEPI) * 32;   // 544
+constexpr int NTHREADS = (EPI_WARP0 + NEPI) * 32;   // 800
 constexpr uint32_t SK = 2048;                   // atom stride along K (128 mn x 8 k per 2 atoms)
 constexpr uint32_t ATOM_MN = 1024;
 constexpr uint32_t PLANE = 128 * BK * 2;        // one digit plane of one operand: 4 KB
@@ -79,14 +79,15 @@ __device__ __forceinline__ uint32_t instr_desc(int M, int N) {
          ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+// Four 8-column loads (one per accumulator), then one wait.
+__device__ __forceinline__ void tmem_ld8x4(uint32_t taddr, uint32_t (&r)[4][8]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r[q][0]), "=r"(r[q][1]), "=r"(r[q][2]), "=r"(r[q][3]), "=r"(r[q][4]),
+          "=r"(r[q][5]), "=r"(r[q][6]), "=r"(r[q][7])
+        : "r"(taddr + 128u * (uint32_t)q));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
@@ -186,12 +187,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx_col(GramTcxArgs g) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) sc[o][u] = s_scale[128 * o + 4 * lane + u];
     // loads run PF stages ahead of the conversion (register ring), so each
-    // warp keeps ~3 stages of 16-byte loads in flight
-    constexpr int PF = 2;
-    float4 ring[PF + 1][2][2];
-    auto load_stage = [&](int s, float4 (&v)[2][2]) {
+    // warp keeps PF + 1 stages of 16-byte loads in flight (~80 KB per SM)
+    constexpr int PF = 4;
+    float4 ring[PF + 1][2][1];
+    auto load_stage = [&](int s, float4 (&v)[2][1]) {
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
+      for (int j = 0; j < 1; ++j) {
         const int kl = warp + NPROD * j;
         const int64_t kc = k0 + (int64_t)s * BK + kl;
         const bool kok = (s < nst) && kc < k1;
@@ -213,14 +214,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx_col(GramTcxArgs g) {
         const int s = s0 + u;
         if (s >= nst || !go) break;
         load_stage(s + PF, ring[(u + PF) % (PF + 1)]);
-        const float4 (&v)[2][2] = ring[u];
+        const float4 (&v)[2][1] = ring[u];
         const int slot = s % NSTAGE;
         if (s >= NSTAGE) {
           if (!mbar_wait(smem_u32(&bar_empty[slot]), ((s / NSTAGE) - 1) & 1, g.err)) { go = false; break; }
         }
         uint8_t* st = smem + (size_t)slot * STAGE_BYTES;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < 1; ++j) {
           const int kl = warp + NPROD * j;
           const uint32_t o = mn_off(4 * lane, kl);
           uint2 p[4];
@@ -285,23 +286,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx_col(GramTcxArgs g) {
     for (int w = 0; w < nwin; ++w) {
       if (!mbar_wait(smem_u32(&bar_accf), w & 1, g.err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      for (int cc = 0; cc < 64; cc += 16) {
-        uint32_t r0[16], r1[16], r2[16], r3[16];
+      for (int cc = 0; cc < 64; cc += 8) {
+        uint32_t r[4][8];
         const uint32_t col = (uint32_t)(c0 + cc);
-        tmem_ld16(lane_base + col, r0);
-        tmem_ld16(lane_base + 128u + col, r1);
-        tmem_ld16(lane_base + 256u + col, r2);
-        tmem_ld16(lane_base + 384u + col, r3);
+        tmem_ld8x4(lane_base + col, r);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < 8; ++j) {
           // the four parts D0, D1 / 2^8, D2 / 2^16, D3 / 2^24 (each scaling
           // exact) enter the pair one by one (TwoSum each): nothing is
           // rounded before the compensated sum
           const int idx = (c0 + cc + j) * 128 + row;
           float h = hi[idx], l = lo[idx];
-          const float parts[4] = {__uint_as_float(r0[j]), __uint_as_float(r1[j]) * 0x1p-8f,
-                                  __uint_as_float(r2[j]) * 0x1p-16f,
-                                  __uint_as_float(r3[j]) * 0x1p-24f};
+          const float parts[4] = {__uint_as_float(r[0][j]), __uint_as_float(r[1][j]) * 0x1p-8f,
+                                  __uint_as_float(r[2][j]) * 0x1p-16f,
+                                  __uint_as_float(r[3][j]) * 0x1p-24f};
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const float v = parts[q];
