@@ -227,7 +227,7 @@ constexpr double kMinFp32GramThreshold = 1e-9;
 // Which kernel serves a Gram / TTM step: 0 SIMT FP64, 1 SIMT FP32, 2 tcgen05
 // (rounded FP16 split products), 3 small-mode FP64 (I < 64, every
 // precision), 4 FP32 with exact (compensated) block sums (row modes with few
-// slabs), 5 tcgen05 on exact integer digit products (MIXED, mode-0 view).
+// slabs), 5 tcgen05 on exact integer digit products (MIXED, 128 <= I <= 2048).
 int gram_kernel_for(tucker_prec prec, tucker_dtype dt, const SlabView& v, int sms) {
   if (plan_gram_small(v.L, v.I, v.Rt, sms, v.L0).nctas > 0) return 3;
   if (prec == TUCKER_PREC_FP64) return 0;
@@ -262,7 +262,8 @@ tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabV
                       tucker_prec prec, double* S, int* kernel_used, double maxabs = -1.0,
                       bool check = true, const unsigned* rowmax = nullptr) {
   int kern = gram_kernel_for(prec, dt, v, c->num_sms);
-  if ((kern == 2 || kern == 5) && (((uintptr_t)y) & 15) != 0) kern = 1;
+  if ((kern == 2 || (kern == 5 && v.L == 1)) && (((uintptr_t)y) & 15) != 0) kern = 1;
+  if (kern == 5 && (((uintptr_t)y) & 3) != 0) kern = 1;
   if (kernel_used) *kernel_used = kern;
   if (kern == 5) {
     const GramPlan p = plan_gram_tcx(v.L, v.I, v.Rt, c->num_sms);
@@ -270,12 +271,16 @@ tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabV
     TK_TRY(dev_alloc(c, scratch, p.scratch_bytes));
     if (!rowmax) {
       TK_TRY(dev_alloc(c, rm, sizeof(unsigned) * v.I));
-      TK_TRY(rowmax_pass(c, (const float*)y, v.I, v.Rt, rm.as<unsigned>()));
+      if (v.L == 1)
+        TK_TRY(rowmax_pass(c, (const float*)y, v.I, v.Rt, rm.as<unsigned>()));
+      else
+        TK_CUDA(c, launch_rowmax_slab((const float*)y, v.L, v.I, v.Rt, c->num_sms,
+                                      rm.as<unsigned>(), c->stream));
       rowmax = rm.as<unsigned>();
     }
     if (check) TK_CUDA(c, cudaMemsetAsync(c->d_words + 8, 0, sizeof(unsigned), c->stream));
-    TK_CUDA(c, launch_gram_tcx((const float*)y, v.I, v.Rt, p, rowmax, scratch.p, c->d_words + 8, S,
-                               c->stream));
+    TK_CUDA(c, launch_gram_tcx((const float*)y, v.L, v.I, v.Rt, p, rowmax, scratch.p,
+                               c->d_words + 8, S, c->stream));
     if (!check) return TUCKER_OK;
     unsigned err = 0;
     TK_CUDA(c, cudaMemcpyAsync(&err, c->d_words + 8, sizeof(unsigned), cudaMemcpyDeviceToHost,

@@ -2,42 +2,46 @@
 // exact digit products: S = X X^T for the I x K matrix X of FP32 columns.
 //
 // Arithmetic.  Row i of X is scaled by a power of two s_i with max_k |x_ik s_i|
-// in [64, 128) (s_i from the row maxima the norm pass records), and every
-// scaled value is split exactly into three integer digits,
-//     x s_i = d0 + d1 / 2^8 + d2 / 2^16,   |d0|, |d1|, |d2| <= 128,
-// by two rounds of "round to the nearest integer, subtract, scale by 2^8"
-// (each subtraction and scaling is exact; the last rounding, for values below
-// half the row maximum, is the only one: <= 2^-17 in these units, unbiased
-// and independent of the value).  Digits are integers below 2^11, exact in
-// FP16, and so is d2 / 2^8.  The tensor cores (kind::f16, FP32 accumulators in
-// tensor memory) form all nine digit products, grouped by weight:
+// in [32, 64) (s_i from the row maxima the norm pass records), and every
+// scaled value is split exactly into three integer digits in base 2^7,
+//     x s_i = d0 + d1 / 2^7 + d2 / 2^14 + r,   |d0|, |d1|, |d2| <= 64,
+// by two rounds of "round to the nearest integer, subtract, scale by 2^7"
+// (each subtraction and scaling is exact; r, the last rounding, is the only
+// error: |r| <= 2^-15 in these units, 2^-20 of the row maximum, unbiased and
+// independent of the value).  Digits, and d2 / 2^7, are exact in FP16.  The
+// tensor cores (kind::f16, FP32 accumulators in tensor memory) form all nine
+// digit products, grouped by weight:
 //     D0 = sum d0 d0'                                      (weight 1)
-//     D1 = sum (d0 d1' + d1 d0')                          (2^-8)
-//     D2 = sum (d0 d2' + d1 d1' + d2 d0')                 (2^-16)
-//     D3 = sum (d1 d2' + d2 d1' + (d2 / 2^8) d2')         (2^-24)
-// D0..D2 sum integers below 2^14 each; over a window of 256 columns every
-// partial sum stays an integer below 2^24, so those accumulators are exact and
-// the accumulator's truncation never acts (it is what moves the eps cut for
-// the rounded-product tensor-core Gram of tc.cu).  D3 is not integral, but at
-// weight 2^-24 its truncation is ~2^-48 of an entry.  Leaving D3 out is not
-// an option: its terms have nonzero mean (d2^2 > 0; and when d1 rounds to
-// +-128 the remainder d2 takes the opposite sign) and measured as a +1e-8
-// relative bias on a trace and -0.1 threshold on a discarded eigenvalue sum.
-// After each window the epilogue warps drain the four sums and add D0, D1 /
-// 2^8, D2 / 2^16 and D3 / 2^24 one by one into an exact FP32 pair (TwoSum,
-// hi + lo) in shared memory (a combined value rounded to FP32 first measured a
-// +1e-8 trace bias).  The pairs go out as FP64 per-CTA partial tiles; a second
-// kernel sums the K splits in a fixed order and removes the scales,
-// S_ij = D_ij / (s_i s_j).
+//     D1 = sum (d0 d1' + d1 d0')                          (2^-7)
+//     D2 = sum (d0 d2' + d1 d1' + d2 d0')                 (2^-14)
+//     D3 = sum (d1 d2' + d2 d1' + (d2 / 2^7) d2')         (2^-21)
+// D0..D2 sum integers of at most 2^12 each (three per column for D2); over a
+// window of 1024 columns every partial sum stays an integer below 2^24, so
+// those accumulators are exact and the accumulator's truncation never acts
+// (it is what moves the eps cut for the rounded-product tensor-core Gram of
+// tc.cu).  D3 is not integral, but at weight 2^-21 its truncation is ~2^-45 of
+// an entry.  Leaving D3 out is not an option: its terms have nonzero mean
+// (d2^2 > 0; and when d1 rounds to +-64 the remainder d2 takes the opposite
+// sign), measured as a +1e-8 relative bias on a trace.  After each window the
+// epilogue warps drain the four sums and add D0, D1 / 2^7, D2 / 2^14 and
+// D3 / 2^21 one by one into an exact FP32 pair (TwoSum, hi + lo) in shared
+// memory (a combined value rounded to FP32 first measured a +1e-8 trace
+// bias).  The pairs go out as FP64 per-CTA partial tiles; a second kernel sums
+// the K splits in a fixed order and removes the scales, S_ij = D_ij / (s_i s_j).
+//
+// The digit split and the TwoSums run on packed FP32 pairs (f32x2
+// instructions, two values per instruction, each rounded as the scalar op);
+// rounding to an integer is the add-and-subtract of 1.5 * 2^23.
 //
 // Work split.  Tiles of 128 x 128 over the lower triangle (ta >= tb), times K
 // splits sized to one wave of the SMs; the CTAs of a split are adjacent in
 // launch order so their shared columns are served from L2.
 //
-// Roles (25 warps): warps 0-15 load X with 16-byte loads, split it into the
-// digit planes of the A (rows 128 ta..) and B (rows 128 tb..) operands,
-// MN-major SW128 (three-stage ring); warp 16 issues the MMAs (one thread);
-// warps 17-24 drain tensor memory, two per lane quarter, 64 columns each.  Every wait
+// Roles (24 warps, 80 registers each): warps 0-15 load X with 16-byte loads,
+// split it into the digit planes of the A (rows 128 ta..) and B (rows
+// 128 tb..) operands, MN-major SW128 (three-stage ring); warps 16-23 drain
+// tensor memory, two per lane quarter, 64 columns each, and one thread of
+// warp 16 issues each window's MMAs before its drain.  Every wait
 // is bounded: one that gives up sets DEV_ERR_MBAR_TIMEOUT and the kernel winds
 // down; tensor memory is always released.
 #include <cuda_fp16.h>
@@ -53,24 +57,31 @@ using namespace tc;
 
 constexpr int BK = 16;                          // columns (K) per stage: one MMA step
 constexpr int NSTAGE = 3;
-constexpr int WIN = 16;                         // stages per exact window (256 columns)
+constexpr int WIN = 64;                         // stages per exact window (1024 columns)
 constexpr int NPROD = 16;                       // one column of the stage each
-constexpr int MMA_WARP = 16;
-constexpr int EPI_WARP0 = 17;
+constexpr int EPI_WARP0 = 16;
+constexpr int MMA_WARP = EPI_WARP0;             // the first drain warp also issues the MMAs
 constexpr int NEPI = 8;
-constexpr int NTHREADS = (EPI_WARP0 + NEPI) * 32;   // 800
-constexpr uint32_t SK = 2048;                   // atom stride along K (128 mn x 8 k per 2 atoms)
-constexpr uint32_t ATOM_MN = 1024;
-constexpr uint32_t PLANE = 128 * BK * 2;        // one digit plane of one operand: 4 KB
-constexpr uint32_t OFF_A = 0, OFF_B = 4 * PLANE;  // A: d0, d1, d2, d2 / 2^8; B: d0, d1, d2
-constexpr uint32_t STAGE_BYTES = 7 * PLANE;     // 28 KB
-constexpr uint32_t PAIR_BYTES = 128 * 128 * 4;  // hi or lo tile, [col][row]
-constexpr uint32_t SMEM_BYTES = NSTAGE * STAGE_BYTES + 2 * PAIR_BYTES + 1024;
+constexpr int NTHREADS = (EPI_WARP0 + NEPI) * 32;   // 768: 24 warps, 80 registers each
+// Stage layout, MN-major SW128 FP16: atoms of 64 mn x 8 k (1 KB).  Each
+// operand region is [k group of 8][atom], the digit planes side by side along
+// mn (plane q = atoms 2q, 2q + 1), so consecutive planes form one operand of
+// 256 rows: A (rows 128 ta..) holds d0, d1, d2, d2 / 2^7 (8 atoms per k
+// group), B (rows 128 tb..) holds d0, d1, d2 (6 atoms per k group).
+constexpr uint32_t ATOM = 1024;
+constexpr uint32_t PLANE_STEP = 2 * ATOM;       // plane q starts at atom 2q
+constexpr uint32_t KG_A = 8 * ATOM, KG_B = 6 * ATOM;   // k-group strides
+constexpr uint32_t OFF_A = 0, OFF_B = 2 * KG_A;
+constexpr uint32_t STAGE_BYTES = 2 * KG_A + 2 * KG_B;   // 28 KB
+constexpr uint32_t PAIR_BYTES = 128 * 128 * 4;  // hi or lo tile, [col / 2][row][col % 2]
+constexpr uint32_t RSUM_BYTES = 16 * 128 * 4;   // remainder sums, [producer warp][row]
+constexpr uint32_t SMEM_BYTES = NSTAGE * STAGE_BYTES + 2 * PAIR_BYTES + RSUM_BYTES + 1024;
 constexpr int TILE_ELEMS = 128 * 128;
 
-// Byte offset of (mn, k) in an MN-major SW128 FP16 tile (as in tc.cu).
-__device__ __forceinline__ uint32_t mn_off(int mn, int k) {
-  return (uint32_t)(mn >> 6) * ATOM_MN + (uint32_t)(k >> 3) * SK + (uint32_t)(k & 7) * 128u +
+// Byte offset of (mn, k) (mn < 128, k < 16) in plane 0 of an operand region
+// with k-group stride kg.
+__device__ __forceinline__ uint32_t mn_off(int mn, int k, uint32_t kg) {
+  return (uint32_t)(k >> 3) * kg + (uint32_t)(mn >> 6) * ATOM + (uint32_t)(k & 7) * 128u +
          ((uint32_t)(((mn & 63) >> 3) ^ (k & 7)) << 4) + (uint32_t)(mn & 7) * 2u;
 }
 
@@ -91,35 +102,84 @@ __device__ __forceinline__ void tmem_ld8x4(uint32_t taddr, uint32_t (&r)[4][8]) 
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// The digits of four scaled values, packed as FP16 pairs per plane: d0, d1,
-// d2 and (NP == 4) d2 / 2^8.
-template <int NP>
-__device__ __forceinline__ void digits4(float4 v, const float* s, uint2 (&p)[4]) {
-  const float x[4] = {v.x * s[0], v.y * s[1], v.z * s[2], v.w * s[3]};
-  float d[4][4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float d0 = rintf(x[j]);
-    const float r1 = (x[j] - d0) * 256.f;
-    const float d1 = rintf(r1);
-    const float d2 = rintf((r1 - d1) * 256.f);
-    d[0][j] = d0;
-    d[1][j] = d1;
-    d[2][j] = d2;
-    d[3][j] = d2 * 0x1p-8f;
+// 16-byte load that does not allocate in L1 (each value is read once per
+// CTA) and keeps the normal L2 policy (the other tiles of the split re-read it).
+__device__ __forceinline__ float4 ld_nl1(const float4* p) {
+  float4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
+// Packed FP32 pair arithmetic (f32x2), each lane rounded to nearest.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {    // a - b, one rounding
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
+// The digits of two scaled values x (|x| < 64): d0, d1, d2 and d2 / 2^7.
+// x + 1.5 * 2^23 lies in [2^23, 2^24), where the FP32 spacing is 1, so the add
+// rounds x to the nearest integer and the subtraction of the constant is exact.
+// R: also add r^2 to racc, r = 2^14 (x - d0 - d1 / 2^7 - d2 / 2^14) the exact
+// remainder of the last rounding.
+template <bool R>
+__device__ __forceinline__ void digits2(float2 x, float2 (&d)[4], float2& racc) {
+  const float2 M = make_float2(0x1.8p23f, 0x1.8p23f), NM = make_float2(-0x1.8p23f, -0x1.8p23f);
+  const float2 B = make_float2(128.f, 128.f);
+  const float2 d0 = add2(add2(x, M), NM);
+  const float2 e = sub2(x, d0);                  // |e| <= 1/2, exact
+  const float2 t1 = fma2(e, B, M);
+  const float2 d1 = add2(t1, NM);                // round(128 e)
+  const float2 f = fma2(e, B, sub2(M, t1));      // 128 e - d1, exact, |f| <= 1/2
+  const float2 t2 = fma2(f, B, M);
+  const float2 d2 = add2(t2, NM);                // round(128 f)
+  if (R) {
+    const float2 r = fma2(f, B, sub2(M, t2));    // 128 f - d2, exact, |r| <= 1/2
+    racc = fma2(r, r, racc);
   }
+  d[0] = d0;
+  d[1] = d1;
+  d[2] = d2;
+  d[3] = mul2(d2, make_float2(0x1p-7f, 0x1p-7f));
+}
+
+// The digit planes of four values (scaled by s) as FP16 pairs: d0, d1, d2 and
+// (NP == 4) d2 / 2^7; R: squared remainders added to racc.
+template <int NP, bool R>
+__device__ __forceinline__ void digits4(float4 v, const float2 (&s)[2], uint2 (&p)[4],
+                                        float2 (&racc)[2]) {
+  float2 a[4], b[4];
+  digits2<R>(mul2(make_float2(v.x, v.y), s[0]), a, racc[0]);
+  digits2<R>(mul2(make_float2(v.z, v.w), s[1]), b, racc[1]);
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
-    const __half2 a = __floats2half2_rn(d[q][0], d[q][1]);
-    const __half2 b = __floats2half2_rn(d[q][2], d[q][3]);
-    p[q].x = *reinterpret_cast<const uint32_t*>(&a);
-    p[q].y = *reinterpret_cast<const uint32_t*>(&b);
+    const __half2 lo = __float22half2_rn(a[q]);
+    const __half2 hi = __float22half2_rn(b[q]);
+    p[q].x = *reinterpret_cast<const uint32_t*>(&lo);
+    p[q].y = *reinterpret_cast<const uint32_t*>(&hi);
   }
 }
 
+// (h, l) += v exactly for two entries (TwoSum; l collects the rounding errors).
+__device__ __forceinline__ void two_sum2(float2& h, float2& l, float2 v) {
+  const float2 s = add2(h, v);
+  const float2 bb = sub2(s, h);
+  const float2 err = add2(sub2(h, sub2(s, bb)), sub2(v, bb));
+  l = add2(l, err);
+  h = s;
+}
+
+// Column mode (L == 1): X is the column-major I x K matrix, a stage is 16
+// consecutive columns.  Row mode (L > 1): element (l, i, r) of the slab view
+// at x[l + L (i + I r)]; a stage is 16 consecutive l of one slab r (the last
+// l-block of a slab zero-filled past L), K = Rt slabs of nlb blocks each.
 struct GramTcxArgs {
-  const float* x;          // column-major I x K
-  int64_t I, K;
+  const float* x;
+  int64_t L, I, K;         // K: columns (column mode) or slabs (row mode)
+  int nlb;                 // row mode: l-blocks per slab, ceil(L / 16)
   int ntiles, nkg, T;      // tiles of the lower triangle, K splits, row blocks
   const float* scale;      // I power-of-two row scales s_i
   double* part;            // gridDim.x partial tiles, [col][row], FP64 (scaled units)
@@ -134,11 +194,152 @@ __device__ __forceinline__ void tile_of(int t, int& ta, int& tb) {
   tb = t - a * (a + 1) / 2;
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx_col(GramTcxArgs g) {
+// Producer warp (one of NPROD): loads its share of every stage (rows
+// 128 ta.. for A and, NOPS == 2, rows 128 tb.. for B), splits it into digit
+// planes and hands the stage to the MMA thread.  Each lane holds four
+// consecutive rows of one stage column, as four floats:
+//   column mode: rows 4 lane .. 4 lane + 3 of column k0 + 16 s + warp, one
+//     16-byte load per operand (the column exists for s < nvalid);
+//   row mode: rows 8 warp + 4 h .. + 3 (h = lane / 16) at l = 16 lb + lane % 16
+//     of the stage's block (r, lb), four 4-byte loads L apart per operand.
+// Loads run PF stages ahead of the conversion (register ring), so each warp
+// keeps PF + 1 stages of loads in flight (PF = 3; PF = 4 spills).  Column
+// mode also prefetches PD stages ahead into L2.  NOPS == 1 (diagonal tile):
+// the squared last-digit remainders of the lane's rows go to rsum[slot][row]
+// (slot: the warp in column mode, lane % 16 in row mode).
+template <int NOPS, bool ROW>
+__device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uint64_t* bar_full,
+                                        uint64_t* bar_empty, const float* s_scale, int ta,
+                                        int tb, int64_t k0, int64_t k1, int64_t gs0, int nst,
+                                        int warp, int lane, float* rsum) {
+  float2 racc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  const int mn = ROW ? 8 * warp + 4 * (lane >> 4) : 4 * lane;   // first row of the lane
+  const int kcol = ROW ? (lane & 15) : warp;                     // stage column of the lane
+  const int64_t row0[2] = {(int64_t)ta * 128 + mn, (int64_t)tb * 128 + mn};
+  float2 sc[NOPS][2];
+#pragma unroll
+  for (int o = 0; o < NOPS; ++o)
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      sc[o][u] = make_float2(s_scale[128 * o + mn + 2 * u], s_scale[128 * o + mn + 2 * u + 1]);
+  constexpr int PF = 3;
+  float4 ring[PF + 1][NOPS];
+  int ls = 0;                                   // next stage to load
+  // column mode
+  const int64_t kfirst = k0 + warp;
+  const int nvalid = ROW ? 0 : (kfirst < k1 ? (int)((k1 - kfirst + BK - 1) / BK) : 0);
+  bool rok[NOPS];
+  const float* lp[NOPS];
+  const int64_t step = (int64_t)BK * g.I;
+  constexpr int PD = 16;
+  const int po = lane >> 3, pj = lane & 7;
+  const int64_t prow = (int64_t)(po == 0 ? ta : tb) * 128;
+  const bool pact = !ROW && po < NOPS && pj < 5 && prow < g.I;
+  const int64_t pnb = pact ? 4 * (min((int64_t)128, g.I - prow) - 1) : 0;   // last valid byte offset
+  const char* pp = nullptr;
+  // row mode: rows valid per operand and row, this lane's pointer at slab 0,
+  // block 0, and the block of the next load
+  unsigned rmask[NOPS];
+  int64_t rl = 0;
+  int lbl = 0;
+  const int64_t LI = g.L * g.I;
+  if (ROW) {
+#pragma unroll
+    for (int o = 0; o < NOPS; ++o) {
+      rmask[o] = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) rmask[o] |= (row0[o] + j < g.I) ? (1u << j) : 0u;
+      lp[o] = g.x + (rmask[o] ? g.L * row0[o] : 0) + kcol;
+    }
+    rl = gs0 / g.nlb;
+    lbl = (int)(gs0 % g.nlb);
+  } else {
+#pragma unroll
+    for (int o = 0; o < NOPS; ++o) {
+      rok[o] = row0[o] < g.I;
+      lp[o] = g.x + kfirst * g.I + (rok[o] ? row0[o] : 0);
+    }
+    pp = reinterpret_cast<const char*>(g.x + kfirst * g.I + (pact ? prow : 0)) +
+         min((int64_t)128 * pj, pnb) + (int64_t)PD * step * 4;
+  }
+  auto load_next = [&](float4 (&v)[NOPS]) {
+    if (ROW) {
+      const bool lok = ls < nst && 16 * lbl + kcol < g.L;
+      const int64_t off = rl * LI + 16 * lbl;
+#pragma unroll
+      for (int o = 0; o < NOPS; ++o) {
+        const float* q = lp[o] + off;
+        const unsigned m = lok ? rmask[o] : 0u;
+        v[o].x = (m & 1u) ? __ldg(q) : 0.f;
+        v[o].y = (m & 2u) ? __ldg(q + g.L) : 0.f;
+        v[o].z = (m & 4u) ? __ldg(q + 2 * g.L) : 0.f;
+        v[o].w = (m & 8u) ? __ldg(q + 3 * g.L) : 0.f;
+      }
+      if (++lbl == g.nlb) { lbl = 0; ++rl; }
+    } else {
+      const bool kok = ls < nvalid;
+      if (pact && ls + PD < nvalid) asm volatile("prefetch.global.L2 [%0];" ::"l"(pp));
+      pp += step * 4;
+#pragma unroll
+      for (int o = 0; o < NOPS; ++o) {
+        v[o] = (kok && rok[o]) ? ld_nl1(reinterpret_cast<const float4*>(lp[o]))
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        lp[o] += step;
+      }
+    }
+    ++ls;
+  };
+  const uint32_t o_a = OFF_A + mn_off(mn, kcol, KG_A);
+  const uint32_t o_b = OFF_B + mn_off(mn, kcol, KG_B);
+#pragma unroll
+  for (int u = 0; u < PF; ++u) load_next(ring[u]);
+  bool go = true;
+  int slot = 0;
+  uint32_t eph = 1;                              // parity of the next empty-slot wait
+  for (int s0 = 0; s0 < nst && go; s0 += PF + 1) {
+#pragma unroll
+    for (int u = 0; u <= PF; ++u) {
+      const int s = s0 + u;
+      if (s >= nst || !go) break;
+      load_next(ring[(u + PF) % (PF + 1)]);
+      const float4 (&v)[NOPS] = ring[u];
+      if (s >= NSTAGE) {
+        if (!mbar_wait(smem_u32(&bar_empty[slot]), eph, g.err)) { go = false; break; }
+      }
+      uint8_t* st = smem + (size_t)slot * STAGE_BYTES;
+      uint2 p[4];
+      digits4<4, NOPS == 1>(v[0], sc[0], p, racc);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) *reinterpret_cast<uint2*>(st + o_a + q * PLANE_STEP) = p[q];
+      if (NOPS == 2) {
+        digits4<3, false>(v[NOPS - 1], sc[NOPS - 1], p, racc);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) *reinterpret_cast<uint2*>(st + o_b + q * PLANE_STEP) = p[q];
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_full[slot]));
+      if (++slot == NSTAGE) { slot = 0; eph ^= 1u; }
+    }
+  }
+  if (NOPS == 1) {
+    const int slotw = ROW ? kcol : warp;
+    rsum[slotw * 128 + mn + 0] = racc[0].x;
+    rsum[slotw * 128 + mn + 1] = racc[0].y;
+    rsum[slotw * 128 + mn + 2] = racc[1].x;
+    rsum[slotw * 128 + mn + 3] = racc[1].y;
+  }
+}
+
+template <bool ROW>
+__global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx(GramTcxArgs g) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float* hi = reinterpret_cast<float*>(smem + NSTAGE * STAGE_BYTES);
   float* lo = hi + TILE_ELEMS;
+  float2* hi2 = reinterpret_cast<float2*>(hi);
+  float2* lo2 = reinterpret_cast<float2*>(lo);
+  float* rsum = lo + TILE_ELEMS;
   __shared__ uint64_t bar_full[NSTAGE], bar_empty[NSTAGE], bar_accf, bar_acce, bar_done;
   __shared__ uint32_t tmem_base_sh;
   __shared__ float s_scale[256];
@@ -148,8 +349,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx_col(GramTcxArgs g) {
   int ta, tb;
   tile_of(tile, ta, tb);
   const bool diag = ta == tb;
-  const int64_t k0 = g.K * kg / g.nkg, k1 = g.K * (kg + 1) / g.nkg;
-  const int nst = (int)((k1 - k0 + BK - 1) / BK);
+  // this CTA's K range: columns [k0, k1) (column mode) or stages [gs0, gs1)
+  const int64_t ku = ROW ? g.K * g.nlb : g.K;
+  const int64_t k0 = ku * kg / g.nkg, k1 = ku * (kg + 1) / g.nkg;
+  const int nst = ROW ? (int)(k1 - k0) : (int)((k1 - k0 + BK - 1) / BK);
   const int nwin = (nst + WIN - 1) / WIN;
 
   for (int t = threadIdx.x; t < 256; t += NTHREADS) {
@@ -176,114 +379,72 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx_col(GramTcxArgs g) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base_sh;
+  // Diagonal tiles: the last-digit remainder r is unbiased, but r^2 > 0
+  // biases every diagonal entry by sum_k r_ik^2 (2^-28 in scaled units); the
+  // producers' sums are subtracted before the tile goes out, leaving the
+  // zero-mean 2 sum_k x r.
 
   if (warp < NPROD) {
     // ---------------- producers: X -> digit planes of A (and B)
-    const int nops = diag ? 1 : 2;
-    const int64_t row0[2] = {(int64_t)ta * 128 + 4 * lane, (int64_t)tb * 128 + 4 * lane};
-    float sc[2][4];
-#pragma unroll
-    for (int o = 0; o < 2; ++o)
-#pragma unroll
-      for (int u = 0; u < 4; ++u) sc[o][u] = s_scale[128 * o + 4 * lane + u];
-    // loads run PF stages ahead of the conversion (register ring), so each
-    // warp keeps PF + 1 stages of 16-byte loads in flight (~80 KB per SM)
-    constexpr int PF = 4;
-    float4 ring[PF + 1][2][1];
-    auto load_stage = [&](int s, float4 (&v)[2][1]) {
-#pragma unroll
-      for (int j = 0; j < 1; ++j) {
-        const int kl = warp + NPROD * j;
-        const int64_t kc = k0 + (int64_t)s * BK + kl;
-        const bool kok = (s < nst) && kc < k1;
-        const float* col = g.x + kc * g.I;
-#pragma unroll
-        for (int o = 0; o < 2; ++o) {
-          const bool ok = kok && (o < nops) && row0[o] < g.I;
-          v[o][j] = ok ? __ldcs(reinterpret_cast<const float4*>(col + row0[o]))
-                       : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-      }
-    };
-#pragma unroll
-    for (int u = 0; u < PF; ++u) load_stage(u, ring[u]);
-    bool go = true;
-    for (int s0 = 0; s0 < nst && go; s0 += PF + 1) {
-#pragma unroll
-      for (int u = 0; u <= PF; ++u) {
-        const int s = s0 + u;
-        if (s >= nst || !go) break;
-        load_stage(s + PF, ring[(u + PF) % (PF + 1)]);
-        const float4 (&v)[2][1] = ring[u];
-        const int slot = s % NSTAGE;
-        if (s >= NSTAGE) {
-          if (!mbar_wait(smem_u32(&bar_empty[slot]), ((s / NSTAGE) - 1) & 1, g.err)) { go = false; break; }
-        }
-        uint8_t* st = smem + (size_t)slot * STAGE_BYTES;
-#pragma unroll
-        for (int j = 0; j < 1; ++j) {
-          const int kl = warp + NPROD * j;
-          const uint32_t o = mn_off(4 * lane, kl);
-          uint2 p[4];
-          digits4<4>(v[0][j], sc[0], p);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) *reinterpret_cast<uint2*>(st + OFF_A + o + q * PLANE) = p[q];
-          if (nops == 2) {
-            digits4<3>(v[1][j], sc[1], p);
-#pragma unroll
-            for (int q = 0; q < 3; ++q) *reinterpret_cast<uint2*>(st + OFF_B + o + q * PLANE) = p[q];
-          }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&bar_full[slot]));
-      }
-    }
-  } else if (warp == MMA_WARP) {
-    // ---------------- MMA issue (one thread)
-    if (lane == 0) {
-      const uint32_t idesc = instr_desc(128, 128);
-      const uint32_t sbase = smem_u32(smem);
-      const uint32_t boff = diag ? OFF_A : OFF_B;
-      bool ok = true;
-      for (int s = 0; s < nst && ok; ++s) {
-        const int slot = s % NSTAGE;
-        const int w = s / WIN;
-        const bool first = (s % WIN) == 0;
-        if (first && w >= 1) ok = mbar_wait(smem_u32(&bar_acce), (w - 1) & 1, g.err);
-        if (ok) ok = mbar_wait(smem_u32(&bar_full[slot]), (s / NSTAGE) & 1, g.err);
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t st = sbase + (uint32_t)slot * STAGE_BYTES;
-        uint64_t a[4], b[3];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) a[q] = smem_desc(st + OFF_A + q * PLANE, ATOM_MN, SK);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) b[q] = smem_desc(st + boff + q * PLANE, ATOM_MN, SK);
-        const uint32_t fresh = first ? 0u : 1u;
-        tc_mma(tmem + 0u, a[0], b[0], idesc, fresh);
-        tc_mma(tmem + 128u, a[0], b[1], idesc, fresh);
-        tc_mma(tmem + 128u, a[1], b[0], idesc, 1u);
-        tc_mma(tmem + 256u, a[0], b[2], idesc, fresh);
-        tc_mma(tmem + 256u, a[1], b[1], idesc, 1u);
-        tc_mma(tmem + 256u, a[2], b[0], idesc, 1u);
-        tc_mma(tmem + 384u, a[1], b[2], idesc, fresh);
-        tc_mma(tmem + 384u, a[2], b[1], idesc, 1u);
-        tc_mma(tmem + 384u, a[3], b[2], idesc, 1u);
-        tc_commit(smem_u32(&bar_empty[slot]));
-        if ((s % WIN) == WIN - 1 || s == nst - 1) tc_commit(smem_u32(&bar_accf));
-      }
-      tc_commit(smem_u32(&bar_done));
-    }
-    __syncwarp();
+    if (diag)
+      produce<1, ROW>(g, smem, bar_full, bar_empty, s_scale, ta, tb, k0, k1, k0, nst, warp, lane,
+                      rsum);
+    else
+      produce<2, ROW>(g, smem, bar_full, bar_empty, s_scale, ta, tb, k0, k1, k0, nst, warp, lane,
+                      rsum);
   } else {
-    // ---------------- epilogue: exact window sums -> FP32 pairs
+    // ---------------- drain warps: exact window sums -> FP32 pairs.  Lane 0
+    // of warp MMA_WARP first issues the window's MMAs (nine per stage, one
+    // thread); the next window cannot start before this drain ends anyway.
     const int e = warp - EPI_WARP0;
     const int q = warp & 3;                  // lane quarter this warp may access
     const int c0 = (e >> 2) * 64;            // this warp's 64 columns
     const int row = 32 * q + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+    const bool issuer = warp == MMA_WARP && lane == 0;
+    bool ok = true, done = false;
+    int slot = 0;
+    uint32_t fph = 0;                        // parity of the next full-slot wait
     for (int w = 0; w < nwin; ++w) {
+      if (warp == MMA_WARP) {
+        if (issuer && ok) {
+          const uint32_t id128 = instr_desc(128, 128), id256 = instr_desc(128, 256);
+          const uint32_t sbase = smem_u32(smem);
+          const uint32_t boff = diag ? OFF_A : OFF_B, bkg = diag ? KG_A : KG_B;
+          const int s_end = min(nst, (w + 1) * WIN);
+          if (w >= 1) ok = mbar_wait(smem_u32(&bar_acce), (w - 1) & 1, g.err);
+          for (int s = w * WIN; s < s_end && ok; ++s) {
+            ok = mbar_wait(smem_u32(&bar_full[slot]), fph, g.err);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t st = sbase + (uint32_t)slot * STAGE_BYTES;
+            uint64_t a[4], b[3];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = smem_desc(st + OFF_A + u * PLANE_STEP, ATOM, KG_A);
+#pragma unroll
+            for (int u = 0; u < 3; ++u) b[u] = smem_desc(st + boff + u * PLANE_STEP, ATOM, bkg);
+            // b[0] spans planes d0, d1 as one 256-row operand; tensor memory
+            // holds D0 | D1 | D2 | D3 at columns 0 | 128 | 256 | 384, so
+            // a_q x [d0 | d1] lands on two adjacent accumulators.  Each
+            // accumulator's first product of a window overwrites (fresh).
+            const uint32_t fresh = s == w * WIN ? 0u : 1u;
+            tc_mma(tmem + 0u, a[0], b[0], id256, fresh);      // D0 += a0 d0', D1 += a0 d1'
+            tc_mma(tmem + 256u, a[0], b[2], id128, fresh);    // D2 += a0 d2'
+            tc_mma(tmem + 128u, a[1], b[0], id256, 1u);       // D1 += a1 d0', D2 += a1 d1'
+            tc_mma(tmem + 384u, a[1], b[2], id128, fresh);    // D3 += a1 d2'
+            tc_mma(tmem + 256u, a[2], b[0], id256, 1u);       // D2 += a2 d0', D3 += a2 d1'
+            tc_mma(tmem + 384u, a[3], b[2], id128, 1u);       // D3 += (d2 / 2^7) d2'
+            tc_commit(smem_u32(&bar_empty[slot]));
+            if (++slot == NSTAGE) { slot = 0; fph ^= 1u; }
+          }
+          if (ok) tc_commit(smem_u32(&bar_accf));
+          if (!ok || w == nwin - 1) {
+            tc_commit(smem_u32(&bar_done));
+            done = true;
+          }
+        }
+        __syncwarp();
+      }
       if (!mbar_wait(smem_u32(&bar_accf), w & 1, g.err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
       for (int cc = 0; cc < 64; cc += 8) {
@@ -291,31 +452,33 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx_col(GramTcxArgs g) {
         const uint32_t col = (uint32_t)(c0 + cc);
         tmem_ld8x4(lane_base + col, r);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          // the four parts D0, D1 / 2^8, D2 / 2^16, D3 / 2^24 (each scaling
+        for (int j = 0; j < 8; j += 2) {
+          // the four parts D0, D1 / 2^7, D2 / 2^14, D3 / 2^21 (each scaling
           // exact) enter the pair one by one (TwoSum each): nothing is
-          // rounded before the compensated sum
-          const int idx = (c0 + cc + j) * 128 + row;
-          float h = hi[idx], l = lo[idx];
-          const float parts[4] = {__uint_as_float(r[0][j]), __uint_as_float(r[1][j]) * 0x1p-8f,
-                                  __uint_as_float(r[2][j]) * 0x1p-16f,
-                                  __uint_as_float(r[3][j]) * 0x1p-24f};
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float v = parts[q];
-            const float s2 = h + v;
-            const float bb = s2 - h;
-            l += (h - (s2 - bb)) + (v - bb);
-            h = s2;
-          }
-          hi[idx] = h;
-          lo[idx] = l;
+          // rounded before the compensated sum; columns j, j + 1 packed
+          const int idx = ((c0 + cc + j) >> 1) * 128 + row;
+          float2 h = hi2[idx], l = lo2[idx];
+          const float2 p0 = make_float2(__uint_as_float(r[0][j]), __uint_as_float(r[0][j + 1]));
+          const float2 p1 = mul2(make_float2(__uint_as_float(r[1][j]), __uint_as_float(r[1][j + 1])),
+                                 make_float2(0x1p-7f, 0x1p-7f));
+          const float2 p2 = mul2(make_float2(__uint_as_float(r[2][j]), __uint_as_float(r[2][j + 1])),
+                                 make_float2(0x1p-14f, 0x1p-14f));
+          const float2 p3 = mul2(make_float2(__uint_as_float(r[3][j]), __uint_as_float(r[3][j + 1])),
+                                 make_float2(0x1p-21f, 0x1p-21f));
+          two_sum2(h, l, p0);
+          two_sum2(h, l, p1);
+          two_sum2(h, l, p2);
+          two_sum2(h, l, p3);
+          hi2[idx] = h;
+          lo2[idx] = l;
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bar_acce));
     }
+    // a drain that gave up early still lets the issued MMAs retire first
+    if (issuer && !done) tc_commit(smem_u32(&bar_done));
   }
   // every tcgen05 op issued by the MMA thread has completed once bar_done fires
   mbar_wait(smem_u32(&bar_done), 0, g.err);
@@ -327,8 +490,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx_col(GramTcxArgs g) {
   }
   // partial tile out (FP64, scaled units)
   double* pt = g.part + (size_t)blockIdx.x * TILE_ELEMS;
-  for (int idx = threadIdx.x; idx < TILE_ELEMS; idx += NTHREADS)
-    pt[idx] = (double)hi[idx] + (double)lo[idx];
+  for (int idx = threadIdx.x; idx < TILE_ELEMS; idx += NTHREADS) {
+    const int c = idx >> 7, rr = idx & 127;
+    const int sidx = ((c >> 1) * 128 + rr) * 2 + (c & 1);
+    double v = (double)hi[sidx] + (double)lo[sidx];
+    if (diag && c == rr) {
+      double r2 = 0.0;
+      for (int w = 0; w < NPROD; ++w) r2 += (double)rsum[w * 128 + rr];
+      v -= r2 * 0x1p-28;
+    }
+    pt[idx] = v;
+  }
 }
 
 // S[i][j] = S[j][i] = (sum over the K splits of tile (ta, tb) at [col][row])
@@ -351,7 +523,7 @@ __global__ void k_gram_tcx_reduce(const double* __restrict__ part, int ntiles, i
 }
 
 // Power-of-two row scales from the row maxima (as FP32 bit patterns): the
-// largest |x s| in [64, 128); a zero row gets 1; exponents are clamped to the
+// largest |x s| in [32, 64); a zero row gets 1; exponents are clamped to the
 // FP32 range.
 __global__ void k_gram_tcx_scales(const unsigned* __restrict__ rowmax_bits, int64_t I,
                                   float* __restrict__ scale) {
@@ -359,23 +531,56 @@ __global__ void k_gram_tcx_scales(const unsigned* __restrict__ rowmax_bits, int6
   if (i >= I) return;
   const unsigned b = rowmax_bits[i] & 0x7fffffffu;
   int e = (int)(b >> 23) - 127;              // floor(log2 max) for normal values
-  if (b == 0u) e = 6;
-  int se = 6 - e;
+  if (b == 0u) e = 5;
+  int se = 5 - e;
   if (se > 126) se = 126;
   if (se < -126) se = -126;
   scale[i] = __uint_as_float((unsigned)(se + 127) << 23);
 }
 
+// Row maxima of a row-mode slab view, max over (l, r) of |x(l, i, r)|, as
+// FP32 bits (non-negative floats order as unsigned integers; rowmax starts at
+// 0).  One warp per (row i, run of slabs): lanes stride over l, the warp's
+// maximum enters rowmax[i] by one atomicMax.
+__global__ void k_rowmax_slab(const float* __restrict__ y, int64_t L, int64_t I, int64_t Rt,
+                              int nck, unsigned* __restrict__ rowmax) {
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= I * nck) return;
+  const int64_t i = gw % I, ck = gw / I;
+  const int64_t r0 = Rt * ck / nck, r1 = Rt * (ck + 1) / nck;
+  float m = 0.f;
+  for (int64_t r = r0; r < r1; ++r) {
+    const float* row = y + L * (i + I * r);
+    for (int64_t l = lane; l < L; l += 32) m = fmaxf(m, fabsf(__ldg(row + l)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) atomicMax(rowmax + i, __float_as_uint(m));
+}
+
 }  // namespace
 
+// Row-mode views whose last l-block is mostly padding stay on the FP32 Gram:
+// the l-blocks of a slab may hold at most 25 % zero fill.
 GramPlan plan_gram_tcx(int64_t L, int64_t I, int64_t Rt, int num_sms) {
   GramPlan p;
-  if (L != 1 || I < 128 || I > 2048 || (I % 4) != 0 || Rt < 4 * BK) return p;
+  if (I < 128 || I > 2048 || L < 1 || Rt < 1) return p;
+  int64_t stages;
+  if (L == 1) {
+    if ((I % 4) != 0 || Rt < 4 * BK) return p;
+    stages = (Rt + BK - 1) / BK;
+  } else {
+    const int64_t nlb = (L + BK - 1) / BK;
+    if (4 * nlb * BK > 5 * L || L * I >= ((int64_t)1 << 31)) return p;
+    stages = Rt * nlb;
+    if (stages < 4) return p;
+  }
   const int T = (int)((I + 127) / 128);
   const int ntiles = T * (T + 1) / 2;
   int nkg = num_sms / ntiles;
   if (nkg < 1) nkg = 1;
-  const int64_t maxkg = Rt / (4 * BK);
+  const int64_t maxkg = stages / 4;
   if (nkg > maxkg) nkg = (int)(maxkg < 1 ? 1 : maxkg);
   p.ntiles = ntiles;
   p.ksplit = nkg;
@@ -384,11 +589,13 @@ GramPlan plan_gram_tcx(int64_t L, int64_t I, int64_t Rt, int num_sms) {
   return p;
 }
 
-cudaError_t launch_gram_tcx(const float* y, int64_t I, int64_t Rt, const GramPlan& p,
+cudaError_t launch_gram_tcx(const float* y, int64_t L, int64_t I, int64_t Rt, const GramPlan& p,
                             const unsigned* rowmax_bits, void* scratch, unsigned* err, double* S,
                             cudaStream_t st) {
-  if (p.nctas <= 0 || ((uintptr_t)y & 15) != 0) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_gram_tcx_col, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (p.nctas <= 0 || (L == 1 && ((uintptr_t)y & 15) != 0) || ((uintptr_t)y & 3) != 0)
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(L == 1 ? k_gram_tcx<false> : k_gram_tcx<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)SMEM_BYTES);
   if (e != cudaSuccess) return e;
   double* part = static_cast<double*>(scratch);
@@ -396,19 +603,37 @@ cudaError_t launch_gram_tcx(const float* y, int64_t I, int64_t Rt, const GramPla
   k_gram_tcx_scales<<<(unsigned)((I + 255) / 256), 256, 0, st>>>(rowmax_bits, I, scale);
   GramTcxArgs a;
   a.x = y;
+  a.L = L;
   a.I = I;
   a.K = Rt;
+  a.nlb = (int)((L + BK - 1) / BK);
   a.ntiles = p.ntiles;
   a.nkg = p.ksplit;
   a.T = (int)((I + 127) / 128);
   a.scale = scale;
   a.part = part;
   a.err = err;
-  k_gram_tcx_col<<<(unsigned)p.nctas, NTHREADS, SMEM_BYTES, st>>>(a);
+  if (L == 1)
+    k_gram_tcx<false><<<(unsigned)p.nctas, NTHREADS, SMEM_BYTES, st>>>(a);
+  else
+    k_gram_tcx<true><<<(unsigned)p.nctas, NTHREADS, SMEM_BYTES, st>>>(a);
   const int64_t tot = I * I;
   k_gram_tcx_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, p.ntiles, p.ksplit, I,
                                                                    scale, S);
   count_launches(3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rowmax_slab(const float* y, int64_t L, int64_t I, int64_t Rt, int num_sms,
+                               unsigned* rowmax_bits, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(rowmax_bits, 0, sizeof(unsigned) * (size_t)I, st);
+  if (e != cudaSuccess) return e;
+  int64_t nck = ((int64_t)num_sms * 64 + I - 1) / I;     // ~64 warps per SM
+  if (nck > Rt) nck = Rt;
+  if (nck < 1) nck = 1;
+  const int64_t warps = I * nck;
+  k_rowmax_slab<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(y, L, I, Rt, (int)nck, rowmax_bits);
+  count_launches(1);
   return cudaGetLastError();
 }
 

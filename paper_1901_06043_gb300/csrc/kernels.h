@@ -27,13 +27,17 @@ struct GramPlan {
   int nctas = 0;         // plan_gram_f32: CTAs (= partial tiles)
   size_t scratch_bytes = 0;
 };
-// ---- tensor-core Gram of the mode-0 view on exact digit products
-// (gram_tcx.cu): plan.nctas == 0 when it does not apply (L == 1, 128 <= I <=
-// 2048, I % 4 == 0); rowmax_bits from launch_sumsq_rowmax
+// ---- tensor-core Gram of a slab view on exact digit products
+// (gram_tcx.cu): plan.nctas == 0 when it does not apply (128 <= I <= 2048;
+// column mode L == 1 with I % 4 == 0; row mode L > 1 with l-blocks of 16 at
+// most 25 % zero fill); rowmax_bits: FP32 bits of the row maxima, from
+// launch_sumsq_rowmax (column mode) or launch_rowmax_slab (row mode)
 GramPlan plan_gram_tcx(int64_t L, int64_t I, int64_t Rt, int num_sms);
-cudaError_t launch_gram_tcx(const float* y, int64_t I, int64_t Rt, const GramPlan& p,
+cudaError_t launch_gram_tcx(const float* y, int64_t L, int64_t I, int64_t Rt, const GramPlan& p,
                             const unsigned* rowmax_bits, void* scratch, unsigned* err, double* S,
                             cudaStream_t st);
+cudaError_t launch_rowmax_slab(const float* y, int64_t L, int64_t I, int64_t Rt, int num_sms,
+                               unsigned* rowmax_bits, cudaStream_t st);
 
 // L0: the fastest sub-index of l (the first dim of the tensor for a mode
 // n > 0); row-mode K-blocks never cross a multiple of it
