@@ -473,12 +473,15 @@ tucker_status do_cut(tucker_ctx* c, const double* w, int n, double thr, int fixe
 
 // ymax: max|y| if the caller knows it (e.g. from the norm pass), else <= 0.
 // check = false: as do_gram, for the tensor-core TTM's error word (d_words[9]).
+// zt (column-mode views): Z written transposed, slab fastest (the new mode
+// becomes the slowest index).
 tucker_status do_ttm(tucker_ctx* c, const void* y, tucker_dtype ydt, const SlabView& v,
                      const double* A, int64_t K, int64_t lda, int arow, tucker_prec prec, void* z,
-                     tucker_dtype zdt, int* kernel_used, double ymax = -1.0, bool check = true) {
+                     tucker_dtype zdt, int* kernel_used, double ymax = -1.0, bool check = true,
+                     bool zt = false) {
   const bool tc = (prec == TUCKER_PREC_MIXED || prec == TUCKER_PREC_TENSOR) && ydt == TUCKER_F32 &&
                   zdt == TUCKER_F32 && (((uintptr_t)y) & 15) == 0 &&
-                  ttm_tc_supported(v.L, v.I, v.Rt, K);
+                  (!zt || (((uintptr_t)z) & 15) == 0) && ttm_tc_supported(v.L, v.I, v.Rt, K);
   if (kernel_used) *kernel_used = tc ? 2 : (prec == TUCKER_PREC_FP64 ? 0 : 1);
   if (tc) {
     if (!(ymax >= 0.0)) {
@@ -489,7 +492,7 @@ tucker_status do_ttm(tucker_ctx* c, const void* y, tucker_dtype ydt, const SlabV
     TK_TRY(dev_alloc(c, scratch, ttm_tc_scratch_bytes(v.I, K)));
     if (check) TK_CUDA(c, cudaMemsetAsync(c->d_words + 9, 0, sizeof(unsigned), c->stream));
     TK_CUDA(c, launch_ttm_tc((const float*)y, v.L, v.I, v.Rt, A, K, lda, arow, split_scale(ymax),
-                             (float*)z, scratch.p, c->d_words + 9, c->num_sms, c->stream));
+                             (float*)z, zt, scratch.p, c->d_words + 9, c->num_sms, c->stream));
     if (!check) return TUCKER_OK;
     unsigned err = 0;
     TK_CUDA(c, cudaMemcpyAsync(&err, c->d_words + 9, sizeof(unsigned), cudaMemcpyDeviceToHost,
@@ -507,7 +510,7 @@ tucker_status do_ttm(tucker_ctx* c, const void* y, tucker_dtype ydt, const SlabV
   if (prec != TUCKER_PREC_FP64 && (double)v.L * (double)v.Rt * (double)K >= 16777216.0)
     TK_TRY(dev_alloc(c, a32, sizeof(float) * (size_t)K * v.I));
   TK_CUDA(c, launch_ttm_simt(y, ydt, prec == TUCKER_PREC_FP64, v.L, v.I, v.Rt, A, K, lda, arow,
-                             a32.as<float>(), z, zdt, c->stream));
+                             a32.as<float>(), z, zdt, c->stream, zt));
   return TUCKER_OK;
 }
 
@@ -790,15 +793,42 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
   tucker_dtype ydt = dt;
   int64_t cur[TUCKER_MAX_MODES];
   for (int k = 0; k < ndim; ++k) cur[k] = dims[k];
+  // Rotated layout (mode order 0, 1, ..., N-1): every TTM contracts the
+  // fastest mode and writes its new mode last (transposed output), so mode n
+  // is always the fastest index of the working tensor and every Gram and TTM
+  // sees a column-mode view; after N modes the core is back in the natural
+  // order.  Other orders keep the natural layout (row-mode views).
+  bool rotate = true;
+  for (int k = 0; k < ndim; ++k) rotate = rotate && order[k] == k;
   bool noconv = false;
   for (int s = 0; s < ndim; ++s) {
     const int n = order[s];
-    const SlabView v = slab_view(ndim, cur, n);
+    SlabView v = slab_view(ndim, cur, n);
+    if (rotate) v = SlabView{1, v.I, v.L * v.Rt, 1};
     const int I = (int)v.I;
     Timer tmg, tme, tmt;
     tmg.start(c);
-    TK_TRY(do_gram(c, y, ydt, v, gram_prec, S.as<double>(), &r->gram_kernel[n],
-                   s == 0 ? xmax : -1.0, true, s == 0 ? rowmax.as<unsigned>() : nullptr));
+    // later modes of the rotated layout: digit scales from a row-maxima pass
+    // of the column-mode view, whose largest entry is the TTM's split scale
+    DevBuf rowmax_s;
+    double ymax = s == 0 ? xmax : -1.0;
+    const unsigned* rmx = s == 0 ? rowmax.as<unsigned>() : nullptr;
+    if (rotate && s > 0 && ydt == TUCKER_F32 &&
+        gram_kernel_for(gram_prec, ydt, v, c->num_sms) == 5 && (((uintptr_t)y) & 15) == 0) {
+      TK_TRY(dev_alloc(c, rowmax_s, sizeof(unsigned) * v.I));
+      TK_TRY(rowmax_pass(c, (const float*)y, v.I, v.Rt, rowmax_s.as<unsigned>()));
+      std::vector<unsigned> hb((size_t)v.I);
+      TK_CUDA(c, cudaMemcpyAsync(hb.data(), rowmax_s.p, sizeof(unsigned) * v.I,
+                                 cudaMemcpyDeviceToHost, c->stream));
+      TK_TRY(sync(c));
+      unsigned mb = 0;
+      for (unsigned b : hb) mb = std::max(mb, b & 0x7fffffffu);
+      float mf;
+      memcpy(&mf, &mb, sizeof mf);
+      ymax = (double)mf;
+      rmx = rowmax_s.as<unsigned>();
+    }
+    TK_TRY(do_gram(c, y, ydt, v, gram_prec, S.as<double>(), &r->gram_kernel[n], ymax, true, rmx));
     tmg.stop(c);
     DevBuf w, U;
     TK_TRY(dev_alloc(c, w, sizeof(double) * I));
@@ -840,7 +870,7 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
     TK_TRY(dev_alloc(c, z, dtype_size(wdt) * numel(ndim, nd)));
     tmt.start(c);
     TK_TRY(do_ttm(c, y, ydt, v, r->factors[n], R, I, 1, prec, z.p, wdt, &r->ttm_kernel[n],
-                  s == 0 ? xmax : -1.0));
+                  ymax, true, rotate));
     tmt.stop(c);
     ycur.reset();
     ycur.p = z.release();

@@ -203,8 +203,10 @@ __device__ __forceinline__ void tile_of(int t, int& ta, int& tb) {
 //   row mode: rows 8 warp + 4 h .. + 3 (h = lane / 16) at l = 16 lb + lane % 16
 //     of the stage's block (r, lb), four 4-byte loads L apart per operand.
 // Loads run PF stages ahead of the conversion (register ring), so each warp
-// keeps PF + 1 stages of loads in flight (PF = 3; PF = 4 spills).  Column
-// mode also prefetches PD stages ahead into L2.  NOPS == 1 (diagonal tile):
+// keeps PF + 1 stages of loads in flight (PF = 3 in column mode, where 4
+// spills; 2 in row mode, measured faster than 3 there).  (An L2
+// prefetch PD stages ahead changed nothing in column mode and cost 30 % in row
+// mode, where the extra instructions outweighed the latency they hid.)  NOPS == 1 (diagonal tile):
 // the squared last-digit remainders of the lane's rows go to rsum[slot][row]
 // (slot: the warp in column mode, lane % 16 in row mode).
 template <int NOPS, bool ROW>
@@ -222,7 +224,7 @@ __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uin
 #pragma unroll
     for (int u = 0; u < 2; ++u)
       sc[o][u] = make_float2(s_scale[128 * o + mn + 2 * u], s_scale[128 * o + mn + 2 * u + 1]);
-  constexpr int PF = 3;
+  constexpr int PF = ROW ? 2 : 3;
   float4 ring[PF + 1][NOPS];
   int ls = 0;                                   // next stage to load
   // column mode
@@ -231,12 +233,6 @@ __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uin
   bool rok[NOPS];
   const float* lp[NOPS];
   const int64_t step = (int64_t)BK * g.I;
-  constexpr int PD = 16;
-  const int po = lane >> 3, pj = lane & 7;
-  const int64_t prow = (int64_t)(po == 0 ? ta : tb) * 128;
-  const bool pact = !ROW && po < NOPS && pj < 5 && prow < g.I;
-  const int64_t pnb = pact ? 4 * (min((int64_t)128, g.I - prow) - 1) : 0;   // last valid byte offset
-  const char* pp = nullptr;
   // row mode: rows valid per operand and row, this lane's pointer at slab 0,
   // block 0, and the block of the next load
   unsigned rmask[NOPS];
@@ -259,8 +255,6 @@ __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uin
       rok[o] = row0[o] < g.I;
       lp[o] = g.x + kfirst * g.I + (rok[o] ? row0[o] : 0);
     }
-    pp = reinterpret_cast<const char*>(g.x + kfirst * g.I + (pact ? prow : 0)) +
-         min((int64_t)128 * pj, pnb) + (int64_t)PD * step * 4;
   }
   auto load_next = [&](float4 (&v)[NOPS]) {
     if (ROW) {
@@ -278,8 +272,6 @@ __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uin
       if (++lbl == g.nlb) { lbl = 0; ++rl; }
     } else {
       const bool kok = ls < nvalid;
-      if (pact && ls + PD < nvalid) asm volatile("prefetch.global.L2 [%0];" ::"l"(pp));
-      pp += step * 4;
 #pragma unroll
       for (int o = 0; o < NOPS; ++o) {
         v[o] = (kok && rok[o]) ? ld_nl1(reinterpret_cast<const float4*>(lp[o]))
@@ -303,18 +295,20 @@ __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uin
       if (s >= nst || !go) break;
       load_next(ring[(u + PF) % (PF + 1)]);
       const float4 (&v)[NOPS] = ring[u];
+      // split first, then wait for the slot: a freed slot only waits for
+      // the stores (the split is off the MMA -> producer -> MMA hand-off)
+      uint2 p[4], pb[4];
+      digits4<4, NOPS == 1>(v[0], sc[0], p, racc);
+      if (NOPS == 2) digits4<3, false>(v[NOPS - 1], sc[NOPS - 1], pb, racc);
       if (s >= NSTAGE) {
         if (!mbar_wait(smem_u32(&bar_empty[slot]), eph, g.err)) { go = false; break; }
       }
       uint8_t* st = smem + (size_t)slot * STAGE_BYTES;
-      uint2 p[4];
-      digits4<4, NOPS == 1>(v[0], sc[0], p, racc);
 #pragma unroll
       for (int q = 0; q < 4; ++q) *reinterpret_cast<uint2*>(st + o_a + q * PLANE_STEP) = p[q];
       if (NOPS == 2) {
-        digits4<3, false>(v[NOPS - 1], sc[NOPS - 1], p, racc);
 #pragma unroll
-        for (int q = 0; q < 3; ++q) *reinterpret_cast<uint2*>(st + o_b + q * PLANE_STEP) = p[q];
+        for (int q = 0; q < 3; ++q) *reinterpret_cast<uint2*>(st + o_b + q * PLANE_STEP) = pb[q];
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
@@ -540,8 +534,8 @@ __global__ void k_gram_tcx_scales(const unsigned* __restrict__ rowmax_bits, int6
 
 // Row maxima of a row-mode slab view, max over (l, r) of |x(l, i, r)|, as
 // FP32 bits (non-negative floats order as unsigned integers; rowmax starts at
-// 0).  One warp per (row i, run of slabs): lanes stride over l, the warp's
-// maximum enters rowmax[i] by one atomicMax.
+// 0).  One warp per (row i, run of slabs): lanes stride over l, four slabs at
+// a time, and the warp's maximum enters rowmax[i] by one atomicMax.
 __global__ void k_rowmax_slab(const float* __restrict__ y, int64_t L, int64_t I, int64_t Rt,
                               int nck, unsigned* __restrict__ rowmax) {
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -550,7 +544,17 @@ __global__ void k_rowmax_slab(const float* __restrict__ y, int64_t L, int64_t I,
   const int64_t i = gw % I, ck = gw / I;
   const int64_t r0 = Rt * ck / nck, r1 = Rt * (ck + 1) / nck;
   float m = 0.f;
-  for (int64_t r = r0; r < r1; ++r) {
+  const int64_t LI = L * I;
+  int64_t r = r0;
+  for (; r + 4 <= r1; r += 4) {                 // four slabs' loads in flight
+    const float* row = y + L * (i + I * r);
+    for (int64_t l = lane; l < L; l += 32) {
+      const float a = __ldg(row + l), b = __ldg(row + LI + l);
+      const float c = __ldg(row + 2 * LI + l), d = __ldg(row + 3 * LI + l);
+      m = fmaxf(m, fmaxf(fmaxf(fabsf(a), fabsf(b)), fmaxf(fabsf(c), fabsf(d))));
+    }
+  }
+  for (; r < r1; ++r) {
     const float* row = y + L * (i + I * r);
     for (int64_t l = lane; l < L; l += 32) m = fmaxf(m, fabsf(__ldg(row + l)));
   }

@@ -66,9 +66,11 @@ cudaError_t launch_gram_small(const void* y, tucker_dtype dt, int64_t L, int64_t
 
 // ---- SIMT TTM
 // a32_scratch: K * I floats for the FP32 copy of A (FP32 arithmetic), or NULL
+// zt (column mode only): Z written transposed, z[slab + Rt k] (the new mode last)
 cudaError_t launch_ttm_simt(const void* y, tucker_dtype ydt, bool fp64, int64_t L, int64_t I,
                             int64_t Rt, const double* A, int64_t K, int64_t lda, int a_rowmajor,
-                            float* a32_scratch, void* z, tucker_dtype zdt, cudaStream_t st);
+                            float* a32_scratch, void* z, tucker_dtype zdt, cudaStream_t st,
+                            bool zt = false);
 
 // ---- tensor-core (tcgen05) Gram and TTM on the FP16 hi/lo split
 struct TcGramPlan {
@@ -83,8 +85,8 @@ cudaError_t launch_gram_tc(const float* y, int64_t L, int64_t I, int64_t Rt, con
 // power-of-two scale of y with max|y sy| <= 2^14
 int ttm_tc_supported(int64_t L, int64_t I, int64_t Rt, int64_t K);
 cudaError_t launch_ttm_tc(const float* y, int64_t L, int64_t I, int64_t Rt, const double* A,
-                          int64_t K, int64_t lda, int a_rowmajor, float sy, float* z, void* scratch,
-                          unsigned* err, int num_sms, cudaStream_t st);
+                          int64_t K, int64_t lda, int a_rowmajor, float sy, float* z, bool zt,
+                          void* scratch, unsigned* err, int num_sms, cudaStream_t st);
 size_t ttm_tc_scratch_bytes(int64_t I, int64_t K);
 
 // ---- Jacobi eigensolver, sort and rank cut

@@ -495,21 +495,23 @@ constexpr int TBI = 16;   // contraction step
 
 // Z (K x M) = A (K x I) * Y (I x M), M = the (r, l) pairs of the slab view.
 // Row mode (L > 1): an m-tile is 64 consecutive l of one slab.  Column mode
-// (L == 1): an m-tile is 64 consecutive slabs.
+// (L == 1): an m-tile is 64 consecutive slabs; zt writes Z transposed
+// (z[r + Rt k], slab fastest: the new mode last).
 template <typename TIn, typename TOut, typename TC>
 __global__ void __launch_bounds__(256) k_ttm_simt(const TIn* __restrict__ y, int64_t L, int64_t I,
                                                   int64_t Rt, int64_t nLT,
                                                   const double* __restrict__ A, int64_t K,
                                                   int64_t lda, int a_rowmajor,
                                                   const float* __restrict__ A32,
-                                                  TOut* __restrict__ z) {
+                                                  TOut* __restrict__ z, int zt) {
   __shared__ TC As[TBI][TT + 1];   // As[i][k]
   __shared__ TC Ys[TBI][TT + 1];   // Ys[i][m]
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   // output coordinates of this thread: the index that is contiguous in Z goes
   // to consecutive threads (k in column mode, l in row mode)
-  const int kq = (L == 1) ? tx : ty, mq = (L == 1) ? ty : tx;
+  const bool kfast = (L == 1) && !zt;
+  const int kq = kfast ? tx : ty, mq = kfast ? ty : tx;
   const int64_t mt = blockIdx.x;
   const int64_t k0 = (int64_t)blockIdx.y * TT;
   int64_t r0, l0;
@@ -581,7 +583,10 @@ __global__ void __launch_bounds__(256) k_ttm_simt(const TIn* __restrict__ y, int
       int mm = mq + 16 * v;
       if (L == 1) {
         int64_t r = r0 + mm;
-        if (r < Rt) z[k + K * r] = (TOut)acc[u][v];
+        if (r < Rt) {
+          if (zt) z[r + Rt * k] = (TOut)acc[u][v];
+          else z[k + K * r] = (TOut)acc[u][v];
+        }
       } else {
         int64_t l = l0 + mm;
         if (l < L) z[l + L * (k + K * r0)] = (TOut)acc[u][v];
@@ -606,18 +611,20 @@ __global__ void k_ttm_a32(const double* __restrict__ A, int64_t K, int64_t I, in
 template <typename TIn, typename TOut>
 static void ttm_dispatch_c(bool fp64, dim3 grid, cudaStream_t st, const void* y, int64_t L, int64_t I,
                            int64_t Rt, int64_t nLT, const double* A, int64_t K, int64_t lda,
-                           int arow, const float* A32, void* z) {
+                           int arow, const float* A32, void* z, int zt) {
   if (fp64)
     k_ttm_simt<TIn, TOut, double><<<grid, 256, 0, st>>>((const TIn*)y, L, I, Rt, nLT, A, K, lda, arow,
-                                                        nullptr, (TOut*)z);
+                                                        nullptr, (TOut*)z, zt);
   else
     k_ttm_simt<TIn, TOut, float><<<grid, 256, 0, st>>>((const TIn*)y, L, I, Rt, nLT, A, K, lda, arow,
-                                                       A32, (TOut*)z);
+                                                       A32, (TOut*)z, zt);
 }
 
 cudaError_t launch_ttm_simt(const void* y, tucker_dtype ydt, bool fp64, int64_t L, int64_t I,
                             int64_t Rt, const double* A, int64_t K, int64_t lda, int a_rowmajor,
-                            float* a32_scratch, void* z, tucker_dtype zdt, cudaStream_t st) {
+                            float* a32_scratch, void* z, tucker_dtype zdt, cudaStream_t st,
+                            bool zt) {
+  if (zt && L != 1) return cudaErrorInvalidValue;
   int64_t nLT = 1, nMT;
   if (L == 1) nMT = (Rt + TT - 1) / TT;
   else { nLT = (L + TT - 1) / TT; nMT = Rt * nLT; }
@@ -634,11 +641,11 @@ cudaError_t launch_ttm_simt(const void* y, tucker_dtype ydt, bool fp64, int64_t 
   }
   count_launches(1);
   if (ydt == TUCKER_F64) {
-    if (zdt == TUCKER_F64) ttm_dispatch_c<double, double>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, A32, z);
-    else ttm_dispatch_c<double, float>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, A32, z);
+    if (zdt == TUCKER_F64) ttm_dispatch_c<double, double>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, A32, z, zt);
+    else ttm_dispatch_c<double, float>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, A32, z, zt);
   } else {
-    if (zdt == TUCKER_F64) ttm_dispatch_c<float, double>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, A32, z);
-    else ttm_dispatch_c<float, float>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, A32, z);
+    if (zdt == TUCKER_F64) ttm_dispatch_c<float, double>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, A32, z, zt);
+    else ttm_dispatch_c<float, float>(fp64, grid, st, y, L, I, Rt, nLT, A, K, lda, a_rowmajor, A32, z, zt);
   }
   return cudaGetLastError();
 }

@@ -2,7 +2,8 @@
 // n = 0): Z (K x Rt) = A (K x I) Y (I x Rt), where slab m of the mode-0 view
 // is column m of Y (contiguous in i) and A = U_0^T (or any K x I operator of
 // the multi-TTM), K <= 128.  Z is written column-major: the K outputs of one
-// slab are contiguous, which is the natural-descending layout of the result.
+// slab are contiguous, which is the natural-descending layout of the result;
+// or transposed (zt), slab fastest, which puts the new mode last.
 //
 // Arithmetic.  Y and A are scaled by powers of two (max|y s_y| <= 2^14,
 // max|a s_a| <= 2^14) and split into two FP16 numbers each, x s = h + l with
@@ -146,7 +147,8 @@ struct TtmTcArgs {
   float sy;              // power of two
   const uint8_t* aprep;  // nks x [A_h | A_l] images
   const float* sa;       // the power-of-two scale of A (device)
-  float* z;              // K x Rt column-major
+  float* z;              // K x Rt column-major, or (zt) Rt x K column-major
+  int zt;                // transposed output: z[r * Rt + slab]
   unsigned* err;
 };
 
@@ -303,10 +305,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           uint32_t rr[32];
           tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * (uint32_t)TN + (uint32_t)c0, rr);
           if (r < g.K) {
+            if (!g.zt) {
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) {
-              const int64_t slab = m0 + c0 + jj;
-              if (slab < g.Rt) g.z[slab * g.K + r] = __uint_as_float(rr[jj]) * inv;
+              for (int jj = 0; jj < 32; ++jj) {
+                const int64_t slab = m0 + c0 + jj;
+                if (slab < g.Rt) g.z[slab * g.K + r] = __uint_as_float(rr[jj]) * inv;
+              }
+            } else if ((g.Rt & 3) == 0) {
+              // transposed: this lane's 32 slabs are contiguous in its row of
+              // Z; 16-byte stores (Rt % 4 == 0: the row starts are aligned)
+              float* zr = g.z + (int64_t)r * g.Rt;
+#pragma unroll
+              for (int jj = 0; jj < 32; jj += 4) {
+                const int64_t slab = m0 + c0 + jj;
+                if (slab < g.Rt)
+                  *reinterpret_cast<float4*>(zr + slab) =
+                      make_float4(__uint_as_float(rr[jj]) * inv, __uint_as_float(rr[jj + 1]) * inv,
+                                  __uint_as_float(rr[jj + 2]) * inv, __uint_as_float(rr[jj + 3]) * inv);
+              }
+            } else {
+              float* zr = g.z + (int64_t)r * g.Rt;
+#pragma unroll
+              for (int jj = 0; jj < 32; ++jj) {
+                const int64_t slab = m0 + c0 + jj;
+                if (slab < g.Rt) zr[slab] = __uint_as_float(rr[jj]) * inv;
+              }
             }
           }
         }
@@ -360,9 +383,10 @@ size_t ttm_tc_scratch_bytes(int64_t I, int64_t K) {
 }
 
 cudaError_t launch_ttm_tc(const float* y, int64_t L, int64_t I, int64_t Rt, const double* A,
-                          int64_t K, int64_t lda, int a_rowmajor, float sy, float* z, void* scratch,
-                          unsigned* err, int num_sms, cudaStream_t st) {
+                          int64_t K, int64_t lda, int a_rowmajor, float sy, float* z, bool zt,
+                          void* scratch, unsigned* err, int num_sms, cudaStream_t st) {
   if (!ttm_tc_supported(L, I, Rt, K) || ((uintptr_t)y & 15) != 0) return cudaErrorInvalidValue;
+  if (zt && (Rt & 3) == 0 && ((uintptr_t)z & 15) != 0) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_ttm_tc_col, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -385,6 +409,7 @@ cudaError_t launch_ttm_tc(const float* y, int64_t L, int64_t I, int64_t Rt, cons
   a.aprep = aprep;
   a.sa = sa;
   a.z = z;
+  a.zt = zt ? 1 : 0;
   a.err = err;
   // Y as a 2D tensor: x = i (contiguous), y = slab; boxes of 64 i x 128 slabs
   EncodeTiledFn enc = encode_tiled();

@@ -802,9 +802,10 @@ def test_sthosvd_mixed_path_ranks_and_error(ctx, eps):
     res = ctx.sthosvd(x, dims, eps=eps, prec="mixed")
     assert res.gram_kernel[0] == "tcgen05-x3"
     assert res.ttm_kernel[0] == "tcgen05"
-    # mode 1 is the row-mode view (L = R_0) of the truncated tensor
-    v1 = (res.ranks[0],) + dims[1:]
-    assert (res.gram_kernel[1] == "tcgen05-x3") == _tcx_applies(v1, 1)
+    # natural mode order: the working tensor is kept rotated (each TTM writes
+    # its new mode last), so mode 1 is a column-mode view (I = 160) and both
+    # its Gram and its TTM run on the tensor cores
+    assert res.gram_kernel[1] == "tcgen05-x3" and res.ttm_kernel[1] == "tcgen05"
     assert res.ranks == ref["ranks"]
     ours = {"core": host(res.core), "core_dims": res.ranks,
             "factors": [host(f) for f in res.factors], "discarded": res.discarded,
