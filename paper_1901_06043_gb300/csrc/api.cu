@@ -505,6 +505,35 @@ tucker_status do_ttm(tucker_ctx* c, const void* y, tucker_dtype ydt, const SlabV
     }
     return TUCKER_OK;
   }
+  // row-mode views with a short contraction (I <= 64: the reconstruction's
+  // expansions) on the tensor cores, l as the MMA's M
+  const bool tc_row = !zt && (prec == TUCKER_PREC_MIXED || prec == TUCKER_PREC_TENSOR) &&
+                      ydt == TUCKER_F32 && zdt == TUCKER_F32 && (((uintptr_t)y) & 15) == 0 &&
+                      ttm_tc_row_supported(v.L, v.I, v.Rt, K);
+  if (tc_row) {
+    if (kernel_used) *kernel_used = 2;
+    if (!(ymax >= 0.0)) {
+      double nrm;
+      TK_TRY(do_norm(c, y, ydt, v.L * v.I * v.Rt, &nrm, &ymax));
+    }
+    DevBuf scratch;
+    TK_TRY(dev_alloc(c, scratch, ttm_tc_row_scratch_bytes(K)));
+    if (check) TK_CUDA(c, cudaMemsetAsync(c->d_words + 9, 0, sizeof(unsigned), c->stream));
+    TK_CUDA(c, launch_ttm_tc_row((const float*)y, v.L, v.I, v.Rt, A, K, lda, arow,
+                                 split_scale(ymax), (float*)z, scratch.p, c->d_words + 9,
+                                 c->num_sms, c->stream));
+    if (!check) return TUCKER_OK;
+    unsigned err = 0;
+    TK_CUDA(c, cudaMemcpyAsync(&err, c->d_words + 9, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                               c->stream));
+    TK_TRY(sync(c));
+    if (err) {
+      char m[96];
+      snprintf(m, sizeof m, "tensor-core TTM reported device error word 0x%x", err);
+      return set_err(c, TUCKER_ERR_CUDA, m);
+    }
+    return TUCKER_OK;
+  }
   // the FP32 copy of the operator pays off once the TTM spans several waves
   DevBuf a32;
   if (prec != TUCKER_PREC_FP64 && (double)v.L * (double)v.Rt * (double)K >= 16777216.0)

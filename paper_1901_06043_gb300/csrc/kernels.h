@@ -88,6 +88,13 @@ cudaError_t launch_ttm_tc(const float* y, int64_t L, int64_t I, int64_t Rt, cons
                           int64_t K, int64_t lda, int a_rowmajor, float sy, float* z, bool zt,
                           void* scratch, unsigned* err, int num_sms, cudaStream_t st);
 size_t ttm_tc_scratch_bytes(int64_t I, int64_t K);
+// row-mode views (L > 1, L % 4 == 0, I <= 64, K <= 1024): Z(l, k, r) =
+// sum_i A(k, i) Y(l, i, r), z[l + L (k + K r)] (ttm_tc.cu)
+int ttm_tc_row_supported(int64_t L, int64_t I, int64_t Rt, int64_t K);
+size_t ttm_tc_row_scratch_bytes(int64_t K);
+cudaError_t launch_ttm_tc_row(const float* y, int64_t L, int64_t I, int64_t Rt, const double* A,
+                              int64_t K, int64_t lda, int a_rowmajor, float sy, float* z,
+                              void* scratch, unsigned* err, int num_sms, cudaStream_t st);
 
 // ---- Jacobi eigensolver, sort and rank cut
 size_t jacobi_work_bytes(int n);

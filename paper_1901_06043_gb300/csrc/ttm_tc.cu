@@ -349,6 +349,276 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
+// ------------------------------------------------------------------------
+// Row-mode views (L > 1, L % 4 == 0, I <= 64): per slab r,
+// Z_r (L x K, l fastest) = Y_r (L x I) A^T, i.e. Z(l, k, r) = sum_i A(k, i)
+// Y(l, i, r) -- the expansions of the multi-TTM reconstruction, where I is a
+// core rank.  The MMA's M is l: a work item is 128 consecutive l of one slab
+// against an N-tile of 256 outputs k.  Y comes through a three-slot raw ring
+// (3D TMA box of 128 l x 64 i, zero-filled outside the view) and eight
+// converter warps split it into the MN-major SW128 FP16 hi/lo A operand (l
+// contiguous, as loaded).  B = A^T of the CTA's N-tile (K-major SW128 hi/lo
+// images, split by a prep kernel) stays resident.  Three products per
+// K step, as in the column kernel; double-buffered 2 x 256 accumulator
+// columns; four epilogue warps write Z coalesced along l.  Each CTA serves
+// one N-tile (blockIdx.x % NT) and walks the items (slab, l-tile)
+// blockIdx.x / NT, + gridDim.x / NT, ...; the NT CTAs of an item run side by
+// side, so Y is read from HBM about once.
+constexpr int RN = 256;                        // MMA N: outputs per N-tile
+constexpr int RM = 128;                        // MMA M: l per item
+constexpr uint32_t RA_BYTES = RM * SK * 2;     // 16 KB: one of A hi / lo
+constexpr uint32_t RB_BYTES = RN * SK * 2;     // 32 KB: one of B hi / lo
+constexpr uint32_t ROP_BYTES = 2 * RA_BYTES;   // A operand slot (hi | lo)
+constexpr uint32_t RRAW_BYTES = RM * SK * 4;   // 32 KB raw FP32 box
+constexpr int RNOP = 2, RNRAW = 3;
+constexpr uint32_t RSMEM_BYTES = 2 * RB_BYTES + RNOP * ROP_BYTES + RNRAW * RRAW_BYTES + 1024;
+constexpr uint32_t RKG = 2 * 1024;             // k-group stride of the MN-major A operand
+
+// Byte offset of (l, i) (l < 128, i < 64) in the MN-major SW128 A operand:
+// atoms of 64 l x 8 i (1 KB), [k group of 8 i][atom].
+__device__ __forceinline__ uint32_t rmn_off(int l, int i) {
+  return (uint32_t)(i >> 3) * RKG + (uint32_t)(l >> 6) * 1024u + (uint32_t)(i & 7) * 128u +
+         ((uint32_t)(((l & 63) >> 3) ^ (i & 7)) << 4) + (uint32_t)(l & 7) * 2u;
+}
+
+// Instruction descriptor: kind::f16, FP16 A and B, FP32 D, A MN-major, B K-major.
+__device__ __forceinline__ uint32_t instr_desc_mk(int M, int N) {
+  return (1u << 4) | (1u << 15) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// B images of A^T: N-tile t holds rows k = 256 t + row (row < 256) and
+// columns i < 64 of A scaled by s_a, K-major SW128, [B_h | B_l] (64 KB per
+// tile, zero outside K x I); *sa_out = s_a.  One CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_ttm_tc_prep_rows(const double* __restrict__ A, int K,
+                                                           int64_t I, int64_t lda, int arow,
+                                                           int ntile, uint8_t* __restrict__ out,
+                                                           float* __restrict__ sa_out) {
+  __shared__ double red[32];
+  __shared__ float s_sa;
+  double mx = 0.0;
+  for (int64_t e = threadIdx.x; e < (int64_t)K * I; e += blockDim.x) {
+    const int64_t k = e / I, i = e % I;
+    const double a = arow ? A[k * lda + i] : A[k + lda * i];
+    mx = fmax(mx, fabs(a));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = red[threadIdx.x];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) {
+      int ex = 0;
+      frexp(v, &ex);                       // v < 2^ex
+      int e2 = 14 - ex;
+      e2 = e2 > 100 ? 100 : (e2 < -100 ? -100 : e2);
+      s_sa = (v > 0.0) ? ldexpf(1.f, e2) : 1.f;
+      *sa_out = s_sa;
+    }
+  }
+  __syncthreads();
+  const double sa = s_sa;
+  const int64_t tot = (int64_t)ntile * RN * (SK / 2);   // element pairs (i, i + 1)
+  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int t = (int)(e / (RN * (SK / 2)));
+    const int rem = (int)(e % (RN * (SK / 2)));
+    const int row = rem / (SK / 2), kp = 2 * (rem % (SK / 2));
+    const int64_t k = (int64_t)t * RN + row;
+    float v2[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t i = kp + u;
+      double a = 0.0;
+      if (k < K && i < I) a = arow ? A[k * lda + i] : A[k + lda * i];
+      v2[u] = (float)(a * sa);
+    }
+    uint32_t h, l;
+    split_pack(v2[0], v2[1], h, l);
+    uint8_t* base = out + (size_t)t * 2 * RB_BYTES;
+    const uint32_t o = kmaj_off(row, kp);
+    *reinterpret_cast<uint32_t*>(base + o) = h;
+    *reinterpret_cast<uint32_t*>(base + RB_BYTES + o) = l;
+  }
+}
+
+struct TtmTcRowArgs {
+  int64_t L, I, Rt;
+  int K;                   // outputs per slab
+  int NT;                  // N-tiles of 256 outputs
+  int64_t ntl;             // l-tiles per slab, ceil(L / 128)
+  int64_t nitems;          // Rt * ntl
+  float sy;                // power of two
+  const uint8_t* bprep;    // NT x [B_h | B_l]
+  const float* sa;         // the power-of-two scale of A (device)
+  float* z;                // z[l + L (k + K r)]
+  unsigned* err;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_ttm_tc_row(TtmTcRowArgs g, const __grid_constant__ CUtensorMap ymap) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* bimg = smem;                                  // [B_h | B_l], resident
+  uint8_t* ops = smem + 2 * RB_BYTES;                    // RNOP A slots
+  uint8_t* raw = ops + RNOP * ROP_BYTES;                 // RNRAW raw slots
+  __shared__ uint64_t raw_full[RNRAW], raw_empty[RNRAW], op_full[RNOP], op_empty[RNOP];
+  __shared__ uint64_t bar_b, bar_accf[2], bar_acce[2], bar_done;
+  __shared__ uint32_t tmem_base_sh;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nt = (int)(blockIdx.x % g.NT);
+  const int64_t c0 = blockIdx.x / g.NT, cstep = gridDim.x / g.NT;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < RNRAW; ++s) {
+      mbar_init(smem_u32(&raw_full[s]), 1);
+      mbar_init(smem_u32(&raw_empty[s]), NCONV);
+    }
+    for (int s = 0; s < RNOP; ++s) {
+      mbar_init(smem_u32(&op_full[s]), NCONV);
+      mbar_init(smem_u32(&op_empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bar_accf[b]), 1);
+      mbar_init(smem_u32(&bar_acce[b]), 4);
+    }
+    mbar_init(smem_u32(&bar_b), 1);
+    mbar_init(smem_u32(&bar_done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+        smem_u32(&tmem_base_sh)), "n"(2 * RN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base_sh;
+  const int64_t my_items = (g.nitems > c0) ? (g.nitems - 1 - c0) / cstep + 1 : 0;
+
+  if (warp == LOAD_WARP) {
+    // ---------------- loader: B images once, then Y boxes -> raw slots (TMA)
+    if (lane == 0) {
+      mbar_arrive_expect_tx(smem_u32(&bar_b), 2 * RB_BYTES);   // bar_b counts this one arrival
+      bulk_g2s(smem_u32(bimg), g.bprep + (size_t)nt * 2 * RB_BYTES, 2 * RB_BYTES, smem_u32(&bar_b));
+      for (int64_t j = 0; j < my_items; ++j) {
+        const int r = (int)(j % RNRAW);
+        if (j >= RNRAW &&
+            !mbar_wait(smem_u32(&raw_empty[r]), (uint32_t)(((j / RNRAW) - 1) & 1), g.err))
+          break;
+        const int64_t it = c0 + j * cstep;
+        const int64_t slab = it / g.ntl, lt = it - slab * g.ntl;
+        mbar_arrive_expect_tx(smem_u32(&raw_full[r]), RRAW_BYTES);
+        tma_load_3d(smem_u32(raw + (size_t)r * RRAW_BYTES), &ymap, (int)(lt * RM), 0, (int)slab,
+                    smem_u32(&raw_full[r]));
+      }
+    }
+    __syncwarp();
+  } else if (warp <= NCONV) {
+    // ---------------- converters: raw [i][l] FP32 -> MN-major FP16 hi/lo A
+    const int ct = threadIdx.x - 32;   // 0..255
+    for (int64_t j = 0; j < my_items; ++j) {
+      const int r = (int)(j % RNRAW), o = (int)(j % RNOP);
+      if (!mbar_wait(smem_u32(&raw_full[r]), (uint32_t)((j / RNRAW) & 1), g.err)) break;
+      if (j >= RNOP &&
+          !mbar_wait(smem_u32(&op_empty[o]), (uint32_t)(((j / RNOP) - 1) & 1), g.err))
+        break;
+      uint8_t* st = ops + (size_t)o * ROP_BYTES;
+      const uint8_t* src = raw + (size_t)r * RRAW_BYTES;
+      float4 v[CV4];
+#pragma unroll
+      for (int e = 0; e < CV4; ++e) {
+        const int c = ct + NCONV * 32 * e;          // i = c / 32, l = 4 (c % 32)
+        v[e] = *reinterpret_cast<const float4*>(src + (size_t)c * 16);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&raw_empty[r]));   // raw slot read
+#pragma unroll
+      for (int e = 0; e < CV4; ++e) {
+        const int c = ct + NCONV * 32 * e;
+        const int i = c >> 5, l = 4 * (c & 31);
+        uint2 hp, lp;
+        split_pack(v[e].x * g.sy, v[e].y * g.sy, hp.x, lp.x);
+        split_pack(v[e].z * g.sy, v[e].w * g.sy, hp.y, lp.y);
+        const uint32_t off = rmn_off(l, i);
+        *reinterpret_cast<uint2*>(st + off) = hp;
+        *reinterpret_cast<uint2*>(st + RA_BYTES + off) = lp;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&op_full[o]));
+    }
+  } else if (warp == MMA_WARP) {
+    // ---------------- MMA issue (one thread)
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc_mk(RM, RN);
+      bool ok = mbar_wait(smem_u32(&bar_b), 0, g.err);
+      const uint64_t bh0 = smem_desc(smem_u32(bimg), 16, 1024);
+      const uint64_t bl0 = smem_desc(smem_u32(bimg + RB_BYTES), 16, 1024);
+      for (int64_t j = 0; j < my_items && ok; ++j) {
+        const int buf = (int)(j & 1), o = (int)(j % RNOP);
+        if (j >= 2) ok = mbar_wait(smem_u32(&bar_acce[buf]), (uint32_t)(((j / 2) - 1) & 1), g.err);
+        if (ok) ok = mbar_wait(smem_u32(&op_full[o]), (uint32_t)((j / RNOP) & 1), g.err);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t st = smem_u32(ops + (size_t)o * ROP_BYTES);
+        const uint32_t d = tmem + (uint32_t)buf * (uint32_t)RN;
+#pragma unroll
+        for (int kk = 0; kk < SK / 16; ++kk) {
+          // A: a K step of 16 i is two k groups (2 x RKG bytes); B: 32 bytes
+          // along its swizzled rows (+2 in the address field)
+          const uint64_t ah = smem_desc(st + (uint32_t)kk * 2u * RKG, 1024, RKG);
+          const uint64_t al = smem_desc(st + RA_BYTES + (uint32_t)kk * 2u * RKG, 1024, RKG);
+          const uint64_t bh = bh0 + 2u * kk, bl = bl0 + 2u * kk;
+          const uint32_t acc0 = kk > 0 ? 1u : 0u;
+          tc_mma(d, ah, bh, idesc, acc0);
+          tc_mma(d, ah, bl, idesc, 1u);
+          tc_mma(d, al, bh, idesc, 1u);
+        }
+        tc_commit(smem_u32(&op_empty[o]));
+        tc_commit(smem_u32(&bar_accf[buf]));
+      }
+      tc_commit(smem_u32(&bar_done));
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: tensor memory -> Z, coalesced along l
+    const int q = warp & 3;          // the lane quarter this warp may access
+    const float inv = (float)(1.0 / ((double)g.sy * (double)*g.sa));   // powers of two: exact
+    const int kbase = nt * RN;
+    for (int64_t j = 0; j < my_items; ++j) {
+      const int buf = (int)(j & 1);
+      if (!mbar_wait(smem_u32(&bar_accf[buf]), (uint32_t)((j / 2) & 1), g.err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int64_t it = c0 + j * cstep;
+      const int64_t slab = it / g.ntl, lt = it - slab * g.ntl;
+      const int64_t l = lt * RM + 32 * q + lane;
+      float* zl = g.z + l + g.L * g.K * slab;
+      for (int cb = 0; cb < RN && kbase + cb < g.K; cb += 32) {
+        uint32_t rr[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * (uint32_t)RN + (uint32_t)cb, rr);
+        if (l < g.L) {
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) {
+            const int k = kbase + cb + jj;
+            if (k < g.K) zl[g.L * (int64_t)k] = __uint_as_float(rr[jj]) * inv;
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_acce[buf]));
+    }
+  }
+  mbar_wait(smem_u32(&bar_done), 0, g.err);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(2 * RN));
+  }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -425,6 +695,64 @@ cudaError_t launch_ttm_tc(const float* y, int64_t L, int64_t I, int64_t Rt, cons
     return cudaErrorInvalidValue;
   const int grid = (int)(a.ntiles < num_sms ? a.ntiles : num_sms);
   k_ttm_tc_col<<<grid, NTHREADS, SMEM_BYTES, st>>>(a, ymap);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+int ttm_tc_row_supported(int64_t L, int64_t I, int64_t Rt, int64_t K) {
+  return L > 1 && (L % 4) == 0 && L < (1ll << 31) && I >= 1 && I <= SK && K >= 1 &&
+         K <= 4 * RN && Rt >= 1 && Rt < (1ll << 31) && L * I * Rt < (1ll << 40);
+}
+
+size_t ttm_tc_row_scratch_bytes(int64_t K) {
+  return (size_t)((K + RN - 1) / RN) * 2 * RB_BYTES + 256;
+}
+
+cudaError_t launch_ttm_tc_row(const float* y, int64_t L, int64_t I, int64_t Rt, const double* A,
+                              int64_t K, int64_t lda, int a_rowmajor, float sy, float* z,
+                              void* scratch, unsigned* err, int num_sms, cudaStream_t st) {
+  if (!ttm_tc_row_supported(L, I, Rt, K) || ((uintptr_t)y & 15) != 0) return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_ttm_tc_row, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)RSMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int NT = (int)((K + RN - 1) / RN);
+  uint8_t* bprep = (uint8_t*)scratch;
+  float* sa = (float*)(bprep + (size_t)NT * 2 * RB_BYTES);
+  k_ttm_tc_prep_rows<<<1, 1024, 0, st>>>(A, (int)K, I, lda, a_rowmajor, NT, bprep, sa);
+  TtmTcRowArgs a;
+  a.L = L;
+  a.I = I;
+  a.Rt = Rt;
+  a.K = (int)K;
+  a.NT = NT;
+  a.ntl = (L + RM - 1) / RM;
+  a.nitems = Rt * a.ntl;
+  a.sy = sy;
+  a.bprep = bprep;
+  a.sa = sa;
+  a.z = z;
+  a.err = err;
+  // Y as a 3D tensor: x = l (contiguous), y = i, z = slab; boxes of 128 l x 64 i x 1
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  alignas(64) CUtensorMap ymap;
+  const cuuint64_t gdim[3] = {(cuuint64_t)L, (cuuint64_t)I, (cuuint64_t)Rt};
+  const cuuint64_t gstride[2] = {(cuuint64_t)L * sizeof(float), (cuuint64_t)(L * I) * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)RM, (cuuint32_t)SK, 1};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  if (enc(&ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)y, gdim, gstride, box, estride,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  int64_t per = num_sms / NT;
+  if (per < 1) per = 1;
+  if (per > a.nitems) per = a.nitems;
+  const int grid = (int)(per * NT);
+  k_ttm_tc_row<<<grid, NTHREADS, RSMEM_BYTES, st>>>(a, ymap);
   count_launches(2);
   return cudaGetLastError();
 }

@@ -685,6 +685,50 @@ def test_ttm_mixed_tensor_cores_mode0(ctx, dims, K):
     assert np.all(np.abs(got - want) <= bound)
 
 
+TC_ROW_TTM_CASES = [((128, 54, 11), 1, 500), ((20, 40, 7), 1, 300), ((252, 13, 5), 1, 70),
+                    ((4, 64, 9), 1, 1000), ((132, 7, 3, 5), 2, 40), ((8, 3, 600), 1, 17)]
+
+
+@pytest.mark.parametrize("dims,n,K", TC_ROW_TTM_CASES)
+def test_ttm_mixed_tensor_cores_rowmode(ctx, dims, n, K):
+    """Row-mode TTM on tcgen05 (L = prod dims[:n] with L % 4 == 0, I <= 64:
+    the reconstruction's expansions), l as the MMA's M, one or more N-tiles
+    of 256 outputs, the same two-term FP16 split and three products as the
+    mode-0 kernel: every output within 2e-5 of sum_i |a_ki| |y_i| of the
+    oracle's TTM.  Ragged L and I, K above 256, both layouts of A."""
+    L = math.prod(dims[:n])
+    assert L % 4 == 0 and dims[n] <= 64
+    rng = np.random.default_rng(K + 7 * n)
+    x = rng.standard_normal(oracle.linear_size(dims))
+    t = dev(x, torch.float32)
+    xs = host(t)
+    A = rng.standard_normal((K, dims[n]))
+    want = oracle.ttm(xs, dims, n, A)
+    bound = 2e-5 * oracle.ttm(np.abs(xs), dims, n, np.abs(A))
+    got = host(ctx.ttm(t, dims, n, dev(A), "mixed"))
+    assert np.all(np.abs(got - want) <= bound), np.max(np.abs(got - want) / bound)
+    Ac = dev(np.asfortranarray(A)).t().contiguous().t()
+    got = host(ctx.ttm(t, dims, n, Ac, "mixed"))
+    assert np.all(np.abs(got - want) <= bound)
+
+
+def test_reconstruct_mixed_tensor_cores(ctx):
+    """Multi-TTM reconstruction in MIXED precision (tensor-core TTMs for the
+    row-mode expansions) against the oracle: within 1e-4 of the same
+    multi-TTM applied to absolute values (four chained TTMs, each within
+    2e-5 of its absolute sums)."""
+    dims = (64, 48, 40, 6)
+    x = synth.tucker_torch(dims, (20, 16, 12, 4), decay=0.05, eta=1e-6, seed=4)
+    res32 = ctx.sthosvd(x, dims, eps=1e-3, prec="mixed")
+    b, e = (0, 0, 0, 0), (64, 48, 40, 5)
+    got = host(res32.reconstruct(b, e, prec="mixed"))
+    want32, _ = oracle.reconstruct(host(res32.core), res32.ranks,
+                                   [host(f) for f in res32.factors], b, e)
+    abs32, _ = oracle.reconstruct(np.abs(host(res32.core)), res32.ranks,
+                                  [np.abs(host(f)) for f in res32.factors], b, e)
+    assert np.all(np.abs(got - want32) <= 1e-4 * abs32), np.max(np.abs(got - want32) / abs32)
+
+
 # --------------------------------------------------------- whole ST-HOSVD
 
 def _check_against_oracle(x, dims, res, ref, err_tol=1e-12, eig_tol=1e-10, angle_tol=1e-8,
