@@ -360,7 +360,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // contiguous, as loaded).  B = A^T of the CTA's N-tile (K-major SW128 hi/lo
 // images, split by a prep kernel) stays resident.  Three products per
 // K step, as in the column kernel; double-buffered 2 x 256 accumulator
-// columns; four epilogue warps write Z coalesced along l.  Each CTA serves
+// columns; eight epilogue warps (two per tensor-memory lane quarter, 128
+// columns each, two 32-column loads per wait: with one warp per quarter and
+// one load per wait the tensor-memory reads bounded the kernel) write Z
+// coalesced along l.  Each CTA serves
 // one N-tile (blockIdx.x % NT) and walks the items (slab, l-tile)
 // blockIdx.x / NT, + gridDim.x / NT, ...; the NT CTAs of an item run side by
 // side, so Y is read from HBM about once.
@@ -371,6 +374,8 @@ constexpr uint32_t RB_BYTES = RN * SK * 2;     // 32 KB: one of B hi / lo
 constexpr uint32_t ROP_BYTES = 2 * RA_BYTES;   // A operand slot (hi | lo)
 constexpr uint32_t RRAW_BYTES = RM * SK * 4;   // 32 KB raw FP32 box
 constexpr int RNOP = 2, RNRAW = 3;
+constexpr int RNEPI = 8;                       // epilogue warps 10..17, two per lane quarter
+constexpr int RNTHREADS = (MMA_WARP + 1 + RNEPI) * 32;
 constexpr uint32_t RSMEM_BYTES = 2 * RB_BYTES + RNOP * ROP_BYTES + RNRAW * RRAW_BYTES + 1024;
 constexpr uint32_t RKG = 2 * 1024;             // k-group stride of the MN-major A operand
 
@@ -454,7 +459,7 @@ struct TtmTcRowArgs {
   unsigned* err;
 };
 
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(RNTHREADS, 1)
     k_ttm_tc_row(TtmTcRowArgs g, const __grid_constant__ CUtensorMap ymap) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -479,7 +484,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&bar_accf[b]), 1);
-      mbar_init(smem_u32(&bar_acce[b]), 4);
+      mbar_init(smem_u32(&bar_acce[b]), RNEPI);
     }
     mbar_init(smem_u32(&bar_b), 1);
     mbar_init(smem_u32(&bar_done), 1);
@@ -583,9 +588,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncwarp();
   } else {
     // ---------------- epilogue: tensor memory -> Z, coalesced along l
-    const int q = warp & 3;          // the lane quarter this warp may access
+    const int q = warp & 3;                          // the lane quarter this warp may access
+    const int half = (warp - MMA_WARP - 1) >> 2;     // columns [128 half, 128 half + 128)
     const float inv = (float)(1.0 / ((double)g.sy * (double)*g.sa));   // powers of two: exact
-    const int kbase = nt * RN;
+    const int kbase = nt * RN + 128 * half;
     for (int64_t j = 0; j < my_items; ++j) {
       const int buf = (int)(j & 1);
       if (!mbar_wait(smem_u32(&bar_accf[buf]), (uint32_t)((j / 2) & 1), g.err)) break;
@@ -594,12 +600,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t slab = it / g.ntl, lt = it - slab * g.ntl;
       const int64_t l = lt * RM + 32 * q + lane;
       float* zl = g.z + l + g.L * g.K * slab;
-      for (int cb = 0; cb < RN && kbase + cb < g.K; cb += 32) {
-        uint32_t rr[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * (uint32_t)RN + (uint32_t)cb, rr);
+      const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * (uint32_t)RN +
+                             128u * (uint32_t)half;
+      for (int cb = 0; cb < 128 && kbase + cb < g.K; cb += 64) {
+        uint32_t rr[64];
+        tmem_ld32x2(tbase + (uint32_t)cb, rr);
         if (l < g.L) {
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) {
+          for (int jj = 0; jj < 64; ++jj) {
             const int k = kbase + cb + jj;
             if (k < g.K) zl[g.L * (int64_t)k] = __uint_as_float(rr[jj]) * inv;
           }
@@ -752,7 +760,7 @@ cudaError_t launch_ttm_tc_row(const float* y, int64_t L, int64_t I, int64_t Rt, 
   if (per < 1) per = 1;
   if (per > a.nitems) per = a.nitems;
   const int grid = (int)(per * NT);
-  k_ttm_tc_row<<<grid, NTHREADS, RSMEM_BYTES, st>>>(a, ymap);
+  k_ttm_tc_row<<<grid, RNTHREADS, RSMEM_BYTES, st>>>(a, ymap);
   count_launches(2);
   return cudaGetLastError();
 }
