@@ -530,11 +530,11 @@ FP64_PEAK_TFLOPS = 1.19   # measured FP64 FMA throughput on this part (in-regist
 # a launch of the same kernel streams its input once, so its traffic scales
 # with I x K.  Only kernels whose source has not changed since the capture.
 CAPTURED_TRAFFIC = {
-    # k_gram_f32<LD_COL16>, mode-0 Gram of 500x500x40x11x2 FP32
-    ("gram", "simt-fp32", "col"): dict(bytes=1700.2e6, elems=500 * 440000,
-                                        src="profiles/k_gram_f32_col_prof_500x500x40x11x2.md"),
-    # k_ttm_tc_col, mode-0 TTM of 500x500x40x11x2 FP32 to 54 rows
-    ("ttm", "tcgen05", "col"): dict(bytes=964.7e6, elems=500 * 440000,
+    # k_gram_tcx (column mode), mode-0 Gram of 500x500x40x11x2 FP32
+    ("gram", "tcgen05-x3", "col"): dict(bytes=1266.0e6, elems=500 * 440000,
+                                         src="profiles/k_gram_tcx_col_prof_500x500x40x11x2.md"),
+    # k_ttm_tc_col (transposed output), mode-0 TTM of 500x500x40x11x2 FP32 to 54 rows
+    ("ttm", "tcgen05", "col"): dict(bytes=966.8e6, elems=500 * 440000,
                                     src="profiles/k_ttm_tc_col_prof_500x500x40x11x2.md"),
 }
 
@@ -546,6 +546,9 @@ def step_rooflines(res, w, pk):
     written; Jacobi ~6 I^3 FP64 flops per sweep)."""
     ms, ranks = res.ms, res.ranks
     cur = list(w["dims"])
+    # the natural mode order keeps the working tensor rotated: every mode's
+    # Gram and TTM run on a column-mode view
+    rotated = list(res.mode_order) == list(range(len(cur)))
     in_esz = 4 if w["dtype"] == "f32" else 8
     wk_esz = 8 if res.core_dtype == 1 else 4
     out = []
@@ -564,7 +567,7 @@ def step_rooflines(res, w, pk):
             ("eig", ms["eig"][n], eig_flops, 0, eig_k)]:
             t = max(t_ms, 1e-6) / 1e3
             traffic, tsrc = None, None
-            cap = CAPTURED_TRAFFIC.get((kind, kern, "col" if L == 1 else "row"))
+            cap = CAPTURED_TRAFFIC.get((kind, kern, "col" if (L == 1 or rotated) else "row"))
             if cap is not None and I >= 64:
                 traffic = cap["bytes"] * (I * K) / cap["elems"]
                 tsrc = "ncu capture scaled by I*K: " + cap["src"]
