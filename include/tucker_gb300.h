@@ -64,12 +64,24 @@ typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
  *   FP32   : FP32 products, round-to-nearest FP32 sums over short chunks
  *            combined exactly (TwoSum) and in FP64; working tensor and core
  *            in the input dtype.
- *   MIXED  : FP32 Gram as above; TTMs on the tensor cores (tcgen05) with a
- *            two-term FP16 split of both operands where the shape allows.
- *            FP32 input only.  The rank cut at small eps is decided by a
- *            tail sum that is ~1e-9 of the trace; the Gram needs unbiased
- *            rounding for that, while TTM rounding errors act as
- *            perturbations of the data and do not bias the next cut.
+ *   MIXED  : Grams of views with 128 <= I_n <= 2048 on the tensor cores
+ *            with exact integer digit products: each value is split under a
+ *            per-row power-of-two scale into three 7-bit digits (exact in
+ *            FP16), all nine digit products accumulate exactly in FP32 over
+ *            windows of 1024 columns, and the windows are summed in exact
+ *            FP32 pairs; the only error is the last digit's rounding, 2^-20
+ *            of the row maximum, unbiased (its squared mean is removed from
+ *            the diagonal).  Other Grams as FP32.  TTMs on the tensor cores
+ *            (tcgen05) with a two-term FP16 split of both operands where the
+ *            shape allows (column-mode views with K <= 128; row-mode views
+ *            with L % 4 == 0 and I_n <= 64, the reconstruction's expansions).
+ *            In the natural mode order the working tensor is kept rotated
+ *            (every TTM writes its new mode last), so every mode's Gram and
+ *            TTM see a column-mode view.  FP32 input only.  The rank cut at
+ *            small eps is decided by a tail sum that is ~1e-9 of the trace;
+ *            the Gram needs unbiased rounding for that, while TTM rounding
+ *            errors act as perturbations of the data and do not bias the
+ *            next cut.
  *   TENSOR : MIXED plus the Gram of the column-major mode-0 view on tcgen05
  *            (two-term FP16 split, all four products).  The tensor-core FP32
  *            accumulator truncates toward zero, a relative bias of ~1e-7
