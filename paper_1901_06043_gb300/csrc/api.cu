@@ -506,8 +506,12 @@ tucker_status do_ttm(tucker_ctx* c, const void* y, tucker_dtype ydt, const SlabV
     return TUCKER_OK;
   }
   // row-mode views with a short contraction (I <= 64: the reconstruction's
-  // expansions) on the tensor cores, l as the MMA's M
-  const bool tc_row = !zt && (prec == TUCKER_PREC_MIXED || prec == TUCKER_PREC_TENSOR) &&
+  // expansions) on the tensor cores, l as the MMA's M.  Its split scale needs
+  // max|y|: a caller that runs without host syncs (check = false, the batched
+  // path on side streams) and does not know it keeps the SIMT TTM rather than
+  // pay a synchronizing norm pass.
+  const bool tc_row = !zt && (check || ymax >= 0.0) &&
+                      (prec == TUCKER_PREC_MIXED || prec == TUCKER_PREC_TENSOR) &&
                       ydt == TUCKER_F32 && zdt == TUCKER_F32 && (((uintptr_t)y) & 15) == 0 &&
                       ttm_tc_row_supported(v.L, v.I, v.Rt, K);
   if (tc_row) {
