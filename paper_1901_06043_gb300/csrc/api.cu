@@ -479,8 +479,9 @@ tucker_status do_ttm(tucker_ctx* c, const void* y, tucker_dtype ydt, const SlabV
                      const double* A, int64_t K, int64_t lda, int arow, tucker_prec prec, void* z,
                      tucker_dtype zdt, int* kernel_used, double ymax = -1.0, bool check = true,
                      bool zt = false) {
+  // (the split scale needs max|y|: without it and without host syncs, SIMT)
   const bool tc = (prec == TUCKER_PREC_MIXED || prec == TUCKER_PREC_TENSOR) && ydt == TUCKER_F32 &&
-                  zdt == TUCKER_F32 && (((uintptr_t)y) & 15) == 0 &&
+                  zdt == TUCKER_F32 && (((uintptr_t)y) & 15) == 0 && (check || ymax >= 0.0) &&
                   (!zt || (((uintptr_t)z) & 15) == 0) && ttm_tc_supported(v.L, v.I, v.Rt, K);
   if (kernel_used) *kernel_used = tc ? 2 : (prec == TUCKER_PREC_FP64 ? 0 : 1);
   if (tc) {
@@ -932,6 +933,12 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
   return TUCKER_OK;
 }
 
+// The batched ST-HOSVD runs modes 0, 1, ... in order on every tensor and keeps
+// each working tensor rotated (every TTM writes its new mode last), so mode s
+// is the fastest index when its turn comes: the column-mode view of slab_view's
+// (L, I, Rt).
+static SlabView rot_view(const SlabView& v) { return SlabView{1, v.I, v.L * v.Rt, 1}; }
+
 tucker_status tucker_sthosvd_batched(tucker_ctx* c, int count, const void* const* xs,
                                      tucker_dtype dt, const int* ndims,
                                      const int64_t* const* dimss, double eps, tucker_prec prec,
@@ -1067,7 +1074,7 @@ tucker_status tucker_sthosvd_batched(tucker_ctx* c, int count, const void* const
       P.team_off = q == 0 ? 0 : h[q - 1].team_off + h[q - 1].team_size;
       P.w = wbuf[q].as<double>();
       thr[q] = res[i]->threshold;
-      const SlabView v = slab_view(ndims[i], cur[i].data(), s);
+      const SlabView v = rot_view(slab_view(ndims[i], cur[i].data(), s));
       StreamSwap sw(c);
       sw.to(q);
       TK_TRY(do_gram(c, y[i], ydt[i], v, gprec[i], P.A, &res[i]->gram_kernel[s],
@@ -1144,7 +1151,7 @@ tucker_status tucker_sthosvd_batched(tucker_ctx* c, int count, const void* const
         DevBuf S2, V2, U2;
         TK_TRY(dev_alloc(c, S2, sizeof(double) * (size_t)n * n));
         TK_TRY(dev_alloc(c, V2, sizeof(double) * (size_t)n * n));
-        const SlabView v = slab_view(ndims[i], cur[i].data(), s);
+        const SlabView v = rot_view(slab_view(ndims[i], cur[i].data(), s));
         TK_TRY(do_gram(c, y[i], ydt[i], v, gprec[i], S2.as<double>(), nullptr, -1.0, false));
         int sweeps = 0;
         tucker_status es = do_eig(c, S2.as<double>(), n, h[q].w, V2.as<double>(), &sweeps);
@@ -1178,11 +1185,11 @@ tucker_status tucker_sthosvd_batched(tucker_ctx* c, int count, const void* const
     TK_TRY(fork_side(c));
     for (int q = 0; q < m; ++q) {
       const int i = act[q];
-      const SlabView v = slab_view(ndims[i], cur[i].data(), s);
+      const SlabView v = rot_view(slab_view(ndims[i], cur[i].data(), s));
       StreamSwap sw(c);
       sw.to(q);
       TK_TRY(do_ttm(c, y[i], ydt[i], v, res[i]->factors[s], res[i]->ranks[s], h[q].n, 1, prec,
-                    znew[q].p, wdt, &res[i]->ttm_kernel[s], s == 0 ? xmax[i] : -1.0, false));
+                    znew[q].p, wdt, &res[i]->ttm_kernel[s], s == 0 ? xmax[i] : -1.0, false, true));
     }
     TK_TRY(join_side(c));
     for (int q = 0; q < m; ++q) {
