@@ -48,10 +48,12 @@ the design notes of the repository):
 * Section 3.3 says "for n > 1" the partial core is used; Algorithm 1 uses
   the partial core for every n >= 1, which is what is implemented.
 
-Parity unpinned: ``order_memory_comparator`` (the "R_i/K_i ascending" rule
-of Section 7) -- the paper gives no worked example for it, and its memory
-figures in the partial-reconstruction table come from the parallel code,
-not from a serial model.
+* Section 7's memory comparator is printed as "R_i/K_i < R_j/K_j"; taken
+  literally it orders the most-growing TTMs first, which the exhaustive
+  search (the section's definition of the optimal order) never does.  The
+  oracle reads it as K_i/R_i < K_j/R_j (most-shrinking first), pinned against
+  that search.  The memory figures of the partial-reconstruction table come
+  from the parallel code and are not reproduced by a serial model.
 """
 from __future__ import annotations
 
@@ -362,11 +364,21 @@ def order_flop_comparator(core_dims, out_dims):
 
 
 def order_memory_comparator(core_dims, out_dims):
-    """Section 7's memory rule: mode i precedes mode j if R_i/K_i < R_j/K_j.
-    Parity unpinned (no worked example in the paper)."""
+    """Section 7's memory rule, read with R and K in the order its exchange
+    argument needs: a TTM in mode i scales the tensor by K_i / R_i, so the
+    temporary memory is smallest when the most-shrinking modes go first --
+    mode i precedes mode j if K_i/R_i < K_j/R_j.  (As printed the inequality
+    reads R_i/K_i < R_j/K_j, which puts the most-growing modes first; the
+    exhaustive search the same section calls optimal never picks that order.)
+    Compared division-free: K_i R_j < K_j R_i."""
     R = [int(r) for r in core_dims]
     K = [int(k) for k in out_dims]
-    return tuple(sorted(range(len(R)), key=lambda i: (R[i] / K[i], i)))
+
+    def cmp(i, j):
+        a, b = K[i] * R[j], K[j] * R[i]
+        return -1 if a < b else (1 if a > b else (i > j) - (i < j))
+
+    return tuple(sorted(range(len(R)), key=functools.cmp_to_key(cmp)))
 
 
 # ------------------------------------------------------------ error metrics

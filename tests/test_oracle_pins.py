@@ -349,3 +349,44 @@ def test_43120_is_a_memory_minimiser_high_compression():
     _, cost = oracle.best_order(core, out, "memory")
     s = oracle.ttm_chain_sizes(core, out, (4, 3, 1, 2, 0))
     assert max(s[i] + s[i + 1] for i in range(5)) == cost
+
+
+def test_memory_comparator_matches_the_exhaustive_search():
+    """Section 7: the optimal order is the one the exhaustive search over all
+    N! permutations finds; the pairwise memory rule must reproduce it.  For
+    every serial measure of temporary memory -- the largest input + output of
+    one TTM, the largest intermediate, the sum of the intermediates -- the
+    oracle's comparator (most-shrinking mode first, K_i/R_i ascending) attains
+    the minimum on random cores and outputs, while the inequality as printed
+    (R_i/K_i ascending, most-growing first) does not."""
+    import random
+
+    def pair(core, out, order):
+        s = oracle.ttm_chain_sizes(core, out, order)
+        return max(s[i] + s[i + 1] for i in range(len(order)))
+
+    def peak(core, out, order):
+        return max(oracle.ttm_chain_sizes(core, out, order))
+
+    def total(core, out, order):
+        return sum(oracle.ttm_chain_sizes(core, out, order)[1:])
+
+    rng = random.Random(7)
+    printed_optimal = 0
+    for _ in range(200):
+        N = rng.randint(2, 5)
+        core = [rng.randint(2, 40) for _ in range(N)]
+        out = [rng.randint(1, 80) for _ in range(N)]
+        order = oracle.order_memory_comparator(core, out)
+        assert sorted(order) == list(range(N))
+        printed = tuple(sorted(range(N), key=lambda i: (core[i] / out[i], i)))
+        for f in (pair, peak, total):
+            best = min(f(core, out, p) for p in itertools.permutations(range(N)))
+            assert f(core, out, order) == best, (core, out, f.__name__)
+        printed_optimal += pair(core, out, printed) == min(
+            pair(core, out, p) for p in itertools.permutations(range(N)))
+    assert printed_optimal == 0
+    # the library's memory objective (exhaustive) agrees with the comparator's cost
+    core, out = (30, 38, 35, 6, 11), (500, 500, 500, 1, 1)
+    _, cost = oracle.best_order(core, out, "memory")
+    assert pair(core, out, oracle.order_memory_comparator(core, out)) == cost
