@@ -449,5 +449,5 @@ def gram_noalloc(y, dims, mode, S, prec="fp64", stream=None):
     return S
 
 
-# MIXED precision (tensor-core Gram of the column-major mode-0 view) is built.
+# MIXED precision (exact-digit tensor-core Grams, tensor-core TTMs) is built.
 MIXED_AVAILABLE = True
