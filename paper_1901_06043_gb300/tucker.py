@@ -430,6 +430,26 @@ def kernel_launches():
     return int(lib().tucker_kernel_launches())
 
 
+def _check_gram_out(y, dims, mode, S):
+    """Shape, dtype and device checks of a Gram call whose output S the
+    caller supplies: the kernels write I_n x I_n FP64 values through S's
+    pointer and read prod(dims) elements of y, so a mismatch would reach
+    memory outside both tensors.  Raises ValueError before anything runs."""
+    import torch
+    if not 0 <= int(mode) < len(dims):
+        raise ValueError(f"mode {mode} out of range for {len(dims)} modes")
+    if y.numel() != int(np.prod([int(d) for d in dims])):
+        raise ValueError(f"y holds {y.numel()} elements, dims {tuple(dims)} need "
+                         f"{int(np.prod([int(d) for d in dims]))}")
+    I = int(dims[mode])
+    if S.dtype != torch.float64:
+        raise ValueError(f"S must be float64, got {S.dtype}")
+    if tuple(S.shape) != (I, I):
+        raise ValueError(f"S must have shape ({I}, {I}), got {tuple(S.shape)}")
+    if S.device != y.device:
+        raise ValueError(f"S is on {S.device}, y on {y.device}")
+
+
 def gram_noalloc(y, dims, mode, S, prec="fp64", stream=None):
     """tucker_gram_noalloc: the Gram of one mode into the caller's FP64
     (I, I) device tensor S, with the library's fixed device scratch instead
@@ -437,6 +457,7 @@ def gram_noalloc(y, dims, mode, S, prec="fp64", stream=None):
     For callers that cannot allocate device memory; calls that overlap on
     the GPU share the scratch and race."""
     import torch
+    _check_gram_out(y, dims, mode, S)
     _check_dev(y, "y")
     _check_dev(S, "S")
     if stream is None:
