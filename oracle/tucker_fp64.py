@@ -26,6 +26,15 @@ Tensor Decomposition" (arXiv 1901.06043):
                                  and Corollary 1
 * multi-TTM reconstruction
   and mode ordering           -- Section 7 ("Optimized reconstruction")
+* HOSVD                       -- Section 3.2 (Eq. Un on the Gram of X in every
+                                 mode, Theorem 1's error bound)
+* ST-HOSVD mode order for
+  given ranks                 -- the flop counts of the cost analysis of
+                                 Section 6 (Gram, eigensolve, TTM per mode),
+                                 minimised over all orders as Section 7 does
+                                 for reconstruction
+* pre- and post-processing    -- Section 3.5 (hyperslice statistics,
+                                 standardization, max rescaling, inverses)
 
 Storage convention: a tensor of dims (J_0, ..., J_{N-1}) is a flat 1-D
 float64 array in natural-descending order (first index fastest), exactly
@@ -70,7 +79,9 @@ __all__ = [
     "sthosvd", "multi_ttm", "reconstruct",
     "ttm_chain_sizes", "ttm_chain_flops", "best_order",
     "order_flop_comparator", "order_memory_comparator",
-    "relative_errors",
+    "relative_errors", "sthosvd_chunked", "hosvd",
+    "sthosvd_flops", "best_sthosvd_order", "sthosvd_order_ratio_rule",
+    "slice_stats", "standardize_params", "max_rescale_params", "slice_transform",
 ]
 
 
@@ -255,30 +266,130 @@ def sthosvd(x, dims, eps=None, ranks=None, mode_order=None):
     x = np.asarray(x, dtype=np.float64).reshape(-1)
     nrm2 = norm_sq(x)
     thr = (float(eps) ** 2) * nrm2 / N if eps is not None else None
-    y, cur = x, list(dims)
-    factors, eigvals = [None] * N, [None] * N
-    out_ranks, discarded = [0] * N, [0.0] * N
+    state = _new_state(x, dims)
     for n in order:
-        S = gram(y, cur, n)
-        lam, V = eig_desc(S)
-        if ranks is not None:
-            R = int(ranks[n])
-            if not 1 <= R <= cur[n]:
-                raise ValueError("rank out of range")
-            _, tail = rank_cut(lam, 0.0)
-        else:
-            R, tail = rank_cut(lam, thr)
-        U = V[:, :R].copy()
-        y = ttm(y, cur, n, U.T)
-        cur[n] = R
-        factors[n], eigvals[n] = U, lam
-        out_ranks[n], discarded[n] = R, float(tail[R])
+        S = gram(state["y"], state["cur"], n)
+        _truncate_mode(state, n, S, thr, ranks)
+    return _finish(state, nrm2, thr, order)
+
+
+def _new_state(y, dims):
+    N = len(dims)
+    return {"y": y, "cur": list(dims), "factors": [None] * N, "eigvals": [None] * N,
+            "ranks": [0] * N, "discarded": [0.0] * N}
+
+
+def _choose_factor(S, cur_n, thr, rank):
+    """One mode of Algorithm 1 after the Gram: eigenpairs in descending
+    order, R_n by Eq. Un (or the given rank), U_n = the leading R_n
+    eigenvectors.  Returns (U, eigenvalues, R, discarded sum)."""
+    lam, V = eig_desc(S)
+    if rank is not None:
+        R = int(rank)
+        if not 1 <= R <= cur_n:
+            raise ValueError("rank out of range")
+        _, tail = rank_cut(lam, 0.0)
+    else:
+        R, tail = rank_cut(lam, thr)
+    return V[:, :R].copy(), lam, R, float(tail[R])
+
+
+def _truncate_mode(state, n, S, thr, ranks):
+    """Algorithm 1's steps after the Gram of mode n: eig, cut, Y <- Y x_n U_n^T."""
+    U, lam, R, disc = _choose_factor(S, state["cur"][n], thr,
+                                     None if ranks is None else ranks[n])
+    state["y"] = ttm(state["y"], state["cur"], n, U.T)
+    state["cur"][n] = R
+    state["factors"][n], state["eigvals"][n] = U, lam
+    state["ranks"][n], state["discarded"][n] = R, disc
+
+
+def _finish(state, nrm2, thr, order):
     return {
-        "core": y, "core_dims": tuple(cur), "factors": factors,
-        "eigvals": eigvals, "ranks": tuple(out_ranks),
-        "discarded": discarded, "norm_sq": nrm2, "threshold": thr,
+        "core": state["y"], "core_dims": tuple(state["cur"]), "factors": state["factors"],
+        "eigvals": state["eigvals"], "ranks": tuple(state["ranks"]),
+        "discarded": state["discarded"], "norm_sq": nrm2, "threshold": thr,
         "mode_order": tuple(order),
     }
+
+
+def sthosvd_chunked(chunk, nchunks, dims, eps=None, ranks=None):
+    """ST-HOSVD (Algorithm 1, mode order 0..N-1) of a tensor supplied in
+    pieces, for inputs too large to hold in FP64 at once.  ``chunk(c)``
+    returns the flat natural-descending sub-tensor whose last-mode indices
+    are [J_{N-1} c / nchunks, J_{N-1} (c + 1) / nchunks), c = 0..nchunks-1
+    (N >= 2).  Each piece is a contiguous run of the block columns of every
+    unfolding of modes n < N-1, so:
+      ||X||^2 = sum over pieces of their sums of squares (Section 2.2.2);
+      the mode-0 Gram = sum over pieces of their mode-0 Grams (Algorithm 2
+        sums over block columns; the column-major mode-0 unfolding of a
+        piece is a contiguous range of columns of X's);
+      the mode-0 TTM acts on each column independently (Algorithm 3), so
+        the partial core is the pieces' TTMs laid end to end.
+    Modes 1..N-1 then run on the partial core exactly as in :func:`sthosvd`.
+    Same result dict as :func:`sthosvd`."""
+    dims = tuple(int(d) for d in dims)
+    N = len(dims)
+    if N < 2:
+        raise ValueError("sthosvd_chunked needs N >= 2")
+    if (eps is None) == (ranks is None):
+        raise ValueError("give exactly one of eps or ranks")
+    last = dims[-1]
+    bounds = [(last * c // nchunks, last * (c + 1) // nchunks) for c in range(nchunks)]
+    nrm2, S0 = 0.0, np.zeros((dims[0], dims[0]), dtype=np.float64)
+    for c, (a, b) in enumerate(bounds):
+        if b <= a:
+            continue
+        piece = np.asarray(chunk(c), dtype=np.float64).reshape(-1)
+        pdims = dims[:-1] + (b - a,)
+        nrm2 += norm_sq(piece)
+        S0 += gram(piece, pdims, 0)
+    thr = (float(eps) ** 2) * nrm2 / N if eps is not None else None
+    U, lam, R, disc = _choose_factor(S0, dims[0], thr, None if ranks is None else ranks[0])
+    parts = []
+    for c, (a, b) in enumerate(bounds):
+        if b <= a:
+            continue
+        piece = np.asarray(chunk(c), dtype=np.float64).reshape(-1)
+        parts.append(ttm(piece, dims[:-1] + (b - a,), 0, U.T))
+    state = _new_state(np.concatenate(parts), dims)
+    state["cur"][0] = R
+    state["factors"][0], state["eigvals"][0] = U, lam
+    state["ranks"][0], state["discarded"][0] = R, disc
+    for n in range(1, N):
+        S = gram(state["y"], state["cur"], n)
+        _truncate_mode(state, n, S, thr, ranks)
+    return _finish(state, nrm2, thr, list(range(N)))
+
+
+# ------------------------------------------------------------ HOSVD (3.2)
+
+def hosvd(x, dims, eps=None, ranks=None):
+    """HOSVD (Section 3.2): for every mode n the eigendecomposition of the
+    Gram of X's own mode-n unfolding (Eq. Xeigprob), R_n by Eq. Un with the
+    same threshold eps^2 ||X||^2 / N (or the given ranks), U_n the leading
+    R_n eigenvectors; then the core G = X x_0 U_0^T ... x_{N-1} U_{N-1}^T.
+    Theorem 1 bounds the error: ||X - Xhat||^2 <= sum_n discarded_n.
+    Same result dict as :func:`sthosvd` (mode_order records 0..N-1)."""
+    dims = tuple(int(d) for d in dims)
+    N = len(dims)
+    if (eps is None) == (ranks is None):
+        raise ValueError("give exactly one of eps or ranks")
+    x = np.asarray(x, dtype=np.float64).reshape(-1)
+    nrm2 = norm_sq(x)
+    thr = (float(eps) ** 2) * nrm2 / N if eps is not None else None
+    state = _new_state(x, dims)
+    for n in range(N):
+        U, lam, R, disc = _choose_factor(gram(x, dims, n), dims[n], thr,
+                                         None if ranks is None else ranks[n])
+        state["factors"][n], state["eigvals"][n] = U, lam
+        state["ranks"][n], state["discarded"][n] = R, disc
+    y, cur = x, list(dims)
+    for n in range(N):
+        y = ttm(y, cur, n, state["factors"][n].T)
+        cur[n] = state["ranks"][n]
+    state["y"], state["cur"] = y, cur
+    return _finish(state, nrm2, thr, list(range(N)))
 
 
 # --------------------------------------------------- reconstruction (Sec. 7)
@@ -379,6 +490,112 @@ def order_memory_comparator(core_dims, out_dims):
         return -1 if a < b else (1 if a > b else (i > j) - (i < j))
 
     return tuple(sorted(range(len(R)), key=functools.cmp_to_key(cmp)))
+
+
+# ------------------------------------------- ST-HOSVD mode order (Sec. 6, 7)
+
+def sthosvd_flops(dims, ranks, order):
+    """Flops of ST-HOSVD in the given mode order with the given ranks, from
+    the cost analysis of Section 6: the mode-n Gram of the current tensor
+    (L, I_n, Rt) performs L I_n^2 Rt flops (symmetry exploited), the
+    eigensolve (10/3) I_n^3, the TTM 2 L R_n I_n Rt; L and Rt are products
+    of the ranks of the modes already processed and the sizes of the rest."""
+    cur = [int(d) for d in dims]
+    total = 0.0
+    for n in order:
+        numel = float(linear_size(cur))           # L I_n Rt
+        I, R = int(dims[n]), int(ranks[n])
+        total += numel * I + (10.0 / 3.0) * I ** 3 + 2.0 * numel * R
+        cur[n] = R
+    return total
+
+
+def best_sthosvd_order(dims, ranks):
+    """The flop-minimal ST-HOSVD mode order for given ranks, by exhaustive
+    search over all N! orders of :func:`sthosvd_flops` (the way Section 7
+    picks reconstruction orders); ties to the lexicographically first.
+    Returns (order, flops)."""
+    best, best_cost = None, None
+    for perm in itertools.permutations(range(len(dims))):
+        cost = sthosvd_flops(dims, ranks, perm)
+        if best_cost is None or cost < best_cost:
+            best, best_cost = perm, cost
+    return tuple(best), best_cost
+
+
+def sthosvd_order_ratio_rule(dims, ranks):
+    """The same order from a pairwise exchange argument.  Step n costs
+    c_n = I_n + 2 R_n per entry of the current tensor (plus the eigensolve,
+    which no order changes) and multiplies its size by a_n = R_n / I_n.  For
+    adjacent modes i, j after a prefix of size P, i first costs
+    P (c_i + a_i c_j) and j first P (c_j + a_j c_i): i goes first iff
+    c_i (1 - a_j) < c_j (1 - a_i), i.e. by c_n / (1 - a_n) ascending, and
+    modes that do not shrink (R_n = I_n) go last.  Compared without
+    division: c_i (I_j - R_j) I_i < c_j (I_i - R_i) I_j."""
+    I = [int(d) for d in dims]
+    R = [int(r) for r in ranks]
+    c = [I[n] + 2 * R[n] for n in range(len(I))]
+
+    def cmp(i, j):
+        a = c[i] * (I[j] - R[j]) * I[i]
+        b = c[j] * (I[i] - R[i]) * I[j]
+        return -1 if a < b else (1 if a > b else (i > j) - (i < j))
+
+    return tuple(sorted(range(len(I)), key=functools.cmp_to_key(cmp)))
+
+
+# ------------------------------------------ pre- and post-processing (3.5)
+
+STAT_NAMES = ("mean", "std", "max", "min", "norm1", "norm2")
+
+
+def slice_stats(x, dims, n: int) -> np.ndarray:
+    """Statistics of every mode-n hyperslice X(:, ..., i, ..., :) (Section
+    3.5): an (I_n, 6) array of mean, standard deviation, maximum, minimum,
+    1-norm and 2-norm of its J^*/I_n entries.  The standard deviation is the
+    population one, sqrt(sum (x - mean)^2 / count) (the paper does not say
+    which; this one makes a standardized slice have variance exactly 1).
+    The hyperslice is row i of the explicit mode-n unfolding."""
+    X = slab_view(np.asarray(x, dtype=np.float64), dims, n)   # (Rt, I, L)
+    I = int(dims[n])
+    out = np.zeros((I, 6), dtype=np.float64)
+    for i in range(I):
+        v = X[:, i, :].reshape(-1)
+        mean = v.sum() / v.size
+        out[i] = (mean, math.sqrt(((v - mean) ** 2).sum() / v.size), v.max(), v.min(),
+                  np.abs(v).sum(), math.sqrt((v * v).sum()))
+    return out
+
+
+def standardize_params(stats):
+    """Standardization (Section 3.5 (a)): shift by the mean, scale by the
+    standard deviation, i.e. y = (x - mean_i) / std_i; returned as
+    (shift, scale) with y = (x - shift_i) * scale_i.  A constant slice
+    (std 0) keeps scale 1."""
+    st = np.asarray(stats, dtype=np.float64)
+    shift = st[:, 0].copy()
+    scale = np.where(st[:, 1] > 0, 1.0 / np.where(st[:, 1] > 0, st[:, 1], 1.0), 1.0)
+    return shift, scale
+
+
+def max_rescale_params(stats):
+    """Max rescaling (Section 3.5 (b)): divide by the largest absolute value
+    of the slice, so it ranges within [-1, 1]; (shift, scale) = (0, 1 /
+    max |x|).  An all-zero slice keeps scale 1."""
+    st = np.asarray(stats, dtype=np.float64)
+    m = np.maximum(np.abs(st[:, 2]), np.abs(st[:, 3]))
+    return np.zeros(st.shape[0]), np.where(m > 0, 1.0 / np.where(m > 0, m, 1.0), 1.0)
+
+
+def slice_transform(x, dims, n: int, shift, scale, inverse=False) -> np.ndarray:
+    """Applies one linear function per mode-n hyperslice (Section 3.5):
+    y = (x - shift_i) * scale_i, or its inverse x = y / scale_i + shift_i
+    (post-processing after a reconstruction)."""
+    X = slab_view(np.asarray(x, dtype=np.float64), dims, n).copy()
+    sh = np.asarray(shift, dtype=np.float64)[None, :, None]
+    sc = np.asarray(scale, dtype=np.float64)[None, :, None]
+    Y = X / sc + sh if inverse else (X - sh) * sc
+    return Y.reshape(-1)
 
 
 # ------------------------------------------------------------ error metrics
