@@ -364,8 +364,8 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk,
         "per_mode_ms": {k: v for k, v in ms_detail.items()},
-        "steps_roofline": [{k: r[k] for k in ("kernel", "ms", "bound", "achieved", "unit", "frac")}
-                           for r in step_rows] +
+        "steps_roofline": [{k: r[k] for k in ("kernel", "ms", "bound", "achieved", "unit", "frac")
+                            if k in r} for r in step_rows] +
                           [recon_roofline(ranks, w, ms_detail["recon"], rec_bytes, prec, pk)],
     }
 
@@ -529,21 +529,39 @@ FP64_PEAK_TFLOPS = 1.19   # measured FP64 FMA throughput on this part (in-regist
 # capture per kernel, with the input elements (I x K) that launch processed;
 # a launch of the same kernel streams its input once, so its traffic scales
 # with I x K.  Only kernels whose source has not changed since the capture.
+# Both captures: `ncu --set full --clock-control none -k regex:<kernel> -c 1`
+# of `bench.py --workload prof --steps 1 --warmup 3 --no-fp64 --no-e2e
+# --no-cpu` (the 500x500x40x11x2 FP32 tensor), mode 0.
 CAPTURED_TRAFFIC = {
     # k_gram_tcx (column mode), mode-0 Gram of 500x500x40x11x2 FP32
-    ("gram", "tcgen05-x3", "col"): dict(bytes=1266.0e6, elems=500 * 440000,
-                                         src="profiles/k_gram_tcx_col_prof_500x500x40x11x2.md"),
+    ("gram", "tcgen05-x3", "col"): dict(bytes=1266.0e6, elems=500 * 440000),
+    # (no capture of the two-digit variant yet)
     # k_ttm_tc_col (transposed output), mode-0 TTM of 500x500x40x11x2 FP32 to 54 rows
-    ("ttm", "tcgen05", "col"): dict(bytes=966.8e6, elems=500 * 440000,
-                                    src="profiles/k_ttm_tc_col_prof_500x500x40x11x2.md"),
+    ("ttm", "tcgen05", "col"): dict(bytes=966.8e6, elems=500 * 440000),
 }
+
+
+def algorithmic_roofline(flops, nbytes, t, pk):
+    """The roofline of a step from the work the method must do: the floor
+    time is max(bytes / HBM copy bandwidth, flops / dense BF16 tensor peak),
+    both measured on this part; frac = floor / measured time, `bound` the
+    resource of the larger term, `achieved` that resource's rate."""
+    t_hbm = nbytes / (pk["hbm_gbs"] * 1e9)
+    t_flop = flops / (pk["bf16_tflops"] * 1e12)
+    if t_hbm >= t_flop:
+        return "hbm", nbytes / t / 1e9, pk["hbm_gbs"], "GB/s", t_hbm / t
+    return "tensor", flops / t / 1e12, pk["bf16_tflops"], "TFLOP/s", t_flop / t
 
 
 def step_rooflines(res, w, pk):
     """Roofline of every Gram / TTM / eigensolve step of one ST-HOSVD, from
-    the library's own CUDA events on its stream (algorithmic work: Gram
-    I(I+1)K flops on I*K read elements; TTM 2RIK flops on I*K read + R*K
-    written; Jacobi ~6 I^3 FP64 flops per sweep)."""
+    the library's own CUDA events on its stream.  Gram and TTM rows are
+    rated on their algorithmic work (Gram I(I+1)K flops on I*K read
+    elements; TTM 2RIK flops on I*K read + R*K written) against the HBM and
+    tensor-core peaks, whichever binds; the eigensolves on their FP64 flops
+    ((4/3) I^3 for the tridiagonal reduction, ~6 I^3 per Jacobi sweep)
+    against the FP64 peak.  The digit Gram also reports its executed
+    FP16 digit products against the tensor peak (mma_frac)."""
     ms, ranks = res.ms, res.ranks
     cur = list(w["dims"])
     # the natural mode order keeps the working tensor rotated: every mode's
@@ -566,46 +584,44 @@ def step_rooflines(res, w, pk):
             ("ttm", ms["ttm"][n], 2 * R * I * K, I * K * esz + R * K * wk_esz, res.ttm_kernel[n]),
             ("eig", ms["eig"][n], eig_flops, 0, eig_k)]:
             t = max(t_ms, 1e-6) / 1e3
-            traffic, tsrc = None, None
+            traffic = None
             cap = CAPTURED_TRAFFIC.get((kind, kern, "col" if (L == 1 or rotated) else "row"))
             if cap is not None and I >= 64:
                 traffic = cap["bytes"] * (I * K) / cap["elems"]
-                tsrc = "ncu capture scaled by I*K: " + cap["src"]
             extra = {}
-            if kern == "tcgen05-x3":
-                # FP32-exact products from three FP16 digits each: 9 FP16
-                # tensor-core products per product of the method
-                bound, ach, unit = "tensor", flops / t / 1e12, "TFLOP/s"
-                peak = pk["bf16_tflops"] / 9.0
-                src = "measured dense BF16/FP16 burst / 9 (3-digit FP16 split, all 9 products)"
-                T = (I + 127) // 128
-                mma = 9 * 2 * 128 * 128 * K * (T * (T + 1) // 2)
-                extra = {"mma_tflops": mma / t / 1e12, "mma_frac": mma / t / 1e12 / pk["bf16_tflops"]}
-            elif kern == "tcgen05":
-                bound, ach, peak, unit = "hbm", nbytes / t / 1e9, pk["hbm_gbs"], "GB/s"
-                src = "measured HBM copy"
-            elif kern in ("simt-fp32", "simt-fp32c"):
-                bound, ach, peak, unit = "alu", flops / t / 1e12, FP32_PEAK_TFLOPS, "TFLOP/s"
-                src = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
-            else:
+            if kind == "eig":
                 bound, ach, peak, unit = "alu", flops / t / 1e12, FP64_PEAK_TFLOPS, "TFLOP/s"
+                frac = ach / peak
                 src = "measured FP64 FMA probe"
+            else:
+                bound, ach, peak, unit, frac = algorithmic_roofline(flops, nbytes, t, pk)
+                src = "measured HBM copy" if bound == "hbm" else "measured dense BF16 burst"
+            if kern in ("tcgen05-x3", "tcgen05-x2"):
+                # executed: 9 (three digits) or 4 (two) FP16 digit products per
+                # product, on 128 x 128 lower-triangle tiles
+                T = (I + 127) // 128
+                nprod = 9 if kern == "tcgen05-x3" else 4
+                mma = nprod * 2 * 128 * 128 * K * (T * (T + 1) // 2)
+                extra = {"mma_tflops": mma / t / 1e12, "mma_frac": mma / t / 1e12 / pk["bf16_tflops"]}
             row = {"kernel": f"{kind} mode {n} ({kern})", "bound": bound, "achieved": ach,
-                   "peak": peak, "unit": unit, "frac": ach / peak, "traffic": traffic,
-                   "ms": t_ms, "hbm_gbs_achieved": nbytes / t / 1e9, "peak_src": src}
+                   "peak": peak, "unit": unit, "frac": frac, "traffic": traffic,
+                   "ms": t_ms, "algorithmic_bytes": nbytes, "algorithmic_flops": flops,
+                   "peak_src": src}
             row.update(extra)
-            if tsrc:
-                row["traffic_src"] = tsrc
-                row["algorithmic_bytes"] = nbytes
+            if traffic is not None:
+                row["traffic_src"] = ("ncu DRAM bytes of the same kernel on the 500x500x40x11x2 "
+                                      "FP32 tensor, scaled by I*K")
             out.append(row)
         cur[n] = R
     return out
 
 
 def recon_roofline(ranks, w, ms, out_bytes, prec, pk):
-    """The multi-TTM reconstruction of the step: its flops under the chain
-    order the library picks (sum over the chain of 2 x output elements x
-    contracted rank), against the FP32 (or FP64) SIMT peak."""
+    """The multi-TTM reconstruction of the step: its algorithmic work is the
+    subtensor it writes (out_bytes) and the flops of the chain order the
+    library picks (sum over the chain of 2 x output elements x contracted
+    rank); rated like the Gram and TTM rows (HBM or tensor peak, whichever
+    binds)."""
     from paper_1901_06043_gb300 import tucker
     order = tucker.ttm_order(ranks, w["recon"], "flops")
     cur = list(ranks)
@@ -613,11 +629,11 @@ def recon_roofline(ranks, w, ms, out_bytes, prec, pk):
     for n in order:
         cur[n] = w["recon"][n]
         flops += 2.0 * float(np.prod(cur)) * ranks[n]
-    peak = FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS
-    ach = flops / (ms / 1e3) / 1e12
-    return {"kernel": f"multi-TTM reconstruction (order {list(order)})", "ms": ms, "bound": "alu",
-            "achieved": ach, "unit": "TFLOP/s", "frac": ach / peak,
-            "hbm_gbs_achieved": out_bytes / (ms / 1e3) / 1e9}
+    t = ms / 1e3
+    bound, ach, peak, unit, frac = algorithmic_roofline(flops, out_bytes, t, pk)
+    return {"kernel": f"multi-TTM reconstruction (order {list(order)})", "ms": ms, "bound": bound,
+            "achieved": ach, "peak": peak, "unit": unit, "frac": frac,
+            "algorithmic_bytes": out_bytes, "algorithmic_flops": flops}
 
 
 def dominant(res, w, pk):
@@ -628,14 +644,17 @@ def dominant(res, w, pk):
 
 def e2e_leg(ctx, x, w, prec, args):
     """Same metric end to end: pinned host input -> device copy -> the step
-    through the C ABI (ST-HOSVD and the subtensor reconstruction, which stays
-    on the device) -> core and factors back to the host, per step."""
+    through the C ABI (ST-HOSVD and the subtensor reconstruction) -> the
+    reconstructed subtensor, the core and the factors back to pinned host
+    memory, per step."""
     import torch
     try:
         xh = torch.empty(x.numel(), dtype=x.dtype, pin_memory=True)
+        rh = torch.empty(int(np.prod(w["recon"])), dtype=x.dtype, pin_memory=True)
         pinned = True
     except Exception:
         xh = torch.empty(x.numel(), dtype=x.dtype)
+        rh = torch.empty(int(np.prod(w["recon"])), dtype=x.dtype)
         pinned = False
     xh.copy_(x)
     xd = torch.empty_like(x)
@@ -645,16 +664,21 @@ def e2e_leg(ctx, x, w, prec, args):
     t0 = time.perf_counter()
     for _ in range(steps):
         xd.copy_(xh, non_blocking=True)
-        r = step(ctx, xd, w, prec)
+        r = ctx.sthosvd(xd, w["dims"], eps=w["eps"], prec=prec)
+        rec = r.reconstruct((0,) * len(w["dims"]), w["recon"], prec=prec)
+        rh.copy_(rec.view(-1).to(rh.dtype), non_blocking=True)
         core, fac = r.to_host()
-        d2h = core.nbytes + sum(f.nbytes for f in fac)
+        torch.cuda.synchronize()
+        d2h = rh.numel() * rh.element_size() + core.nbytes + sum(f.nbytes for f in fac)
+        del rec
         r.close()
     torch.cuda.synchronize()
     el = (time.perf_counter() - t0) / steps
     nb = x.numel() * x.element_size()
-    del xd, xh
+    del xd, xh, rh
     return {"value": nb / 1e9 / el, "unit": "GB/s", "h2d_bytes_per_step": nb,
-            "d2h_bytes_per_step": int(d2h), "steps": steps, "pinned": pinned, "ms": el * 1e3}
+            "d2h_bytes_per_step": int(d2h), "steps": steps, "pinned": pinned, "ms": el * 1e3,
+            "returns": "reconstructed subtensor, core and factors"}
 
 
 if __name__ == "__main__":

@@ -64,14 +64,21 @@ typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
  *   FP32   : FP32 products, round-to-nearest FP32 sums over short chunks
  *            combined exactly (TwoSum) and in FP64; working tensor and core
  *            in the input dtype.
- *   MIXED  : Grams of views with 128 <= I_n <= 2048 on the tensor cores
- *            with exact integer digit products: each value is split under a
- *            per-row power-of-two scale into three 7-bit digits (exact in
- *            FP16), all nine digit products accumulate exactly in FP32 over
- *            windows of 1024 columns, and the windows are summed in exact
- *            FP32 pairs; the only error is the last digit's rounding, 2^-20
- *            of the row maximum, unbiased (its squared mean is removed from
- *            the diagonal).  Other Grams as FP32.  TTMs on the tensor cores
+ *   MIXED  : Grams of column-mode views with 64 <= I_n <= 2048 (row-mode
+ *            views: 128 <= I_n <= 2048) on the tensor cores with exact
+ *            integer digit products: each value is split under a per-row
+ *            power-of-two scale into two or three 7-bit digits (exact in
+ *            FP16), all digit products accumulate exactly in FP32 over
+ *            windows of 2048 or 1024 columns, and the windows are summed in
+ *            exact FP32 pairs; the only error is the last digit's rounding,
+ *            2^-13 (two digits) or 2^-20 (three) of the row maximum,
+ *            unbiased (its squared mean is removed from the diagonal).  An
+ *            eps-driven tucker_sthosvd bounds that error on the discarded
+ *            subspace from the row maxima, the view's size and the
+ *            threshold, and takes two digits where six standard deviations
+ *            stay below 1 % of eps^2 ||X||^2 / N, else three, else an FP64
+ *            Gram; a single tucker_gram uses three.  Other Grams as FP32.
+ *            TTMs on the tensor cores
  *            (tcgen05) with a two-term FP16 split of both operands where the
  *            shape allows (column-mode views with K <= 128; row-mode views
  *            with L % 4 == 0 and I_n <= 64, the reconstruction's expansions).
@@ -111,7 +118,10 @@ typedef struct tucker_result {
   double threshold;                  /* eps^2 ||X||^2 / N (0 when ranks were given)    */
   double discarded_sq[TUCKER_MAX_MODES]; /* sum of discarded eigenvalues per mode      */
   int jacobi_sweeps[TUCKER_MAX_MODES];
-  int gram_kernel[TUCKER_MAX_MODES]; /* kernel that ran: 0 SIMT FP64, 1 SIMT FP32, 2 tcgen05 */
+  int gram_kernel[TUCKER_MAX_MODES]; /* kernel that ran: 0 SIMT FP64, 1 SIMT FP32, 2 tcgen05
+                                        (rounded split), 3 small-mode FP64, 4 FP32 with
+                                        exact block sums, 5 / 6 tcgen05 on exact three- /
+                                        two-digit products */
   int ttm_kernel[TUCKER_MAX_MODES];
   int eig_kernel[TUCKER_MAX_MODES];  /* 0 Jacobi, 1 tridiagonal + inverse iteration          */
   float ms_norm;                     /* device time per step (CUDA events), ms         */
@@ -135,16 +145,46 @@ const char* tucker_last_error(const tucker_ctx* ctx);
  *   TUCKER_OPT_EIG_SOLVER  eigensolver of the truncation step (tucker_sthosvd,
  *                          tucker_eig_trunc): 0 auto (tridiagonal for
  *                          64 <= I <= 4096, Jacobi otherwise), 1 Jacobi,
- *                          2 tridiagonal for every I <= 4096 */
+ *                          2 tridiagonal for every I <= 4096
+ *   TUCKER_OPT_BARRIER_POLLS  polls a CTA of the eigensolvers' grid barriers
+ *                          (Jacobi sweeps, Householder reduction) makes
+ *                          before it gives up (default 2^24, about a second
+ *                          with its back-off; 1 .. 2^40).  A barrier that
+ *                          gives up makes every CTA return, and the call
+ *                          returns TUCKER_ERR_CUDA ("grid barrier gave up
+ *                          waiting"); the context stays usable.
+ *   TUCKER_OPT_MEM_LIMIT   device bytes tucker_sthosvd may hold at once
+ *                          (0, the default: the device's free memory plus
+ *                          what the default memory pool holds unused).
+ *                          tucker_sthosvd predicts its workspace from the
+ *                          mode sizes before it starts (the Gram and
+ *                          eigenvector matrices, the first Gram's split-K
+ *                          scratch, the first TTM output at rank 1) and, once
+ *                          each rank is cut, the TTM output; a prediction
+ *                          above the figure returns TUCKER_ERR_OOM before
+ *                          that step launches or allocates anything.
+ *   TUCKER_OPT_GRAM_DIGITS digits per value of the exact-digit Gram (MIXED):
+ *                          0 (default) chooses per view (see MIXED), 2 or 3
+ *                          forces that count wherever the digit Gram runs. */
 #define TUCKER_OPT_TIMING 1
 #define TUCKER_OPT_MAX_SWEEPS 2
 #define TUCKER_OPT_JACOBI_TOL 3
 #define TUCKER_OPT_EIG_SOLVER 4
+#define TUCKER_OPT_BARRIER_POLLS 5
+#define TUCKER_OPT_MEM_LIMIT 6
+#define TUCKER_OPT_GRAM_DIGITS 7
 tucker_status tucker_set_option(tucker_ctx* ctx, int key, double value);
 
 /* Diagnostics: number of device kernels this library has launched in the
  * process so far (all contexts).  Host only; never fails. */
 uint64_t tucker_kernel_launches(void);
+
+/* Diagnostics: y_dev[i] = the FP64 reciprocal the tridiagonal eigensolver
+ * uses (an FP32 seed refined by two Newton-Raphson steps, within one ulp of
+ * 1/x for normal x) of x_dev[i], i < n, on `stream` (a cudaStream_t, NULL =
+ * legacy default stream); synchronises it.  Errors: INVALID, CUDA. */
+tucker_status tucker_selftest_rcp64(const double* x_dev, double* y_dev, int64_t n,
+                                    void* stream);
 
 /* ST-HOSVD, Algorithm 1 (Section 3.3).
  *   x_dev      input tensor (dtype, dims), read only.
@@ -156,8 +196,10 @@ uint64_t tucker_kernel_launches(void);
  *              1 <= R_n <= I_n.
  *   mode_order permutation of 0..N-1 (NULL = 0..N-1).
  * On success *out receives a result to release with tucker_result_destroy.
- * Errors: INVALID, OOM, NONFINITE (input has NaN/Inf), EIG_NOCONV (a
- * result is still returned), UNSUPPORTED (MIXED with FP64 input), CUDA. */
+ * Errors: INVALID, OOM (predicted before the first mode or before a TTM, see
+ * TUCKER_OPT_MEM_LIMIT, or a failed allocation), NONFINITE (input has
+ * NaN/Inf), EIG_NOCONV (a result is still returned), UNSUPPORTED (MIXED with
+ * FP64 input), CUDA. */
 tucker_status tucker_sthosvd(tucker_ctx* ctx, const void* x_dev, tucker_dtype dtype,
                              int ndim, const int64_t* dims, double eps,
                              const int64_t* ranks_or_null, const int* mode_order_or_null,
@@ -212,6 +254,73 @@ tucker_status tucker_multi_ttm(tucker_ctx* ctx, const void* core_dev, tucker_dty
  * ties to the lexicographically first.  order_out receives N modes. */
 tucker_status tucker_ttm_order(int ndim, const int64_t* core_dims, const int64_t* out_dims,
                                int objective, int* order_out);
+
+/* HOSVD, Section 3.2: every factor from the Gram of X's own mode-n
+ * unfolding (Eq. Xeigprob), R_n by Eq. Un with the threshold
+ * eps^2 ||X||^2 / N (or the given ranks), U_n its leading R_n eigenvectors;
+ * then the core G = X x_0 U_0^T ... x_{N-1} U_{N-1}^T (TTMs in the
+ * flop-minimal order of that chain).  Theorem 1 bounds the error:
+ * ||X - Xhat||^2 <= sum_n discarded_sq[n].  Arguments, precision, result and
+ * errors as tucker_sthosvd (mode_order records 0..N-1, the order of the
+ * Grams, which all read X). */
+tucker_status tucker_hosvd(tucker_ctx* ctx, const void* x_dev, tucker_dtype dtype, int ndim,
+                           const int64_t* dims, double eps, const int64_t* ranks_or_null,
+                           tucker_prec prec, tucker_result** out);
+
+/* ST-HOSVD mode order for given (or estimated) ranks, host only: the
+ * permutation of 0..N-1 with the fewest flops under the cost analysis of
+ * Section 6 (mode-n Gram L I_n^2 Rt, TTM 2 L R_n I_n Rt on the current
+ * tensor; the eigensolves cost the same in every order), by exhaustive
+ * search over the N! orders, ties to the lexicographically first.  Pass it
+ * as tucker_sthosvd's mode order; for an eps-driven run the ranks are an
+ * estimate (e.g. those of a similar tensor), since they are not known before
+ * the run (Section 8.4).  1 <= ranks[n] <= dims[n].  Errors: INVALID. */
+tucker_status tucker_sthosvd_order(int ndim, const int64_t* dims, const int64_t* ranks,
+                                   int* order_out);
+
+/* ---- pre- and post-processing, Section 3.5 ---- */
+
+/* Statistics of every mode-`mode` hyperslice X(:, .., i, .., :) (its
+ * J^* / I_n entries), FP64: stats_dev[6 i + k] with k = TUCKER_STAT_*.
+ * The standard deviation is the population one (sum (x - mean)^2 / count),
+ * computed in a second pass over the data.  stats_dev (6 I_n doubles) is
+ * caller-owned.  Synchronises.  Errors: INVALID, NONFINITE (a statistic is
+ * NaN or Inf: the tensor holds NaN or Inf), OOM, CUDA. */
+#define TUCKER_STAT_MEAN 0
+#define TUCKER_STAT_STD 1
+#define TUCKER_STAT_MAX 2
+#define TUCKER_STAT_MIN 3
+#define TUCKER_STAT_NORM1 4
+#define TUCKER_STAT_NORM2 5
+tucker_status tucker_slice_stats(tucker_ctx* ctx, const void* x_dev, tucker_dtype dtype, int ndim,
+                                 const int64_t* dims, int mode, double* stats_dev);
+
+/* One linear function per mode-`mode` hyperslice i:
+ *   inverse = 0 (pre-processing):  y = (x - shift_i) * scale_i
+ *   inverse = 1 (post-processing): y = x / scale_i + shift_i
+ * evaluated in FP64 and rounded once to dtype.  shift_dev, scale_dev: I_n
+ * FP64 values each (for a reconstructed subtensor whose mode-`mode` range
+ * starts at b, pass shift + b and scale + b); scale_i must be nonzero for
+ * the inverse.  y_dev (same dims and dtype) may equal x_dev (in place).
+ * Synchronises.  Errors: INVALID, CUDA. */
+tucker_status tucker_slice_transform(tucker_ctx* ctx, const void* x_dev, tucker_dtype dtype,
+                                     int ndim, const int64_t* dims, int mode,
+                                     const double* shift_dev, const double* scale_dev,
+                                     int inverse, void* y_dev);
+
+/* Pre-processing in one call (Section 3.5): the hyperslice statistics, the
+ * parameters of `method` into shift_dev and scale_dev (I_n FP64 each,
+ * caller-owned, kept for the post-processing inverse), then the transform
+ * into y_dev (may equal x_dev).
+ *   TUCKER_PRE_STANDARDIZE: shift = mean, scale = 1 / std (mean 0, variance 1)
+ *   TUCKER_PRE_MAX_RESCALE: shift = 0, scale = 1 / max |x| (range -1..1)
+ * A slice with std 0 (standardization) or all zeros (max rescaling) keeps
+ * scale 1.  Synchronises.  Errors as tucker_slice_stats. */
+#define TUCKER_PRE_STANDARDIZE 0
+#define TUCKER_PRE_MAX_RESCALE 1
+tucker_status tucker_preprocess(tucker_ctx* ctx, const void* x_dev, tucker_dtype dtype, int ndim,
+                                const int64_t* dims, int mode, int method, double* shift_dev,
+                                double* scale_dev, void* y_dev);
 
 /* ---- single steps of the hot path (each one row of Algorithm 1) ---- */
 

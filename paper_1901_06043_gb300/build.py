@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtucker_gb300.so")
 SOURCES = ["api.cu", "simt.cu", "gram_f32.cu", "gram_small.cu", "gram_tcx.cu", "jacobi.cu",
-           "tridiag.cu", "tc.cu", "ttm_tc.cu", "noalloc.cu"]
+           "tridiag.cu", "tc.cu", "ttm_tc.cu", "noalloc.cu", "prepost.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

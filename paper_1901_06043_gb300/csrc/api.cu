@@ -27,6 +27,9 @@ struct tucker_ctx {
   double tol_rel = 1e-15;
   double tol_abs = 1e-15;
   int eig_solver = 0;            // 0 auto, 1 Jacobi, 2 tridiagonal
+  unsigned long long barrier_polls = 1ull << 24;   // grid-barrier poll limit of the eigensolvers
+  double mem_limit = 0.0;        // bytes assumed available to a call (0: ask the device)
+  int gram_digits = 0;           // digits of the exact-digit Gram: 0 auto, 2 or 3
   std::string err;
   // small device scratch
   unsigned* d_words = nullptr;   // 256 words
@@ -220,14 +223,52 @@ float split_scale(double maxabs) {
   return std::ldexp(1.0f, e);
 }
 
-// Smallest eps^2 / N at which an eps-driven ST-HOSVD keeps a reduced-precision
+// Smallest eps^2 / N at which an eps-driven ST-HOSVD keeps an FP32-product
 // Gram (see tucker_sthosvd).
 constexpr double kMinFp32GramThreshold = 1e-9;
+
+// Digits of the exact-digit Gram of an I x K view for the eps cut at
+// threshold thr: 2 or 3, or 0 when neither is accurate enough (FP64 Gram).
+// The Gram's only error is the representation of each value by its digits:
+// |r_ik| <= delta_i = 2^(floor(log2 max_k |x_ik|) - 20) with three digits,
+// 2^(... - 13) with two, unbiased, independent of x (variance
+// sigma_i^2 <= delta_i^2 / 3); the mean of r r^T's diagonal is removed
+// exactly.  On the discarded subspace (projector P, rank I - R) the error is
+//   2 sum_k (P x_k).r_k + sum_k sum_{i != j} P_ij r_ik r_jk,
+// whose variance is at most 4 sigma^2 tail + 2 K (I - R) sigma^4 with
+// sigma = max_i sigma_i and tail <= thr at the cut.  A digit count is
+// accepted when six standard deviations stay below 1 % of thr (the FP64
+// path's own margins at the cut are a few percent of thr on the benchmarked
+// tensors); two digits are preferred, four products instead of nine.  With
+// no threshold (ranks given) three digits.
+double digit_gram_err6(const unsigned* rowmax_bits, int64_t I, int64_t K, double thr, int ndig) {
+  double dmax = 0.0;
+  for (int64_t i = 0; i < I; ++i) {
+    const unsigned b = rowmax_bits[i] & 0x7fffffffu;
+    if (b == 0u) continue;
+    float m;
+    memcpy(&m, &b, sizeof m);
+    int e = 0;
+    std::frexp((double)m, &e);                      // m in [2^(e-1), 2^e)
+    dmax = std::max(dmax, std::ldexp(1.0, e - (ndig == 3 ? 21 : 14)));
+  }
+  const double s2 = dmax * dmax / 3.0;
+  return 6.0 * std::sqrt(4.0 * s2 * thr + 2.0 * (double)K * (double)I * s2 * s2);
+}
+
+int digit_gram_digits(const unsigned* rowmax_bits, int64_t I, int64_t K, double thr) {
+  if (!(thr > 0.0)) return 3;
+  if (digit_gram_err6(rowmax_bits, I, K, thr, 2) <= 0.01 * thr) return 2;
+  if (digit_gram_err6(rowmax_bits, I, K, thr, 3) <= 0.01 * thr) return 3;
+  return 0;
+}
 
 // Which kernel serves a Gram / TTM step: 0 SIMT FP64, 1 SIMT FP32, 2 tcgen05
 // (rounded FP16 split products), 3 small-mode FP64 (I < 64, every
 // precision), 4 FP32 with exact (compensated) block sums (row modes with few
-// slabs), 5 tcgen05 on exact integer digit products (MIXED, 128 <= I <= 2048).
+// slabs), 5 tcgen05 on exact integer digit products (MIXED, I <= 2048;
+// column-mode views from I = 64, row-mode views from 128), three digits;
+// 6 the same with two digits.
 int gram_kernel_for(tucker_prec prec, tucker_dtype dt, const SlabView& v, int sms) {
   if (plan_gram_small(v.L, v.I, v.Rt, sms, v.L0).nctas > 0) return 3;
   if (prec == TUCKER_PREC_FP64) return 0;
@@ -258,13 +299,16 @@ tucker_status rowmax_pass(tucker_ctx* c, const float* y, int64_t I0, int64_t nco
 // check = false: the tensor-core kernel's error word (d_words[8]) is neither
 // cleared nor read here; the caller clears it before and reads it after a
 // batch of calls.
+// ndig: digits of the exact-digit Gram (2 or 3; TUCKER_OPT_GRAM_DIGITS
+// overrides it).
 tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabView& v,
                       tucker_prec prec, double* S, int* kernel_used, double maxabs = -1.0,
-                      bool check = true, const unsigned* rowmax = nullptr) {
+                      bool check = true, const unsigned* rowmax = nullptr, int ndig = 3) {
   int kern = gram_kernel_for(prec, dt, v, c->num_sms);
   if ((kern == 2 || (kern == 5 && v.L == 1)) && (((uintptr_t)y) & 15) != 0) kern = 1;
   if (kern == 5 && (((uintptr_t)y) & 3) != 0) kern = 1;
-  if (kernel_used) *kernel_used = kern;
+  if (c->gram_digits) ndig = c->gram_digits;
+  if (kernel_used) *kernel_used = (kern == 5 && ndig == 2) ? 6 : kern;
   if (kern == 5) {
     const GramPlan p = plan_gram_tcx(v.L, v.I, v.Rt, c->num_sms);
     DevBuf scratch, rm;
@@ -280,7 +324,7 @@ tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabV
     }
     if (check) TK_CUDA(c, cudaMemsetAsync(c->d_words + 8, 0, sizeof(unsigned), c->stream));
     TK_CUDA(c, launch_gram_tcx((const float*)y, v.L, v.I, v.Rt, p, rowmax, scratch.p,
-                               c->d_words + 8, S, c->stream));
+                               c->d_words + 8, S, c->stream, ndig));
     if (!check) return TUCKER_OK;
     unsigned err = 0;
     TK_CUDA(c, cudaMemcpyAsync(&err, c->d_words + 8, sizeof(unsigned), cudaMemcpyDeviceToHost,
@@ -343,6 +387,53 @@ tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabV
   return TUCKER_OK;
 }
 
+// Device bytes of the split-K scratch do_gram allocates for a view.
+size_t gram_scratch_bytes(const tucker_ctx* c, tucker_prec prec, tucker_dtype dt,
+                          const SlabView& v) {
+  const int kern = gram_kernel_for(prec, dt, v, c->num_sms);
+  if (kern == 5) return plan_gram_tcx(v.L, v.I, v.Rt, c->num_sms).scratch_bytes + 8 * (size_t)v.I;
+  if (kern == 2) return plan_gram_tc(v.L, v.I, v.Rt, c->num_sms).scratch_bytes;
+  if (kern == 3) return plan_gram_small(v.L, v.I, v.Rt, c->num_sms, v.L0).scratch_bytes;
+  if (kern == 1 && dt == TUCKER_F32) {
+    const GramPlan pc = plan_gram_f32(v.L, v.I, v.Rt, c->num_sms, v.L0);
+    if (pc.ntiles > 0) return pc.scratch_bytes;
+  }
+  return plan_gram_simt(v.L, v.I, v.Rt, c->num_sms, v.L0).scratch_bytes;
+}
+
+// Bytes a call may still allocate: with TUCKER_OPT_MEM_LIMIT set, that
+// figure less what the call already holds; otherwise the device's free
+// memory plus what the default memory pool has reserved and not handed out.
+double mem_available(tucker_ctx* c, double held) {
+  if (c->mem_limit > 0.0) return c->mem_limit - held;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return std::numeric_limits<double>::infinity();
+  }
+  double avail = (double)fr;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+    uint64_t reserved = 0, used = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) ==
+            cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess &&
+        reserved > used)
+      avail += (double)(reserved - used);
+  }
+  cudaGetLastError();
+  return avail;
+}
+
+tucker_status predict_oom(tucker_ctx* c, double need, double held, const char* what) {
+  const double avail = mem_available(c, held);
+  if (need <= avail) return TUCKER_OK;
+  char m[192];
+  snprintf(m, sizeof m, "predicted out of memory before %s: %.0f bytes needed, %.0f available",
+           what, need, avail > 0.0 ? avail : 0.0);
+  return set_err(c, TUCKER_ERR_OOM, m);
+}
+
 tucker_status do_eig(tucker_ctx* c, const double* S, int n, double* w, double* V, int* sweeps) {
   DevBuf work;
   TK_TRY(dev_alloc(c, work, jacobi_work_bytes(n)));
@@ -355,7 +446,8 @@ tucker_status do_eig(tucker_ctx* c, const double* S, int n, double* w, double* V
   int ms = c->max_sweeps;
   if (ms > 200) ms = 200;
   TK_CUDA(c, launch_jacobi(S, n, work.as<double>(), c->d_small + 8, c->d_words + 32, ms,
-                           c->tol_rel, c->tol_abs, c->num_sms, w, V, c->d_info, c->stream));
+                           c->tol_rel, c->tol_abs, c->num_sms, w, V, c->d_info, c->stream,
+                           c->barrier_polls));
   int info[4] = {0, 0, 0, -1};
   unsigned words[3] = {0, 0, 0};
   TK_CUDA(c, cudaMemcpyAsync(info, c->d_info, sizeof(info), cudaMemcpyDeviceToHost, c->stream));
@@ -415,7 +507,7 @@ tucker_status do_eig_tri(tucker_ctx* c, const double* S, int n, double thr, int 
   TK_CUDA(c, cudaMemcpyAsync(h.A, S, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
   TK_CUDA(c, cudaMemsetAsync(c->d_words + 32, 0, sizeof(unsigned) * 3, st));
   TK_CUDA(c, cudaMemsetAsync(info, 0, sizeof(int), st));
-  TK_CUDA(c, launch_tridiag(pd, &h, 1, c->d_words + 32, c->d_words + 34, st));
+  TK_CUDA(c, launch_tridiag(pd, &h, 1, c->d_words + 32, c->d_words + 34, st, c->barrier_polls));
   TK_CUDA(c, launch_bisect(pd, 1, n, n, c->num_sms, st));
   TK_CUDA(c, launch_rank_cut(w, n, thr, fixed_R, c->d_i64, c->d_small + 2, tail, st));
   int64_t R = 0;
@@ -654,6 +746,21 @@ tucker_status tucker_set_option(tucker_ctx* c, int key, double value) {
         return set_err(c, TUCKER_ERR_INVALID, "eigensolver must be 0 (auto), 1 or 2");
       c->eig_solver = (int)value;
       return TUCKER_OK;
+    case TUCKER_OPT_GRAM_DIGITS:
+      if (value != 0.0 && value != 2.0 && value != 3.0)
+        return set_err(c, TUCKER_ERR_INVALID, "Gram digits must be 0 (auto), 2 or 3");
+      c->gram_digits = (int)value;
+      return TUCKER_OK;
+    case TUCKER_OPT_BARRIER_POLLS:
+      if (!(value >= 1.0 && value <= 1099511627776.0))
+        return set_err(c, TUCKER_ERR_INVALID, "barrier poll limit out of [1, 2^40]");
+      c->barrier_polls = (unsigned long long)value;
+      return TUCKER_OK;
+    case TUCKER_OPT_MEM_LIMIT:
+      if (!(value >= 0.0 && std::isfinite(value)))
+        return set_err(c, TUCKER_ERR_INVALID, "memory limit must be >= 0");
+      c->mem_limit = value;
+      return TUCKER_OK;
     case TUCKER_OPT_JACOBI_TOL:
       if (!(value > 0.0 && value < 1e-3)) return set_err(c, TUCKER_ERR_INVALID, "tolerance out of (0, 1e-3)");
       c->tol_rel = value;
@@ -779,6 +886,18 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
   for (int k = 0; k < ndim; ++k) imax = std::max(imax, dims[k]);
   if (imax > 8192) return set_err(c, TUCKER_ERR_INVALID, "mode size above 8192");
 
+  const tucker_dtype wdt = (prec == TUCKER_PREC_FP64) ? TUCKER_F64 : dt;
+  // workspace the first mode needs at least (nothing is launched or
+  // allocated when it does not fit): the Gram and eigenvector matrices,
+  // the first Gram's split-K scratch and its TTM output at rank 1
+  const double ws_fixed = 16.0 * (double)imax * (double)imax;
+  {
+    const SlabView v0 = slab_view(ndim, dims, order[0]);
+    const double need0 = ws_fixed + (double)gram_scratch_bytes(c, prec, dt, v0) +
+                         (double)dtype_size(wdt) * (double)(numel(ndim, dims) / dims[order[0]]);
+    TK_TRY(predict_oom(c, need0, 0.0, "the first mode"));
+  }
+
   tucker_result* r = new tucker_result();
   memset(r, 0, sizeof(*r));
   struct Guard {
@@ -786,9 +905,9 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
     ~Guard() { if (r) tucker_result_destroy(r); }
   } guard{r};
   r->ndim = ndim;
-  const tucker_dtype wdt = (prec == TUCKER_PREC_FP64) ? TUCKER_F64 : dt;
   r->core_dtype = wdt;
   for (int k = 0; k < ndim; ++k) { r->dims[k] = dims[k]; r->mode_order[k] = order[k]; }
+  double held_factors = 0.0;
 
   Timer t_total, t_norm;
   t_total.start(c);
@@ -800,9 +919,8 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
   DevBuf rowmax;
   {
     const SlabView v0 = slab_view(ndim, dims, 0);
-    const bool tcx = order[0] == 0 && !(!ranks && prec != TUCKER_PREC_FP64 &&
-                                        eps * eps / ndim < kMinFp32GramThreshold) &&
-                     gram_kernel_for(prec, dt, v0, c->num_sms) == 5 && (((uintptr_t)x) & 15) == 0;
+    const bool tcx = order[0] == 0 && gram_kernel_for(prec, dt, v0, c->num_sms) == 5 &&
+                     (((uintptr_t)x) & 15) == 0;
     if (tcx) TK_TRY(dev_alloc(c, rowmax, sizeof(unsigned) * v0.I));
   }
   TK_TRY(do_norm(c, x, dt, nx, &nrm2, &xmax, rowmax.as<unsigned>(), dims[0]));
@@ -814,11 +932,13 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
   // An FP32-product Gram (unbiased rounding, split and ordered as in the
   // kernels) leaves up to ~1.5e-10 ||X||^2 on the discarded subspace of the
   // later modes, whose energy sits in a few components; below
-  // eps^2 / N = 1e-9 that is no longer far below the threshold, so the
-  // Grams are computed in FP64 there (the TTMs keep their precision).
-  tucker_prec gram_prec = prec;
-  if (!ranks && prec != TUCKER_PREC_FP64 && eps * eps / ndim < kMinFp32GramThreshold)
-    gram_prec = TUCKER_PREC_FP64;
+  // eps^2 / N = 1e-9 that is no longer far below the threshold, so those
+  // Grams are computed in FP64 there (the TTMs keep their precision).  The
+  // exact-digit Gram's error is bounded per view from its row maxima
+  // (digit_gram_digits): it keeps the tensor cores, with two digits or
+  // three, while that bound allows.
+  const bool small_eps =
+      !ranks && prec != TUCKER_PREC_FP64 && eps * eps / ndim < kMinFp32GramThreshold;
 
   DevBuf S, V, ycur;
   TK_TRY(dev_alloc(c, S, sizeof(double) * imax * imax));
@@ -847,22 +967,33 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
     DevBuf rowmax_s;
     double ymax = s == 0 ? xmax : -1.0;
     const unsigned* rmx = s == 0 ? rowmax.as<unsigned>() : nullptr;
-    if (rotate && s > 0 && ydt == TUCKER_F32 &&
-        gram_kernel_for(gram_prec, ydt, v, c->num_sms) == 5 && (((uintptr_t)y) & 15) == 0) {
+    const int gk = gram_kernel_for(prec, ydt, v, c->num_sms);
+    tucker_prec gram_prec = prec;
+    int ndig = 3;
+    if (gk == 5 && rotate && s > 0 && ydt == TUCKER_F32 && (((uintptr_t)y) & 15) == 0) {
       TK_TRY(dev_alloc(c, rowmax_s, sizeof(unsigned) * v.I));
       TK_TRY(rowmax_pass(c, (const float*)y, v.I, v.Rt, rowmax_s.as<unsigned>()));
-      std::vector<unsigned> hb((size_t)v.I);
-      TK_CUDA(c, cudaMemcpyAsync(hb.data(), rowmax_s.p, sizeof(unsigned) * v.I,
-                                 cudaMemcpyDeviceToHost, c->stream));
-      TK_TRY(sync(c));
-      unsigned mb = 0;
-      for (unsigned b : hb) mb = std::max(mb, b & 0x7fffffffu);
-      float mf;
-      memcpy(&mf, &mb, sizeof mf);
-      ymax = (double)mf;
       rmx = rowmax_s.as<unsigned>();
     }
-    TK_TRY(do_gram(c, y, ydt, v, gram_prec, S.as<double>(), &r->gram_kernel[n], ymax, true, rmx));
+    if (gk == 5 && rmx) {
+      std::vector<unsigned> hb((size_t)v.I);
+      TK_CUDA(c, cudaMemcpyAsync(hb.data(), rmx, sizeof(unsigned) * v.I, cudaMemcpyDeviceToHost,
+                                 c->stream));
+      TK_TRY(sync(c));
+      if (s > 0) {
+        unsigned mb = 0;
+        for (unsigned b : hb) mb = std::max(mb, b & 0x7fffffffu);
+        float mf;
+        memcpy(&mf, &mb, sizeof mf);
+        ymax = (double)mf;
+      }
+      ndig = digit_gram_digits(hb.data(), v.I, v.L * v.Rt, thr);
+      if (ndig == 0) gram_prec = TUCKER_PREC_FP64;
+    } else if (small_eps && gk != 3) {
+      gram_prec = TUCKER_PREC_FP64;
+    }
+    TK_TRY(do_gram(c, y, ydt, v, gram_prec, S.as<double>(), &r->gram_kernel[n], ymax, true, rmx,
+                   ndig > 0 ? ndig : 3));
     tmg.stop(c);
     DevBuf w, U;
     TK_TRY(dev_alloc(c, w, sizeof(double) * I));
@@ -900,6 +1031,13 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
     int64_t nd[TUCKER_MAX_MODES];
     for (int k = 0; k < ndim; ++k) nd[k] = cur[k];
     nd[n] = R;
+    held_factors += 8.0 * (double)I * (double)(R + 1);
+    {
+      const double held = ws_fixed + held_factors +
+                          (s > 0 ? (double)dtype_size(ydt) * (double)numel(ndim, cur) : 0.0);
+      TK_TRY(predict_oom(c, (double)dtype_size(wdt) * (double)numel(ndim, nd), held,
+                         "a TTM"));
+    }
     DevBuf z;
     TK_TRY(dev_alloc(c, z, dtype_size(wdt) * numel(ndim, nd)));
     tmt.start(c);
@@ -1085,7 +1223,7 @@ tucker_status tucker_sthosvd_batched(tucker_ctx* c, int count, const void* const
     te.start(c);
     TK_CUDA(c, cudaMemsetAsync(info_d, 0, sizeof(int) * m + sizeof(unsigned) * (m + 1), st));
     TK_CUDA(c, cudaMemcpyAsync(thr_d, thr.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
-    TK_CUDA(c, launch_tridiag(pd, h.data(), m, bars_d, bars_d + m, st));
+    TK_CUDA(c, launch_tridiag(pd, h.data(), m, bars_d, bars_d + m, st, c->barrier_polls));
     int neig = 0;
     for (int q = 0; q < m; ++q) neig += h[q].n;
     TK_CUDA(c, launch_bisect(pd, m, nmax, neig, c->num_sms, st));
@@ -1311,6 +1449,274 @@ tucker_status tucker_reconstruct(tucker_ctx* c, const tucker_result* r, const in
   }
   return tucker_multi_ttm(c, r->core, r->core_dtype, N, r->ranks, mats, lda, od, order, prec,
                           out, odt);
+}
+
+// ---------------------------------------------------------------- HOSVD
+
+namespace {
+
+// Eigendecomposition and cut of one mode (Algorithm 1's steps after the
+// Gram): all eigenvalues into w, R by Eq. Un (or fixed_R), the R leading
+// eigenvectors into U (I x R column-major), by the tridiagonal solver where
+// it applies, else (or when its Cholesky QR rejects the vectors) Jacobi.
+tucker_status do_truncate(tucker_ctx* c, const double* S, int I, double thr, int fixed_R,
+                          DevBuf& w, DevBuf& U, int64_t* R, double* disc, int* sweeps,
+                          int* eig_kernel, bool* noconv) {
+  TK_TRY(dev_alloc(c, w, sizeof(double) * I));
+  *sweeps = 0;
+  if (use_tridiag(c, I)) {
+    bool failed = false;
+    TK_TRY(do_eig_tri(c, S, I, thr, fixed_R, w.as<double>(), U, R, disc, &failed));
+    *eig_kernel = 1;
+    if (!failed) return TUCKER_OK;
+  }
+  DevBuf V;
+  TK_TRY(dev_alloc(c, V, sizeof(double) * (size_t)I * I));
+  tucker_status es = do_eig(c, S, I, w.as<double>(), V.as<double>(), sweeps);
+  if (es != TUCKER_OK && es != TUCKER_ERR_EIG_NOCONV) return es;
+  if (es == TUCKER_ERR_EIG_NOCONV) *noconv = true;
+  TK_TRY(do_cut(c, w.as<double>(), I, thr, fixed_R, R, disc));
+  TK_TRY(dev_alloc(c, U, sizeof(double) * I * (*R)));
+  TK_CUDA(c, cudaMemcpyAsync(U.p, V.p, sizeof(double) * I * (*R), cudaMemcpyDeviceToDevice,
+                             c->stream));
+  *eig_kernel = 0;
+  return TUCKER_OK;
+}
+
+// Flops of ST-HOSVD in mode order `perm` with ranks R (the cost analysis of
+// Section 6, without the eigensolve, which every order pays alike): the
+// mode-n Gram of the current tensor costs numel I_n, its TTM 2 numel R_n.
+long double sthosvd_order_cost(int N, const int64_t* I, const int64_t* R, const int* perm) {
+  long double cur[TUCKER_MAX_MODES], cost = 0;
+  for (int k = 0; k < N; ++k) cur[k] = (long double)I[k];
+  for (int s = 0; s < N; ++s) {
+    const int n = perm[s];
+    long double numel = 1;
+    for (int k = 0; k < N; ++k) numel *= cur[k];
+    cost += numel * (long double)(I[n] + 2 * R[n]);
+    cur[n] = (long double)R[n];
+  }
+  return cost;
+}
+
+}  // namespace
+
+tucker_status tucker_selftest_rcp64(const double* x_dev, double* y_dev, int64_t n,
+                                   void* stream) {
+  if (!x_dev || !y_dev || n < 0) return TUCKER_ERR_INVALID;
+  if (launch_rcp64_probe(x_dev, y_dev, n, (cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    return TUCKER_ERR_CUDA;
+  }
+  return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? TUCKER_OK : TUCKER_ERR_CUDA;
+}
+
+tucker_status tucker_sthosvd_order(int ndim, const int64_t* dims, const int64_t* ranks,
+                                   int* order_out) {
+  if (!check_dims(ndim, dims) || !ranks || !order_out) return TUCKER_ERR_INVALID;
+  for (int k = 0; k < ndim; ++k)
+    if (ranks[k] < 1 || ranks[k] > dims[k]) return TUCKER_ERR_INVALID;
+  std::vector<int> perm(ndim);
+  for (int k = 0; k < ndim; ++k) perm[k] = k;
+  bool first = true;
+  long double best = 0;
+  do {
+    const long double cost = sthosvd_order_cost(ndim, dims, ranks, perm.data());
+    if (first || cost < best) {
+      best = cost;
+      first = false;
+      for (int k = 0; k < ndim; ++k) order_out[k] = perm[k];
+    }
+  } while (std::next_permutation(perm.begin(), perm.end()));
+  return TUCKER_OK;
+}
+
+tucker_status tucker_hosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int ndim,
+                           const int64_t* dims, double eps, const int64_t* ranks,
+                           tucker_prec prec, tucker_result** out) {
+  if (!c) return TUCKER_ERR_INVALID;
+  if (!out) return set_err(c, TUCKER_ERR_INVALID, "null result pointer");
+  *out = nullptr;
+  if (!x || !check_dims(ndim, dims) || (dt != TUCKER_F32 && dt != TUCKER_F64) || prec < 0 ||
+      prec > 3)
+    return set_err(c, TUCKER_ERR_INVALID, "tucker_hosvd: bad argument");
+  if (!ranks && !(eps >= 0.0 && std::isfinite(eps)))
+    return set_err(c, TUCKER_ERR_INVALID, "eps must be finite and >= 0");
+  if (ranks)
+    for (int k = 0; k < ndim; ++k)
+      if (ranks[k] < 1 || ranks[k] > dims[k])
+        return set_err(c, TUCKER_ERR_INVALID, "ranks must satisfy 1 <= R_n <= I_n");
+  if ((prec == TUCKER_PREC_MIXED || prec == TUCKER_PREC_TENSOR) && dt != TUCKER_F32)
+    return set_err(c, TUCKER_ERR_UNSUPPORTED, "MIXED/TENSOR precision needs FP32 input");
+  int64_t imax = 0;
+  for (int k = 0; k < ndim; ++k) imax = std::max(imax, dims[k]);
+  if (imax > 8192) return set_err(c, TUCKER_ERR_INVALID, "mode size above 8192");
+
+  tucker_result* r = new tucker_result();
+  memset(r, 0, sizeof(*r));
+  struct Guard {
+    tucker_result*& r;
+    ~Guard() { if (r) tucker_result_destroy(r); }
+  } guard{r};
+  r->ndim = ndim;
+  const tucker_dtype wdt = (prec == TUCKER_PREC_FP64) ? TUCKER_F64 : dt;
+  r->core_dtype = wdt;
+  for (int k = 0; k < ndim; ++k) { r->dims[k] = dims[k]; r->mode_order[k] = k; }
+  Timer t_total, t_norm;
+  t_total.start(c);
+  t_norm.start(c);
+  double nrm2 = 0.0, xmax = 0.0;
+  // Gram precision as in tucker_sthosvd: the mode-0 digit Gram by its
+  // bound from the row maxima, FP32-product Grams (and row-mode digit Grams,
+  // whose row maxima stay on the device) in FP64 below eps^2 / N = 1e-9
+  const bool small_eps = !ranks && prec != TUCKER_PREC_FP64 &&
+                         eps * eps / ndim < kMinFp32GramThreshold;
+  DevBuf rowmax;
+  {
+    const SlabView v0 = slab_view(ndim, dims, 0);
+    if (gram_kernel_for(prec, dt, v0, c->num_sms) == 5 && (((uintptr_t)x) & 15) == 0)
+      TK_TRY(dev_alloc(c, rowmax, sizeof(unsigned) * v0.I));
+  }
+  TK_TRY(do_norm(c, x, dt, numel(ndim, dims), &nrm2, &xmax, rowmax.as<unsigned>(), dims[0]));
+  t_norm.stop(c);
+  r->norm_x_sq = nrm2;
+  const double thr = ranks ? 0.0 : eps * eps * nrm2 / ndim;
+  r->threshold = thr;
+  DevBuf S;
+  TK_TRY(dev_alloc(c, S, sizeof(double) * imax * imax));
+  bool noconv = false;
+  // every factor from the Gram of X itself (Section 3.2)
+  for (int n = 0; n < ndim; ++n) {
+    const SlabView v = slab_view(ndim, dims, n);
+    Timer tmg, tme;
+    tmg.start(c);
+    const int gk = gram_kernel_for(prec, dt, v, c->num_sms);
+    tucker_prec gram_prec = prec;
+    int ndig = 3;
+    if (gk == 5 && n == 0 && rowmax.p) {
+      std::vector<unsigned> hb((size_t)v.I);
+      TK_CUDA(c, cudaMemcpyAsync(hb.data(), rowmax.p, sizeof(unsigned) * v.I,
+                                 cudaMemcpyDeviceToHost, c->stream));
+      TK_TRY(sync(c));
+      ndig = digit_gram_digits(hb.data(), v.I, v.L * v.Rt, thr);
+      if (ndig == 0) gram_prec = TUCKER_PREC_FP64;
+    } else if (small_eps && gk != 3) {
+      gram_prec = TUCKER_PREC_FP64;
+    }
+    TK_TRY(do_gram(c, x, dt, v, gram_prec, S.as<double>(), &r->gram_kernel[n], xmax, true,
+                   n == 0 ? rowmax.as<unsigned>() : nullptr, ndig > 0 ? ndig : 3));
+    tmg.stop(c);
+    tme.start(c);
+    DevBuf w, U;
+    int64_t R = 0;
+    double disc = 0.0;
+    TK_TRY(do_truncate(c, S.as<double>(), (int)v.I, thr, ranks ? (int)ranks[n] : 0, w, U, &R,
+                       &disc, &r->jacobi_sweeps[n], &r->eig_kernel[n], &noconv));
+    tme.stop(c);
+    r->ranks[n] = R;
+    r->discarded_sq[n] = disc;
+    r->eigvals[n] = w.as<double>();
+    w.release();
+    r->factors[n] = U.as<double>();
+    U.release();
+    TK_TRY(sync(c));
+    if (c->timing) {
+      r->ms_gram[n] = tmg.ms();
+      r->ms_eig[n] = tme.ms();
+    }
+  }
+  // core G = X x_0 U_0^T ... x_{N-1} U_{N-1}^T, the TTMs in the flop-minimal
+  // order of the shrinking chain; A = U_n^T is U_n's storage read row-major
+  int order[TUCKER_MAX_MODES];
+  order_search(ndim, dims, r->ranks, 0, order);
+  int64_t cur[TUCKER_MAX_MODES];
+  for (int k = 0; k < ndim; ++k) cur[k] = dims[k];
+  const void* y = x;
+  tucker_dtype ydt = dt;
+  DevBuf hold;
+  for (int s = 0; s < ndim; ++s) {
+    const int n = order[s];
+    const SlabView v = slab_view(ndim, cur, n);
+    int64_t nd[TUCKER_MAX_MODES];
+    for (int k = 0; k < ndim; ++k) nd[k] = cur[k];
+    nd[n] = r->ranks[n];
+    DevBuf z;
+    TK_TRY(dev_alloc(c, z, dtype_size(wdt) * numel(ndim, nd)));
+    Timer tmt;
+    tmt.start(c);
+    TK_TRY(do_ttm(c, y, ydt, v, r->factors[n], r->ranks[n], v.I, 1, prec, z.p, wdt,
+                  &r->ttm_kernel[n], s == 0 ? xmax : -1.0));
+    tmt.stop(c);
+    hold.reset();
+    hold.p = z.release();
+    hold.st = c->stream;
+    y = hold.p;
+    ydt = wdt;
+    cur[n] = r->ranks[n];
+    TK_TRY(sync(c));
+    if (c->timing) r->ms_ttm[n] = tmt.ms();
+  }
+  r->core = hold.release();
+  t_total.stop(c);
+  TK_TRY(sync(c));
+  if (c->timing) {
+    r->ms_norm = t_norm.ms();
+    r->ms_total = t_total.ms();
+  }
+  *out = r;
+  r = nullptr;
+  if (noconv) return set_err(c, TUCKER_ERR_EIG_NOCONV, "Jacobi reached the sweep cap in some mode");
+  return TUCKER_OK;
+}
+
+// ------------------------------------------------ pre- and post-processing
+
+tucker_status tucker_slice_stats(tucker_ctx* c, const void* x, tucker_dtype dt, int ndim,
+                                 const int64_t* dims, int mode, double* stats) {
+  if (!c) return TUCKER_ERR_INVALID;
+  if (!x || !stats || !check_dims(ndim, dims) || mode < 0 || mode >= ndim ||
+      (dt != TUCKER_F32 && dt != TUCKER_F64))
+    return set_err(c, TUCKER_ERR_INVALID, "tucker_slice_stats: bad argument");
+  const SlabView v = slab_view(ndim, dims, mode);
+  DevBuf work;
+  TK_TRY(dev_alloc(c, work, slice_stats_work_bytes(v.I)));
+  TK_CUDA(c, cudaMemsetAsync(c->d_words + 40, 0, sizeof(unsigned), c->stream));
+  TK_CUDA(c, launch_slice_stats(x, dt, v.L, v.I, v.Rt, work.p, stats, c->d_words + 40,
+                                c->num_sms, c->stream));
+  unsigned bad = 0;
+  TK_CUDA(c, cudaMemcpyAsync(&bad, c->d_words + 40, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                             c->stream));
+  TK_TRY(sync(c));
+  if (bad) return set_err(c, TUCKER_ERR_NONFINITE, "tensor holds NaN or Inf");
+  return TUCKER_OK;
+}
+
+tucker_status tucker_slice_transform(tucker_ctx* c, const void* x, tucker_dtype dt, int ndim,
+                                     const int64_t* dims, int mode, const double* shift,
+                                     const double* scale, int inverse, void* y) {
+  if (!c) return TUCKER_ERR_INVALID;
+  if (!x || !y || !shift || !scale || !check_dims(ndim, dims) || mode < 0 || mode >= ndim ||
+      (dt != TUCKER_F32 && dt != TUCKER_F64) || (inverse != 0 && inverse != 1))
+    return set_err(c, TUCKER_ERR_INVALID, "tucker_slice_transform: bad argument");
+  const SlabView v = slab_view(ndim, dims, mode);
+  TK_CUDA(c, launch_slice_apply(x, dt, v.L, v.I, v.Rt, shift, scale, inverse, y, c->num_sms,
+                                c->stream));
+  return sync(c);
+}
+
+tucker_status tucker_preprocess(tucker_ctx* c, const void* x, tucker_dtype dt, int ndim,
+                                const int64_t* dims, int mode, int method, double* shift,
+                                double* scale, void* y) {
+  if (!c) return TUCKER_ERR_INVALID;
+  if (!x || !y || !shift || !scale || !check_dims(ndim, dims) || mode < 0 || mode >= ndim ||
+      (dt != TUCKER_F32 && dt != TUCKER_F64) || (method != 0 && method != 1))
+    return set_err(c, TUCKER_ERR_INVALID, "tucker_preprocess: bad argument");
+  const int64_t I = dims[mode];
+  DevBuf st;
+  TK_TRY(dev_alloc(c, st, sizeof(double) * 6 * I));
+  TK_TRY(tucker_slice_stats(c, x, dt, ndim, dims, mode, st.as<double>()));
+  TK_CUDA(c, launch_slice_params(st.as<double>(), I, method, shift, scale, c->stream));
+  return tucker_slice_transform(c, x, dt, ndim, dims, mode, shift, scale, 0, y);
 }
 
 }  // extern "C"

@@ -56,8 +56,6 @@ namespace {
 using namespace tc;
 
 constexpr int BK = 16;                          // columns (K) per stage: one MMA step
-constexpr int NSTAGE = 3;
-constexpr int WIN = 64;                         // stages per exact window (1024 columns)
 constexpr int NPROD = 16;                       // one column of the stage each
 constexpr int EPI_WARP0 = 16;
 constexpr int MMA_WARP = EPI_WARP0;             // the first drain warp also issues the MMAs
@@ -66,17 +64,34 @@ constexpr int NTHREADS = (EPI_WARP0 + NEPI) * 32;   // 768: 24 warps, 80 registe
 // Stage layout, MN-major SW128 FP16: atoms of 64 mn x 8 k (1 KB).  Each
 // operand region is [k group of 8][atom], the digit planes side by side along
 // mn (plane q = atoms 2q, 2q + 1), so consecutive planes form one operand of
-// 256 rows: A (rows 128 ta..) holds d0, d1, d2, d2 / 2^7 (8 atoms per k
-// group), B (rows 128 tb..) holds d0, d1, d2 (6 atoms per k group).
+// 256 rows.
 constexpr uint32_t ATOM = 1024;
 constexpr uint32_t PLANE_STEP = 2 * ATOM;       // plane q starts at atom 2q
-constexpr uint32_t KG_A = 8 * ATOM, KG_B = 6 * ATOM;   // k-group strides
-constexpr uint32_t OFF_A = 0, OFF_B = 2 * KG_A;
-constexpr uint32_t STAGE_BYTES = 2 * KG_A + 2 * KG_B;   // 28 KB
 constexpr uint32_t PAIR_BYTES = 128 * 128 * 4;  // hi or lo tile, [col / 2][row][col % 2]
 constexpr uint32_t RSUM_BYTES = 16 * 128 * 4;   // remainder sums, [producer warp][row]
-constexpr uint32_t SMEM_BYTES = NSTAGE * STAGE_BYTES + 2 * PAIR_BYTES + RSUM_BYTES + 1024;
 constexpr int TILE_ELEMS = 128 * 128;
+
+// Per digit count: three 7-bit digits (all nine products, four weight
+// classes, windows of 1024 columns) or two (four products, three classes,
+// windows of 2048 columns: D1 sums two products of at most 2^12 per column,
+// 2048 of them stay within 2^24).  A (rows 128 ta..) holds the digit planes
+// and, with three digits, d2 / 2^7 as a fourth; B (rows 128 tb..) the digit
+// planes.
+template <int NDIG>
+struct Dig {
+  static constexpr int NPA = NDIG == 3 ? 4 : 2;              // planes of A
+  static constexpr int NPB = NDIG;                           // planes of B
+  static constexpr int NACC = NDIG == 3 ? 4 : 3;             // accumulators (weight classes)
+  static constexpr int NSTAGE = NDIG == 3 ? 3 : 5;
+  static constexpr int WIN = NDIG == 3 ? 64 : 128;           // stages per exact window
+  static constexpr uint32_t KG_A = 2 * NPA * ATOM, KG_B = 2 * NPB * ATOM;   // k-group strides
+  static constexpr uint32_t OFF_A = 0, OFF_B = 2 * KG_A;
+  static constexpr uint32_t STAGE_BYTES = 2 * KG_A + 2 * KG_B;   // 28 KB / 16 KB
+  static constexpr uint32_t SMEM_BYTES =
+      NSTAGE * STAGE_BYTES + 2 * PAIR_BYTES + RSUM_BYTES + 1024;
+  // squared last-digit remainders are summed in units of the last digit
+  static constexpr float RSCALE = NDIG == 3 ? 0x1p-28f : 0x1p-14f;
+};
 
 // Byte offset of (mn, k) (mn < 128, k < 16) in plane 0 of an operand region
 // with k-group stride kg.
@@ -90,10 +105,11 @@ __device__ __forceinline__ uint32_t instr_desc(int M, int N) {
          ((uint32_t)(M >> 4) << 24);
 }
 
-// Four 8-column loads (one per accumulator), then one wait.
-__device__ __forceinline__ void tmem_ld8x4(uint32_t taddr, uint32_t (&r)[4][8]) {
+// NA 8-column loads (one per accumulator), then one wait.
+template <int NA>
+__device__ __forceinline__ void tmem_ld8xn(uint32_t taddr, uint32_t (&r)[4][8]) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < NA; ++q)
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=r"(r[q][0]), "=r"(r[q][1]), "=r"(r[q][2]), "=r"(r[q][3]), "=r"(r[q][4]),
@@ -120,12 +136,13 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {    // a - b, one ro
   return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
 }
 
-// The digits of two scaled values x (|x| < 64): d0, d1, d2 and d2 / 2^7.
-// x + 1.5 * 2^23 lies in [2^23, 2^24), where the FP32 spacing is 1, so the add
-// rounds x to the nearest integer and the subtraction of the constant is exact.
-// R: also add r^2 to racc, r = 2^14 (x - d0 - d1 / 2^7 - d2 / 2^14) the exact
-// remainder of the last rounding.
-template <bool R>
+// The digits of two scaled values x (|x| < 64): d0, d1 and (NDIG == 3) d2
+// and d2 / 2^7.  x + 1.5 * 2^23 lies in [2^23, 2^24), where the FP32 spacing
+// is 1, so the add rounds x to the nearest integer and the subtraction of the
+// constant is exact.  R: also add r^2 to racc, r the exact remainder of the
+// last rounding in units of the last digit (|r| <= 1/2):
+// r = 2^14 (x - d0 - d1 / 2^7 - d2 / 2^14), or 2^7 (x - d0 - d1 / 2^7).
+template <int NDIG, bool R>
 __device__ __forceinline__ void digits2(float2 x, float2 (&d)[4], float2& racc) {
   const float2 M = make_float2(0x1.8p23f, 0x1.8p23f), NM = make_float2(-0x1.8p23f, -0x1.8p23f);
   const float2 B = make_float2(128.f, 128.f);
@@ -134,26 +151,30 @@ __device__ __forceinline__ void digits2(float2 x, float2 (&d)[4], float2& racc) 
   const float2 t1 = fma2(e, B, M);
   const float2 d1 = add2(t1, NM);                // round(128 e)
   const float2 f = fma2(e, B, sub2(M, t1));      // 128 e - d1, exact, |f| <= 1/2
+  d[0] = d0;
+  d[1] = d1;
+  if (NDIG == 2) {
+    if (R) racc = fma2(f, f, racc);
+    return;
+  }
   const float2 t2 = fma2(f, B, M);
   const float2 d2 = add2(t2, NM);                // round(128 f)
   if (R) {
     const float2 r = fma2(f, B, sub2(M, t2));    // 128 f - d2, exact, |r| <= 1/2
     racc = fma2(r, r, racc);
   }
-  d[0] = d0;
-  d[1] = d1;
   d[2] = d2;
   d[3] = mul2(d2, make_float2(0x1p-7f, 0x1p-7f));
 }
 
-// The digit planes of four values (scaled by s) as FP16 pairs: d0, d1, d2 and
-// (NP == 4) d2 / 2^7; R: squared remainders added to racc.
-template <int NP, bool R>
+// The digit planes of four values (scaled by s) as FP16 pairs: the first NP
+// of d0, d1, d2, d2 / 2^7; R: squared remainders added to racc.
+template <int NP, int NDIG, bool R>
 __device__ __forceinline__ void digits4(float4 v, const float2 (&s)[2], uint2 (&p)[4],
                                         float2 (&racc)[2]) {
   float2 a[4], b[4];
-  digits2<R>(mul2(make_float2(v.x, v.y), s[0]), a, racc[0]);
-  digits2<R>(mul2(make_float2(v.z, v.w), s[1]), b, racc[1]);
+  digits2<NDIG, R>(mul2(make_float2(v.x, v.y), s[0]), a, racc[0]);
+  digits2<NDIG, R>(mul2(make_float2(v.z, v.w), s[1]), b, racc[1]);
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
     const __half2 lo = __float22half2_rn(a[q]);
@@ -209,7 +230,7 @@ __device__ __forceinline__ void tile_of(int t, int& ta, int& tb) {
 // mode, where the extra instructions outweighed the latency they hid.)  NOPS == 1 (diagonal tile):
 // the squared last-digit remainders of the lane's rows go to rsum[slot][row]
 // (slot: the warp in column mode, lane % 16 in row mode).
-template <int NOPS, bool ROW>
+template <int NOPS, bool ROW, int NDIG>
 __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uint64_t* bar_full,
                                         uint64_t* bar_empty, const float* s_scale, int ta,
                                         int tb, int64_t k0, int64_t k1, int64_t gs0, int nst,
@@ -281,8 +302,10 @@ __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uin
     }
     ++ls;
   };
-  const uint32_t o_a = OFF_A + mn_off(mn, kcol, KG_A);
-  const uint32_t o_b = OFF_B + mn_off(mn, kcol, KG_B);
+  using D = Dig<NDIG>;
+  constexpr int NSTAGE = D::NSTAGE;
+  const uint32_t o_a = D::OFF_A + mn_off(mn, kcol, D::KG_A);
+  const uint32_t o_b = D::OFF_B + mn_off(mn, kcol, D::KG_B);
 #pragma unroll
   for (int u = 0; u < PF; ++u) load_next(ring[u]);
   bool go = true;
@@ -298,17 +321,18 @@ __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uin
       // split first, then wait for the slot: a freed slot only waits for
       // the stores (the split is off the MMA -> producer -> MMA hand-off)
       uint2 p[4], pb[4];
-      digits4<4, NOPS == 1>(v[0], sc[0], p, racc);
-      if (NOPS == 2) digits4<3, false>(v[NOPS - 1], sc[NOPS - 1], pb, racc);
+      digits4<D::NPA, NDIG, NOPS == 1>(v[0], sc[0], p, racc);
+      if (NOPS == 2) digits4<D::NPB, NDIG, false>(v[NOPS - 1], sc[NOPS - 1], pb, racc);
       if (s >= NSTAGE) {
         if (!mbar_wait(smem_u32(&bar_empty[slot]), eph, g.err)) { go = false; break; }
       }
-      uint8_t* st = smem + (size_t)slot * STAGE_BYTES;
+      uint8_t* st = smem + (size_t)slot * D::STAGE_BYTES;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) *reinterpret_cast<uint2*>(st + o_a + q * PLANE_STEP) = p[q];
+      for (int q = 0; q < D::NPA; ++q) *reinterpret_cast<uint2*>(st + o_a + q * PLANE_STEP) = p[q];
       if (NOPS == 2) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) *reinterpret_cast<uint2*>(st + o_b + q * PLANE_STEP) = pb[q];
+        for (int q = 0; q < D::NPB; ++q)
+          *reinterpret_cast<uint2*>(st + o_b + q * PLANE_STEP) = pb[q];
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
@@ -325,11 +349,14 @@ __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uin
   }
 }
 
-template <bool ROW>
+template <bool ROW, int NDIG>
 __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx(GramTcxArgs g) {
+  using D = Dig<NDIG>;
+  constexpr int NSTAGE = D::NSTAGE;
+  constexpr int WIN = D::WIN;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* hi = reinterpret_cast<float*>(smem + NSTAGE * STAGE_BYTES);
+  float* hi = reinterpret_cast<float*>(smem + NSTAGE * D::STAGE_BYTES);
   float* lo = hi + TILE_ELEMS;
   float2* hi2 = reinterpret_cast<float2*>(hi);
   float2* lo2 = reinterpret_cast<float2*>(lo);
@@ -381,11 +408,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx(GramTcxArgs g) {
   if (warp < NPROD) {
     // ---------------- producers: X -> digit planes of A (and B)
     if (diag)
-      produce<1, ROW>(g, smem, bar_full, bar_empty, s_scale, ta, tb, k0, k1, k0, nst, warp, lane,
-                      rsum);
+      produce<1, ROW, NDIG>(g, smem, bar_full, bar_empty, s_scale, ta, tb, k0, k1, k0, nst, warp,
+                            lane, rsum);
     else
-      produce<2, ROW>(g, smem, bar_full, bar_empty, s_scale, ta, tb, k0, k1, k0, nst, warp, lane,
-                      rsum);
+      produce<2, ROW, NDIG>(g, smem, bar_full, bar_empty, s_scale, ta, tb, k0, k1, k0, nst, warp,
+                            lane, rsum);
   } else {
     // ---------------- drain warps: exact window sums -> FP32 pairs.  Lane 0
     // of warp MMA_WARP first issues the window's MMAs (nine per stage, one
@@ -404,30 +431,40 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx(GramTcxArgs g) {
         if (issuer && ok) {
           const uint32_t id128 = instr_desc(128, 128), id256 = instr_desc(128, 256);
           const uint32_t sbase = smem_u32(smem);
-          const uint32_t boff = diag ? OFF_A : OFF_B, bkg = diag ? KG_A : KG_B;
+          const uint32_t boff = diag ? D::OFF_A : D::OFF_B, bkg = diag ? D::KG_A : D::KG_B;
           const int s_end = min(nst, (w + 1) * WIN);
           if (w >= 1) ok = mbar_wait(smem_u32(&bar_acce), (w - 1) & 1, g.err);
           for (int s = w * WIN; s < s_end && ok; ++s) {
             ok = mbar_wait(smem_u32(&bar_full[slot]), fph, g.err);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t st = sbase + (uint32_t)slot * STAGE_BYTES;
+            const uint32_t st = sbase + (uint32_t)slot * D::STAGE_BYTES;
             uint64_t a[4], b[3];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) a[u] = smem_desc(st + OFF_A + u * PLANE_STEP, ATOM, KG_A);
+            for (int u = 0; u < D::NPA; ++u)
+              a[u] = smem_desc(st + D::OFF_A + u * PLANE_STEP, ATOM, D::KG_A);
 #pragma unroll
-            for (int u = 0; u < 3; ++u) b[u] = smem_desc(st + boff + u * PLANE_STEP, ATOM, bkg);
+            for (int u = 0; u < D::NPB; ++u) b[u] = smem_desc(st + boff + u * PLANE_STEP, ATOM, bkg);
             // b[0] spans planes d0, d1 as one 256-row operand; tensor memory
-            // holds D0 | D1 | D2 | D3 at columns 0 | 128 | 256 | 384, so
+            // holds D0 | D1 | D2 (| D3) at columns 0 | 128 | 256 (| 384), so
             // a_q x [d0 | d1] lands on two adjacent accumulators.  Each
             // accumulator's first product of a window overwrites (fresh).
             const uint32_t fresh = s == w * WIN ? 0u : 1u;
-            tc_mma(tmem + 0u, a[0], b[0], id256, fresh);      // D0 += a0 d0', D1 += a0 d1'
-            tc_mma(tmem + 256u, a[0], b[2], id128, fresh);    // D2 += a0 d2'
-            tc_mma(tmem + 128u, a[1], b[0], id256, 1u);       // D1 += a1 d0', D2 += a1 d1'
-            tc_mma(tmem + 384u, a[1], b[2], id128, fresh);    // D3 += a1 d2'
-            tc_mma(tmem + 256u, a[2], b[0], id256, 1u);       // D2 += a2 d0', D3 += a2 d1'
-            tc_mma(tmem + 384u, a[3], b[2], id128, 1u);       // D3 += (d2 / 2^7) d2'
+            if (NDIG == 3) {
+              tc_mma(tmem + 0u, a[0], b[0], id256, fresh);      // D0 += a0 d0', D1 += a0 d1'
+              tc_mma(tmem + 256u, a[0], b[2], id128, fresh);    // D2 += a0 d2'
+              tc_mma(tmem + 128u, a[1], b[0], id256, 1u);       // D1 += a1 d0', D2 += a1 d1'
+              tc_mma(tmem + 384u, a[1], b[2], id128, fresh);    // D3 += a1 d2'
+              tc_mma(tmem + 256u, a[2], b[0], id256, 1u);       // D2 += a2 d0', D3 += a2 d1'
+              tc_mma(tmem + 384u, a[3], b[2], id128, 1u);       // D3 += (d2 / 2^7) d2'
+            } else if (fresh) {
+              tc_mma(tmem + 0u, a[0], b[0], id256, 1u);         // D0 += a0 d0', D1 += a0 d1'
+              tc_mma(tmem + 128u, a[1], b[0], id256, 1u);       // D1 += a1 d0', D2 += a1 d1'
+            } else {                                            // first stage of a window
+              tc_mma(tmem + 0u, a[0], b[0], id256, 0u);         // D0 = a0 d0', D1 = a0 d1'
+              tc_mma(tmem + 256u, a[1], b[1], id128, 0u);       // D2 = a1 d1'
+              tc_mma(tmem + 128u, a[1], b[0], id128, 1u);       // D1 += a1 d0'
+            }
             tc_commit(smem_u32(&bar_empty[slot]));
             if (++slot == NSTAGE) { slot = 0; fph ^= 1u; }
           }
@@ -444,10 +481,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx(GramTcxArgs g) {
       for (int cc = 0; cc < 64; cc += 8) {
         uint32_t r[4][8];
         const uint32_t col = (uint32_t)(c0 + cc);
-        tmem_ld8x4(lane_base + col, r);
+        tmem_ld8xn<D::NACC>(lane_base + col, r);
 #pragma unroll
         for (int j = 0; j < 8; j += 2) {
-          // the four parts D0, D1 / 2^7, D2 / 2^14, D3 / 2^21 (each scaling
+          // the parts D0, D1 / 2^7, D2 / 2^14 (, D3 / 2^21) (each scaling
           // exact) enter the pair one by one (TwoSum each): nothing is
           // rounded before the compensated sum; columns j, j + 1 packed
           const int idx = ((c0 + cc + j) >> 1) * 128 + row;
@@ -457,12 +494,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx(GramTcxArgs g) {
                                  make_float2(0x1p-7f, 0x1p-7f));
           const float2 p2 = mul2(make_float2(__uint_as_float(r[2][j]), __uint_as_float(r[2][j + 1])),
                                  make_float2(0x1p-14f, 0x1p-14f));
-          const float2 p3 = mul2(make_float2(__uint_as_float(r[3][j]), __uint_as_float(r[3][j + 1])),
-                                 make_float2(0x1p-21f, 0x1p-21f));
           two_sum2(h, l, p0);
           two_sum2(h, l, p1);
           two_sum2(h, l, p2);
-          two_sum2(h, l, p3);
+          if (D::NACC == 4) {
+            const float2 p3 =
+                mul2(make_float2(__uint_as_float(r[3][j]), __uint_as_float(r[3][j + 1])),
+                     make_float2(0x1p-21f, 0x1p-21f));
+            two_sum2(h, l, p3);
+          }
           hi2[idx] = h;
           lo2[idx] = l;
         }
@@ -491,7 +531,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx(GramTcxArgs g) {
     if (diag && c == rr) {
       double r2 = 0.0;
       for (int w = 0; w < NPROD; ++w) r2 += (double)rsum[w * 128 + rr];
-      v -= r2 * 0x1p-28;
+      v -= r2 * (double)D::RSCALE;
     }
     pt[idx] = v;
   }
@@ -566,10 +606,12 @@ __global__ void k_rowmax_slab(const float* __restrict__ y, int64_t L, int64_t I,
 }  // namespace
 
 // Row-mode views whose last l-block is mostly padding stay on the FP32 Gram:
-// the l-blocks of a slab may hold at most 25 % zero fill.
+// the l-blocks of a slab may hold at most 25 % zero fill.  Column-mode views
+// from 64 rows up (one diagonal tile, its rows past I zero), row-mode views
+// from 128.
 GramPlan plan_gram_tcx(int64_t L, int64_t I, int64_t Rt, int num_sms) {
   GramPlan p;
-  if (I < 128 || I > 2048 || L < 1 || Rt < 1) return p;
+  if (I < (L == 1 ? 64 : 128) || I > 2048 || L < 1 || Rt < 1) return p;
   int64_t stages;
   if (L == 1) {
     if ((I % 4) != 0 || Rt < 4 * BK) return p;
@@ -593,15 +635,23 @@ GramPlan plan_gram_tcx(int64_t L, int64_t I, int64_t Rt, int num_sms) {
   return p;
 }
 
+template <bool ROW, int NDIG>
+cudaError_t run_gram_tcx(const GramTcxArgs& a, int nctas, cudaStream_t st) {
+  constexpr uint32_t smem = Dig<NDIG>::SMEM_BYTES;
+  cudaError_t e = cudaFuncSetAttribute(k_gram_tcx<ROW, NDIG>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_gram_tcx<ROW, NDIG><<<(unsigned)nctas, NTHREADS, smem, st>>>(a);
+  return cudaSuccess;
+}
+
 cudaError_t launch_gram_tcx(const float* y, int64_t L, int64_t I, int64_t Rt, const GramPlan& p,
                             const unsigned* rowmax_bits, void* scratch, unsigned* err, double* S,
-                            cudaStream_t st) {
-  if (p.nctas <= 0 || (L == 1 && ((uintptr_t)y & 15) != 0) || ((uintptr_t)y & 3) != 0)
+                            cudaStream_t st, int ndig) {
+  if (p.nctas <= 0 || (L == 1 && ((uintptr_t)y & 15) != 0) || ((uintptr_t)y & 3) != 0 ||
+      (ndig != 2 && ndig != 3))
     return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(L == 1 ? k_gram_tcx<false> : k_gram_tcx<true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)SMEM_BYTES);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   double* part = static_cast<double*>(scratch);
   float* scale = reinterpret_cast<float*>(part + (size_t)p.nctas * TILE_ELEMS);
   k_gram_tcx_scales<<<(unsigned)((I + 255) / 256), 256, 0, st>>>(rowmax_bits, I, scale);
@@ -618,9 +668,10 @@ cudaError_t launch_gram_tcx(const float* y, int64_t L, int64_t I, int64_t Rt, co
   a.part = part;
   a.err = err;
   if (L == 1)
-    k_gram_tcx<false><<<(unsigned)p.nctas, NTHREADS, SMEM_BYTES, st>>>(a);
+    e = ndig == 3 ? run_gram_tcx<false, 3>(a, p.nctas, st) : run_gram_tcx<false, 2>(a, p.nctas, st);
   else
-    k_gram_tcx<true><<<(unsigned)p.nctas, NTHREADS, SMEM_BYTES, st>>>(a);
+    e = ndig == 3 ? run_gram_tcx<true, 3>(a, p.nctas, st) : run_gram_tcx<true, 2>(a, p.nctas, st);
+  if (e != cudaSuccess) return e;
   const int64_t tot = I * I;
   k_gram_tcx_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, p.ntiles, p.ksplit, I,
                                                                    scale, S);

@@ -169,6 +169,7 @@ struct JacobiArgs {
   int* info;          // [0] sweeps, [1] converged, [2] final A buffer, [3] dummy position
   const double* fro2; // ||S||_F^2
   GridBarrier bar;
+  unsigned long long poll_limit;   // polls before a grid barrier gives up
   int n, np, max_sweeps, vwarps;
   double tol_rel, tol_abs;
 };
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
       count_rotation(a.counts, 0, a.max_sweeps);
     reinterpret_cast<double2*>(rot0)[j] = make_double2(c, s);
   }
-  if (!grid_sync(a.bar, gen)) return;
+  if (!grid_sync(a.bar, gen, a.poll_limit)) return;
 
   for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
     // the sweep's step-0 rotations into the log
@@ -323,7 +324,7 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
       if (dpos >= 0) dpos = next_pos(dpos, np);
       cur ^= 1;
       rc ^= 1;
-      if (!grid_sync(a.bar, gen)) return;
+      if (!grid_sync(a.bar, gen, a.poll_limit)) return;
     }
     sweeps = sweep + 1;
     // replay the sweep's rotations on the rows of V (V' = V J_0 ... J_{np-2})
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(256, 1) k_jacobi(JacobiArgs a) {
         __syncwarp();
       }
     }
-    if (!grid_sync(a.bar, gen)) return;
+    if (!grid_sync(a.bar, gen, a.poll_limit)) return;
     if (ld_acquire_u32(&a.counts[sweep]) == 0u) { converged = 1; break; }
   }
   if (gtid == 0) {
@@ -498,7 +499,8 @@ int jacobi_max_n() { return 8192; }
 
 cudaError_t launch_jacobi(const double* S, int n, double* work, const double* fro2, unsigned* words,
                           int max_sweeps, double tol_rel, double tol_abs, int num_sms,
-                          double* w_out, double* V_out, int* info_dev, cudaStream_t st) {
+                          double* w_out, double* V_out, int* info_dev, cudaStream_t st,
+                          unsigned long long poll_limit) {
   const int np = n + (n & 1);
   const JacobiLayout L = jacobi_layout(n, work);
   // words: [0] barrier count, [1] barrier gen, [2] err, [3..] per-sweep counts
@@ -514,6 +516,7 @@ cudaError_t launch_jacobi(const double* S, int n, double* work, const double* fr
   a.info = info_dev;
   a.fro2 = fro2;
   a.bar = GridBarrier{words, words + 1, words + 2};
+  a.poll_limit = poll_limit;
   a.n = n; a.np = np; a.max_sweeps = max_sweeps;
   a.tol_rel = tol_rel; a.tol_abs = tol_abs;
   a.vwarps = vpass_warps(np);

@@ -28,14 +28,17 @@ struct GramPlan {
   size_t scratch_bytes = 0;
 };
 // ---- tensor-core Gram of a slab view on exact digit products
-// (gram_tcx.cu): plan.nctas == 0 when it does not apply (128 <= I <= 2048;
+// (gram_tcx.cu): plan.nctas == 0 when it does not apply (I <= 2048;
+// column mode 64 <= I, row mode 128 <= I;
 // column mode L == 1 with I % 4 == 0; row mode L > 1 with l-blocks of 16 at
 // most 25 % zero fill); rowmax_bits: FP32 bits of the row maxima, from
 // launch_sumsq_rowmax (column mode) or launch_rowmax_slab (row mode)
 GramPlan plan_gram_tcx(int64_t L, int64_t I, int64_t Rt, int num_sms);
+// ndig: 3 (three 7-bit digits, all nine products) or 2 (two digits, four
+// products; representation error 2^-13 instead of 2^-20 of the row maximum)
 cudaError_t launch_gram_tcx(const float* y, int64_t L, int64_t I, int64_t Rt, const GramPlan& p,
                             const unsigned* rowmax_bits, void* scratch, unsigned* err, double* S,
-                            cudaStream_t st);
+                            cudaStream_t st, int ndig);
 cudaError_t launch_rowmax_slab(const float* y, int64_t L, int64_t I, int64_t Rt, int num_sms,
                                unsigned* rowmax_bits, cudaStream_t st);
 
@@ -100,7 +103,8 @@ cudaError_t launch_ttm_tc_row(const float* y, int64_t L, int64_t I, int64_t Rt, 
 size_t jacobi_work_bytes(int n);
 cudaError_t launch_jacobi(const double* S, int n, double* work, const double* fro2, unsigned* words,
                           int max_sweeps, double tol_rel, double tol_abs, int num_sms,
-                          double* w_out, double* V_out, int* info_dev, cudaStream_t st);
+                          double* w_out, double* V_out, int* info_dev, cudaStream_t st,
+                          unsigned long long poll_limit);
 cudaError_t launch_eig_finish(int n, double* work, const int* info_host, int* info_dev,
                               double* w_out, double* V_out, cudaStream_t st);
 cudaError_t launch_rank_cut(const double* w, int n, double thr, int fixed_R, int64_t* out_R,
@@ -138,8 +142,12 @@ size_t eig_wy_doubles(int n);
 // team_size * n / ... as planned; probs_host is the host copy of the
 // descriptors (it sets the launch shape and each team's shared-memory rows).
 // bar_counts: `count` zeroed words (one barrier per team), err: error word.
+// poll_limit: polls before a team's grid barrier gives up (sets *err)
 cudaError_t launch_tridiag(const EigProblem* probs_dev, EigProblem* probs_host, int count,
-                           unsigned* bar_counts, unsigned* err, cudaStream_t st);
+                           unsigned* bar_counts, unsigned* err, cudaStream_t st,
+                           unsigned long long poll_limit);
+// y[i] = the tridiagonal solver's FP64 reciprocal of x[i] (diagnostics)
+cudaError_t launch_rcp64_probe(const double* x, double* y, int64_t n, cudaStream_t st);
 // total_eigs: the sum of n over the problems (sets the lanes per eigenvalue)
 cudaError_t launch_bisect(const EigProblem* probs_dev, int count, int nmax, int total_eigs,
                           int num_sms, cudaStream_t st);
@@ -154,5 +162,21 @@ cudaError_t launch_rank_cut_batched(const EigProblem* probs_dev, int count, cons
                                     cudaStream_t st);
 int zgram_batched_max_r();
 cudaError_t launch_zgram_batched(const EigProblem* probs_dev, int count, cudaStream_t st);
+
+// ---- pre- and post-processing of Section 3.5 (prepost.cu)
+// Statistics of every hyperslice of the slab view (Rt, I, L): stats[6 i + k]
+// = mean, population standard deviation, max, min, 1-norm, 2-norm (FP64);
+// work: slice_stats_work_bytes(I); *bad |= 1 when a statistic is not finite
+size_t slice_stats_work_bytes(int64_t I);
+cudaError_t launch_slice_stats(const void* x, tucker_dtype dt, int64_t L, int64_t I, int64_t Rt,
+                               void* work, double* stats, unsigned* bad, int num_sms,
+                               cudaStream_t st);
+// shift/scale of a method (0 standardization, 1 max rescaling) from stats
+cudaError_t launch_slice_params(const double* stats, int64_t I, int method, double* shift,
+                                double* scale, cudaStream_t st);
+// y = (x - shift_i) * scale_i, or (inverse) x / scale_i + shift_i; y may be x
+cudaError_t launch_slice_apply(const void* x, tucker_dtype dt, int64_t L, int64_t I, int64_t Rt,
+                               const double* shift, const double* scale, int inverse, void* y,
+                               int num_sms, cudaStream_t st);
 
 }  // namespace tk

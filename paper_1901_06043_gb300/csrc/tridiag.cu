@@ -117,7 +117,8 @@ __device__ void house(double* vx, int k2, int n, double* red, double& tau, doubl
 // bounded barrier.  P.srows: the CTA's own rows live in shared memory;
 // otherwise they are read and written in place in A (L2-resident).
 __global__ void __launch_bounds__(TNT, 1) k_tridiag(const EigProblem* probs, int count,
-                                                    unsigned* bar_counts, unsigned* err) {
+                                                    unsigned* bar_counts, unsigned* err,
+                                                    unsigned long long poll_limit) {
   extern __shared__ __align__(16) double tsm[];
   int pidx = 0;
   while (pidx + 1 < count && probs[pidx + 1].team_off <= (int)blockIdx.x) ++pidx;
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(TNT, 1) k_tridiag(const EigProblem* probs, int
     if (threadIdx.x == 0) xv[c] = s;
   }
   { double* t = vk; vk = vn; vn = t; }
-  if (G > 1) { if (!grid_sync(bar, gen, 1ull << 24, (unsigned)G)) return; } else __syncthreads();
+  if (G > 1) { if (!grid_sync(bar, gen, poll_limit, (unsigned)G)) return; } else __syncthreads();
 
   // ---- phases 0 .. n-3
   for (int k = 0; k <= n - 3; ++k) {
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(TNT, 1) k_tridiag(const EigProblem* probs, int
     if (threadIdx.x == 0) xv[nb * G + c] = sp;
     { double* t = vk; vk = vn; vn = t; }
     tau_k = tau_n;
-    if (G > 1) { if (!grid_sync(bar, gen, 1ull << 24, (unsigned)G)) return; } else __syncthreads();
+    if (G > 1) { if (!grid_sync(bar, gen, poll_limit, (unsigned)G)) return; } else __syncthreads();
   }
 }
 
@@ -444,6 +445,11 @@ __device__ __forceinline__ double rcp64(double x) {
   r = fma(r, e, r);
   e = fma(-x, r, 1.0);
   return fma(r, e, r);
+}
+
+__global__ void k_rcp64_probe(const double* x, double* y, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = rcp64(x[i]);
 }
 
 __global__ void k_invit(const EigProblem* probs, int nprob) {
@@ -888,7 +894,8 @@ void tridiag_batch_teams(const int* n, int count, int num_sms, int* team) {
 }
 
 cudaError_t launch_tridiag(const EigProblem* probs_dev, EigProblem* probs_host, int count,
-                           unsigned* bar_counts, unsigned* err, cudaStream_t st) {
+                           unsigned* bar_counts, unsigned* err, cudaStream_t st,
+                           unsigned long long poll_limit) {
   int nmax = 0, grid = 0, multi = 0;
   size_t rows_max = 0;
   for (int p = 0; p < count; ++p) {
@@ -913,10 +920,11 @@ cudaError_t launch_tridiag(const EigProblem* probs_dev, EigProblem* probs_host, 
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag, TNT, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-    void* args[] = {(void*)&probs_dev, (void*)&count, (void*)&bar_counts, (void*)&err};
+    void* args[] = {(void*)&probs_dev, (void*)&count, (void*)&bar_counts, (void*)&err,
+                    (void*)&poll_limit};
     return cudaLaunchCooperativeKernel((void*)k_tridiag, dim3(grid), dim3(TNT), args, smem, st);
   }
-  k_tridiag<<<grid, TNT, smem, st>>>(probs_dev, count, bar_counts, err);
+  k_tridiag<<<grid, TNT, smem, st>>>(probs_dev, count, bar_counts, err, poll_limit);
   return cudaGetLastError();
 }
 
@@ -970,6 +978,12 @@ cudaError_t launch_backtransform(const EigProblem* probs_dev, int count, int tot
   if (e != cudaSuccess) return e;
   k_backtransform<<<total_vectors, 256, smem, st>>>(probs_dev, count);
   count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rcp64_probe(const double* x, double* y, int64_t n, cudaStream_t st) {
+  if (n > 0) k_rcp64_probe<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, n);
+  count_launches(n > 0 ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@ STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "NONFINITE", 4: "EIG_NOCONV", 5: "
 F32, F64 = 0, 1
 PREC = {"fp64": 0, "fp32": 1, "mixed": 2, "tensor": 3}
 OPT_TIMING, OPT_MAX_SWEEPS, OPT_JACOBI_TOL, OPT_EIG_SOLVER = 1, 2, 3, 4
+OPT_BARRIER_POLLS, OPT_MEM_LIMIT, OPT_GRAM_DIGITS = 5, 6, 7
 EIG_SOLVER = {"auto": 0, "jacobi": 1, "tridiag": 2}
 
 EXPORTS = ["tucker_create", "tucker_destroy", "tucker_last_error", "tucker_set_option",
@@ -28,7 +29,11 @@ EXPORTS = ["tucker_create", "tucker_destroy", "tucker_last_error", "tucker_set_o
            "tucker_reconstruct",
            "tucker_multi_ttm", "tucker_ttm_order", "tucker_norm_sq", "tucker_gram",
            "tucker_eig", "tucker_eig_trunc", "tucker_rank_cut", "tucker_ttm",
-           "tucker_kernel_launches", "tucker_gram_noalloc"]
+           "tucker_kernel_launches", "tucker_gram_noalloc", "tucker_hosvd",
+           "tucker_sthosvd_order", "tucker_slice_stats", "tucker_slice_transform",
+           "tucker_preprocess", "tucker_selftest_rcp64"]
+STATS = ("mean", "std", "max", "min", "norm1", "norm2")
+PRE_METHOD = {"standardize": 0, "max": 1}
 
 
 class TuckerError(RuntimeError):
@@ -106,6 +111,13 @@ def lib():
         L.tucker_kernel_launches.argtypes = []
         L.tucker_kernel_launches.restype = ctypes.c_uint64
         L.tucker_gram_noalloc.argtypes = [vp, c_int, c_int, i64p, c_int, c_int, vp, vp]
+        L.tucker_hosvd.argtypes = [vp, vp, c_int, c_int, i64p, ctypes.c_double, i64p, c_int,
+                                   ctypes.POINTER(ctypes.POINTER(CResult))]
+        L.tucker_sthosvd_order.argtypes = [c_int, i64p, i64p, ctypes.POINTER(c_int)]
+        L.tucker_selftest_rcp64.argtypes = [vp, vp, ctypes.c_int64, vp]
+        L.tucker_slice_stats.argtypes = [vp, vp, c_int, c_int, i64p, c_int, vp]
+        L.tucker_slice_transform.argtypes = [vp, vp, c_int, c_int, i64p, c_int, vp, vp, c_int, vp]
+        L.tucker_preprocess.argtypes = [vp, vp, c_int, c_int, i64p, c_int, c_int, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -168,7 +180,7 @@ class Result:
         self.discarded = [r.discarded_sq[k] for k in range(N)]
         self.sweeps = [r.jacobi_sweeps[k] for k in range(N)]
         names = {0: "simt-fp64", 1: "simt-fp32", 2: "tcgen05", 3: "small-fp64", 4: "simt-fp32c",
-                 5: "tcgen05-x3"}
+                 5: "tcgen05-x3", 6: "tcgen05-x2"}
         self.gram_kernel = [names.get(r.gram_kernel[k], "?") for k in range(N)]
         self.ttm_kernel = [names.get(r.ttm_kernel[k], "?") for k in range(N)]
         self.eig_kernel = [{0: "jacobi", 1: "tridiag"}.get(r.eig_kernel[k], "?") for k in range(N)]
@@ -278,6 +290,67 @@ class Context:
             lib().tucker_result_destroy(out)   # EIG_NOCONV still returns a result
         self._check(st)
         return Result(self, out)
+
+    def hosvd(self, x, dims, eps=None, ranks=None, prec="fp64"):
+        """HOSVD (tucker_hosvd): every factor from the Gram of x itself."""
+        _check_dev(x, "x")
+        out = ctypes.POINTER(CResult)()
+        st = lib().tucker_hosvd(
+            self._c, ctypes.c_void_p(x.data_ptr()), _dtype_code(x), len(dims), _i64(dims),
+            float(eps) if eps is not None else 0.0,
+            _i64(ranks) if ranks is not None else None, PREC[prec], ctypes.byref(out))
+        if st != 0 and out:
+            lib().tucker_result_destroy(out)
+        self._check(st)
+        return Result(self, out)
+
+    def slice_stats(self, x, dims, mode):
+        """(I_n, 6) FP64 device tensor of hyperslice statistics (STATS order)."""
+        import torch
+        _check_dev(x, "x")
+        I = int(dims[mode])
+        st = torch.empty((I, 6), dtype=torch.float64, device=x.device)
+        self._check(lib().tucker_slice_stats(self._c, ctypes.c_void_p(x.data_ptr()),
+                                             _dtype_code(x), len(dims), _i64(dims), int(mode),
+                                             ctypes.c_void_p(st.data_ptr())))
+        return st
+
+    def slice_transform(self, x, dims, mode, shift, scale, inverse=False, out=None):
+        """y = (x - shift_i) * scale_i per mode-`mode` hyperslice (inverse:
+        x / scale_i + shift_i); out may be x (in place)."""
+        import torch
+        _check_dev(x, "x")
+        I = int(dims[mode])
+        for t, nm in ((shift, "shift"), (scale, "scale")):
+            _check_dev(t, nm)
+            if t.dtype != torch.float64 or t.numel() < I:
+                raise ValueError(f"{nm} must hold {I} float64 values")
+        y = torch.empty_like(x) if out is None else out
+        _check_dev(y, "out")
+        if y.dtype != x.dtype or y.numel() != x.numel():
+            raise ValueError("out must match x in dtype and size")
+        self._check(lib().tucker_slice_transform(
+            self._c, ctypes.c_void_p(x.data_ptr()), _dtype_code(x), len(dims), _i64(dims),
+            int(mode), ctypes.c_void_p(shift.data_ptr()), ctypes.c_void_p(scale.data_ptr()),
+            1 if inverse else 0, ctypes.c_void_p(y.data_ptr())))
+        return y
+
+    def preprocess(self, x, dims, mode, method="standardize", out=None):
+        """Section 3.5 pre-processing; returns (y, shift, scale)."""
+        import torch
+        _check_dev(x, "x")
+        I = int(dims[mode])
+        shift = torch.empty(I, dtype=torch.float64, device=x.device)
+        scale = torch.empty(I, dtype=torch.float64, device=x.device)
+        y = torch.empty_like(x) if out is None else out
+        _check_dev(y, "out")
+        if y.dtype != x.dtype or y.numel() != x.numel():
+            raise ValueError("out must match x in dtype and size")
+        self._check(lib().tucker_preprocess(
+            self._c, ctypes.c_void_p(x.data_ptr()), _dtype_code(x), len(dims), _i64(dims),
+            int(mode), PRE_METHOD[method], ctypes.c_void_p(shift.data_ptr()),
+            ctypes.c_void_p(scale.data_ptr()), ctypes.c_void_p(y.data_ptr())))
+        return y, shift, scale
 
     def sthosvd_batched(self, xs, dims_list, eps, prec="fp64"):
         """ST-HOSVD of several tensors at once (tucker_sthosvd_batched);
@@ -423,6 +496,31 @@ def ttm_order(core_dims, out_dims, objective="flops"):
     if st != 0:
         raise TuckerError(st, "tucker_ttm_order")
     return tuple(out[k] for k in range(N))
+
+
+def sthosvd_order(dims, ranks):
+    """Flop-minimal ST-HOSVD mode order for given ranks (host-only C call)."""
+    N = len(dims)
+    out = (ctypes.c_int * MAX_MODES)()
+    st = lib().tucker_sthosvd_order(N, _i64(dims), _i64(ranks), out)
+    if st != 0:
+        raise TuckerError(st, "tucker_sthosvd_order")
+    return tuple(out[k] for k in range(N))
+
+
+def selftest_rcp64(x):
+    """The tridiagonal eigensolver's FP64 reciprocal of every entry of the
+    FP64 device tensor x (diagnostics)."""
+    import torch
+    _check_dev(x, "x")
+    if x.dtype != torch.float64:
+        raise ValueError("x must be float64")
+    y = torch.empty_like(x)
+    st = lib().tucker_selftest_rcp64(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                     x.numel(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != 0:
+        raise TuckerError(st, "tucker_selftest_rcp64")
+    return y
 
 
 def kernel_launches():

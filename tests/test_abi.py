@@ -48,3 +48,28 @@ def test_ttm_order_host_call_matches_oracle():
         out = (500, 500, 500, 1, 1)[:len(core)] if len(core) == 5 else tuple(c + 3 for c in core)
         assert tucker.ttm_order(core, out, "flops") == oracle.best_order(core, out, "flops")[0]
         assert tucker.ttm_order(core, out, "memory") == oracle.best_order(core, out, "memory")[0]
+
+
+def test_sthosvd_order_host_call_matches_oracle():
+    """tucker_sthosvd_order is host-only C code: its order costs exactly the
+    oracle's exhaustive minimum of the Section 6 flop count."""
+    import math
+
+    import numpy as np
+
+    import oracle
+    from paper_1901_06043_gb300 import tucker
+    rng = np.random.default_rng(4)
+    cases = [((500, 500, 500, 11, 8), (54, 54, 54, 11, 6)), ((100, 100, 100), (100, 1, 100)),
+             ((9,), (3,))]
+    for _ in range(60):
+        N = int(rng.integers(2, 6))
+        dims = tuple(int(v) for v in rng.integers(2, 80, size=N))
+        cases.append((dims, tuple(int(rng.integers(1, d + 1)) for d in dims)))
+    for dims, ranks in cases:
+        got = tucker.sthosvd_order(dims, ranks)
+        assert sorted(got) == list(range(len(dims)))
+        _, best = oracle.best_sthosvd_order(dims, ranks)
+        assert math.isclose(oracle.sthosvd_flops(dims, ranks, got), best, rel_tol=1e-12)
+    with pytest.raises(tucker.TuckerError):
+        tucker.sthosvd_order((5, 4), (6, 1))

@@ -4,14 +4,17 @@ configuration bench.py times (the same library calls at the same shapes).
 - 200x200x200x50 FP64 (3.2 GB): the whole FP64 ST-HOSVD against the oracle,
   which finishes in seconds at this size; reconstruction of the
   200x200x200x1 slice by multi-TTM.
-- 256x256x256x11x32 FP32 (23 GB) at eps 1e-2, 1e-4, 1e-5: the mixed path
-  against the FP64 GPU path (same ranks, errors within the bound), and
-  sampled mode-0 Gram entries against the oracle.
-- 500x500x500x11x8 FP32 (44 GB), eps 1e-4: sampled mode-0 Gram entries of
-  both precisions against the oracle, mixed ranks equal to the FP64 path's,
-  Cor. 1 (error estimate from the discarded eigenvalues), and sampled
-  entries of the 500x500x500x11x1 reconstruction against the oracle's
-  multi-TTM of the same core and factors.
+- 256x256x256x11x32 FP32 (23 GB) at eps 1e-2, 1e-4, 1e-5 and
+  500x500x500x11x8 FP32 (44 GB) at eps 1e-4: both GPU paths (FP64 and
+  mixed) against the oracle's ST-HOSVD of the same tensor, run over pieces
+  of the last mode on the host (oracle.sthosvd_chunked: the mode-0 Gram
+  summed over the pieces, the mode-0 TTM applied piece by piece, then the
+  usual Algorithm 1); sampled mode-0 Gram entries of the FP32, FP64 and
+  exact-digit (mixed) Grams against the oracle's Gram of the sampled rows.
+- 500x500x500x11x8 also: Cor. 1 (error estimate from the discarded
+  eigenvalues against the explicit error of the full reconstruction), and
+  sampled entries of the 500x500x500x11x1 reconstruction against the
+  oracle's multi-TTM of the same core and factors.
 
 Inputs follow the synthetic recipe of the workloads (synth.tucker_torch).
 """
@@ -61,6 +64,85 @@ def _check_gram_samples(S, samples, rel):
         assert abs(S[j, j] - G[1, 1]) <= rel * G[1, 1]
 
 
+def _check_digit_gram_samples(S, x, dims, samples):
+    """The exact-digit Gram's bound at sampled entries: the only error is the
+    representation of each value by its digits, |x - digits| <= delta_i =
+    2^(floor(log2 max_k |x_ik|) - 20), so an entry is within delta_j |x_i|_1
+    + delta_i |x_j|_1 + K delta_i delta_j of the FP64 Gram (plus 1e-12 of
+    sum_k |x_ik x_jk| for the compensated sums)."""
+    xv = x.view(-1, dims[0])
+    K = xv.shape[0]
+    for (i, j), G in samples.items():
+        ci, cj = xv[:, i].double(), xv[:, j].double()
+        mi, mj = float(ci.abs().max()), float(cj.abs().max())
+        di = math.ldexp(1.0, math.frexp(mi)[1] - 21) if mi > 0 else 0.0
+        dj = math.ldexp(1.0, math.frexp(mj)[1] - 21) if mj > 0 else 0.0
+        li, lj = float(ci.abs().sum()), float(cj.abs().sum())
+        lij = float((ci * cj).abs().sum())
+        for (a, b, g, da, db, la, lb, lab) in [(i, j, G[0, 1], di, dj, li, lj, lij),
+                                               (i, i, G[0, 0], di, di, li, li, float(G[0, 0])),
+                                               (j, j, G[1, 1], dj, dj, lj, lj, float(G[1, 1]))]:
+            bound = db * la + da * lb + K * da * db + 1e-12 * lab
+            assert abs(S[a, b] - g) <= bound, ((a, b), S[a, b], g, bound)
+
+
+def _chunked_oracle(x, dims, eps):
+    """The oracle's ST-HOSVD of the device tensor x, fed to it in pieces of
+    the last mode (each piece copied to the host in FP64)."""
+    xt = x.view(dims[-1], -1)
+    return oracle.sthosvd_chunked(lambda c: xt[c].double().cpu().numpy(), dims[-1], dims, eps=eps)
+
+
+def _check_fp64_path(res, ref, dims):
+    """The FP64 GPU path against the oracle: identical ranks, eigenvalues
+    within 1e-10 of the largest, kept subspaces within 1e-8 rad where the
+    eigenvalue gap at the cut is wide, and Cor. 1's squared error estimate
+    sum_n discarded_n / ||X||^2 within the eigensolvers' rounding: every
+    computed eigenvalue carries an absolute error of a few u64 ||S_n||, so
+    the discarded sums of the two FP64 paths may differ by up to
+    1e-15 sum_n I_n lambda_max,n.  (The explicit error, which needs the full
+    reconstruction on the host, is compared to 1e-12 at 200x200x200x50.)"""
+    assert res.ranks == ref["ranks"]
+    for n in range(len(dims)):
+        lam = host(res.eigvals[n])
+        w = ref["eigvals"][n]
+        assert np.abs(lam - w).max() <= 1e-10 * abs(w).max(), n
+        R = res.ranks[n]
+        if R < dims[n] and (w[R - 1] - w[R]) > 1e-6 * w[0]:
+            # sin of the largest principal angle, ||(I - U U^T) W||_2 (the
+            # arccos of the cosines cannot resolve angles below ~3e-8)
+            U = host(res.factors[n])
+            W = ref["factors"][n]
+            assert np.linalg.norm(W - U @ (U.T @ W), 2) <= 1e-8, n
+    e1 = sum(res.discarded) / res.norm_sq
+    e0 = sum(ref["discarded"]) / ref["norm_sq"]
+    tol = 1e-15 * sum(d * ref["eigvals"][n][0] for n, d in enumerate(dims)) / ref["norm_sq"]
+    assert abs(e1 - e0) <= tol, (e1, e0, tol)
+    # FP64 sums of 1e10 squares in two different orders
+    assert abs(res.norm_sq - ref["norm_sq"]) <= 1e-11 * ref["norm_sq"]
+
+
+def _check_mixed_path(res, ref, dims, eps):
+    """The mixed path against the oracle: identical ranks, every mode's
+    discarded sum within 2 % of the threshold eps^2 ||X||^2 / N (its Grams'
+    error on the discarded subspace; the FP64 path's own margins at the cut
+    are 4-8 % on these tensors), and the leading eigenvalues within 1e-4
+    relative: the tensor-core TTMs' truncating accumulators shrink each
+    partial core by up to ~1e-5 relative (measured 1.4e-5 on the eigenvalues
+    of mode 3 of the 500x500x500x11x8 tensor, after three of them)."""
+    thr = ref["threshold"]
+    assert res.ranks == ref["ranks"], (res.ranks, ref["ranks"])
+    assert abs(res.norm_sq - ref["norm_sq"]) <= 1e-11 * ref["norm_sq"]
+    for n in range(len(dims)):
+        assert abs(res.discarded[n] - ref["discarded"][n]) <= 0.02 * thr, (
+            n, (res.discarded[n] - ref["discarded"][n]) / thr)
+        lam = host(res.eigvals[n])[:res.ranks[n]]
+        w = ref["eigvals"][n][:res.ranks[n]]
+        assert np.abs(lam - w).max() <= 1e-4 * w[0], n
+    # (a mode that keeps every component may leave a rounding-level negative tail)
+    assert math.sqrt(max(sum(res.discarded), 0.0) / res.norm_sq) <= eps
+
+
 def _result_dict(res):
     return {"core": host(res.core), "core_dims": res.ranks,
             "factors": [host(f) for f in res.factors], "discarded": res.discarded,
@@ -83,8 +165,8 @@ def test_c200_fp64_full_parity(ctx):
         w = ref["eigvals"][n]
         if R < dims[n] and (w[R - 1] - w[R]) > 1e-6 * w[0]:
             # largest principal angle between the kept subspaces
-            sv = np.linalg.svd(U.T @ ref["factors"][n], compute_uv=False)
-            assert math.acos(min(1.0, sv.min())) <= 1e-8
+            W = ref["factors"][n]
+            assert np.linalg.norm(W - U @ (U.T @ W), 2) <= 1e-8
     ours = _result_dict(res)
     # the explicit error ||X - Xhat|| / ||X||: the estimate from the
     # discarded eigenvalues carries their FP64 rounding (~1e-16 lambda_max
@@ -100,22 +182,22 @@ def test_c200_fp64_full_parity(ctx):
     assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
 
 
-def test_c256_mixed_vs_fp64_ranks_and_errors(ctx):
+def test_c256_both_paths_against_the_oracle(ctx):
     dims, core = (256, 256, 256, 11, 32), (40, 40, 40, 11, 16)
     x = synth.tucker_torch(dims, core, decay=0.1, eta=1e-7, seed=0)
     rng = np.random.default_rng(1)
     pairs = [(int(a), int(b)) for a, b in rng.integers(0, dims[0], size=(6, 2))]
-    _check_gram_samples(host(ctx.gram(x, dims, 0, "fp32")), _mode0_gram_samples(x, dims, pairs),
-                        2e-6)
+    samples = _mode0_gram_samples(x, dims, pairs)
+    _check_gram_samples(host(ctx.gram(x, dims, 0, "fp32")), samples, 2e-6)
+    _check_digit_gram_samples(host(ctx.gram(x, dims, 0, "mixed")), x, dims, samples)
     for eps in (1e-2, 1e-4, 1e-5):
+        ref = _chunked_oracle(x, dims, eps)
         r64 = ctx.sthosvd(x, dims, eps=eps, prec="fp64")
+        _check_fp64_path(r64, ref, dims)
         rmx = ctx.sthosvd(x, dims, eps=eps, prec="mixed")
-        assert rmx.ranks == r64.ranks, (eps, rmx.ranks, r64.ranks)
-        d64, dmx = sum(r64.discarded), sum(rmx.discarded)
-        assert d64 <= eps ** 2 * r64.norm_sq and dmx <= eps ** 2 * rmx.norm_sq
-        # the FP32 Gram rounds without bias: its discarded sum stays within a
-        # small fraction of the eps^2 ||X||^2 budget of the FP64 path's
-        assert abs(dmx - d64) <= 0.02 * eps ** 2 * r64.norm_sq, (eps, dmx, d64)
+        # the exact-digit Gram's error bound allows it down to eps = 1e-5 here
+        assert rmx.gram_kernel[:3] == ["tcgen05-x3"] * 3, (eps, rmx.gram_kernel)
+        _check_mixed_path(rmx, ref, dims, eps)
         r64.close()
         rmx.close()
 
@@ -132,8 +214,14 @@ def test_large_mixed_path_full_size(ctx):
     S = host(ctx.gram(x, dims, 0, "fp64"))
     _check_gram_samples(S, samples, 1e-12)
     del S
+    S = host(ctx.gram(x, dims, 0, "mixed"))
+    _check_digit_gram_samples(S, x, dims, samples)
+    del S
+    ref = _chunked_oracle(x, dims, 1e-4)
     r64 = ctx.sthosvd(x, dims, eps=1e-4, prec="fp64")
+    _check_fp64_path(r64, ref, dims)
     rmx = ctx.sthosvd(x, dims, eps=1e-4, prec="mixed")
+    _check_mixed_path(rmx, ref, dims, 1e-4)
     assert rmx.ranks == r64.ranks
     assert rmx.gram_kernel[0] == "tcgen05-x3" and rmx.ttm_kernel[0] == "tcgen05"
     err = math.sqrt(sum(rmx.discarded) / rmx.norm_sq)

@@ -227,7 +227,7 @@ def test_gram_tensor_error_on_discarded_subspace(ctx):
     keeps the FP32 round-to-nearest Gram."""
     dims = (256, 64, 40, 11)
     x = synth.tucker_torch(dims, (40, 20, 20, 11), decay=0.1, eta=1e-7, seed=3)
-    want = host(ctx.gram(x, dims, 0, "fp64"))
+    want = oracle.gram(host(x), dims, 0)
     got = host(ctx.gram(x, dims, 0, "tensor"))
     w, V = oracle.eig_desc(want)
     nrm2 = float(np.trace(want))
@@ -242,20 +242,37 @@ def test_gram_tensor_error_on_discarded_subspace(ctx):
 
 
 MIXED_X3_SHAPES = [(128, 3000), (500, 2000), (256, 33, 70), (132, 700), (1024, 300), (2048, 64),
-                   (500, 257)]
+                   (500, 257), (64, 3000), (100, 650)]
 
 
+@pytest.fixture
+def digits(ctx, request):
+    """Forces the exact-digit Gram's digit count for one test."""
+    from paper_1901_06043_gb300 import tucker
+    ctx.set_option(tucker.OPT_GRAM_DIGITS, request.param)
+    yield request.param
+    ctx.set_option(tucker.OPT_GRAM_DIGITS, 0)
+
+
+def _digit_delta(X, digits):
+    """Half the last digit's unit per row: 2^(floor(log2 max_k |x_ik|) - 20)
+    with three 7-bit digits, 2^(... - 13) with two."""
+    _, ex = np.frexp(X.max(axis=1))
+    return np.where(X.max(axis=1) > 0, np.ldexp(1.0, ex - (21 if digits == 3 else 14)), 0.0)
+
+
+@pytest.mark.parametrize("digits", [3, 2], indirect=True)
 @pytest.mark.parametrize("dims", MIXED_X3_SHAPES)
-def test_gram_mixed_mode0_exact_digits(ctx, dims):
+def test_gram_mixed_mode0_exact_digits(ctx, dims, digits):
     """Mode-0 Gram of MIXED precision: tensor cores on exact integer digit
-    products (three 7-bit digits of each value under a per-row power-of-two
-    scale; window sums below 2^24 are exact in the FP32 accumulator).  Rows
-    of very different magnitude (10^-3 .. 10^3), one zero row, a few exact
-    zeros and a ragged K.  The only error is the digit representation,
-    |x - digits| <= delta_i = 2^(floor(log2 max_k |x_ik|) - 20), so every
-    entry lies within delta_j |x_i|_1 + delta_i |x_j|_1 + K delta_i delta_j
-    of the oracle's FP64 Gram (plus 1e-12 of sum_k |x_ik x_jk| for the
-    compensated sums)."""
+    products (three or two 7-bit digits of each value under a per-row
+    power-of-two scale; window sums below 2^24 are exact in the FP32
+    accumulator).  Rows of very different magnitude (10^-3 .. 10^3), one
+    zero row, a few exact zeros and a ragged K.  The only error is the digit
+    representation, |x - digits| <= delta_i = 2^(floor(log2 max_k |x_ik|) -
+    20) (three digits) or 2^(... - 13) (two), so every entry lies within
+    delta_j |x_i|_1 + delta_i |x_j|_1 + K delta_i delta_j of the oracle's
+    FP64 Gram (plus 1e-12 of sum_k |x_ik x_jk| for the compensated sums)."""
     rng = np.random.default_rng(dims[0] * 7 + dims[-1])
     n = oracle.linear_size(dims)
     rows = np.arange(n) % dims[0]
@@ -269,8 +286,7 @@ def test_gram_mixed_mode0_exact_digits(ctx, dims):
     got = host(ctx.gram(t, dims, 0, "mixed"))
     X = np.abs(xs.reshape(-1, dims[0]).T)          # I x K, |x|
     K = X.shape[1]
-    _, ex = np.frexp(X.max(axis=1))
-    delta = np.where(X.max(axis=1) > 0, np.ldexp(1.0, ex - 21), 0.0)
+    delta = _digit_delta(X, digits)
     l1 = X.sum(axis=1)
     bound = (np.outer(l1, delta) + np.outer(delta, l1) + K * np.outer(delta, delta)
              + 1e-12 * (X @ X.T))
@@ -281,20 +297,22 @@ def test_gram_mixed_mode0_exact_digits(ctx, dims):
     assert np.array_equal(got, got.T)
 
 
-def _digit_trace_sigma(X):
+def _digit_trace_sigma(X, digits=3):
     """Standard deviation of the trace error of the exact-digit Gram for the
     I x K matrix X (torch, any device): the last digit rounds each value to
-    the grid 2^(floor(log2 max_k |x_ik|) - 19), an error uniform in +-half a
-    step, independent of x; trace(S~) - trace(S) = sum 2 x d + sum d^2, and
-    the diagonal correction removes the mean of sum d^2."""
+    the grid 2^(floor(log2 max_k |x_ik|) - 19) (three digits; - 12 with two),
+    an error uniform in +-half a step, independent of x; trace(S~) -
+    trace(S) = sum 2 x d + sum d^2, and the diagonal correction removes the
+    mean of sum d^2."""
     rmax = X.abs().amax(dim=1).double().cpu().numpy()
     rn2 = (X.double() ** 2).sum(dim=1).cpu().numpy()
     _, ex = np.frexp(rmax)
-    half = np.where(rmax > 0, np.ldexp(1.0, ex - 21), 0.0)
+    half = np.where(rmax > 0, np.ldexp(1.0, ex - (21 if digits == 3 else 14)), 0.0)
     return float(np.sqrt(np.sum(4.0 * half ** 2 / 3.0 * rn2)))
 
 
-def test_gram_mixed_mode0_trace_unbiased(ctx):
+@pytest.mark.parametrize("digits", [3, 2], indirect=True)
+def test_gram_mixed_mode0_trace_unbiased(ctx, digits):
     """trace(S) = ||Y||^2 on 1.3e8 Gaussian entries: the exact-digit
     tensor-core Gram rounds only unbiasedly (the last digit of each value;
     its square is removed from the diagonal), so its trace matches the FP64
@@ -305,12 +323,13 @@ def test_gram_mixed_mode0_trace_unbiased(ctx):
     t = torch.randn(dims[::-1], generator=g, device="cuda", dtype=torch.float32).reshape(-1)
     want = float((t.double() ** 2).sum())
     got = float(torch.trace(ctx.gram(t, dims, 0, "mixed")))
-    sigma = _digit_trace_sigma(t.view(-1, dims[0]).T)
-    assert sigma < 1e-9 * want
+    sigma = _digit_trace_sigma(t.view(-1, dims[0]).T, digits)
+    assert sigma < (1e-9 if digits == 3 else 2e-7) * want
     assert abs(got - want) <= 6 * sigma, ((got - want) / want, (got - want) / sigma)
 
 
-def test_gram_mixed_mode0_error_on_discarded_subspace(ctx):
+@pytest.mark.parametrize("digits", [3, 2], indirect=True)
+def test_gram_mixed_mode0_error_on_discarded_subspace(ctx, digits):
     """What the eps cut sees, at eps = 1e-4 (the regime MIXED is meant for):
     the exact-digit Gram's error projected on the discarded eigenvectors of a
     Tucker tensor's mode-0 Gram stays below 2 % of the threshold.  The trace
@@ -318,7 +337,7 @@ def test_gram_mixed_mode0_error_on_discarded_subspace(ctx):
     within 6 sigma of it."""
     dims = (256, 64, 40, 11)
     x = synth.tucker_torch(dims, (40, 20, 20, 11), decay=0.1, eta=1e-7, seed=3)
-    want = host(ctx.gram(x, dims, 0, "fp64"))
+    want = oracle.gram(host(x), dims, 0)
     got = host(ctx.gram(x, dims, 0, "mixed"))
     w, V = oracle.eig_desc(want)
     nrm2 = float(np.trace(want))
@@ -327,19 +346,58 @@ def test_gram_mixed_mode0_error_on_discarded_subspace(ctx):
     P = V[:, R:]
     E = got - want
     proj = np.trace(P.T @ E @ P)
-    sigma = _digit_trace_sigma(x.view(-1, dims[0]).T)
+    sigma = _digit_trace_sigma(x.view(-1, dims[0]).T, digits)
     assert abs(np.trace(E)) <= 6 * sigma, np.trace(E) / sigma
     assert abs(proj) <= 0.02 * thr, proj / thr
 
 
+def test_mixed_two_digit_gram_where_its_bound_allows(ctx):
+    """An eps-driven MIXED ST-HOSVD takes two digits for a view whose bound
+    (six standard deviations of the representation error on the discarded
+    subspace below 1 % of the threshold) allows it: the long mode-0 view of
+    a 256 x 64 x 200 x 11 tensor at eps = 1e-3.  Ranks and discarded sums as
+    the oracle's."""
+    dims = (256, 64, 200, 11)
+    x = synth.tucker_torch(dims, (40, 20, 30, 11), decay=0.1, eta=1e-7, seed=4)
+    res = ctx.sthosvd(x, dims, eps=1e-3, prec="mixed")
+    ref = oracle.sthosvd(host(x), dims, eps=1e-3)
+    assert res.gram_kernel[0] == "tcgen05-x2", res.gram_kernel
+    assert res.ranks == ref["ranks"]
+    for n in range(4):
+        assert abs(res.discarded[n] - ref["discarded"][n]) <= 0.02 * ref["threshold"]
+    res.close()
+
+
+@pytest.mark.parametrize("eps,kernel", [(1e-4, "tcgen05-x3"), (1e-6, "simt-fp64")])
+def test_mixed_digit_gram_kept_while_its_bound_allows(ctx, eps, kernel):
+    """MIXED keeps the exact-digit Gram of a view while six standard
+    deviations of its representation error on the discarded subspace,
+    sqrt(4 sigma^2 thr + 2 K I sigma^4) with sigma^2 = delta_max^2 / 3, stay
+    below 1 % of the threshold; this 256 x 28160 mode-0 view passes at
+    eps = 1e-4 (~2 % of the allowance) and fails at eps = 1e-6, where the
+    Gram is computed in FP64.  The mode-0 cut equals the oracle's either way;
+    at eps = 1e-4 every mode's does (at eps = 1e-6 the later modes see the
+    mixed TTMs' rounding, ~1e-14 ||X||^2, a few percent of that threshold)."""
+    dims = (256, 64, 40, 11)
+    x = synth.tucker_torch(dims, (40, 20, 20, 11), decay=0.1, eta=1e-7, seed=3)
+    res = ctx.sthosvd(x, dims, eps=eps, prec="mixed")
+    ref = oracle.sthosvd(host(x), dims, eps=eps)
+    assert res.gram_kernel[0] == kernel, res.gram_kernel
+    modes = range(4) if eps >= 1e-4 else range(1)
+    for n in modes:
+        assert res.ranks[n] == ref["ranks"][n]
+        assert abs(res.discarded[n] - ref["discarded"][n]) <= 0.02 * ref["threshold"]
+    res.close()
+
+
 def _tcx_applies(dims, mode):
     """Whether the exact-digit tensor-core Gram serves this slab view (the
-    plan's rule: 128 <= I <= 2048; column mode needs I % 4 == 0 and >= 64
+    plan's rule: I <= 2048; column mode needs 64 <= I, I % 4 == 0 and >= 64
     columns; row mode 16-l blocks with at most 25 % zero fill)."""
     L = math.prod(dims[:mode])
     I = dims[mode]
     Rt = math.prod(dims[mode + 1:])
-    if not 128 <= I <= 2048:
+    if not (64 if L == 1 else 128) <= I <= 2048:
         return False
     if L == 1:
         return I % 4 == 0 and Rt >= 64
@@ -359,8 +417,9 @@ ROW_X3_CASES = [((54, 300, 40), 1), ((60, 129, 11), 1), ((100, 500, 20), 1),
                 ((12, 10, 200, 30), 2), ((16, 136, 9), 1)]
 
 
+@pytest.mark.parametrize("digits", [3, 2], indirect=True)
 @pytest.mark.parametrize("dims,mode", ROW_X3_CASES)
-def test_gram_mixed_rowmode_exact_digits(ctx, dims, mode):
+def test_gram_mixed_rowmode_exact_digits(ctx, dims, mode, digits):
     """Row-mode slab views (L > 1: row i's values L apart, stages of 16
     consecutive l of one slab, the last block of a slab zero-filled) on the
     exact-digit tensor-core Gram, row maxima from the slab pass: every entry
@@ -382,8 +441,7 @@ def test_gram_mixed_rowmode_exact_digits(ctx, dims, mode):
     got = host(ctx.gram(t, dims, mode, "mixed"))
     X = np.abs(_unfold(xs, dims, mode))
     K = X.shape[1]
-    _, ex = np.frexp(X.max(axis=1))
-    delta = np.where(X.max(axis=1) > 0, np.ldexp(1.0, ex - 21), 0.0)
+    delta = _digit_delta(X, digits)
     l1 = X.sum(axis=1)
     bound = (np.outer(l1, delta) + np.outer(delta, l1) + K * np.outer(delta, delta)
              + 1e-12 * (X @ X.T))
@@ -393,7 +451,8 @@ def test_gram_mixed_rowmode_exact_digits(ctx, dims, mode):
     assert np.array_equal(got, got.T)
 
 
-def test_gram_mixed_rowmode_error_on_discarded_subspace(ctx):
+@pytest.mark.parametrize("digits", [3, 2], indirect=True)
+def test_gram_mixed_rowmode_error_on_discarded_subspace(ctx, digits):
     """Mode 1 (row mode, L = 64) of a Tucker tensor at eps = 1e-4: the
     exact-digit Gram's error on the discarded eigenvectors stays below 2 % of
     the threshold and its trace error within 6 sigma of the digit rounding
@@ -401,7 +460,7 @@ def test_gram_mixed_rowmode_error_on_discarded_subspace(ctx):
     dims = (64, 256, 40, 11)
     assert _tcx_applies(dims, 1)
     x = synth.tucker_torch(dims, (20, 40, 20, 11), decay=0.1, eta=1e-7, seed=5)
-    want = host(ctx.gram(x, dims, 1, "fp64"))
+    want = oracle.gram(host(x), dims, 1)
     got = host(ctx.gram(x, dims, 1, "mixed"))
     w, V = oracle.eig_desc(want)
     nrm2 = float(np.trace(want))
@@ -410,7 +469,7 @@ def test_gram_mixed_rowmode_error_on_discarded_subspace(ctx):
     P = V[:, R:]
     E = got - want
     proj = np.trace(P.T @ E @ P)
-    sigma = _digit_trace_sigma(_unfold(x, dims, 1))
+    sigma = _digit_trace_sigma(_unfold(x, dims, 1), digits)
     assert abs(np.trace(E)) <= 6 * sigma, np.trace(E) / sigma
     assert abs(proj) <= 0.02 * thr, proj / thr
 
@@ -580,6 +639,34 @@ def test_sthosvd_batched_uneven(ctx, prec):
         one = ctx.sthosvd(t, dims, eps=1e-4, prec=prec)
         assert one.ranks == r.ranks
         one.close()
+        r.close()
+
+
+def test_sthosvd_batched_mixed_digit_grams(ctx):
+    """Sides of 128-256 (multiples of 4), where the batched MIXED path runs
+    the exact-digit tensor-core Gram with its side-stream row maxima: every
+    tensor against the oracle (identical ranks, discarded sums within 2 % of
+    the threshold, explicit error within eps)."""
+    shapes = [((128, 128, 128), (20, 20, 20)), ((132, 140, 24, 6), (16, 12, 10, 4)),
+              ((200, 200, 60), (24, 24, 16)), ((256, 136, 20, 5), (30, 20, 10, 5)),
+              ((160, 160, 160), (12, 30, 20))]
+    xs, dims_list = [], []
+    for k, (dims, core) in enumerate(shapes):
+        x, _ = synth.tucker_numpy(dims, core, decay=0.15, eta=1e-6, seed=70 + k)
+        xs.append(dev(x, torch.float32))
+        dims_list.append(dims)
+    res = ctx.sthosvd_batched(xs, dims_list, eps=1e-4, prec="mixed")
+    for t, dims, r in zip(xs, dims_list, res):
+        xh = host(t)
+        ref = oracle.sthosvd(xh, dims, eps=1e-4)
+        assert r.gram_kernel[0] == "tcgen05-x3", r.gram_kernel
+        assert r.ranks == ref["ranks"], (dims, r.ranks, ref["ranks"])
+        for n in range(len(dims)):
+            assert abs(r.discarded[n] - ref["discarded"][n]) <= 0.02 * ref["threshold"]
+        e = oracle.relative_errors(xh, dims, {"core": host(r.core), "core_dims": r.ranks,
+                                              "factors": [host(f) for f in r.factors],
+                                              "discarded": r.discarded, "norm_sq": r.norm_sq})
+        assert e["err_explicit"] <= 1e-4
         r.close()
 
 
