@@ -252,6 +252,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-slices", type=int, default=None)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="split-K autotuner of the Gram kernels (tuned during the warm-up)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -307,9 +309,12 @@ def main():
         return
 
     # warm-up on a context that records per-step CUDA events (kernel times for
-    # the roofline); the timed steps below run on a context without them
+    # the roofline); the timed steps below run on a context without them.  The
+    # autotuner's cache is per process: the warm-up tunes, the timed steps reuse
     ctx_t = tucker.Context(timing=True)
     ctx = tucker.Context()
+    for cx in (ctx_t, ctx):
+        cx.set_option(tucker.OPT_AUTOTUNE, args.autotune)
     last = None
     for _ in range(args.warmup):
         if last is not None:
@@ -357,6 +362,7 @@ def main():
         "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {describe(w)}", "prec": prec,
                    "l2": "input larger than L2 (no flush)", "ranks": list(ranks),
+                   "autotune": args.autotune,
                    "parallelism": f"replicas x{ws}"},
         "roofline": dom,
         "step": "ST-HOSVD (norm, Gram, eigensolve, rank cut, TTM per mode) + multi-TTM "
@@ -372,6 +378,7 @@ def main():
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e_leg(ctx, x, w, prec, args)
     if rank == 0 and not args.no_fp64 and prec != "fp64":
+        ctx_t.set_option(tucker.OPT_AUTOTUNE, 0)      # one untuned FP64 step
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record()
@@ -446,6 +453,7 @@ def main_batch(args, w, ws, rank):
         }))
         return
     ctx = tucker.Context()
+    ctx.set_option(tucker.OPT_AUTOTUNE, args.autotune)
     ranks = None
     for _ in range(args.warmup):
         rs = ctx.sthosvd_batched(xs, dims_list, w["eps"], prec=prec)
@@ -479,6 +487,7 @@ def main_batch(args, w, ws, rank):
         "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {describe(w)}", "prec": prec,
                    "total_bytes": in_bytes, "l2": "inputs larger than L2 (no flush)",
+                   "autotune": args.autotune,
                    "parallelism": f"replicas x{ws}"},
         # the whole step against HBM: every input byte is read at least once
         "roofline": {"bound": "hbm", "achieved": value, "peak": pk["hbm_gbs"], "unit": "GB/s",

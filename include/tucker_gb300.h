@@ -165,7 +165,17 @@ const char* tucker_last_error(const tucker_ctx* ctx);
  *                          that step launches or allocates anything.
  *   TUCKER_OPT_GRAM_DIGITS digits per value of the exact-digit Gram (MIXED):
  *                          0 (default) chooses per view (see MIXED), 2 or 3
- *                          forces that count wherever the digit Gram runs. */
+ *                          forces that count wherever the digit Gram runs.
+ *   TUCKER_OPT_AUTOTUNE    1: the K split of every Gram kernel (the number of
+ *                          CTAs the split-K planners give one wave) is chosen
+ *                          by timing: the first call of each (kernel, view
+ *                          shape, dtype, digit count) runs the plans for 0.5,
+ *                          1, 1.5 and 2 waves twice each on the context stream
+ *                          (CUDA events, synchronising) and the fastest is
+ *                          kept for the rest of the process, for every
+ *                          context.  Results differ from the untuned ones only
+ *                          by the order of the FP64 split sums.  0 (default):
+ *                          one wave. */
 #define TUCKER_OPT_TIMING 1
 #define TUCKER_OPT_MAX_SWEEPS 2
 #define TUCKER_OPT_JACOBI_TOL 3
@@ -173,11 +183,16 @@ const char* tucker_last_error(const tucker_ctx* ctx);
 #define TUCKER_OPT_BARRIER_POLLS 5
 #define TUCKER_OPT_MEM_LIMIT 6
 #define TUCKER_OPT_GRAM_DIGITS 7
+#define TUCKER_OPT_AUTOTUNE 8
 tucker_status tucker_set_option(tucker_ctx* ctx, int key, double value);
 
 /* Diagnostics: number of device kernels this library has launched in the
  * process so far (all contexts).  Host only; never fails. */
 uint64_t tucker_kernel_launches(void);
+
+/* Diagnostics: number of (kernel, shape) entries the split-K autotuner has
+ * cached in this process (TUCKER_OPT_AUTOTUNE).  Host only; never fails. */
+int64_t tucker_autotune_entries(void);
 
 /* Diagnostics: y_dev[i] = the FP64 reciprocal the tridiagonal eigensolver
  * uses (an FP32 seed refined by two Newton-Raphson steps, within one ulp of
@@ -283,7 +298,9 @@ tucker_status tucker_sthosvd_order(int ndim, const int64_t* dims, const int64_t*
 /* Statistics of every mode-`mode` hyperslice X(:, .., i, .., :) (its
  * J^* / I_n entries), FP64: stats_dev[6 i + k] with k = TUCKER_STAT_*.
  * The standard deviation is the population one (sum (x - mean)^2 / count),
- * computed in a second pass over the data.  stats_dev (6 I_n doubles) is
+ * computed in a second pass over the data.  FP32 data is summed in exact
+ * FP32 pairs moved into FP64 (within a few units of 2^-48 of the FP64 sums),
+ * FP64 data in FP64.  stats_dev (6 I_n doubles) is
  * caller-owned.  Synchronises.  Errors: INVALID, NONFINITE (a statistic is
  * NaN or Inf: the tensor holds NaN or Inf), OOM, CUDA. */
 #define TUCKER_STAT_MEAN 0
@@ -298,7 +315,9 @@ tucker_status tucker_slice_stats(tucker_ctx* ctx, const void* x_dev, tucker_dtyp
 /* One linear function per mode-`mode` hyperslice i:
  *   inverse = 0 (pre-processing):  y = (x - shift_i) * scale_i
  *   inverse = 1 (post-processing): y = x / scale_i + shift_i
- * evaluated in FP64 and rounded once to dtype.  shift_dev, scale_dev: I_n
+ * FP64 data in FP64; FP32 data in FP32-pair arithmetic (about 48 bits, the
+ * inverse as x * (1 / scale_i)), rounded once to FP32: within one ulp of the
+ * exact value.  shift_dev, scale_dev: I_n
  * FP64 values each (for a reconstructed subtensor whose mode-`mode` range
  * starts at b, pass shift + b and scale + b); scale_i must be nonzero for
  * the inverse.  y_dev (same dims and dtype) may equal x_dev (in place).

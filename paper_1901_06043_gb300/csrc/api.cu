@@ -2,6 +2,9 @@
 // ST-HOSVD (Algorithm 1 of the TuckerMPI paper) and of the multi-TTM
 // reconstruction (Section 7).  Every arithmetic step runs in a device kernel.
 #include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -30,6 +33,7 @@ struct tucker_ctx {
   unsigned long long barrier_polls = 1ull << 24;   // grid-barrier poll limit of the eigensolvers
   double mem_limit = 0.0;        // bytes assumed available to a call (0: ask the device)
   int gram_digits = 0;           // digits of the exact-digit Gram: 0 auto, 2 or 3
+  int autotune = 0;              // 1: split-K of the Gram kernels chosen by timing
   std::string err;
   // small device scratch
   unsigned* d_words = nullptr;   // 256 words
@@ -233,16 +237,18 @@ constexpr double kMinFp32GramThreshold = 1e-9;
 // |r_ik| <= delta_i = 2^(floor(log2 max_k |x_ik|) - 20) with three digits,
 // 2^(... - 13) with two, unbiased, independent of x (variance
 // sigma_i^2 <= delta_i^2 / 3); the mean of r r^T's diagonal is removed
-// exactly.  On the discarded subspace (projector P, rank I - R) the error is
+// exactly.  On the discarded subspace (projector P, tail <= thr at the cut)
+// the error is
 //   2 sum_k (P x_k).r_k + sum_k sum_{i != j} P_ij r_ik r_jk,
-// whose variance is at most 4 sigma^2 tail + 2 K (I - R) sigma^4 with
-// sigma = max_i sigma_i and tail <= thr at the cut.  A digit count is
-// accepted when six standard deviations stay below 1 % of thr (the FP64
-// path's own margins at the cut are a few percent of thr on the benchmarked
-// tensors); two digits are preferred, four products instead of nine.  With
-// no threshold (ranks given) three digits.
+// with variance at most 4 sigma_max^2 tail + 2 K sum_{i != j} P_ij^2
+// sigma_i^2 sigma_j^2, and sum_j P_ij^2 = P_ii <= 1 bounds the second term by
+// 2 K sigma_max^2 sum_i sigma_i^2.  A digit count is accepted when six
+// standard deviations stay below 1 % of thr (the FP64 path's own margins at
+// the cut are a few percent of thr on the benchmarked tensors); two digits
+// are preferred, four products instead of nine.  With no threshold (ranks
+// given) three digits.
 double digit_gram_err6(const unsigned* rowmax_bits, int64_t I, int64_t K, double thr, int ndig) {
-  double dmax = 0.0;
+  double dmax = 0.0, dsum = 0.0;
   for (int64_t i = 0; i < I; ++i) {
     const unsigned b = rowmax_bits[i] & 0x7fffffffu;
     if (b == 0u) continue;
@@ -250,10 +256,12 @@ double digit_gram_err6(const unsigned* rowmax_bits, int64_t I, int64_t K, double
     memcpy(&m, &b, sizeof m);
     int e = 0;
     std::frexp((double)m, &e);                      // m in [2^(e-1), 2^e)
-    dmax = std::max(dmax, std::ldexp(1.0, e - (ndig == 3 ? 21 : 14)));
+    const double d = std::ldexp(1.0, e - (ndig == 3 ? 21 : 14));
+    dmax = std::max(dmax, d);
+    dsum += d * d;
   }
-  const double s2 = dmax * dmax / 3.0;
-  return 6.0 * std::sqrt(4.0 * s2 * thr + 2.0 * (double)K * (double)I * s2 * s2);
+  const double s2max = dmax * dmax / 3.0, s2sum = dsum / 3.0;
+  return 6.0 * std::sqrt(4.0 * s2max * thr + 2.0 * (double)K * s2max * s2sum);
 }
 
 int digit_gram_digits(const unsigned* rowmax_bits, int64_t I, int64_t K, double thr) {
@@ -301,16 +309,14 @@ tucker_status rowmax_pass(tucker_ctx* c, const float* y, int64_t I0, int64_t nco
 // batch of calls.
 // ndig: digits of the exact-digit Gram (2 or 3; TUCKER_OPT_GRAM_DIGITS
 // overrides it).
-tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabView& v,
-                      tucker_prec prec, double* S, int* kernel_used, double maxabs = -1.0,
-                      bool check = true, const unsigned* rowmax = nullptr, int ndig = 3) {
-  int kern = gram_kernel_for(prec, dt, v, c->num_sms);
-  if ((kern == 2 || (kern == 5 && v.L == 1)) && (((uintptr_t)y) & 15) != 0) kern = 1;
-  if (kern == 5 && (((uintptr_t)y) & 3) != 0) kern = 1;
-  if (c->gram_digits) ndig = c->gram_digits;
+// sms: the SM count the split-K planners size their one wave of CTAs for
+// (the device's, or the autotuner's choice).
+tucker_status gram_once(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabView& v,
+                        tucker_prec prec, double* S, int* kernel_used, double maxabs, bool check,
+                        const unsigned* rowmax, int ndig, int kern, int sms) {
   if (kernel_used) *kernel_used = (kern == 5 && ndig == 2) ? 6 : kern;
   if (kern == 5) {
-    const GramPlan p = plan_gram_tcx(v.L, v.I, v.Rt, c->num_sms);
+    const GramPlan p = plan_gram_tcx(v.L, v.I, v.Rt, sms);
     DevBuf scratch, rm;
     TK_TRY(dev_alloc(c, scratch, p.scratch_bytes));
     if (!rowmax) {
@@ -361,7 +367,7 @@ tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabV
     return TUCKER_OK;
   }
   if (kern == 3) {
-    const GramPlan ps = plan_gram_small(v.L, v.I, v.Rt, c->num_sms, v.L0);
+    const GramPlan ps = plan_gram_small(v.L, v.I, v.Rt, sms, v.L0);
     DevBuf scratch;
     TK_TRY(dev_alloc(c, scratch, ps.scratch_bytes));
     TK_CUDA(c, launch_gram_small(y, dt, v.L, v.I, v.Rt, v.L0, ps, scratch.as<double>(), S,
@@ -369,7 +375,7 @@ tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabV
     return TUCKER_OK;
   }
   if (kern == 1 && dt == TUCKER_F32) {
-    const GramPlan pc = plan_gram_f32(v.L, v.I, v.Rt, c->num_sms, v.L0);
+    const GramPlan pc = plan_gram_f32(v.L, v.I, v.Rt, sms, v.L0);
     if (pc.ntiles > 0) {
       if (kernel_used && gram_f32_compensated(v.L, v.Rt)) *kernel_used = 4;
       DevBuf scratch;
@@ -379,12 +385,89 @@ tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabV
       return TUCKER_OK;
     }
   }
-  GramPlan p = plan_gram_simt(v.L, v.I, v.Rt, c->num_sms, v.L0);
+  GramPlan p = plan_gram_simt(v.L, v.I, v.Rt, sms, v.L0);
   DevBuf scratch;
   TK_TRY(dev_alloc(c, scratch, p.scratch_bytes));
   TK_CUDA(c, launch_gram_simt(y, dt, kern == 0, v.L, v.I, v.Rt, v.L0, p, scratch.as<double>(), S,
                               c->stream));
   return TUCKER_OK;
+}
+
+// Process-wide cache of the split-K autotuner: for each (device, kernel,
+// view shape, dtype, digits) the SM count whose one-wave plan ran fastest.
+std::mutex g_tune_mu;
+std::map<std::array<int64_t, 7>, int> g_tune;
+
+// maxabs: max|y| if the caller knows it (e.g. from the norm pass), else <= 0.
+// check = false: the tensor-core kernel's error word (d_words[8]) is neither
+// cleared nor read here; the caller clears it before and reads it after a
+// batch of calls.
+// ndig: digits of the exact-digit Gram (2 or 3; TUCKER_OPT_GRAM_DIGITS
+// overrides it).
+// With TUCKER_OPT_AUTOTUNE the split-K planners size their wave for the SM
+// count the autotuner chose for this kernel and view: on the first call of
+// a (kernel, shape) the candidates 0.5, 1, 1.5 and 2 waves are each run twice
+// on the context stream, timed by CUDA events, and the fastest is cached
+// for the process (tile shapes are those of the kernels; only the K split
+// is tuned).
+tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabView& v,
+                      tucker_prec prec, double* S, int* kernel_used, double maxabs = -1.0,
+                      bool check = true, const unsigned* rowmax = nullptr, int ndig = 3) {
+  int kern = gram_kernel_for(prec, dt, v, c->num_sms);
+  if ((kern == 2 || (kern == 5 && v.L == 1)) && (((uintptr_t)y) & 15) != 0) kern = 1;
+  if (kern == 5 && (((uintptr_t)y) & 3) != 0) kern = 1;
+  if (c->gram_digits) ndig = c->gram_digits;
+  if (!c->autotune || kern == 2)
+    return gram_once(c, y, dt, v, prec, S, kernel_used, maxabs, check, rowmax, ndig, kern,
+                     c->num_sms);
+  const std::array<int64_t, 7> key{c->device, kern, v.L, v.I, v.Rt, (int64_t)dt,
+                                   kern == 5 ? ndig : 0};
+  int best = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) best = it->second;
+  }
+  if (best == 0) {
+    // the digit Gram's row maxima once, outside the timed runs
+    DevBuf rm;
+    if (kern == 5 && !rowmax) {
+      TK_TRY(dev_alloc(c, rm, sizeof(unsigned) * v.I));
+      if (v.L == 1)
+        TK_TRY(rowmax_pass(c, (const float*)y, v.I, v.Rt, rm.as<unsigned>()));
+      else
+        TK_CUDA(c, launch_rowmax_slab((const float*)y, v.L, v.I, v.Rt, c->num_sms,
+                                      rm.as<unsigned>(), c->stream));
+      rowmax = rm.as<unsigned>();
+    }
+    cudaEvent_t e0, e1;
+    TK_CUDA(c, cudaEventCreate(&e0));
+    TK_CUDA(c, cudaEventCreate(&e1));
+    float best_ms = 0.f;
+    tucker_status st = TUCKER_OK;
+    for (double f : {0.5, 1.0, 1.5, 2.0}) {
+      const int sms = std::max(1, (int)std::lround(c->num_sms * f));
+      for (int rep = 0; rep < 2 && st == TUCKER_OK; ++rep) {
+        cudaEventRecord(e0, c->stream);
+        st = gram_once(c, y, dt, v, prec, S, nullptr, maxabs, true, rowmax, ndig, kern, sms);
+        cudaEventRecord(e1, c->stream);
+        float ms = 0.f;
+        if (st == TUCKER_OK && cudaEventSynchronize(e1) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && (best == 0 || ms < best_ms)) {
+          best = sms;
+          best_ms = ms;
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    if (st != TUCKER_OK) return st;
+    if (best == 0) best = c->num_sms;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+  }
+  return gram_once(c, y, dt, v, prec, S, kernel_used, maxabs, check, rowmax, ndig, kern, best);
 }
 
 // Device bytes of the split-K scratch do_gram allocates for a view.
@@ -733,6 +816,11 @@ const char* tucker_last_error(const tucker_ctx* c) { return c ? c->err.c_str() :
 
 uint64_t tucker_kernel_launches(void) { return g_launches.load(); }
 
+int64_t tucker_autotune_entries(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return (int64_t)g_tune.size();
+}
+
 tucker_status tucker_set_option(tucker_ctx* c, int key, double value) {
   if (!c) return TUCKER_ERR_INVALID;
   switch (key) {
@@ -745,6 +833,10 @@ tucker_status tucker_set_option(tucker_ctx* c, int key, double value) {
       if (value != 0.0 && value != 1.0 && value != 2.0)
         return set_err(c, TUCKER_ERR_INVALID, "eigensolver must be 0 (auto), 1 or 2");
       c->eig_solver = (int)value;
+      return TUCKER_OK;
+    case TUCKER_OPT_AUTOTUNE:
+      if (value != 0.0 && value != 1.0) return set_err(c, TUCKER_ERR_INVALID, "autotune must be 0 or 1");
+      c->autotune = (int)value;
       return TUCKER_OK;
     case TUCKER_OPT_GRAM_DIGITS:
       if (value != 0.0 && value != 2.0 && value != 3.0)

@@ -46,6 +46,9 @@
 // down; tensor memory is always released.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+#include <cmath>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "tc_common.cuh"
@@ -70,6 +73,9 @@ constexpr uint32_t PLANE_STEP = 2 * ATOM;       // plane q starts at atom 2q
 constexpr uint32_t PAIR_BYTES = 128 * 128 * 4;  // hi or lo tile, [col / 2][row][col % 2]
 constexpr uint32_t RSUM_BYTES = 16 * 128 * 4;   // remainder sums, [producer warp][row]
 constexpr int TILE_ELEMS = 128 * 128;
+// time per column of a diagonal tile's CTA relative to an off-diagonal one's
+// (the producers, which bound the kernel, split 128 rows instead of 256)
+constexpr double kDiagCost = 1.0;
 
 // Per digit count: three 7-bit digits (all nine products, four weight
 // classes, windows of 1024 columns) or two (four products, three classes,
@@ -201,18 +207,38 @@ struct GramTcxArgs {
   const float* x;
   int64_t L, I, K;         // K: columns (column mode) or slabs (row mode)
   int nlb;                 // row mode: l-blocks per slab, ceil(L / 16)
-  int ntiles, nkg, T;      // tiles of the lower triangle, K splits, row blocks
+  int ntiles, nkg, T;      // tiles of the lower triangle, K splits of an off-diagonal tile, row blocks
+  int nkg_diag;            // K splits of a diagonal tile
+  int noff;                // off-diagonal tiles: CTAs [0, noff * nkg) hold them, the
+                           // diagonal ones follow
   const float* scale;      // I power-of-two row scales s_i
   double* part;            // gridDim.x partial tiles, [col][row], FP64 (scaled units)
   unsigned* err;
 };
 
-__device__ __forceinline__ void tile_of(int t, int& ta, int& tb) {
-  int a = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
-  while ((a + 1) * (a + 2) / 2 <= t) ++a;
-  while (a * (a + 1) / 2 > t) --a;
+// The j-th off-diagonal tile (ta > tb) of the lower triangle, row by row.
+__device__ __forceinline__ void offdiag_tile(int j, int& ta, int& tb) {
+  int a = 1;
+  while (j >= a) { j -= a; ++a; }
   ta = a;
-  tb = t - a * (a + 1) / 2;
+  tb = j;
+}
+
+// This CTA's tile and K split: off-diagonal tiles first (g.nkg splits each,
+// the tiles of a split adjacent in launch order so their shared columns are
+// served from L2), then the diagonal tiles (g.nkg_diag splits each).
+__device__ __forceinline__ void cta_work(const GramTcxArgs& g, int b, int& ta, int& tb, int& kg,
+                                         int& nkg) {
+  if (b < g.noff * g.nkg) {
+    offdiag_tile(b % g.noff, ta, tb);
+    kg = b / g.noff;
+    nkg = g.nkg;
+  } else {
+    b -= g.noff * g.nkg;
+    ta = tb = b % g.T;
+    kg = b / g.T;
+    nkg = g.nkg_diag;
+  }
 }
 
 // Producer warp (one of NPROD): loads its share of every stage (rows
@@ -366,13 +392,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx(GramTcxArgs g) {
   __shared__ float s_scale[256];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x % g.ntiles, kg = blockIdx.x / g.ntiles;
-  int ta, tb;
-  tile_of(tile, ta, tb);
+  int ta, tb, kg, nkg;
+  cta_work(g, (int)blockIdx.x, ta, tb, kg, nkg);
   const bool diag = ta == tb;
   // this CTA's K range: columns [k0, k1) (column mode) or stages [gs0, gs1)
   const int64_t ku = ROW ? g.K * g.nlb : g.K;
-  const int64_t k0 = ku * kg / g.nkg, k1 = ku * (kg + 1) / g.nkg;
+  const int64_t k0 = ku * kg / nkg, k1 = ku * (kg + 1) / nkg;
   const int nst = ROW ? (int)(k1 - k0) : (int)((k1 - k0 + BK - 1) / BK);
   const int nwin = (nst + WIN - 1) / WIN;
 
@@ -538,19 +563,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx(GramTcxArgs g) {
 }
 
 // S[i][j] = S[j][i] = (sum over the K splits of tile (ta, tb) at [col][row])
-// / (s_i s_j), i >= j, splits in order.
-__global__ void k_gram_tcx_reduce(const double* __restrict__ part, int ntiles, int nkg,
-                                  int64_t I, const float* __restrict__ scale,
+// / (s_i s_j), i >= j, splits in order; partial tiles in cta_work's order.
+__global__ void k_gram_tcx_reduce(const double* __restrict__ part, int noff, int nkg, int T,
+                                  int nkg_diag, int64_t I, const float* __restrict__ scale,
                                   double* __restrict__ S) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= I * I) return;
   const int64_t i = idx / I, j = idx % I;
   if (j > i) return;
   const int ta = (int)(i / 128), tb = (int)(j / 128);
-  const int t = ta * (ta + 1) / 2 + tb;
   const size_t off = (size_t)(j - 128 * tb) * 128 + (size_t)(i - 128 * ta);
   double s = 0.0;
-  for (int k = 0; k < nkg; ++k) s += part[(size_t)(t + ntiles * k) * TILE_ELEMS + off];
+  if (ta == tb) {
+    const size_t first = (size_t)noff * nkg + ta;
+    for (int k = 0; k < nkg_diag; ++k) s += part[(first + (size_t)T * k) * TILE_ELEMS + off];
+  } else {
+    const int jo = ta * (ta - 1) / 2 + tb;        // off-diagonal tile index
+    for (int k = 0; k < nkg; ++k) s += part[((size_t)jo + (size_t)noff * k) * TILE_ELEMS + off];
+  }
   s /= (double)scale[i] * (double)scale[j];
   S[i * I + j] = s;
   S[j * I + i] = s;
@@ -623,14 +653,28 @@ GramPlan plan_gram_tcx(int64_t L, int64_t I, int64_t Rt, int num_sms) {
     if (stages < 4) return p;
   }
   const int T = (int)((I + 127) / 128);
-  const int ntiles = T * (T + 1) / 2;
-  int nkg = num_sms / ntiles;
-  if (nkg < 1) nkg = 1;
-  const int64_t maxkg = stages / 4;
-  if (nkg > maxkg) nkg = (int)(maxkg < 1 ? 1 : maxkg);
+  const int ntiles = T * (T + 1) / 2, noff = ntiles - T;
+  const int64_t maxkg = std::max<int64_t>(1, stages / 4);
+  // one wave of CTAs; a diagonal tile splits only its own 128 rows (an
+  // off-diagonal one 256), so its CTAs cover kDiagCost / 1 of the columns per
+  // unit time and get that share of the splits, and all CTAs finish together
+  int ko = 1, kd = 1;
+  if (noff == 0) {
+    kd = num_sms;
+  } else {
+    for (int k = 1; k <= num_sms; ++k) {
+      const int d = std::max(1, (int)std::ceil(kDiagCost * k - 1e-9));
+      if (noff * k + T * d > num_sms) break;
+      ko = k;
+      kd = d;
+    }
+  }
+  ko = (int)std::min<int64_t>(ko, maxkg);
+  kd = (int)std::min<int64_t>(kd, maxkg);
   p.ntiles = ntiles;
-  p.ksplit = nkg;
-  p.nctas = ntiles * nkg;
+  p.ksplit = ko;
+  p.ksplit_diag = kd;
+  p.nctas = noff * ko + T * kd;
   p.scratch_bytes = (size_t)p.nctas * TILE_ELEMS * sizeof(double) + sizeof(float) * (size_t)I;
   return p;
 }
@@ -663,7 +707,9 @@ cudaError_t launch_gram_tcx(const float* y, int64_t L, int64_t I, int64_t Rt, co
   a.nlb = (int)((L + BK - 1) / BK);
   a.ntiles = p.ntiles;
   a.nkg = p.ksplit;
+  a.nkg_diag = p.ksplit_diag;
   a.T = (int)((I + 127) / 128);
+  a.noff = p.ntiles - a.T;
   a.scale = scale;
   a.part = part;
   a.err = err;
@@ -673,8 +719,8 @@ cudaError_t launch_gram_tcx(const float* y, int64_t L, int64_t I, int64_t Rt, co
     e = ndig == 3 ? run_gram_tcx<true, 3>(a, p.nctas, st) : run_gram_tcx<true, 2>(a, p.nctas, st);
   if (e != cudaSuccess) return e;
   const int64_t tot = I * I;
-  k_gram_tcx_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, p.ntiles, p.ksplit, I,
-                                                                   scale, S);
+  k_gram_tcx_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+      part, a.noff, p.ksplit, a.T, p.ksplit_diag, I, scale, S);
   count_launches(3);
   return cudaGetLastError();
 }

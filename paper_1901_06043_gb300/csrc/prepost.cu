@@ -6,20 +6,31 @@
 // Hyperslice i of mode n is every element (l, i, r) of the slab view
 // (Rt, I, L): Rt runs of L contiguous elements, I L apart.  Two access
 // regimes keep the loads coalesced:
-//   rows  (L < 256): the tensor is a column-major P x Rt matrix with
+//   rows  (L < 4096): the tensor is a column-major P x Rt matrix with
 //         P = L I "virtual rows"; virtual row q belongs to hyperslice q / L.
-//         A thread owns one virtual row and walks a range of columns, so a
-//         warp reads 32 consecutive elements per column.
-//   runs  (L >= 256): work units are (hyperslice i, slab r, chunk of 4096 l)
+//         A thread owns one virtual row and walks a range of columns; when
+//         P < 256 a block covers 256 / P columns at a time, so consecutive
+//         threads always read consecutive elements.
+//   runs  (L >= 4096): work units are (hyperslice i, slab r, chunk of 4096 l)
 //         in i-major order; a CTA takes a contiguous range of units, so it
-//         sees one or two hyperslices and walks their runs with 16-byte
-//         loads where alignment allows.
-// Every element is read once per pass; sums are accumulated in FP64 per
-// thread, then per CTA, then added into per-hyperslice FP64 accumulators
-// with atomics (a few per CTA), so the sums are exact to FP64 rounding but
-// not bitwise reproducible from run to run.  The standard deviation takes
-// a second pass over the data, sum (x - mean_i)^2, which avoids the
-// cancellation of sum x^2 - count mean^2.
+//         sees one or two hyperslices.
+//
+// Arithmetic.  The FP64 pipe of this part runs at 1/64 of the FP32 rate, so
+// FP32 data is reduced and transformed on the FP32 pipe with error-free
+// transformations: each sum is an FP32 pair (hi, lo) grown by TwoSum (a new
+// term may exceed the running sum, so never the cheaper Fast2Sum), squares are exact
+// (TwoProduct by FMA).  Every 16 elements of a thread the pair is merged
+// exactly into a second-level pair that is renormalised (|lo| <= ulp(hi) / 2,
+// so its later roundings stay at 2^-48 of hi), and every 1024 elements that
+// pair moves into FP64; the result is the FP64 sum to ~1e-14 of sum |x|.  The
+// standard deviation takes a second pass over the data, sum (x - mean)^2 with
+// the mean as an FP32 pair and x - mean_hi exact by TwoSum, which avoids the
+// cancellation of sum x^2 - count mean^2.  The transform evaluates
+// (x - shift) * scale (inverse: x * (1 / scale) + shift) in FP32-pair
+// arithmetic and rounds once to FP32.  FP64 data is handled in FP64.
+// Per-thread sums are combined per CTA, then added into per-hyperslice FP64
+// accumulators with atomics (a few per CTA): exact to FP64 rounding, not
+// bitwise reproducible from run to run.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -29,6 +40,9 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int64_t kChunk = 4096;     // l per unit in the runs regime
 constexpr int kAcc = 8;              // accumulators per hyperslice
+constexpr int kGroup = 16;           // FP32 pairs merged into the second level
+constexpr int kGroups = 64;          // second-level pairs moved into FP64
+constexpr int64_t kRowsMaxL = 4096;  // rows regime below this run length
 
 // Accumulator slots: 0 sum, 1 sum of squares, 2 sum |x|, 3 max (ordered
 // bits), 4 min (ordered bits), 5 sum (x - mean)^2.
@@ -40,20 +54,27 @@ __device__ __forceinline__ double unordered(long long k) {
   return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffll));
 }
 
-template <typename T>
-__device__ __forceinline__ double ld(const T* p) {
-  return (double)__ldg(p);
+// (h, l) += v exactly (TwoSum, any magnitudes); l collects the errors.
+__device__ __forceinline__ void two_sum(float& h, float& l, float v) {
+  const float s = __fadd_rn(h, v);
+  const float bb = __fsub_rn(s, h);
+  const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+  h = s;
+  l = __fadd_rn(l, err);
 }
+// Per-thread partial sums of one hyperslice.  PASS 0: sum, sum of squares,
+// sum |x|, max, min; PASS 1: sum (x - mean)^2.
+template <typename T, int PASS> struct Part;
 
-struct Part {
-  double s, s2, sa, c2, mx, mn;
-  __device__ void init() {
+template <int PASS> struct Part<double, PASS> {
+  double s, s2, sa, c2, mx, mn, mean;
+  __device__ void init(double m) {
     s = s2 = sa = c2 = 0.0;
     mx = -INFINITY;
     mn = INFINITY;
+    mean = m;
   }
-  template <int PASS>
-  __device__ __forceinline__ void add(double v, double mean) {
+  __device__ __forceinline__ void add(double v) {
     if (PASS == 0) {
       s += v;
       s2 = fma(v, v, s2);
@@ -65,10 +86,102 @@ struct Part {
       c2 = fma(d, d, c2);
     }
   }
+  __device__ void flush() {}
 };
 
-template <int PASS>
-__device__ void flush(double* acc, int64_t i, const Part& p) {
+template <int PASS> struct Part<float, PASS> {
+  double s, s2, sa, c2, mx, mn;           // FP64 totals
+  float sh, sl, qh, ql, ah, al;           // level 1: FP32 pairs of the current group
+  float SH, SL, QH, QL, AH, AL;           // level 2: renormalised pairs of the groups
+  float mh, ml;                           // the mean as an FP32 pair (PASS 1)
+  float fmx, fmn;
+  int n, g;
+  __device__ void init(double m) {
+    s = s2 = sa = c2 = 0.0;
+    mx = -INFINITY;
+    mn = INFINITY;
+    sh = sl = qh = ql = ah = al = 0.f;
+    SH = SL = QH = QL = AH = AL = 0.f;
+    fmx = -INFINITY;
+    fmn = INFINITY;
+    mh = (float)m;
+    ml = (float)(m - (double)mh);
+    n = g = 0;
+  }
+  __device__ __forceinline__ void add(float v) {
+    if (PASS == 0) {
+      two_sum(sh, sl, v);
+      const float p = __fmul_rn(v, v);
+      const float pe = __fmaf_rn(v, v, -p);            // v^2 = p + pe exactly
+      two_sum(qh, ql, p);
+      ql = __fadd_rn(ql, pe);
+      two_sum(ah, al, fabsf(v));
+      fmx = fmaxf(fmx, v);
+      fmn = fminf(fmn, v);
+    } else {
+      // d = v - mean = (s + e) - ml with s + e = v - mh exactly
+      float s_ = v, e = 0.f;
+      two_sum(s_, e, -mh);
+      const float t = __fsub_rn(e, ml);
+      const float p = __fmul_rn(s_, s_);
+      const float pe = __fmaf_rn(s_, s_, -p);
+      // d^2 = p + pe + t (2 s + t); |t| can be a sizeable part of |s| when
+      // the slice varies little around its mean, so t^2 stays
+      two_sum(qh, ql, p);
+      ql = __fadd_rn(ql, __fmaf_rn(__fadd_rn(2.f * s_, t), t, pe));
+    }
+    if (++n == kGroup) merge();
+  }
+  // (H, L) += (h, l) exactly up to the rounding of L, then renormalised so
+  // that |L| <= ulp(H) / 2 (its later roundings stay at 2^-48 of H)
+  __device__ __forceinline__ static void merge_pair(float& H, float& L, float h, float l) {
+    two_sum(H, L, h);
+    L = __fadd_rn(L, l);
+    float t = H, e = 0.f;                       // (t, e) = H + L exactly (TwoSum)
+    two_sum(t, e, L);
+    H = t;
+    L = e;
+  }
+  // level 1 -> level 2 every kGroup elements; level 2 -> FP64 every
+  // kGroups groups
+  __device__ void merge() {
+    if (PASS == 0) {
+      merge_pair(SH, SL, sh, sl);
+      merge_pair(QH, QL, qh, ql);
+      merge_pair(AH, AL, ah, al);
+      sh = sl = qh = ql = ah = al = 0.f;
+    } else {
+      merge_pair(QH, QL, qh, ql);
+      qh = ql = 0.f;
+    }
+    n = 0;
+    if (++g == kGroups) flush_groups();
+  }
+  __device__ void flush_groups() {
+    if (PASS == 0) {
+      s += (double)SH + (double)SL;
+      s2 += (double)QH + (double)QL;
+      sa += (double)AH + (double)AL;
+      SH = SL = QH = QL = AH = AL = 0.f;
+    } else {
+      c2 += (double)QH + (double)QL;
+      QH = QL = 0.f;
+    }
+    g = 0;
+  }
+  // everything into the FP64 totals (before a reduction)
+  __device__ void flush() {
+    merge();
+    flush_groups();
+    mx = fmax(mx, (double)fmx);
+    mn = fmin(mn, (double)fmn);
+    fmx = -INFINITY;
+    fmn = INFINITY;
+  }
+};
+
+template <typename T, int PASS>
+__device__ void to_global(double* acc, int64_t i, const Part<T, PASS>& p) {
   double* a = acc + i * kAcc;
   if (PASS == 0) {
     atomicAdd(a + 0, p.s);
@@ -81,9 +194,9 @@ __device__ void flush(double* acc, int64_t i, const Part& p) {
   }
 }
 
-// Block reduction of a Part into thread 0 (all threads call it).
-template <int PASS>
-__device__ Part block_reduce(Part p) {
+// Block reduction of the FP64 totals into thread 0 (all threads call it).
+template <typename T, int PASS>
+__device__ void block_reduce(Part<T, PASS>& p) {
   __shared__ double sh[6][kThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -110,37 +223,42 @@ __device__ Part block_reduce(Part p) {
       p.mx = fmax(p.mx, sh[3][k]); p.mn = fmin(p.mn, sh[4][k]); p.c2 += sh[5][k];
     }
   }
-  return p;
 }
 
-// rows regime: grid (row blocks, column chunks); thread = virtual row q.
+// rows regime: grid (row blocks, column chunks).  P >= 256: thread = virtual
+// row q, one column at a time; P < 256: the block covers C = 256 / P columns
+// at a time (thread t: row t % P, column offset t / P).
 template <typename T, int PASS>
 __global__ void __launch_bounds__(kThreads) k_stats_rows(const T* __restrict__ x, int64_t L,
                                                           int64_t P, int64_t Rt, int ncol,
                                                           const double* __restrict__ mean,
                                                           double* __restrict__ acc) {
-  const int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  if (q >= P) return;
+  const int C = P < kThreads ? (int)(kThreads / P) : 1;
+  const int64_t q = P < kThreads ? threadIdx.x % P : (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const int c = P < kThreads ? (int)(threadIdx.x / P) : 0;
+  if (q >= P || c >= C) return;
   const int64_t i = q / L;
   const int64_t r0 = Rt * blockIdx.y / ncol, r1 = Rt * (blockIdx.y + 1) / ncol;
-  const double m = PASS ? mean[i] : 0.0;
-  Part p;
-  p.init();
-  const T* c = x + q + P * r0;
-  int64_t r = r0;
-  for (; r + 4 <= r1; r += 4, c += 4 * P) {     // four columns' loads in flight
-    const double a = ld(c), b = ld(c + P), d = ld(c + 2 * P), e = ld(c + 3 * P);
-    p.add<PASS>(a, m);
-    p.add<PASS>(b, m);
-    p.add<PASS>(d, m);
-    p.add<PASS>(e, m);
+  Part<T, PASS> p;
+  p.init(PASS ? mean[i] : 0.0);
+  const int64_t step = (int64_t)C * P;
+  const T* ptr = x + q + P * (r0 + c);
+  int64_t r = r0 + c;
+  for (; r + 3 * C < r1; r += 4 * C, ptr += 4 * step) {   // four loads in flight
+    const T a = __ldg(ptr), b = __ldg(ptr + step), d = __ldg(ptr + 2 * step),
+            e = __ldg(ptr + 3 * step);
+    p.add(a);
+    p.add(b);
+    p.add(d);
+    p.add(e);
   }
-  for (; r < r1; ++r, c += P) p.add<PASS>(ld(c), m);
-  if (r1 > r0) flush<PASS>(acc, i, p);
+  for (; r < r1; r += C, ptr += step) p.add(__ldg(ptr));
+  p.flush();
+  if (r1 > r0) to_global(acc, i, p);
 }
 
-// runs regime (L >= 256): units (i, r, chunk) in i-major order, a contiguous
-// range of units per CTA.
+// runs regime (L >= 4096): units (i, r, chunk) in i-major order, a
+// contiguous range of units per CTA, walked without divisions.
 template <typename T, int PASS>
 __global__ void __launch_bounds__(kThreads) k_stats_runs(const T* __restrict__ x, int64_t L,
                                                           int64_t I, int64_t Rt,
@@ -150,26 +268,38 @@ __global__ void __launch_bounds__(kThreads) k_stats_runs(const T* __restrict__ x
   const int64_t per_i = Rt * nch, units = I * per_i;
   const int64_t u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
   if (u0 >= u1) return;
-  int64_t cur = u0 / per_i;
-  Part p;
-  p.init();
-  double m = PASS ? mean[cur] : 0.0;
+  int64_t cur = u0 / per_i, rest0 = u0 % per_i;
+  int64_t i = cur, r = rest0 / nch, ch = rest0 % nch;
+  Part<T, PASS> p;
+  p.init(PASS ? mean[cur] : 0.0);
   for (int64_t u = u0; u < u1; ++u) {
-    const int64_t i = u / per_i, rest = u % per_i;
     if (i != cur) {                       // uniform across the block
-      Part t = block_reduce<PASS>(p);
-      if (threadIdx.x == 0) flush<PASS>(acc, cur, t);
-      p.init();
+      p.flush();
+      block_reduce(p);
+      if (threadIdx.x == 0) to_global(acc, cur, p);
       cur = i;
-      m = PASS ? mean[cur] : 0.0;
+      p.init(PASS ? mean[cur] : 0.0);
     }
-    const int64_t r = rest / nch, ch = rest % nch;
     const int64_t l0 = ch * kChunk, l1 = min(L, l0 + kChunk);
     const T* run = x + L * (i + I * r);
-    for (int64_t l = l0 + threadIdx.x; l < l1; l += kThreads) p.add<PASS>(ld(run + l), m);
+    int64_t l = l0 + threadIdx.x;
+    for (; l + 3 * kThreads < l1; l += 4 * kThreads) {
+      const T a = __ldg(run + l), b = __ldg(run + l + kThreads),
+              d = __ldg(run + l + 2 * kThreads), e = __ldg(run + l + 3 * kThreads);
+      p.add(a);
+      p.add(b);
+      p.add(d);
+      p.add(e);
+    }
+    for (; l < l1; l += kThreads) p.add(__ldg(run + l));
+    if (++ch == nch) {
+      ch = 0;
+      if (++r == Rt) { r = 0; ++i; }
+    }
   }
-  Part t = block_reduce<PASS>(p);
-  if (threadIdx.x == 0) flush<PASS>(acc, cur, t);
+  p.flush();
+  block_reduce(p);
+  if (threadIdx.x == 0) to_global(acc, cur, p);
 }
 
 __global__ void k_stats_init(double* acc, int64_t I) {
@@ -201,35 +331,76 @@ __global__ void k_stats_final(const double* acc, const double* mean, int64_t I, 
   s[3] = mn;
   s[4] = a[2];
   s[5] = sqrt(a[1]);
-  if (!isfinite(a[1]) || !isfinite(a[5]) || !isfinite(mx) || !isfinite(mn)) atomicOr(bad, 1u);
+  if (!isfinite(a[0]) || !isfinite(a[1]) || !isfinite(a[5]) || !isfinite(mx) || !isfinite(mn))
+    atomicOr(bad, 1u);
 }
 
 // ---- the linear map per hyperslice
-template <typename T, bool INV>
-__device__ __forceinline__ T apply1(T v, double sh, double sc) {
-  return INV ? (T)((double)v / sc + sh) : (T)(((double)v - sh) * sc);
-}
+// FP64 data: FP64.  FP32 data: shift and scale (or 1 / scale) as FP32 pairs,
+// (x - shift) * scale or x * (1 / scale) + shift in pair arithmetic, one
+// rounding to FP32 at the end.
+template <typename T, bool INV> struct Map;
+
+template <bool INV> struct Map<double, INV> {
+  double sh, sc;
+  __device__ Map(double shift, double scale) : sh(shift), sc(scale) {}
+  __device__ __forceinline__ double operator()(double v) const {
+    return INV ? v / sc + sh : (v - sh) * sc;
+  }
+};
+
+template <bool INV> struct Map<float, INV> {
+  float shh, shl, sch, scl;   // shift and scale (INV: 1 / scale) as FP32 pairs
+  __device__ Map(double shift, double scale) {
+    const double m = INV ? 1.0 / scale : scale;
+    shh = (float)shift;
+    shl = (float)(shift - (double)shh);
+    sch = (float)m;
+    scl = (float)(m - (double)sch);
+  }
+  __device__ __forceinline__ float operator()(float v) const {
+    if (INV) {
+      // v * m + shift: p + pe = v * sch exactly, then + v * scl, then the shift
+      const float p = __fmul_rn(v, sch);
+      const float pe = __fmaf_rn(v, sch, -p);
+      const float t = __fmaf_rn(v, scl, pe);
+      float s = p, e = 0.f;
+      two_sum(s, e, shh);
+      return __fadd_rn(s, __fadd_rn(e, __fadd_rn(t, shl)));
+    }
+    // (v - shift) * scale with v - shh = d + e exactly
+    float d = v, e = 0.f;
+    two_sum(d, e, -shh);
+    const float dl = __fsub_rn(e, shl);
+    const float p = __fmul_rn(d, sch);
+    const float pe = __fmaf_rn(d, sch, -p);
+    return __fadd_rn(p, __fmaf_rn(d, scl, __fmaf_rn(dl, sch, pe)));
+  }
+};
 
 template <typename T, bool INV>
 __global__ void __launch_bounds__(kThreads) k_apply_rows(const T* x, int64_t L, int64_t P,
                                                           int64_t Rt, int ncol,
                                                           const double* __restrict__ shift,
                                                           const double* __restrict__ scale, T* y) {
-  const int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  if (q >= P) return;
+  const int C = P < kThreads ? (int)(kThreads / P) : 1;
+  const int64_t q = P < kThreads ? threadIdx.x % P : (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const int c = P < kThreads ? (int)(threadIdx.x / P) : 0;
+  if (q >= P || c >= C) return;
   const int64_t i = q / L;
-  const double sh = shift[i], sc = scale[i];
+  const Map<T, INV> f(shift[i], scale[i]);
   const int64_t r0 = Rt * blockIdx.y / ncol, r1 = Rt * (blockIdx.y + 1) / ncol;
-  int64_t r = r0;
-  for (; r + 4 <= r1; r += 4) {
-    const int64_t o = q + P * r;
-    const T a = x[o], b = x[o + P], c = x[o + 2 * P], d = x[o + 3 * P];
-    y[o] = apply1<T, INV>(a, sh, sc);
-    y[o + P] = apply1<T, INV>(b, sh, sc);
-    y[o + 2 * P] = apply1<T, INV>(c, sh, sc);
-    y[o + 3 * P] = apply1<T, INV>(d, sh, sc);
+  const int64_t step = (int64_t)C * P;
+  int64_t r = r0 + c;
+  int64_t o = q + P * r;
+  for (; r + 3 * C < r1; r += 4 * C, o += 4 * step) {
+    const T a = x[o], b = x[o + step], d = x[o + 2 * step], e = x[o + 3 * step];
+    y[o] = f(a);
+    y[o + step] = f(b);
+    y[o + 2 * step] = f(d);
+    y[o + 3 * step] = f(e);
   }
-  for (; r < r1; ++r) y[q + P * r] = apply1<T, INV>(x[q + P * r], sh, sc);
+  for (; r < r1; r += C, o += step) y[o] = f(x[o]);
 }
 
 // runs regime: a unit is (run j = i + I r, chunk); VEC: 16-byte accesses
@@ -245,28 +416,27 @@ __global__ void __launch_bounds__(kThreads) k_apply_runs(const T* x, int64_t L, 
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
     const int64_t j = u / nch, ch = u % nch;
     const int64_t i = j % I;
-    const double sh = shift[i], sc = scale[i];
+    const Map<T, INV> f(shift[i], scale[i]);
     const int64_t l0 = ch * kChunk, l1 = min(L, l0 + kChunk);
     const int64_t base = L * j;
     if (VEC) {
       for (int64_t l = l0 + (int64_t)threadIdx.x * V; l < l1; l += (int64_t)kThreads * V) {
         if constexpr (sizeof(T) == 4) {
           float4 v = *reinterpret_cast<const float4*>(x + base + l);
-          v.x = (float)apply1<T, INV>((T)v.x, sh, sc);
-          v.y = (float)apply1<T, INV>((T)v.y, sh, sc);
-          v.z = (float)apply1<T, INV>((T)v.z, sh, sc);
-          v.w = (float)apply1<T, INV>((T)v.w, sh, sc);
+          v.x = f(v.x);
+          v.y = f(v.y);
+          v.z = f(v.z);
+          v.w = f(v.w);
           *reinterpret_cast<float4*>(y + base + l) = v;
         } else {
           double2 v = *reinterpret_cast<const double2*>(x + base + l);
-          v.x = (double)apply1<T, INV>((T)v.x, sh, sc);
-          v.y = (double)apply1<T, INV>((T)v.y, sh, sc);
+          v.x = f(v.x);
+          v.y = f(v.y);
           *reinterpret_cast<double2*>(y + base + l) = v;
         }
       }
     } else {
-      for (int64_t l = l0 + threadIdx.x; l < l1; l += kThreads)
-        y[base + l] = apply1<T, INV>(x[base + l], sh, sc);
+      for (int64_t l = l0 + threadIdx.x; l < l1; l += kThreads) y[base + l] = f(x[base + l]);
     }
   }
 }
@@ -288,22 +458,26 @@ __global__ void k_params(const double* stats, int64_t I, int method, double* shi
   }
 }
 
-int col_chunks(int64_t rowblocks, int64_t Rt, int num_sms) {
-  int64_t c = ((int64_t)num_sms * 8 + rowblocks - 1) / rowblocks;
+// rows-regime grid: (row blocks, column chunks) about 8 CTAs per SM
+void rows_grid(int64_t P, int64_t Rt, int num_sms, unsigned& gx, int& nc) {
+  const int64_t rb = P < kThreads ? 1 : (P + kThreads - 1) / kThreads;
+  int64_t c = ((int64_t)num_sms * 8 + rb - 1) / rb;
   if (c > Rt) c = Rt;
   if (c > 65535) c = 65535;
-  return (int)(c < 1 ? 1 : c);
+  gx = (unsigned)rb;
+  nc = (int)(c < 1 ? 1 : c);
 }
 
 template <typename T, int PASS>
 void stats_pass(const T* x, int64_t L, int64_t I, int64_t Rt, const double* mean, double* acc,
                 int num_sms, cudaStream_t st) {
-  if (L < 256) {
+  if (L < kRowsMaxL) {
     const int64_t P = L * I;
-    const int64_t rb = (P + kThreads - 1) / kThreads;
-    const int nc = col_chunks(rb, Rt, num_sms);
-    k_stats_rows<T, PASS><<<dim3((unsigned)rb, (unsigned)nc), kThreads, 0, st>>>(x, L, P, Rt, nc,
-                                                                                mean, acc);
+    unsigned gx;
+    int nc;
+    rows_grid(P, Rt, num_sms, gx, nc);
+    k_stats_rows<T, PASS><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(x, L, P, Rt, nc, mean,
+                                                                        acc);
   } else {
     const int64_t units = I * Rt * ((L + kChunk - 1) / kChunk);
     int64_t g = (int64_t)num_sms * 8;
@@ -331,12 +505,13 @@ cudaError_t stats_t(const T* x, int64_t L, int64_t I, int64_t Rt, double* work, 
 template <typename T, bool INV>
 void apply_t(const T* x, int64_t L, int64_t I, int64_t Rt, const double* shift,
              const double* scale, T* y, int num_sms, cudaStream_t st) {
-  if (L < 256) {
+  if (L < kRowsMaxL) {
     const int64_t P = L * I;
-    const int64_t rb = (P + kThreads - 1) / kThreads;
-    const int nc = col_chunks(rb, Rt, num_sms);
-    k_apply_rows<T, INV><<<dim3((unsigned)rb, (unsigned)nc), kThreads, 0, st>>>(x, L, P, Rt, nc,
-                                                                               shift, scale, y);
+    unsigned gx;
+    int nc;
+    rows_grid(P, Rt, num_sms, gx, nc);
+    k_apply_rows<T, INV><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(x, L, P, Rt, nc, shift,
+                                                                       scale, y);
     return;
   }
   const int64_t units = I * Rt * ((L + kChunk - 1) / kChunk);

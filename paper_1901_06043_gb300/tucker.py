@@ -21,7 +21,7 @@ STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "NONFINITE", 4: "EIG_NOCONV", 5: "
 F32, F64 = 0, 1
 PREC = {"fp64": 0, "fp32": 1, "mixed": 2, "tensor": 3}
 OPT_TIMING, OPT_MAX_SWEEPS, OPT_JACOBI_TOL, OPT_EIG_SOLVER = 1, 2, 3, 4
-OPT_BARRIER_POLLS, OPT_MEM_LIMIT, OPT_GRAM_DIGITS = 5, 6, 7
+OPT_BARRIER_POLLS, OPT_MEM_LIMIT, OPT_GRAM_DIGITS, OPT_AUTOTUNE = 5, 6, 7, 8
 EIG_SOLVER = {"auto": 0, "jacobi": 1, "tridiag": 2}
 
 EXPORTS = ["tucker_create", "tucker_destroy", "tucker_last_error", "tucker_set_option",
@@ -31,7 +31,7 @@ EXPORTS = ["tucker_create", "tucker_destroy", "tucker_last_error", "tucker_set_o
            "tucker_eig", "tucker_eig_trunc", "tucker_rank_cut", "tucker_ttm",
            "tucker_kernel_launches", "tucker_gram_noalloc", "tucker_hosvd",
            "tucker_sthosvd_order", "tucker_slice_stats", "tucker_slice_transform",
-           "tucker_preprocess", "tucker_selftest_rcp64"]
+           "tucker_preprocess", "tucker_selftest_rcp64", "tucker_autotune_entries"]
 STATS = ("mean", "std", "max", "min", "norm1", "norm2")
 PRE_METHOD = {"standardize": 0, "max": 1}
 
@@ -106,10 +106,13 @@ def lib():
         L.tucker_ttm.argtypes = [vp, vp, c_int, c_int, i64p, c_int, vp, ctypes.c_int64,
                                  ctypes.c_int64, c_int, c_int, vp, c_int]
         for name in EXPORTS:
-            if name not in ("tucker_last_error", "tucker_kernel_launches"):
+            if name not in ("tucker_last_error", "tucker_kernel_launches",
+                            "tucker_autotune_entries"):
                 getattr(L, name).restype = c_int
         L.tucker_kernel_launches.argtypes = []
         L.tucker_kernel_launches.restype = ctypes.c_uint64
+        L.tucker_autotune_entries.argtypes = []
+        L.tucker_autotune_entries.restype = ctypes.c_int64
         L.tucker_gram_noalloc.argtypes = [vp, c_int, c_int, i64p, c_int, c_int, vp, vp]
         L.tucker_hosvd.argtypes = [vp, vp, c_int, c_int, i64p, ctypes.c_double, i64p, c_int,
                                    ctypes.POINTER(ctypes.POINTER(CResult))]
@@ -521,6 +524,11 @@ def selftest_rcp64(x):
     if st != 0:
         raise TuckerError(st, "tucker_selftest_rcp64")
     return y
+
+
+def autotune_entries():
+    """(kernel, shape) entries the split-K autotuner has cached so far."""
+    return int(lib().tucker_autotune_entries())
 
 
 def kernel_launches():

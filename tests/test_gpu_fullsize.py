@@ -196,7 +196,9 @@ def test_c256_both_paths_against_the_oracle(ctx):
         _check_fp64_path(r64, ref, dims)
         rmx = ctx.sthosvd(x, dims, eps=eps, prec="mixed")
         # the exact-digit Gram's error bound allows it down to eps = 1e-5 here
-        assert rmx.gram_kernel[:3] == ["tcgen05-x3"] * 3, (eps, rmx.gram_kernel)
+        # (with two digits or three, as the bound decides per view)
+        assert all(k in ("tcgen05-x3", "tcgen05-x2") for k in rmx.gram_kernel[:3]), (
+            eps, rmx.gram_kernel)
         _check_mixed_path(rmx, ref, dims, eps)
         r64.close()
         rmx.close()
@@ -223,7 +225,7 @@ def test_large_mixed_path_full_size(ctx):
     rmx = ctx.sthosvd(x, dims, eps=1e-4, prec="mixed")
     _check_mixed_path(rmx, ref, dims, 1e-4)
     assert rmx.ranks == r64.ranks
-    assert rmx.gram_kernel[0] == "tcgen05-x3" and rmx.ttm_kernel[0] == "tcgen05"
+    assert rmx.gram_kernel[0] in ("tcgen05-x3", "tcgen05-x2") and rmx.ttm_kernel[0] == "tcgen05"
     err = math.sqrt(sum(rmx.discarded) / rmx.norm_sq)
     assert err <= 1e-4
     # Cor. 1: ||X - Xhat||^2 = sum of the discarded eigenvalues (relative to

@@ -297,6 +297,16 @@ def test_gram_mixed_mode0_exact_digits(ctx, dims, digits):
     assert np.array_equal(got, got.T)
 
 
+def _digit_err6(X, thr, digits):
+    """Six standard deviations of the digit representation's error on the
+    discarded subspace of the I x K matrix X (numpy), the bound the library
+    chooses its digit count by: sqrt(4 sigma_max^2 thr + 2 K sigma_max^2
+    sum_i sigma_i^2) with sigma_i^2 = delta_i^2 / 3."""
+    d = _digit_delta(np.abs(X), digits)
+    s2max, s2sum = d.max() ** 2 / 3.0, float((d * d).sum()) / 3.0
+    return 6.0 * math.sqrt(4.0 * s2max * thr + 2.0 * X.shape[1] * s2max * s2sum)
+
+
 def _digit_trace_sigma(X, digits=3):
     """Standard deviation of the trace error of the exact-digit Gram for the
     I x K matrix X (torch, any device): the last digit rounds each value to
@@ -348,20 +358,28 @@ def test_gram_mixed_mode0_error_on_discarded_subspace(ctx, digits):
     proj = np.trace(P.T @ E @ P)
     sigma = _digit_trace_sigma(x.view(-1, dims[0]).T, digits)
     assert abs(np.trace(E)) <= 6 * sigma, np.trace(E) / sigma
-    assert abs(proj) <= 0.02 * thr, proj / thr
+    # within 2 % of the threshold with three digits; with two, within the six
+    # standard deviations of the bound the library chooses its digits by
+    bound = 0.02 * thr if digits == 3 else _digit_err6(host(x).reshape(-1, dims[0]).T, thr, 2)
+    assert abs(proj) <= bound, (proj / thr, bound / thr)
 
 
-def test_mixed_two_digit_gram_where_its_bound_allows(ctx):
-    """An eps-driven MIXED ST-HOSVD takes two digits for a view whose bound
-    (six standard deviations of the representation error on the discarded
-    subspace below 1 % of the threshold) allows it: the long mode-0 view of
-    a 256 x 64 x 200 x 11 tensor at eps = 1e-3.  Ranks and discarded sums as
-    the oracle's."""
+@pytest.mark.parametrize("eps", [1e-2, 1e-3, 1e-4])
+def test_mixed_digit_count_follows_its_bound(ctx, eps):
+    """An eps-driven MIXED ST-HOSVD takes two digits for the mode-0 view when
+    six standard deviations of the two-digit representation error on the
+    discarded subspace stay below 1 % of the threshold, else three: checked
+    against the bound computed here from the view's row maxima, on a
+    256 x 64 x 200 x 11 tensor at three eps.  Ranks and discarded sums as the
+    oracle's."""
     dims = (256, 64, 200, 11)
     x = synth.tucker_torch(dims, (40, 20, 30, 11), decay=0.1, eta=1e-7, seed=4)
-    res = ctx.sthosvd(x, dims, eps=1e-3, prec="mixed")
-    ref = oracle.sthosvd(host(x), dims, eps=1e-3)
-    assert res.gram_kernel[0] == "tcgen05-x2", res.gram_kernel
+    res = ctx.sthosvd(x, dims, eps=eps, prec="mixed")
+    ref = oracle.sthosvd(host(x), dims, eps=eps)
+    two = _digit_err6(host(x).reshape(-1, dims[0]).T, ref["threshold"], 2) <= 0.01 * ref["threshold"]
+    assert res.gram_kernel[0] == ("tcgen05-x2" if two else "tcgen05-x3"), res.gram_kernel
+    if eps == 1e-2:
+        assert two
     assert res.ranks == ref["ranks"]
     for n in range(4):
         assert abs(res.discarded[n] - ref["discarded"][n]) <= 0.02 * ref["threshold"]
@@ -582,6 +600,38 @@ def test_eig_trunc_fp64(ctx, solver, name, S, cut):
     assert np.abs(U.T @ U - np.eye(R)).max() <= 1e-13 * n
     assert np.abs(S @ U - U * w[:R]).max() <= 1e-13 * np.linalg.norm(S) * n
     if R < n and (w_ref[R - 1] - w_ref[R]) > 1e-6 * lmax:
+        assert sin_angle(V_ref[:, :R], U) <= 1e-8
+
+
+@pytest.mark.parametrize("n", [1500, 2080])
+def test_eig_trunc_jicf_sized(ctx, n):
+    """The truncated eigensolve (tridiagonal solver: all eigenvalues, the R
+    leading vectors) at the mode sizes of the JICF dataset (1500 and 2080,
+    the paper's largest modes, where it notes the eigensolve becomes
+    visible) on a graded Tucker-like spectrum, against the oracle; the time
+    of one solve is printed."""
+    import time
+    S = _graded(n, 31 + n, decay=0.02)
+    S = (S + S.T) / 2
+    w_ref, V_ref = oracle.eig_desc(S)
+    lmax = abs(w_ref).max()
+    thr = 1e-8 * abs(w_ref).sum()
+    R_ref, tail = oracle.rank_cut(w_ref, thr)
+    Sd = dev(S)
+    ctx.eig_trunc(Sd, thr=thr)                   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    w, U, R, disc = ctx.eig_trunc(Sd, thr=thr)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3
+    print(f"eig_trunc n={n}: R={R}, {ms:.1f} ms")
+    w, U = host(w), host(U)
+    assert np.abs(w - w_ref).max() <= 1e-10 * lmax
+    assert R == R_ref
+    assert abs(disc - tail[R]) <= 1e-12 * lmax * n
+    assert np.abs(U.T @ U - np.eye(R)).max() <= 1e-13 * n
+    assert np.abs(S @ U - U * w[:R]).max() <= 1e-13 * np.linalg.norm(S) * n
+    if (w_ref[R - 1] - w_ref[R]) > 1e-6 * lmax:
         assert sin_angle(V_ref[:, :R], U) <= 1e-8
 
 
@@ -931,12 +981,13 @@ def test_sthosvd_mixed_path_ranks_and_error(ctx, eps):
     xs = host(x)
     ref = oracle.sthosvd(xs, dims, eps=eps)
     res = ctx.sthosvd(x, dims, eps=eps, prec="mixed")
-    assert res.gram_kernel[0] == "tcgen05-x3"
+    digit = ("tcgen05-x3", "tcgen05-x2")
+    assert res.gram_kernel[0] in digit
     assert res.ttm_kernel[0] == "tcgen05"
     # natural mode order: the working tensor is kept rotated (each TTM writes
     # its new mode last), so mode 1 is a column-mode view (I = 160) and both
     # its Gram and its TTM run on the tensor cores
-    assert res.gram_kernel[1] == "tcgen05-x3" and res.ttm_kernel[1] == "tcgen05"
+    assert res.gram_kernel[1] in digit and res.ttm_kernel[1] == "tcgen05"
     assert res.ranks == ref["ranks"]
     ours = {"core": host(res.core), "core_dims": res.ranks,
             "factors": [host(f) for f in res.factors], "discarded": res.discarded,
