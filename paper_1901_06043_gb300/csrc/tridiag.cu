@@ -164,10 +164,10 @@ __global__ void __launch_bounds__(TNT, 1) k_tridiag(const EigProblem* probs, int
   __syncthreads();
   double tau_k, beta;
   house(vn, 1, n, red0, tau_k, beta);
-  if (c == 0) {
-    if (threadIdx.x == 0) { P.d[0] = A[0]; P.e[0] = beta; P.tau[0] = tau_k; }
-    for (int j = 2 + threadIdx.x; j < n; j += TNT) A[j] = vn[j];
-  }
+  if (c == 0 && threadIdx.x == 0) { P.d[0] = A[0]; P.e[0] = beta; P.tau[0] = tau_k; }
+  // (row 0 of A receives its reflector only after the team's first barrier:
+  // every CTA reads row 0 above, and a CTA that starts late must not see it
+  // overwritten)
   {
     double pv = 0.0;
     const int i0 = 1 + ((c - 1) % G + G) % G;   // smallest own row >= 1
@@ -189,6 +189,8 @@ __global__ void __launch_bounds__(TNT, 1) k_tridiag(const EigProblem* probs, int
   }
   { double* t = vk; vk = vn; vn = t; }
   if (G > 1) { if (!grid_sync(bar, gen, poll_limit, (unsigned)G)) return; } else __syncthreads();
+  if (c == 0)   // v_0 (now vk) into row 0, read by nobody after the barrier
+    for (int j = 2 + threadIdx.x; j < n; j += TNT) A[j] = vk[j];
 
   // ---- phases 0 .. n-3
   for (int k = 0; k <= n - 3; ++k) {
