@@ -542,8 +542,9 @@ FP64_PEAK_TFLOPS = 1.19   # measured FP64 FMA throughput on this part (in-regist
 # of `bench.py --workload prof --steps 1 --warmup 3 --no-fp64 --no-e2e
 # --no-cpu` (the 500x500x40x11x2 FP32 tensor), mode 0.
 CAPTURED_TRAFFIC = {
-    # k_gram_tcx (column mode), mode-0 Gram of 500x500x40x11x2 FP32
-    ("gram", "tcgen05-x3", "col"): dict(bytes=1266.0e6, elems=500 * 440000),
+    # k_gram_tcx (column mode, three digits), mode-0 Gram of 500x500x40x11x2
+    # FP32: 741.3 GB/s x 1.192 ms
+    ("gram", "tcgen05-x3", "col"): dict(bytes=883.3e6, elems=500 * 440000),
     # (no capture of the two-digit variant yet)
     # k_ttm_tc_col (transposed output), mode-0 TTM of 500x500x40x11x2 FP32 to 54 rows
     ("ttm", "tcgen05", "col"): dict(bytes=966.8e6, elems=500 * 440000),

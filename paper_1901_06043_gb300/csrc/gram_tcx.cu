@@ -7,10 +7,10 @@
 //     x s_i = d0 + d1 / 2^7 + d2 / 2^14 + r,   |d0|, |d1|, |d2| <= 64,
 // by two rounds of "round to the nearest integer, subtract, scale by 2^7"
 // (each subtraction and scaling is exact; r, the last rounding, is the only
-// error: |r| <= 2^-15 in these units, 2^-20 of the row maximum, unbiased and
-// independent of the value).  Digits, and d2 / 2^7, are exact in FP16.  The
-// tensor cores (kind::f16, FP32 accumulators in tensor memory) form all nine
-// digit products, grouped by weight:
+// error: |r| <= 2^-15 in these units, 2^-20 of the row maximum).  Digits, and
+// d2 / 2^7, are exact in FP16.  The tensor cores (kind::f16, FP32
+// accumulators in tensor memory) form all nine digit products, grouped by
+// weight:
 //     D0 = sum d0 d0'                                      (weight 1)
 //     D1 = sum (d0 d1' + d1 d0')                          (2^-7)
 //     D2 = sum (d0 d2' + d1 d1' + d2 d0')                 (2^-14)
@@ -19,15 +19,33 @@
 // window of 1024 columns every partial sum stays an integer below 2^24, so
 // those accumulators are exact and the accumulator's truncation never acts
 // (it is what moves the eps cut for the rounded-product tensor-core Gram of
-// tc.cu).  D3 is not integral, but at weight 2^-21 its truncation is ~2^-45 of
-// an entry.  Leaving D3 out is not an option: its terms have nonzero mean
-// (d2^2 > 0; and when d1 rounds to +-64 the remainder d2 takes the opposite
-// sign), measured as a +1e-8 relative bias on a trace.  After each window the
-// epilogue warps drain the four sums and add D0, D1 / 2^7, D2 / 2^14 and
-// D3 / 2^21 one by one into an exact FP32 pair (TwoSum, hi + lo) in shared
-// memory (a combined value rounded to FP32 first measured a +1e-8 trace
-// bias).  The pairs go out as FP64 per-CTA partial tiles; a second kernel sums
-// the K splits in a fixed order and removes the scales, S_ij = D_ij / (s_i s_j).
+// tc.cu).  D3 is not integral: at weight 2^-21 its rounding is ~2^-45 of an
+// entry, zero-mean off the diagonal, but on the diagonal it measured a
+// systematic +1 % of sum_k r_ik^2, enough to move the sum of the small
+// eigenvalues by ~2 % of an eps = 1e-5 threshold; so each diagonal entry's D3
+// is summed exactly by the producers (as integers, 2 d1 d2 and d2^2) and the
+// tensor cores' D3 is left out there.  Leaving D3 out everywhere is not an
+// option: its terms have nonzero mean (d2^2 > 0; and when d1 rounds to +-64
+// the remainder d2 takes the opposite sign), measured as a +1e-8 relative
+// bias on a trace.  After each window the epilogue warps drain the four sums
+// and add D0, D1 / 2^7, D2 / 2^14 and D3 / 2^21 one by one into an exact FP32
+// pair (TwoSum, hi + lo) in shared memory (a combined value rounded to FP32
+// first measured a +1e-8 trace bias).  The pairs go out as FP64 per-CTA
+// partial tiles; a second kernel sums the K splits in a fixed order and
+// removes the scales, S_ij = D_ij / (s_i s_j).
+//
+// The remainders.  The digits give G = sum_k d_ik d_jk with d = x - r, and
+// r is correlated with x (it is x's own low part): for a row whose
+// neighbours are linear in it, E[x_ik r_jk] = rho_j S_ij / K with rho_j =
+// E[r^2] / E[x_j^2] (~2^-40).  So E[G] = S - (S diag(rho) + diag(rho) S) +
+// diag(sum_k r_ik^2): every direction is scaled by 1 - O(rho) except for
+// the diagonal term, which adds v' diag(sum r^2) v to each eigenvalue and
+// so lifts each of the I - R discarded ones by about K E[r^2].  Each diagonal
+// entry therefore gets minus its row's sum of r^2 (exact FP64 sums from the
+// producers): in an emulation of the digit arithmetic on a 256 x 90112
+// view of the benchmarks' recipe (rank 40 plus noise), the sum of the 216
+// small eigenvalues lands within 3e-4 of an eps = 1e-5 threshold of its exact
+// value this way, and half a threshold off without the term.
 //
 // The digit split and the TwoSums run on packed FP32 pairs (f32x2
 // instructions, two values per instruction, each rounded as the scalar op);
@@ -71,7 +89,7 @@ constexpr int NTHREADS = (EPI_WARP0 + NEPI) * 32;   // 768: 24 warps, 80 registe
 constexpr uint32_t ATOM = 1024;
 constexpr uint32_t PLANE_STEP = 2 * ATOM;       // plane q starts at atom 2q
 constexpr uint32_t PAIR_BYTES = 128 * 128 * 4;  // hi or lo tile, [col / 2][row][col % 2]
-constexpr uint32_t RSUM_BYTES = 16 * 128 * 4;   // remainder sums, [producer warp][row]
+constexpr uint32_t DCORR_BYTES = 128 * 8;      // diagonal corrections per row (FP64)
 constexpr int TILE_ELEMS = 128 * 128;
 // time per column of a diagonal tile's CTA relative to an off-diagonal one's
 // (the producers, which bound the kernel, split 128 rows instead of 256)
@@ -94,9 +112,7 @@ struct Dig {
   static constexpr uint32_t OFF_A = 0, OFF_B = 2 * KG_A;
   static constexpr uint32_t STAGE_BYTES = 2 * KG_A + 2 * KG_B;   // 28 KB / 16 KB
   static constexpr uint32_t SMEM_BYTES =
-      NSTAGE * STAGE_BYTES + 2 * PAIR_BYTES + RSUM_BYTES + 1024;
-  // squared last-digit remainders are summed in units of the last digit
-  static constexpr float RSCALE = NDIG == 3 ? 0x1p-28f : 0x1p-14f;
+      NSTAGE * STAGE_BYTES + 2 * PAIR_BYTES + DCORR_BYTES + 1024;
 };
 
 // Byte offset of (mn, k) (mn < 128, k < 16) in plane 0 of an operand region
@@ -142,14 +158,28 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {    // a - b, one ro
   return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
 }
 
+// Per-row sums a diagonal tile's producers keep for its diagonal entries,
+// two rows per float2 (FP32, exact or short; moved into FP64 every 32
+// stages): r2 = sum r^2 (r the last rounding's remainder, in units of the
+// last digit) and, with three digits, the diagonal's D3 terms as integers,
+// a3 = sum 2 d1 d2 and b3 = sum d2^2 (at most 2^18 and 2^17 over 32 stages).
+struct DiagAcc {
+  float2 r2[2], a3[2], b3[2];
+  __device__ void zero() {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) r2[u] = a3[u] = b3[u] = make_float2(0.f, 0.f);
+  }
+};
+
 // The digits of two scaled values x (|x| < 64): d0, d1 and (NDIG == 3) d2
 // and d2 / 2^7.  x + 1.5 * 2^23 lies in [2^23, 2^24), where the FP32 spacing
 // is 1, so the add rounds x to the nearest integer and the subtraction of the
-// constant is exact.  R: also add r^2 to racc, r the exact remainder of the
-// last rounding in units of the last digit (|r| <= 1/2):
-// r = 2^14 (x - d0 - d1 / 2^7 - d2 / 2^14), or 2^7 (x - d0 - d1 / 2^7).
+// constant is exact.  R: also add to the diagonal sums (u = 0, 1: which pair
+// of rows) r^2, r the exact remainder of the last rounding in units of the
+// last digit (|r| <= 1/2): r = 2^14 (x - d0 - d1 / 2^7 - d2 / 2^14), or
+// 2^7 (x - d0 - d1 / 2^7); with three digits also 2 d1 d2 and d2^2.
 template <int NDIG, bool R>
-__device__ __forceinline__ void digits2(float2 x, float2 (&d)[4], float2& racc) {
+__device__ __forceinline__ void digits2(float2 x, float2 (&d)[4], DiagAcc& acc, int u) {
   const float2 M = make_float2(0x1.8p23f, 0x1.8p23f), NM = make_float2(-0x1.8p23f, -0x1.8p23f);
   const float2 B = make_float2(128.f, 128.f);
   const float2 d0 = add2(add2(x, M), NM);
@@ -160,27 +190,29 @@ __device__ __forceinline__ void digits2(float2 x, float2 (&d)[4], float2& racc) 
   d[0] = d0;
   d[1] = d1;
   if (NDIG == 2) {
-    if (R) racc = fma2(f, f, racc);
+    if (R) acc.r2[u] = fma2(f, f, acc.r2[u]);
     return;
   }
   const float2 t2 = fma2(f, B, M);
   const float2 d2 = add2(t2, NM);                // round(128 f)
   if (R) {
     const float2 r = fma2(f, B, sub2(M, t2));    // 128 f - d2, exact, |r| <= 1/2
-    racc = fma2(r, r, racc);
+    acc.r2[u] = fma2(r, r, acc.r2[u]);
+    acc.a3[u] = fma2(mul2(d1, d2), make_float2(2.f, 2.f), acc.a3[u]);   // integers: exact
+    acc.b3[u] = fma2(d2, d2, acc.b3[u]);
   }
   d[2] = d2;
   d[3] = mul2(d2, make_float2(0x1p-7f, 0x1p-7f));
 }
 
 // The digit planes of four values (scaled by s) as FP16 pairs: the first NP
-// of d0, d1, d2, d2 / 2^7; R: squared remainders added to racc.
+// of d0, d1, d2, d2 / 2^7; R: the diagonal sums of the four rows grow.
 template <int NP, int NDIG, bool R>
 __device__ __forceinline__ void digits4(float4 v, const float2 (&s)[2], uint2 (&p)[4],
-                                        float2 (&racc)[2]) {
+                                        DiagAcc& acc) {
   float2 a[4], b[4];
-  digits2<NDIG, R>(mul2(make_float2(v.x, v.y), s[0]), a, racc[0]);
-  digits2<NDIG, R>(mul2(make_float2(v.z, v.w), s[1]), b, racc[1]);
+  digits2<NDIG, R>(mul2(make_float2(v.x, v.y), s[0]), a, acc, 0);
+  digits2<NDIG, R>(mul2(make_float2(v.z, v.w), s[1]), b, acc, 1);
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
     const __half2 lo = __float22half2_rn(a[q]);
@@ -188,6 +220,29 @@ __device__ __forceinline__ void digits4(float4 v, const float2 (&s)[2], uint2 (&
     p[q].x = *reinterpret_cast<const uint32_t*>(&lo);
     p[q].y = *reinterpret_cast<const uint32_t*>(&hi);
   }
+}
+
+// The FP32 diagonal sums of the lane's four rows into the FP64 totals of
+// their diagonal correction, in scaled units: + D3's diagonal terms
+// (2 d1 d2) / 2^21 + d2^2 / 2^28 (three digits), - r^2 times the last
+// digit's squared weight.
+template <int NDIG>
+__device__ __forceinline__ void flush_diag(DiagAcc& acc, double (&tot)[4]) {
+  constexpr double W = NDIG == 3 ? 0x1p-28 : 0x1p-14;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float2 r2 = acc.r2[j >> 1];
+    double v = -(double)((j & 1) ? r2.y : r2.x);
+    if (NDIG == 3) {
+      const float2 a3 = acc.a3[j >> 1], b3 = acc.b3[j >> 1];
+      v += (double)((j & 1) ? b3.y : b3.x);
+      v = fma((double)((j & 1) ? a3.y : a3.x), 0x1p-21, v * W);
+    } else {
+      v *= W;
+    }
+    tot[j] += v;
+  }
+  acc.zero();
 }
 
 // (h, l) += v exactly for two entries (TwoSum; l collects the rounding errors).
@@ -224,12 +279,30 @@ __device__ __forceinline__ void offdiag_tile(int j, int& ta, int& tb) {
   tb = j;
 }
 
-// This CTA's tile and K split: off-diagonal tiles first (g.nkg splits each,
-// the tiles of a split adjacent in launch order so their shared columns are
-// served from L2), then the diagonal tiles (g.nkg_diag splits each).
+// Tile t of the lower triangle in row order: (ta, tb) with t = ta (ta + 1) / 2 + tb.
+__device__ __forceinline__ void tile_of(int t, int& ta, int& tb) {
+  int a = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while ((a + 1) * (a + 2) / 2 <= t) ++a;
+  while (a * (a + 1) / 2 > t) --a;
+  ta = a;
+  tb = t - a * (a + 1) / 2;
+}
+
+// This CTA's tile and K split.  Equal splits (the planner's choice): split
+// by split, all tiles of a split adjacent in launch order, so the CTAs that
+// read the same columns at the same time sit side by side (same die, same
+// L2 partition).  Measured on a 500 x 440000 view: DRAM traffic 1.00x the
+// input in this order, 1.59x with the diagonal tiles' CTAs moved behind the
+// off-diagonal ones (the same columns then read by CTAs far apart).  Unequal
+// splits: the off-diagonal tiles first (g.nkg splits each, the tiles of a
+// split adjacent), then the diagonal ones (g.nkg_diag splits each).
 __device__ __forceinline__ void cta_work(const GramTcxArgs& g, int b, int& ta, int& tb, int& kg,
                                          int& nkg) {
-  if (b < g.noff * g.nkg) {
+  if (g.nkg == g.nkg_diag) {
+    tile_of(b % g.ntiles, ta, tb);
+    kg = b / g.ntiles;
+    nkg = g.nkg;
+  } else if (b < g.noff * g.nkg) {
     offdiag_tile(b % g.noff, ta, tb);
     kg = b / g.noff;
     nkg = g.nkg;
@@ -254,14 +327,19 @@ __device__ __forceinline__ void cta_work(const GramTcxArgs& g, int b, int& ta, i
 // spills; 2 in row mode, measured faster than 3 there).  (An L2
 // prefetch PD stages ahead changed nothing in column mode and cost 30 % in row
 // mode, where the extra instructions outweighed the latency they hid.)  NOPS == 1 (diagonal tile):
-// the squared last-digit remainders of the lane's rows go to rsum[slot][row]
-// (slot: the warp in column mode, lane % 16 in row mode).
+// the lane's rows' diagonal corrections (flush_diag) are added into
+// dcorr[row] (FP64, shared by the CTA's producers).
 template <int NOPS, bool ROW, int NDIG>
 __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uint64_t* bar_full,
                                         uint64_t* bar_empty, const float* s_scale, int ta,
                                         int tb, int64_t k0, int64_t k1, int64_t gs0, int nst,
-                                        int warp, int lane, float* rsum) {
-  float2 racc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                                        int warp, int lane, double* dcorr) {
+  // diagonal sums: FP32 over 32 stages (exact for the integer sums; for r^2
+  // a short sum, where small terms are not lost against a large total),
+  // then FP64 per row
+  DiagAcc acc;
+  acc.zero();
+  double dtot[4] = {0.0, 0.0, 0.0, 0.0};
   const int mn = ROW ? 8 * warp + 4 * (lane >> 4) : 4 * lane;   // first row of the lane
   const int kcol = ROW ? (lane & 15) : warp;                     // stage column of the lane
   const int64_t row0[2] = {(int64_t)ta * 128 + mn, (int64_t)tb * 128 + mn};
@@ -347,8 +425,8 @@ __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uin
       // split first, then wait for the slot: a freed slot only waits for
       // the stores (the split is off the MMA -> producer -> MMA hand-off)
       uint2 p[4], pb[4];
-      digits4<D::NPA, NDIG, NOPS == 1>(v[0], sc[0], p, racc);
-      if (NOPS == 2) digits4<D::NPB, NDIG, false>(v[NOPS - 1], sc[NOPS - 1], pb, racc);
+      digits4<D::NPA, NDIG, NOPS == 1>(v[0], sc[0], p, acc);
+      if (NOPS == 2) digits4<D::NPB, NDIG, false>(v[NOPS - 1], sc[NOPS - 1], pb, acc);
       if (s >= NSTAGE) {
         if (!mbar_wait(smem_u32(&bar_empty[slot]), eph, g.err)) { go = false; break; }
       }
@@ -364,14 +442,14 @@ __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uin
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bar_full[slot]));
       if (++slot == NSTAGE) { slot = 0; eph ^= 1u; }
+      if (NOPS == 1 && (s & 31) == 31) flush_diag<NDIG>(acc, dtot);
     }
   }
   if (NOPS == 1) {
-    const int slotw = ROW ? kcol : warp;
-    rsum[slotw * 128 + mn + 0] = racc[0].x;
-    rsum[slotw * 128 + mn + 1] = racc[0].y;
-    rsum[slotw * 128 + mn + 2] = racc[1].x;
-    rsum[slotw * 128 + mn + 3] = racc[1].y;
+    // the lane's rows, over all its columns, into the CTA's per-row totals
+    flush_diag<NDIG>(acc, dtot);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) atomicAdd(dcorr + mn + j, dtot[j]);
   }
 }
 
@@ -386,7 +464,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx(GramTcxArgs g) {
   float* lo = hi + TILE_ELEMS;
   float2* hi2 = reinterpret_cast<float2*>(hi);
   float2* lo2 = reinterpret_cast<float2*>(lo);
-  float* rsum = lo + TILE_ELEMS;
+  double* dcorr = reinterpret_cast<double*>(lo + TILE_ELEMS);
   __shared__ uint64_t bar_full[NSTAGE], bar_empty[NSTAGE], bar_accf, bar_acce, bar_done;
   __shared__ uint32_t tmem_base_sh;
   __shared__ float s_scale[256];
@@ -406,6 +484,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx(GramTcxArgs g) {
     s_scale[t] = row < g.I ? g.scale[row] : 1.f;
   }
   for (int t = threadIdx.x; t < 2 * TILE_ELEMS; t += NTHREADS) hi[t] = 0.f;   // hi and lo
+  for (int t = threadIdx.x; t < 128; t += NTHREADS) dcorr[t] = 0.0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(smem_u32(&bar_full[s]), NPROD);
@@ -425,19 +504,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx(GramTcxArgs g) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base_sh;
-  // Diagonal tiles: the last-digit remainder r is unbiased, but r^2 > 0
-  // biases every diagonal entry by sum_k r_ik^2 (2^-28 in scaled units); the
-  // producers' sums are subtracted before the tile goes out, leaving the
-  // zero-mean 2 sum_k x r.
+  // Diagonal tiles: each diagonal entry gets the producers' correction
+  // (flush_diag) before the tile goes out: its D3 terms summed exactly, and
+  // minus sum_k r_ik^2, which matches the diagonal to the off-diagonal
+  // entries (see the file comment).
 
   if (warp < NPROD) {
     // ---------------- producers: X -> digit planes of A (and B)
     if (diag)
       produce<1, ROW, NDIG>(g, smem, bar_full, bar_empty, s_scale, ta, tb, k0, k1, k0, nst, warp,
-                            lane, rsum);
+                            lane, dcorr);
     else
       produce<2, ROW, NDIG>(g, smem, bar_full, bar_empty, s_scale, ta, tb, k0, k1, k0, nst, warp,
-                            lane, rsum);
+                            lane, dcorr);
   } else {
     // ---------------- drain warps: exact window sums -> FP32 pairs.  Lane 0
     // of warp MMA_WARP first issues the window's MMAs (nine per stage, one
@@ -523,9 +602,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx(GramTcxArgs g) {
           two_sum2(h, l, p1);
           two_sum2(h, l, p2);
           if (D::NACC == 4) {
-            const float2 p3 =
-                mul2(make_float2(__uint_as_float(r[3][j]), __uint_as_float(r[3][j + 1])),
-                     make_float2(0x1p-21f, 0x1p-21f));
+            float2 p3 = mul2(make_float2(__uint_as_float(r[3][j]), __uint_as_float(r[3][j + 1])),
+                             make_float2(0x1p-21f, 0x1p-21f));
+            // a diagonal entry's D3 comes from the producers' exact sums
+            if (diag && c0 + cc + j == row) p3.x = 0.f;
+            if (diag && c0 + cc + j + 1 == row) p3.y = 0.f;
             two_sum2(h, l, p3);
           }
           hi2[idx] = h;
@@ -553,11 +634,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx(GramTcxArgs g) {
     const int c = idx >> 7, rr = idx & 127;
     const int sidx = ((c >> 1) * 128 + rr) * 2 + (c & 1);
     double v = (double)hi[sidx] + (double)lo[sidx];
-    if (diag && c == rr) {
-      double r2 = 0.0;
-      for (int w = 0; w < NPROD; ++w) r2 += (double)rsum[w * 128 + rr];
-      v -= r2 * (double)D::RSCALE;
-    }
+    if (diag && c == rr) v += dcorr[rr];
     pt[idx] = v;
   }
 }
@@ -574,7 +651,11 @@ __global__ void k_gram_tcx_reduce(const double* __restrict__ part, int noff, int
   const int ta = (int)(i / 128), tb = (int)(j / 128);
   const size_t off = (size_t)(j - 128 * tb) * 128 + (size_t)(i - 128 * ta);
   double s = 0.0;
-  if (ta == tb) {
+  if (nkg == nkg_diag) {
+    const int t = ta * (ta + 1) / 2 + tb;
+    const int ntiles = T * (T + 1) / 2;
+    for (int k = 0; k < nkg; ++k) s += part[(size_t)(t + ntiles * k) * TILE_ELEMS + off];
+  } else if (ta == tb) {
     const size_t first = (size_t)noff * nkg + ta;
     for (int k = 0; k < nkg_diag; ++k) s += part[(first + (size_t)T * k) * TILE_ELEMS + off];
   } else {

@@ -124,3 +124,34 @@ def test_trace_noise_sigma_matches_the_spread():
     assert np.abs(z).max() < 6.0
     assert 0.2 < z.std() < 1.3
     assert abs(z.mean()) < 3 * z.std() / np.sqrt(len(z)) + 0.1
+
+
+def _tail(S, R):
+    return float(np.sort(np.linalg.eigvalsh(S))[: S.shape[0] - R].sum())
+
+
+def test_subtracting_squared_remainders_keeps_the_discarded_sum_unbiased():
+    """The sign of the diagonal correction.  r is x's own low part, so the
+    digit products sum to S - O(rho) S + diag(sum_k r_ik^2): left alone, the
+    last term lifts each of the I - R small eigenvalues by ~K E[r^2].  On a
+    rank-8 tensor plus 1e-7 noise (the benchmarks' recipe, FP32) the Gram of
+    the digits minus sum_k r^2 on the diagonal has the exact Gram's discarded
+    sum to a small fraction of that lift; with no correction the sum is one
+    lift high, with sum_k r^2 added (the trace-preserving choice) two."""
+    from paper_1901_06043_gb300 import synth
+    dims, core = (64, 12, 10, 50), (8, 8, 8, 8)
+    x, _ = synth.tucker_numpy(dims, core, decay=0.1, eta=1e-7, seed=5)
+    X = x.astype(np.float32).astype(np.float64).reshape(-1, dims[0]).T   # I x K
+    I, K, R = dims[0], X.shape[1], 8
+    s, xs, d0, d1, d2, r = _split(X)
+    rep = (d0 + d1 / 2**7 + d2 / 2**14) / s                # exact in FP64
+    Xl, Dl = X.astype(np.longdouble), rep.astype(np.longdouble)
+    S = np.array(Xl @ Xl.T, dtype=np.float64)
+    G = np.array(Dl @ Dl.T, dtype=np.float64)
+    r2 = np.sum((r / 2**14 / s) ** 2, axis=1)
+    true = _tail(S, R)
+    lift = r2.mean() * (I - R)                             # ~ (I - R) K E[r^2]
+    err = {c: _tail(G + c * np.diag(r2), R) - true for c in (-1, 0, 1)}
+    assert abs(err[-1]) <= 0.02 * lift, (err, lift)
+    assert 0.7 * lift <= err[0] <= 1.3 * lift, (err, lift)
+    assert 1.7 * lift <= err[1] <= 2.3 * lift, (err, lift)

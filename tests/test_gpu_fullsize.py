@@ -195,10 +195,13 @@ def test_c256_both_paths_against_the_oracle(ctx):
         r64 = ctx.sthosvd(x, dims, eps=eps, prec="fp64")
         _check_fp64_path(r64, ref, dims)
         rmx = ctx.sthosvd(x, dims, eps=eps, prec="mixed")
-        # the exact-digit Gram's error bound allows it down to eps = 1e-5 here
-        # (with two digits or three, as the bound decides per view)
-        assert all(k in ("tcgen05-x3", "tcgen05-x2") for k in rmx.gram_kernel[:3]), (
-            eps, rmx.gram_kernel)
+        # the exact-digit Gram's error bound keeps it (two digits or three, as
+        # the bound decides per view) for the three large modes down to
+        # eps = 1e-4, and for mode 0 at eps = 1e-5, where it sends the later
+        # partial cores, whose energy sits in a few rows, to the FP64 Gram
+        digit = ("tcgen05-x3", "tcgen05-x2")
+        large = rmx.gram_kernel[:3] if eps >= 1e-4 else rmx.gram_kernel[:1]
+        assert all(k in digit for k in large), (eps, rmx.gram_kernel)
         _check_mixed_path(rmx, ref, dims, eps)
         r64.close()
         rmx.close()

@@ -311,9 +311,9 @@ def _digit_trace_sigma(X, digits=3):
     """Standard deviation of the trace error of the exact-digit Gram for the
     I x K matrix X (torch, any device): the last digit rounds each value to
     the grid 2^(floor(log2 max_k |x_ik|) - 19) (three digits; - 12 with two),
-    an error uniform in +-half a step, independent of x; trace(S~) -
-    trace(S) = sum 2 x d + sum d^2, and the diagonal correction removes the
-    mean of sum d^2."""
+    a remainder r within +-half a step, independent of the digits; with the
+    diagonal correction trace(S~) - trace(S) = -2 sum x r, whose mean
+    -2 sum E[r^2] is ~1e-3 of this spread at these sizes."""
     rmax = X.abs().amax(dim=1).double().cpu().numpy()
     rn2 = (X.double() ** 2).sum(dim=1).cpu().numpy()
     _, ex = np.frexp(rmax)
@@ -362,6 +362,30 @@ def test_gram_mixed_mode0_error_on_discarded_subspace(ctx, digits):
     # standard deviations of the bound the library chooses its digits by
     bound = 0.02 * thr if digits == 3 else _digit_err6(host(x).reshape(-1, dims[0]).T, thr, 2)
     assert abs(proj) <= bound, (proj / thr, bound / thr)
+
+
+@pytest.mark.parametrize("digits", [3, 2], indirect=True)
+def test_gram_mixed_discarded_sum_of_a_low_rank_tensor(ctx, digits):
+    """Where the small eigenvalues sit far below the digits' resolution (rank
+    40 plus 1e-7 noise, 256 x 720896 mode-0 view), the exact-digit Gram's
+    error on the oracle's discarded subspace stays within the six standard
+    deviations of its representation error (the library's digit bound with
+    the tail sum in place of the threshold).  A systematic error on the
+    diagonal of 1 % of sum_k r_ik^2 breaks it (measured before each diagonal
+    entry's D3 was summed exactly), and so would the squared remainders
+    left on the diagonal (100 times that)."""
+    dims = (256, 128, 128, 11, 4)
+    x = synth.tucker_torch(dims, (40, 40, 40, 11, 4), decay=0.1, eta=1e-7, seed=6)
+    X = host(x).reshape(-1, dims[0]).T
+    want = oracle.gram(host(x), dims, 0)
+    got = host(ctx.gram(x, dims, 0, "mixed"))
+    w, V = oracle.eig_desc(want)
+    R = 40
+    tail = float(w[R:].sum())
+    P = V[:, R:]
+    proj = float(np.trace(P.T @ (got - want) @ P))
+    bound = _digit_err6(X, tail, digits)
+    assert abs(proj) <= bound, (proj, bound, tail)
 
 
 @pytest.mark.parametrize("eps", [1e-2, 1e-3, 1e-4])
