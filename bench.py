@@ -653,10 +653,11 @@ def dominant(res, w, pk):
 
 
 def e2e_leg(ctx, x, w, prec, args):
-    """Same metric end to end: pinned host input -> device copy -> the step
-    through the C ABI (ST-HOSVD and the subtensor reconstruction) -> the
-    reconstructed subtensor, the core and the factors back to pinned host
-    memory, per step."""
+    """Same metric end to end: the step through the C ABI from a pinned host
+    input (tucker_sthosvd_host: the library copies the tensor in pieces and
+    runs the norm pass and the mode-0 Gram on each piece as it lands), the
+    subtensor reconstruction, and the reconstructed subtensor, the core and
+    the factors back to pinned host memory, per step."""
     import torch
     try:
         xh = torch.empty(x.numel(), dtype=x.dtype, pin_memory=True)
@@ -667,14 +668,14 @@ def e2e_leg(ctx, x, w, prec, args):
         rh = torch.empty(int(np.prod(w["recon"])), dtype=x.dtype)
         pinned = False
     xh.copy_(x)
-    xd = torch.empty_like(x)
     steps = max(1, min(args.steps, 3))
+    # one untimed call: the autotuner's first visit of the piece shapes
+    ctx.sthosvd_host(xh, w["dims"], eps=w["eps"], prec=prec).close()
     torch.cuda.synchronize()
     d2h = 0
     t0 = time.perf_counter()
     for _ in range(steps):
-        xd.copy_(xh, non_blocking=True)
-        r = ctx.sthosvd(xd, w["dims"], eps=w["eps"], prec=prec)
+        r = ctx.sthosvd_host(xh, w["dims"], eps=w["eps"], prec=prec)
         rec = r.reconstruct((0,) * len(w["dims"]), w["recon"], prec=prec)
         rh.copy_(rec.view(-1).to(rh.dtype), non_blocking=True)
         core, fac = r.to_host()
@@ -685,7 +686,7 @@ def e2e_leg(ctx, x, w, prec, args):
     torch.cuda.synchronize()
     el = (time.perf_counter() - t0) / steps
     nb = x.numel() * x.element_size()
-    del xd, xh, rh
+    del xh, rh
     return {"value": nb / 1e9 / el, "unit": "GB/s", "h2d_bytes_per_step": nb,
             "d2h_bytes_per_step": int(d2h), "steps": steps, "pinned": pinned, "ms": el * 1e3,
             "returns": "reconstructed subtensor, core and factors"}

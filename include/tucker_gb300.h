@@ -175,7 +175,10 @@ const char* tucker_last_error(const tucker_ctx* ctx);
  *                          kept for the rest of the process, for every
  *                          context.  Results differ from the untuned ones only
  *                          by the order of the FP64 split sums.  0 (default):
- *                          one wave. */
+ *                          one wave.
+ *   TUCKER_OPT_HOST_CHUNK  bytes per piece in which tucker_sthosvd_host copies
+ *                          its input (rounded to whole mode-0 columns, four at
+ *                          a time); default 2^30, at least 1. */
 #define TUCKER_OPT_TIMING 1
 #define TUCKER_OPT_MAX_SWEEPS 2
 #define TUCKER_OPT_JACOBI_TOL 3
@@ -184,6 +187,7 @@ const char* tucker_last_error(const tucker_ctx* ctx);
 #define TUCKER_OPT_MEM_LIMIT 6
 #define TUCKER_OPT_GRAM_DIGITS 7
 #define TUCKER_OPT_AUTOTUNE 8
+#define TUCKER_OPT_HOST_CHUNK 9
 tucker_status tucker_set_option(tucker_ctx* ctx, int key, double value);
 
 /* Diagnostics: number of device kernels this library has launched in the
@@ -219,6 +223,28 @@ tucker_status tucker_sthosvd(tucker_ctx* ctx, const void* x_dev, tucker_dtype dt
                              int ndim, const int64_t* dims, double eps,
                              const int64_t* ranks_or_null, const int* mode_order_or_null,
                              tucker_prec prec, tucker_result** out);
+
+/* ST-HOSVD, Algorithm 1 (Section 3.3), of a tensor in HOST memory.
+ *   x_host     input tensor (dtype, dims) in host memory, read only; page-
+ *              locked memory (cudaHostAlloc, cudaHostRegister) lets the copy
+ *              overlap the computation, pageable memory works but is staged
+ *              by the driver.
+ *   other arguments, the result and its ownership as tucker_sthosvd.
+ * The library copies the tensor into a device buffer of its own, in pieces
+ * (TUCKER_OPT_HOST_CHUNK), and runs the norm pass and, when the first mode is
+ * mode 0, that mode's Gram on each piece as it lands (Gram of the piece's
+ * columns, summed in FP64; the exact-digit Gram of a piece uses its own row
+ * maxima and three digits, and an FP64 Gram replaces the sum when the whole
+ * view's bound asks for one, as in tucker_sthosvd).  The rest is
+ * tucker_sthosvd on the device copy, which is freed before the call returns.
+ * Results equal tucker_sthosvd's up to the order of the FP64 sums and the
+ * digit count of the first Gram.  Synchronises the context stream.
+ * Errors: those of tucker_sthosvd; OOM also when the device copy does not
+ * fit (predicted before anything is allocated). */
+tucker_status tucker_sthosvd_host(tucker_ctx* ctx, const void* x_host, tucker_dtype dtype,
+                                  int ndim, const int64_t* dims, double eps,
+                                  const int64_t* ranks_or_null, const int* mode_order_or_null,
+                                  tucker_prec prec, tucker_result** out);
 tucker_status tucker_result_destroy(tucker_result* res);
 
 /* Batched ST-HOSVD: Algorithm 1, eps-driven, mode order 0..N_i-1, for each of

@@ -34,6 +34,7 @@ struct tucker_ctx {
   double mem_limit = 0.0;        // bytes assumed available to a call (0: ask the device)
   int gram_digits = 0;           // digits of the exact-digit Gram: 0 auto, 2 or 3
   int autotune = 0;              // 1: split-K of the Gram kernels chosen by timing
+  double host_chunk = 1073741824.0;   // bytes per piece of tucker_sthosvd_host's copy
   std::string err;
   // small device scratch
   unsigned* d_words = nullptr;   // 256 words
@@ -235,10 +236,12 @@ constexpr double kMinFp32GramThreshold = 1e-9;
 // threshold thr: 2 or 3, or 0 when neither is accurate enough (FP64 Gram).
 // The Gram's only error is the representation of each value by its digits:
 // |r_ik| <= delta_i = 2^(floor(log2 max_k |x_ik|) - 20) with three digits,
-// 2^(... - 13) with two, unbiased, independent of x (variance
-// sigma_i^2 <= delta_i^2 / 3); the mean of r r^T's diagonal is removed
-// exactly.  On the discarded subspace (projector P, tail <= thr at the cut)
-// the error is
+// 2^(... - 13) with two, independent of the digits (variance sigma_i^2 <=
+// delta_i^2 / 3); the kernel subtracts each row's sum of r^2 from its
+// diagonal entry, which leaves the small eigenvalues unbiased (r is x's own
+// low part, so the digits' Gram carries + diag(sum r^2) and a relative
+// O(sigma^2 / E[x^2]) shrink).  On the discarded subspace (projector P,
+// tail <= thr at the cut) the error is then
 //   2 sum_k (P x_k).r_k + sum_k sum_{i != j} P_ij r_ik r_jk,
 // with variance at most 4 sigma_max^2 tail + 2 K sum_{i != j} P_ij^2
 // sigma_i^2 sigma_j^2, and sum_j P_ij^2 = P_ii <= 1 bounds the second term by
@@ -853,6 +856,11 @@ tucker_status tucker_set_option(tucker_ctx* c, int key, double value) {
         return set_err(c, TUCKER_ERR_INVALID, "memory limit must be >= 0");
       c->mem_limit = value;
       return TUCKER_OK;
+    case TUCKER_OPT_HOST_CHUNK:
+      if (!(value >= 1.0 && std::isfinite(value)))
+        return set_err(c, TUCKER_ERR_INVALID, "host piece size must be >= 1 byte");
+      c->host_chunk = value;
+      return TUCKER_OK;
     case TUCKER_OPT_JACOBI_TOL:
       if (!(value > 0.0 && value < 1e-3)) return set_err(c, TUCKER_ERR_INVALID, "tolerance out of (0, 1e-3)");
       c->tol_rel = value;
@@ -954,22 +962,24 @@ tucker_status tucker_result_destroy(tucker_result* r) {
   return TUCKER_OK;
 }
 
-tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int ndim,
-                             const int64_t* dims, double eps, const int64_t* ranks,
-                             const int* order_in, tucker_prec prec, tucker_result** out) {
-  if (!c) return TUCKER_ERR_INVALID;
-  if (!out) return set_err(c, TUCKER_ERR_INVALID, "null result pointer");
-  *out = nullptr;
+// Argument checks shared by tucker_sthosvd and tucker_sthosvd_host; fills
+// order (the default 0..N-1 when order_in is null).
+static tucker_status check_sthosvd_args(tucker_ctx* c, const void* x, tucker_dtype dt, int ndim,
+                                 const int64_t* dims, double eps, const int64_t* ranks,
+                                 const int* order_in, tucker_prec prec, int* order,
+                                 const char* what) {
   if (!x || !check_dims(ndim, dims) || (dt != TUCKER_F32 && dt != TUCKER_F64) || prec < 0 ||
-      prec > 3)
-    return set_err(c, TUCKER_ERR_INVALID, "tucker_sthosvd: bad argument");
+      prec > 3) {
+    char m[96];
+    snprintf(m, sizeof m, "%s: bad argument", what);
+    return set_err(c, TUCKER_ERR_INVALID, m);
+  }
   if (!ranks && !(eps >= 0.0 && std::isfinite(eps)))
     return set_err(c, TUCKER_ERR_INVALID, "eps must be finite and >= 0");
   if (ranks)
     for (int k = 0; k < ndim; ++k)
       if (ranks[k] < 1 || ranks[k] > dims[k])
         return set_err(c, TUCKER_ERR_INVALID, "ranks must satisfy 1 <= R_n <= I_n");
-  int order[TUCKER_MAX_MODES];
   if (!check_order(ndim, order_in, order))
     return set_err(c, TUCKER_ERR_INVALID, "mode order is not a permutation");
   if ((prec == TUCKER_PREC_MIXED || prec == TUCKER_PREC_TENSOR) && dt != TUCKER_F32)
@@ -977,6 +987,27 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
   int64_t imax = 0;
   for (int k = 0; k < ndim; ++k) imax = std::max(imax, dims[k]);
   if (imax > 8192) return set_err(c, TUCKER_ERR_INVALID, "mode size above 8192");
+  return TUCKER_OK;
+}
+
+// What tucker_sthosvd_host computes while the input streams in: the norm
+// pass and, when the first mode is mode 0, that mode's Gram.
+struct StreamedMode0 {
+  double nrm2 = 0.0, xmax = 0.0;
+  const unsigned* rowmax = nullptr;   // mode-0 row maxima (FP32 bits, device) or null
+  const double* S0 = nullptr;         // Gram of the first mode (device) or null
+  int gram_kernel0 = 0;
+  float ms_norm = 0.f, ms_gram0 = 0.f;
+};
+
+// Algorithm 1 on the device tensor x; pre != null: the norm (and maybe the
+// first Gram) come from a streamed input (tucker_sthosvd_host).
+static tucker_status sthosvd_impl(tucker_ctx* c, const void* x, tucker_dtype dt, int ndim,
+                           const int64_t* dims, double eps, const int64_t* ranks,
+                           const int* order, tucker_prec prec, tucker_result** out,
+                           const StreamedMode0* pre) {
+  int64_t imax = 0;
+  for (int k = 0; k < ndim; ++k) imax = std::max(imax, dims[k]);
 
   const tucker_dtype wdt = (prec == TUCKER_PREC_FP64) ? TUCKER_F64 : dt;
   // workspace the first mode needs at least (nothing is launched or
@@ -1009,13 +1040,19 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
   // the exact tensor-core Gram of a first mode 0 takes its digit scales from
   // row maxima that the norm pass records on the way
   DevBuf rowmax;
-  {
+  const unsigned* rowmax0 = nullptr;
+  if (pre) {
+    nrm2 = pre->nrm2;
+    xmax = pre->xmax;
+    rowmax0 = pre->rowmax;
+  } else {
     const SlabView v0 = slab_view(ndim, dims, 0);
     const bool tcx = order[0] == 0 && gram_kernel_for(prec, dt, v0, c->num_sms) == 5 &&
                      (((uintptr_t)x) & 15) == 0;
     if (tcx) TK_TRY(dev_alloc(c, rowmax, sizeof(unsigned) * v0.I));
+    TK_TRY(do_norm(c, x, dt, nx, &nrm2, &xmax, rowmax.as<unsigned>(), dims[0]));
+    rowmax0 = rowmax.as<unsigned>();
   }
-  TK_TRY(do_norm(c, x, dt, nx, &nrm2, &xmax, rowmax.as<unsigned>(), dims[0]));
   t_norm.stop(c);
   r->norm_x_sq = nrm2;
   const double thr = ranks ? 0.0 : eps * eps * nrm2 / ndim;
@@ -1058,8 +1095,9 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
     // of the column-mode view, whose largest entry is the TTM's split scale
     DevBuf rowmax_s;
     double ymax = s == 0 ? xmax : -1.0;
-    const unsigned* rmx = s == 0 ? rowmax.as<unsigned>() : nullptr;
-    const int gk = gram_kernel_for(prec, ydt, v, c->num_sms);
+    const unsigned* rmx = s == 0 ? rowmax0 : nullptr;
+    const bool streamed = s == 0 && pre && pre->S0;   // Gram summed while the input streamed in
+    const int gk = streamed ? -1 : gram_kernel_for(prec, ydt, v, c->num_sms);
     tucker_prec gram_prec = prec;
     int ndig = 3;
     if (gk == 5 && rotate && s > 0 && ydt == TUCKER_F32 && (((uintptr_t)y) & 15) == 0) {
@@ -1081,11 +1119,17 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
       }
       ndig = digit_gram_digits(hb.data(), v.I, v.L * v.Rt, thr);
       if (ndig == 0) gram_prec = TUCKER_PREC_FP64;
-    } else if (small_eps && gk != 3) {
+    } else if (small_eps && gk != 3 && !streamed) {
       gram_prec = TUCKER_PREC_FP64;
     }
-    TK_TRY(do_gram(c, y, ydt, v, gram_prec, S.as<double>(), &r->gram_kernel[n], ymax, true, rmx,
-                   ndig > 0 ? ndig : 3));
+    const double* Sn = S.as<double>();
+    if (streamed) {
+      Sn = pre->S0;
+      r->gram_kernel[n] = pre->gram_kernel0;
+    } else {
+      TK_TRY(do_gram(c, y, ydt, v, gram_prec, S.as<double>(), &r->gram_kernel[n], ymax, true, rmx,
+                     ndig > 0 ? ndig : 3));
+    }
     tmg.stop(c);
     DevBuf w, U;
     TK_TRY(dev_alloc(c, w, sizeof(double) * I));
@@ -1098,12 +1142,12 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
     const int fixed_R = ranks ? (int)ranks[n] : 0;
     if (use_tridiag(c, I)) {
       bool failed = false;
-      TK_TRY(do_eig_tri(c, S.as<double>(), I, thr, fixed_R, w.as<double>(), U, &R, &disc, &failed));
+      TK_TRY(do_eig_tri(c, Sn, I, thr, fixed_R, w.as<double>(), U, &R, &disc, &failed));
       have = !failed;
       r->eig_kernel[n] = 1;
     }
     if (!have) {
-      es = do_eig(c, S.as<double>(), I, w.as<double>(), V.as<double>(), &sweeps);
+      es = do_eig(c, Sn, I, w.as<double>(), V.as<double>(), &sweeps);
       if (es != TUCKER_OK && es != TUCKER_ERR_EIG_NOCONV) return es;
       TK_TRY(do_cut(c, w.as<double>(), I, thr, fixed_R, &R, &disc));
       TK_TRY(dev_alloc(c, U, sizeof(double) * I * R));
@@ -1145,7 +1189,7 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
     if (es == TUCKER_ERR_EIG_NOCONV) noconv = true;
     TK_TRY(sync(c));
     if (c->timing) {
-      r->ms_gram[n] = tmg.ms();
+      r->ms_gram[n] = streamed ? pre->ms_gram0 : tmg.ms();
       r->ms_eig[n] = tme.ms();
       r->ms_ttm[n] = tmt.ms();
     }
@@ -1154,13 +1198,181 @@ tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int 
   t_total.stop(c);
   TK_TRY(sync(c));
   if (c->timing) {
-    r->ms_norm = t_norm.ms();
+    r->ms_norm = pre ? pre->ms_norm : t_norm.ms();
     r->ms_total = t_total.ms();
   }
   *out = r;
   r = nullptr;  // disarm guard
   if (noconv) return set_err(c, TUCKER_ERR_EIG_NOCONV, "Jacobi reached the sweep cap in some mode");
   return TUCKER_OK;
+}
+
+tucker_status tucker_sthosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int ndim,
+                             const int64_t* dims, double eps, const int64_t* ranks,
+                             const int* order_in, tucker_prec prec, tucker_result** out) {
+  if (!c) return TUCKER_ERR_INVALID;
+  if (!out) return set_err(c, TUCKER_ERR_INVALID, "null result pointer");
+  *out = nullptr;
+  int order[TUCKER_MAX_MODES];
+  TK_TRY(check_sthosvd_args(c, x, dt, ndim, dims, eps, ranks, order_in, prec, order,
+                            "tucker_sthosvd"));
+  return sthosvd_impl(c, x, dt, ndim, dims, eps, ranks, order, prec, out, nullptr);
+}
+
+// ST-HOSVD of a tensor in host memory.  The input is copied to the device in
+// pieces of about c->host_chunk bytes on a copy stream, all enqueued first;
+// the context stream takes each piece as its copy lands: the norm pass
+// (with the mode-0 row maxima) and, when the first mode is mode 0, that
+// mode's Gram over the piece's columns, summed in FP64.  So the norm and the
+// largest Gram run under the copy, which bounds the call.
+//   Pieces of the mode-0 Gram: whole columns of the I0 x K view (a multiple
+// of 4, so every piece starts 16-byte aligned).  The exact-digit Gram of a
+// piece takes its scales from the piece's own row maxima and runs with three
+// digits (the digit count needs the threshold, which needs the whole norm);
+// once the norm is complete, the bound of the whole view decides as in
+// tucker_sthosvd, and where it asks for an FP64 Gram, that Gram is computed
+// again over the resident copy.  Then Algorithm 1 goes on as in
+// tucker_sthosvd on the device copy, which is freed before the call returns.
+tucker_status tucker_sthosvd_host(tucker_ctx* c, const void* x_host, tucker_dtype dt, int ndim,
+                                  const int64_t* dims, double eps, const int64_t* ranks,
+                                  const int* order_in, tucker_prec prec, tucker_result** out) {
+  if (!c) return TUCKER_ERR_INVALID;
+  if (!out) return set_err(c, TUCKER_ERR_INVALID, "null result pointer");
+  *out = nullptr;
+  int order[TUCKER_MAX_MODES];
+  TK_TRY(check_sthosvd_args(c, x_host, dt, ndim, dims, eps, ranks, order_in, prec, order,
+                            "tucker_sthosvd_host"));
+  const int64_t nx = numel(ndim, dims);
+  const size_t esz = dtype_size(dt);
+  const int64_t I0 = dims[0];
+  int64_t imax = 0;
+  for (int k = 0; k < ndim; ++k) imax = std::max(imax, dims[k]);
+  // the device copy, then the first mode's workspace (as tucker_sthosvd)
+  {
+    const tucker_dtype wdt = (prec == TUCKER_PREC_FP64) ? TUCKER_F64 : dt;
+    const SlabView v0 = slab_view(ndim, dims, order[0]);
+    const double need = (double)esz * (double)nx + 16.0 * (double)imax * (double)imax * 2.0 +
+                        (double)gram_scratch_bytes(c, prec, dt, v0) +
+                        (double)dtype_size(wdt) * (double)(nx / dims[order[0]]);
+    TK_TRY(predict_oom(c, need, 0.0, "the host input's device copy"));
+  }
+  DevBuf xd;
+  TK_TRY(dev_alloc(c, xd, esz * (size_t)nx));
+
+  // pieces: whole mode-0 columns (4 at a time) when mode 0 comes first
+  const SlabView v0 = slab_view(ndim, dims, 0);
+  const bool gram0 = order[0] == 0;
+  const int64_t ncols = nx / I0;
+  int64_t unit = gram0 ? 4 * I0 : 1024;                 // elements
+  int64_t per = std::max<int64_t>(1, (int64_t)(c->host_chunk / (double)esz) / unit) * unit;
+  if (per > nx) per = nx;
+  const int64_t npieces = (nx + per - 1) / per;
+
+  // copies first (copy stream, after the allocation), one event per piece
+  cudaStream_t cs = nullptr;
+  TK_CUDA(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  std::vector<cudaEvent_t> ev((size_t)npieces, nullptr);
+  struct Cleanup {
+    cudaStream_t& cs;
+    std::vector<cudaEvent_t>& ev;
+    ~Cleanup() {
+      if (cs) { cudaStreamSynchronize(cs); cudaStreamDestroy(cs); }
+      for (cudaEvent_t e : ev) if (e) cudaEventDestroy(e);
+    }
+  } cleanup{cs, ev};
+  TK_CUDA(c, cudaEventRecord(c->fork_ev, c->stream));
+  TK_CUDA(c, cudaStreamWaitEvent(cs, c->fork_ev, 0));
+  for (int64_t p = 0; p < npieces; ++p) {
+    const int64_t e0 = p * per, e1 = std::min(nx, e0 + per);
+    TK_CUDA(c, cudaEventCreateWithFlags(&ev[(size_t)p], cudaEventDisableTiming));
+    TK_CUDA(c, cudaMemcpyAsync(xd.as<char>() + esz * (size_t)e0,
+                               static_cast<const char*>(x_host) + esz * (size_t)e0,
+                               esz * (size_t)(e1 - e0), cudaMemcpyHostToDevice, cs));
+    TK_CUDA(c, cudaEventRecord(ev[(size_t)p], cs));
+  }
+
+  // per piece on the context stream: norm (+ row maxima), Gram of mode 0
+  const tucker_prec gprec = prec;
+  const int gk = gram0 ? gram_kernel_for(gprec, dt, v0, c->num_sms) : -1;
+  const bool tcx = gk == 5;
+  const bool small_eps =
+      !ranks && prec != TUCKER_PREC_FP64 && eps * eps / ndim < kMinFp32GramThreshold;
+  const tucker_prec piece_prec = (gram0 && small_eps && gk != 3 && gk != 5) ? TUCKER_PREC_FP64
+                                                                             : gprec;
+  DevBuf rmx_all, rmx_p, S0, Sp;
+  std::vector<unsigned> rmx_h, rmx_acc;
+  if (tcx) {
+    TK_TRY(dev_alloc(c, rmx_all, sizeof(unsigned) * I0));
+    TK_TRY(dev_alloc(c, rmx_p, sizeof(unsigned) * I0));
+    rmx_h.resize((size_t)I0);
+    rmx_acc.assign((size_t)I0, 0u);
+  }
+  if (gram0) {
+    TK_TRY(dev_alloc(c, S0, sizeof(double) * I0 * I0));
+    TK_TRY(dev_alloc(c, Sp, sizeof(double) * I0 * I0));
+  }
+  StreamedMode0 pre;
+  double xmax = 0.0;
+  // the per-piece sums of squares are added in piece order (FP64)
+  double nrm2 = 0.0;
+  float ms_norm = 0.f, ms_gram = 0.f;
+  int kern0 = 0;
+  for (int64_t p = 0; p < npieces; ++p) {
+    const int64_t e0 = p * per, e1 = std::min(nx, e0 + per);
+    const void* yp = xd.as<char>() + esz * (size_t)e0;
+    TK_CUDA(c, cudaStreamWaitEvent(c->stream, ev[(size_t)p], 0));
+    Timer tn, tg;
+    tn.start(c);
+    double n2 = 0.0, mx = 0.0;
+    TK_TRY(do_norm(c, yp, dt, e1 - e0, &n2, &mx, tcx ? rmx_p.as<unsigned>() : nullptr, I0));
+    tn.stop(c);
+    nrm2 += n2;
+    xmax = std::max(xmax, mx);
+    if (c->timing) ms_norm += tn.ms();
+    if (!gram0) continue;
+    const SlabView vp{1, I0, (e1 - e0) / I0, 1};
+    tg.start(c);
+    double* dst = p == 0 ? S0.as<double>() : Sp.as<double>();
+    TK_TRY(do_gram(c, yp, dt, vp, piece_prec, dst, &kern0, mx, true,
+                   tcx ? rmx_p.as<unsigned>() : nullptr, 3));
+    if (p > 0) TK_CUDA(c, launch_add_f64(Sp.as<double>(), S0.as<double>(), I0 * I0, c->num_sms,
+                                         c->stream));
+    tg.stop(c);
+    if (c->timing) ms_gram += tg.ms();
+    if (tcx) {
+      TK_CUDA(c, cudaMemcpyAsync(rmx_h.data(), rmx_p.p, sizeof(unsigned) * I0,
+                                 cudaMemcpyDeviceToHost, c->stream));
+      TK_TRY(sync(c));
+      for (int64_t i = 0; i < I0; ++i)
+        rmx_acc[(size_t)i] = std::max(rmx_acc[(size_t)i], rmx_h[(size_t)i] & 0x7fffffffu);
+    }
+  }
+  if (tcx) {
+    TK_CUDA(c, cudaMemcpyAsync(rmx_all.p, rmx_acc.data(), sizeof(unsigned) * I0,
+                               cudaMemcpyHostToDevice, c->stream));
+    // the whole view's bound decides as in tucker_sthosvd; a view that needs
+    // an FP64 Gram gets it over the resident copy
+    const double thr = ranks ? 0.0 : eps * eps * nrm2 / ndim;
+    const int nd = c->gram_digits ? c->gram_digits : digit_gram_digits(rmx_acc.data(), I0, ncols,
+                                                                       thr);
+    if (nd == 0) {
+      Timer tg;
+      tg.start(c);
+      TK_TRY(do_gram(c, xd.p, dt, v0, TUCKER_PREC_FP64, S0.as<double>(), &kern0, xmax, true,
+                     nullptr, 3));
+      tg.stop(c);
+      if (c->timing) ms_gram += tg.ms();
+    }
+  }
+  TK_TRY(sync(c));
+  pre.nrm2 = nrm2;
+  pre.xmax = xmax;
+  pre.rowmax = tcx ? rmx_all.as<unsigned>() : nullptr;
+  pre.S0 = gram0 ? S0.as<double>() : nullptr;
+  pre.gram_kernel0 = kern0;
+  pre.ms_norm = ms_norm;
+  pre.ms_gram0 = ms_gram;
+  return sthosvd_impl(c, xd.p, dt, ndim, dims, eps, ranks, order, prec, out, &pre);
 }
 
 // The batched ST-HOSVD runs modes 0, 1, ... in order on every tensor and keeps

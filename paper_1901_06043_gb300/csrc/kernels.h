@@ -20,6 +20,9 @@ cudaError_t launch_sumsq_rowmax(const float* y, int64_t I0, int64_t ncols, doubl
                                 int nblocks, unsigned* nonfinite, unsigned* rowmax_bits, double* out,
                                 cudaStream_t st);
 
+// ---- b[i] += a[i] over n FP64 values (sums of Grams computed in pieces)
+cudaError_t launch_add_f64(const double* a, double* b, int64_t n, int num_sms, cudaStream_t st);
+
 // ---- SIMT Gram (FP64 or FP32 products), split-K partial tiles + reduction
 struct GramPlan {
   int ntiles = 0, ksplit = 0;

@@ -2,6 +2,7 @@
 // slab-batched Gram (Algorithm 2) and slab TTM (Algorithm 3) in FP64 or
 // FP32 arithmetic, over the unfolding-free strided view (Rt, I, L) of
 // Section 4.2: element (l, i, r) of the mode-n view sits at l + L*(i + I*r).
+#include <algorithm>
 #include <cstdio>
 
 #include "common.cuh"
@@ -264,6 +265,21 @@ cudaError_t launch_sumsq(const void* y, tucker_dtype dt, int64_t n, double* part
   else
     k_sumsq_f32<<<nblocks, 256, 0, st>>>((const float*)y, n, partial, nonfinite);
   k_reduce_sum<<<1, 256, 0, st>>>(partial, nblocks, out);
+  return cudaGetLastError();
+}
+
+// b[i] += a[i] (FP64), grid-stride.
+__global__ void k_add_f64(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] += a[i];
+}
+
+cudaError_t launch_add_f64(const double* a, double* b, int64_t n, int num_sms, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int nb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 4);
+  count_launches(1);
+  k_add_f64<<<nb, 256, 0, st>>>(a, b, n);
   return cudaGetLastError();
 }
 

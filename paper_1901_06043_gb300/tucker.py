@@ -22,6 +22,7 @@ F32, F64 = 0, 1
 PREC = {"fp64": 0, "fp32": 1, "mixed": 2, "tensor": 3}
 OPT_TIMING, OPT_MAX_SWEEPS, OPT_JACOBI_TOL, OPT_EIG_SOLVER = 1, 2, 3, 4
 OPT_BARRIER_POLLS, OPT_MEM_LIMIT, OPT_GRAM_DIGITS, OPT_AUTOTUNE = 5, 6, 7, 8
+OPT_HOST_CHUNK = 9
 EIG_SOLVER = {"auto": 0, "jacobi": 1, "tridiag": 2}
 
 EXPORTS = ["tucker_create", "tucker_destroy", "tucker_last_error", "tucker_set_option",
@@ -31,7 +32,8 @@ EXPORTS = ["tucker_create", "tucker_destroy", "tucker_last_error", "tucker_set_o
            "tucker_eig", "tucker_eig_trunc", "tucker_rank_cut", "tucker_ttm",
            "tucker_kernel_launches", "tucker_gram_noalloc", "tucker_hosvd",
            "tucker_sthosvd_order", "tucker_slice_stats", "tucker_slice_transform",
-           "tucker_preprocess", "tucker_selftest_rcp64", "tucker_autotune_entries"]
+           "tucker_preprocess", "tucker_selftest_rcp64", "tucker_autotune_entries",
+           "tucker_sthosvd_host"]
 STATS = ("mean", "std", "max", "min", "norm1", "norm2")
 PRE_METHOD = {"standardize": 0, "max": 1}
 
@@ -116,6 +118,7 @@ def lib():
         L.tucker_gram_noalloc.argtypes = [vp, c_int, c_int, i64p, c_int, c_int, vp, vp]
         L.tucker_hosvd.argtypes = [vp, vp, c_int, c_int, i64p, ctypes.c_double, i64p, c_int,
                                    ctypes.POINTER(ctypes.POINTER(CResult))]
+        L.tucker_sthosvd_host.argtypes = L.tucker_sthosvd.argtypes
         L.tucker_sthosvd_order.argtypes = [c_int, i64p, i64p, ctypes.POINTER(c_int)]
         L.tucker_selftest_rcp64.argtypes = [vp, vp, ctypes.c_int64, vp]
         L.tucker_slice_stats.argtypes = [vp, vp, c_int, c_int, i64p, c_int, vp]
@@ -164,6 +167,24 @@ def _view(ptr, shape, code):
 def _check_dev(t, name):
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError(f"{name} must be a contiguous CUDA tensor")
+
+
+def _host_buffer(x):
+    """(address, dtype code, element count) of a contiguous host array: a CPU
+    torch tensor or a numpy array of float32 / float64."""
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("x must be a contiguous host array")
+        if x.dtype == np.float32:
+            code = F32
+        elif x.dtype == np.float64:
+            code = F64
+        else:
+            raise TypeError(f"unsupported dtype {x.dtype}")
+        return x.ctypes.data, code, x.size
+    if getattr(x, "is_cuda", True) or not x.is_contiguous():
+        raise ValueError("x must be a contiguous host (CPU) tensor or numpy array")
+    return x.data_ptr(), _dtype_code(x), x.numel()
 
 
 class Result:
@@ -291,6 +312,25 @@ class Context:
             PREC[prec], ctypes.byref(out))
         if st != 0 and out:
             lib().tucker_result_destroy(out)   # EIG_NOCONV still returns a result
+        self._check(st)
+        return Result(self, out)
+
+    def sthosvd_host(self, x, dims, eps=None, ranks=None, mode_order=None, prec="fp64"):
+        """ST-HOSVD of a tensor in host memory (tucker_sthosvd_host): x is a
+        contiguous CPU torch tensor (page-locked for an overlapped copy) or
+        numpy array of float32/float64 with prod(dims) elements."""
+        ptr, code, n = _host_buffer(x)
+        if n != int(np.prod([int(d) for d in dims])):
+            raise ValueError(f"x has {n} elements, dims {tuple(dims)} need {int(np.prod(dims))}")
+        out = ctypes.POINTER(CResult)()
+        st = lib().tucker_sthosvd_host(
+            self._c, ctypes.c_void_p(ptr), code, len(dims), _i64(dims),
+            float(eps) if eps is not None else 0.0,
+            _i64(ranks) if ranks is not None else None,
+            _ints(mode_order) if mode_order is not None else None,
+            PREC[prec], ctypes.byref(out))
+        if st != 0 and out:
+            lib().tucker_result_destroy(out)
         self._check(st)
         return Result(self, out)
 

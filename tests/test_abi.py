@@ -39,6 +39,16 @@ def test_binding_lists_every_declared_symbol():
     assert sorted(tucker.EXPORTS) == declared_functions()
 
 
+def test_binding_types_every_call_that_takes_arguments():
+    """Every entry point the binding calls with arguments has its ctypes
+    argument types set (an untyped call cannot pass a double)."""
+    from paper_1901_06043_gb300 import tucker
+    L = tucker.lib()
+    no_args = {"tucker_kernel_launches", "tucker_autotune_entries"}
+    untyped = [n for n in tucker.EXPORTS if n not in no_args and getattr(L, n).argtypes is None]
+    assert not untyped, untyped
+
+
 def test_ttm_order_host_call_matches_oracle():
     """tucker_ttm_order is host-only C code: check it against the oracle's
     exhaustive search (Section 8.5's 43120 optimum) without a GPU."""

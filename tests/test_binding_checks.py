@@ -44,3 +44,24 @@ def test_gram_noalloc_rejects_a_wrong_output_before_any_call():
     y, dims, mode, _ = _ok()
     with pytest.raises(ValueError, match="shape"):
         tucker.gram_noalloc(y, dims, mode, torch.zeros((2, 2), dtype=torch.float64))
+
+
+def test_host_buffer_of_numpy_and_cpu_tensors():
+    import numpy as np
+    a = np.zeros(12, dtype=np.float32)
+    ptr, code, n = tucker._host_buffer(a)
+    assert (ptr, code, n) == (a.ctypes.data, tucker.F32, 12)
+    t = torch.zeros(7, dtype=torch.float64)
+    ptr, code, n = tucker._host_buffer(t)
+    assert (ptr, code, n) == (t.data_ptr(), tucker.F64, 7)
+
+
+@pytest.mark.parametrize("bad", ["strided_numpy", "int_numpy", "strided_tensor", "int_tensor"])
+def test_host_buffer_rejects_what_the_library_cannot_read(bad):
+    import numpy as np
+    x = {"strided_numpy": np.zeros((4, 4), dtype=np.float32)[:, ::2],
+         "int_numpy": np.zeros(4, dtype=np.int32),
+         "strided_tensor": torch.zeros((4, 4))[:, ::2],
+         "int_tensor": torch.zeros(4, dtype=torch.int32)}[bad]
+    with pytest.raises((ValueError, TypeError)):
+        tucker._host_buffer(x)
