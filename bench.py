@@ -669,12 +669,26 @@ def e2e_leg(ctx, x, w, prec, args):
         pinned = False
     xh.copy_(x)
     steps = max(1, min(args.steps, 3))
+    # the plain host-to-device rate of this pinned buffer (a 4 GB copy), for
+    # reading the figure: the copy bounds the end-to-end step
+    nprobe = min(xh.numel(), (4 << 30) // xh.element_size())
+    scratch = torch.empty(nprobe, dtype=xh.dtype, device="cuda")
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    scratch.copy_(xh[:nprobe], non_blocking=True)
+    h0.record()
+    scratch.copy_(xh[:nprobe], non_blocking=True)
+    h1.record()
+    torch.cuda.synchronize()
+    h2d_gbs = nprobe * xh.element_size() / 1e6 / h0.elapsed_time(h1)
+    del scratch
     # one untimed call: the autotuner's first visit of the piece shapes
     ctx.sthosvd_host(xh, w["dims"], eps=w["eps"], prec=prec).close()
     torch.cuda.synchronize()
     d2h = 0
     t0 = time.perf_counter()
+    step_ms = []
     for _ in range(steps):
+        ts = time.perf_counter()
         r = ctx.sthosvd_host(xh, w["dims"], eps=w["eps"], prec=prec)
         rec = r.reconstruct((0,) * len(w["dims"]), w["recon"], prec=prec)
         rh.copy_(rec.view(-1).to(rh.dtype), non_blocking=True)
@@ -683,12 +697,14 @@ def e2e_leg(ctx, x, w, prec, args):
         d2h = rh.numel() * rh.element_size() + core.nbytes + sum(f.nbytes for f in fac)
         del rec
         r.close()
+        step_ms.append((time.perf_counter() - ts) * 1e3)
     torch.cuda.synchronize()
     el = (time.perf_counter() - t0) / steps
     nb = x.numel() * x.element_size()
     del xh, rh
     return {"value": nb / 1e9 / el, "unit": "GB/s", "h2d_bytes_per_step": nb,
             "d2h_bytes_per_step": int(d2h), "steps": steps, "pinned": pinned, "ms": el * 1e3,
+            "h2d_copy_gbs": h2d_gbs, "step_ms": step_ms,
             "returns": "reconstructed subtensor, core and factors"}
 
 

@@ -143,9 +143,10 @@ const char* tucker_last_error(const tucker_ctx* ctx);
  *   TUCKER_OPT_MAX_SWEEPS  Jacobi sweep cap (default 40; 0 = no sweep)
  *   TUCKER_OPT_JACOBI_TOL  relative off-diagonal tolerance (default 1e-15)
  *   TUCKER_OPT_EIG_SOLVER  eigensolver of the truncation step (tucker_sthosvd,
- *                          tucker_eig_trunc): 0 auto (tridiagonal for
- *                          64 <= I <= 4096, Jacobi otherwise), 1 Jacobi,
- *                          2 tridiagonal for every I <= 4096
+ *                          tucker_eig_trunc): 0 auto and 2: tridiagonal for
+ *                          I <= 4096 (Jacobi above, and where the Cholesky
+ *                          QR of the inverse-iteration vectors fails),
+ *                          1 Jacobi
  *   TUCKER_OPT_BARRIER_POLLS  polls a CTA of the eigensolvers' grid barriers
  *                          (Jacobi sweeps, Householder reduction) makes
  *                          before it gives up (default 2^24, about a second
