@@ -64,8 +64,8 @@ typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
  *   FP32   : FP32 products, round-to-nearest FP32 sums over short chunks
  *            combined exactly (TwoSum) and in FP64; working tensor and core
  *            in the input dtype.
- *   MIXED  : Grams of column-mode views with 64 <= I_n <= 2048 (row-mode
- *            views: 128 <= I_n <= 2048) on the tensor cores with exact
+ *   MIXED  : Grams of column-mode views with 64 <= I_n <= 4096 (row-mode
+ *            views: 128 <= I_n <= 4096) on the tensor cores with exact
  *            integer digit products: each value is split under a per-row
  *            power-of-two scale into two or three 7-bit digits (exact in
  *            FP16), all digit products accumulate exactly in FP32 over

@@ -277,7 +277,7 @@ int digit_gram_digits(const unsigned* rowmax_bits, int64_t I, int64_t K, double 
 // Which kernel serves a Gram / TTM step: 0 SIMT FP64, 1 SIMT FP32, 2 tcgen05
 // (rounded FP16 split products), 3 small-mode FP64 (I < 64, every
 // precision), 4 FP32 with exact (compensated) block sums (row modes with few
-// slabs), 5 tcgen05 on exact integer digit products (MIXED, I <= 2048;
+// slabs), 5 tcgen05 on exact integer digit products (MIXED, I <= 4096;
 // column-mode views from I = 64, row-mode views from 128), three digits;
 // 6 the same with two digits.
 int gram_kernel_for(tucker_prec prec, tucker_dtype dt, const SlabView& v, int sms) {

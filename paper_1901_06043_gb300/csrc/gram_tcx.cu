@@ -722,7 +722,7 @@ __global__ void k_rowmax_slab(const float* __restrict__ y, int64_t L, int64_t I,
 // from 128.
 GramPlan plan_gram_tcx(int64_t L, int64_t I, int64_t Rt, int num_sms) {
   GramPlan p;
-  if (I < (L == 1 ? 64 : 128) || I > 2048 || L < 1 || Rt < 1) return p;
+  if (I < (L == 1 ? 64 : 128) || I > 4096 || L < 1 || Rt < 1) return p;
   int64_t stages;
   if (L == 1) {
     if ((I % 4) != 0 || Rt < 4 * BK) return p;

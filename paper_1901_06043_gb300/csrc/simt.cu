@@ -187,61 +187,66 @@ __global__ void __launch_bounds__(256) k_sumsq_f32(const float* __restrict__ y, 
 
 // The same sum of squares over the column-major I0 x ncols view (mode 0),
 // recording also each row's max |x| (as FP32 bits, atomicMax into
-// rowmax_bits[I0], zeroed by the caller): thread t owns rows 4t..4t+3 and
-// walks the columns blockIdx.x, blockIdx.x + gridDim.x, ..., eight columns per
-// iteration in flight.  Needs I0 % 4 == 0, I0 <= 2048 and 16-byte aligned y.
+// rowmax_bits[I0], zeroed by the caller): thread t owns rows 4t..4t+3 (and
+// 4(t + blockDim.x).., ... when I0 / 4 exceeds the block: `passes` rounds over
+// the block's columns, one per row quad) and walks the columns blockIdx.x,
+// blockIdx.x + gridDim.x, ..., eight columns per iteration in flight.  Needs
+// I0 % 4 == 0, I0 <= 8192 and 16-byte aligned y.
 __global__ void __launch_bounds__(512) k_sumsq_rowmax_f32(const float* __restrict__ y, int64_t I0,
-                                                           int64_t ncols, double* __restrict__ partial,
+                                                           int64_t ncols, int passes,
+                                                           double* __restrict__ partial,
                                                            unsigned* __restrict__ nonfinite,
                                                            unsigned* __restrict__ rowmax_bits) {
   SumSqF32 s;
-  const int64_t r4 = 4 * (int64_t)threadIdx.x;
-  const bool active = r4 < I0;
-  unsigned rm[4] = {0u, 0u, 0u, 0u};
   int groups = 0;
-  int64_t c = blockIdx.x;
-  constexpr int U = 8;
-  for (; c + (U - 1) * (int64_t)gridDim.x < ncols; c += U * (int64_t)gridDim.x) {
-    float4 q[U];
+  for (int pass = 0; pass < passes; ++pass) {
+    const int64_t r4 = 4 * ((int64_t)threadIdx.x + (int64_t)pass * blockDim.x);
+    const bool active = r4 < I0;
+    unsigned rm[4] = {0u, 0u, 0u, 0u};
+    int64_t c = blockIdx.x;
+    constexpr int U = 8;
+    for (; c + (U - 1) * (int64_t)gridDim.x < ncols; c += U * (int64_t)gridDim.x) {
+      float4 q[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-      q[u] = active ? __ldcs(reinterpret_cast<const float4*>(y + r4 + I0 * (c + u * (int64_t)gridDim.x)))
-                    : make_float4(0.f, 0.f, 0.f, 0.f);
-    unsigned gm = 0;
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const unsigned b0 = __float_as_uint(q[u].x) & 0x7fffffffu, b1 = __float_as_uint(q[u].y) & 0x7fffffffu;
-      const unsigned b2 = __float_as_uint(q[u].z) & 0x7fffffffu, b3 = __float_as_uint(q[u].w) & 0x7fffffffu;
-      rm[0] = max(rm[0], b0); rm[1] = max(rm[1], b1); rm[2] = max(rm[2], b2); rm[3] = max(rm[3], b3);
-      gm = max(gm, max(max(b0, b1), max(b2, b3)));
-    }
-    s.mxb = max(s.mxb, gm);
-    if (__any_sync(__activemask(), gm >= 0x5f800000u || (gm != 0u && gm < 0x21800000u))) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) { s.add(q[u].x); s.add(q[u].y); s.add(q[u].z); s.add(q[u].w); }
-    } else {
+      for (int u = 0; u < U; ++u)
+        q[u] = active ? __ldcs(reinterpret_cast<const float4*>(y + r4 + I0 * (c + u * (int64_t)gridDim.x)))
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+      unsigned gm = 0;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        s.add_fast(q[u].x); s.add_fast(q[u].y); s.add_fast(q[u].z); s.add_fast(q[u].w);
+        const unsigned b0 = __float_as_uint(q[u].x) & 0x7fffffffu, b1 = __float_as_uint(q[u].y) & 0x7fffffffu;
+        const unsigned b2 = __float_as_uint(q[u].z) & 0x7fffffffu, b3 = __float_as_uint(q[u].w) & 0x7fffffffu;
+        rm[0] = max(rm[0], b0); rm[1] = max(rm[1], b1); rm[2] = max(rm[2], b2); rm[3] = max(rm[3], b3);
+        gm = max(gm, max(max(b0, b1), max(b2, b3)));
       }
+      s.mxb = max(s.mxb, gm);
+      if (__any_sync(__activemask(), gm >= 0x5f800000u || (gm != 0u && gm < 0x21800000u))) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) { s.add(q[u].x); s.add(q[u].y); s.add(q[u].z); s.add(q[u].w); }
+      } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          s.add_fast(q[u].x); s.add_fast(q[u].y); s.add_fast(q[u].z); s.add_fast(q[u].w);
+        }
+      }
+      if (++groups == 4) { s.flush(); groups = 0; }
     }
-    if (++groups == 4) { s.flush(); groups = 0; }
-  }
-  for (; c < ncols; c += gridDim.x) {
-    if (!active) continue;
-    const float4 q = __ldcs(reinterpret_cast<const float4*>(y + r4 + I0 * c));
-    rm[0] = max(rm[0], __float_as_uint(q.x) & 0x7fffffffu);
-    rm[1] = max(rm[1], __float_as_uint(q.y) & 0x7fffffffu);
-    rm[2] = max(rm[2], __float_as_uint(q.z) & 0x7fffffffu);
-    rm[3] = max(rm[3], __float_as_uint(q.w) & 0x7fffffffu);
-    s.add(q.x); s.add(q.y); s.add(q.z); s.add(q.w);
+    for (; c < ncols; c += gridDim.x) {
+      if (!active) continue;
+      const float4 q = __ldcs(reinterpret_cast<const float4*>(y + r4 + I0 * c));
+      rm[0] = max(rm[0], __float_as_uint(q.x) & 0x7fffffffu);
+      rm[1] = max(rm[1], __float_as_uint(q.y) & 0x7fffffffu);
+      rm[2] = max(rm[2], __float_as_uint(q.z) & 0x7fffffffu);
+      rm[3] = max(rm[3], __float_as_uint(q.w) & 0x7fffffffu);
+      s.add(q.x); s.add(q.y); s.add(q.z); s.add(q.w);
+    }
+    if (active) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (rm[u]) atomicMax(rowmax_bits + r4 + u, rm[u]);
+    }
   }
   s.flush();
-  if (active) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (rm[u]) atomicMax(rowmax_bits + r4 + u, rm[u]);
-  }
   const bool bad = s.mxb >= 0x7f800000u;
   block_store_sum_max(s.acc, bad ? 0.0 : (double)__uint_as_float(s.mxb), partial, nonfinite, bad);
 }
@@ -249,10 +254,15 @@ __global__ void __launch_bounds__(512) k_sumsq_rowmax_f32(const float* __restric
 cudaError_t launch_sumsq_rowmax(const float* y, int64_t I0, int64_t ncols, double* partial,
                                 int nblocks, unsigned* nonfinite, unsigned* rowmax_bits, double* out,
                                 cudaStream_t st) {
-  if (I0 % 4 != 0 || I0 > 2048 || ((uintptr_t)y & 15) != 0) return cudaErrorInvalidValue;
-  const int threads = (int)(((I0 / 4) + 31) / 32 * 32);
+  if (I0 % 4 != 0 || I0 > 8192 || I0 < 4 || ((uintptr_t)y & 15) != 0) return cudaErrorInvalidValue;
+  // row quads per thread: as few passes as a 512-thread block allows, the
+  // quads spread evenly over them
+  const int64_t quads = I0 / 4;
+  const int passes = (int)((quads + 511) / 512);
+  const int threads = (int)(((quads + passes - 1) / passes + 31) / 32 * 32);
   count_launches(2);
-  k_sumsq_rowmax_f32<<<nblocks, threads, 0, st>>>(y, I0, ncols, partial, nonfinite, rowmax_bits);
+  k_sumsq_rowmax_f32<<<nblocks, threads, 0, st>>>(y, I0, ncols, passes, partial, nonfinite,
+                                                  rowmax_bits);
   k_reduce_sum<<<1, 256, 0, st>>>(partial, nblocks, out);
   return cudaGetLastError();
 }
