@@ -546,7 +546,8 @@ CAPTURED_TRAFFIC = {
     # FP32: 741.3 GB/s x 1.192 ms
     ("gram", "tcgen05-x3", "col"): dict(bytes=883.3e6, elems=500 * 440000),
     # (no capture of the two-digit variant yet)
-    # k_ttm_tc_col (transposed output), mode-0 TTM of 500x500x40x11x2 FP32 to 54 rows
+    # k_ttm_tc_col<64> (transposed output), mode-0 TTM of 500x500x40x11x2 FP32 to 54
+    # rows: 4.553 TB/s x 212.2 us
     ("ttm", "tcgen05", "col"): dict(bytes=966.8e6, elems=500 * 440000),
 }
 

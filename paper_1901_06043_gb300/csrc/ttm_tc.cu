@@ -21,8 +21,9 @@
 // ~100 KB of reads in flight per SM to approach the HBM rate.  So Y goes
 // through its own ring: one loader thread issues a 2D tiled TMA load of the
 // stage's box (64 i x 128 slabs, 32 KB, zero-filled outside the view) into
-// one of three raw FP32 slots (96 KB in flight), completing on an mbarrier by
-// byte count; eight converter warps split a raw slot into the
+// one of the raw FP32 slots (three, 96 KB in flight; four, 128 KB, when
+// K <= 64 lets the MMA run with M = 64 and the A images halve), completing
+// on an mbarrier by byte count; eight converter warps split a raw slot into the
 // K-major SW128 FP16 hi/lo B operand of one of two operand slots, and one of
 // them bulk-copies the stage's pre-split A chunk next to it; warp 9 issues the
 // MMAs; warps 10-13 drain the double-buffered accumulators (2 x 128
@@ -42,22 +43,31 @@ using namespace tc;
 
 constexpr int TN = 128;                        // slabs per tile (MMA N)
 constexpr uint32_t TMEM_COLS = 2 * TN;         // two accumulator buffers
-constexpr int TM = 128;                        // MMA M (rows of A; K <= TM)
+constexpr int TM = 128;                        // largest MMA M (rows of A; K <= TM)
 constexpr int SK = 64;                         // i per stage
 constexpr int NOP = 2;                         // operand slots
-constexpr int NRAW = 3;                        // raw Y slots
 constexpr int LOAD_WARP = 0;
 constexpr int NCONV = 8;                       // converter warps 1..8
 constexpr int MMA_WARP = 9;
 constexpr int NTHREADS = 14 * 32;              // + epilogue warps 10..13
-constexpr uint32_t A_BYTES = TM * SK * 2;      // 16 KB (one of hi / lo)
 constexpr uint32_t B_BYTES = TN * SK * 2;      // 16 KB
-constexpr uint32_t OFF_AH = 0, OFF_AL = A_BYTES, OFF_BH = 2 * A_BYTES,
-                   OFF_BL = 2 * A_BYTES + B_BYTES;
-constexpr uint32_t OP_BYTES = 2 * A_BYTES + 2 * B_BYTES;     // 64 KB
 constexpr uint32_t RAW_BYTES = TN * SK * 4;                  // 32 KB
-constexpr uint32_t SMEM_BYTES = NOP * OP_BYTES + NRAW * RAW_BYTES + 1024;
 constexpr int CV4 = (TN * SK / 4) / (NCONV * 32);            // float4 per converter thread (8)
+
+// Shapes per MMA M: with K <= 64 outputs an M = 64 MMA halves the A operand
+// (8 KB instead of 16 KB per hi / lo image), which frees a fourth raw Y slot:
+// 128 KB of reads in flight per SM instead of 96 KB.  Tensor memory holds
+// row r of an M = 64 accumulator in lane 32 (r / 16) + r % 16 (measured).
+template <int M>
+struct ColCfg {
+  static constexpr uint32_t A_BYTES = M * SK * 2;
+  static constexpr uint32_t OFF_AH = 0, OFF_AL = A_BYTES, OFF_BH = 2 * A_BYTES,
+                            OFF_BL = 2 * A_BYTES + B_BYTES;
+  static constexpr uint32_t OP_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 64 or 48 KB
+  static constexpr int NRAW = M == 64 ? 4 : 3;                       // raw Y slots
+  static constexpr uint32_t SMEM_BYTES = NOP * OP_BYTES + NRAW * RAW_BYTES + 1024;
+  static constexpr int RPQ = M / 4;                                  // accumulator rows per lane quarter
+};
 
 // Byte offset of (row, k) in a K-major SW128 FP16 tile with 64 k per row:
 // 1024-byte atoms of 8 rows x 128 bytes, 16-byte chunks XOR-swizzled by
@@ -85,12 +95,13 @@ __device__ __forceinline__ void split_pack(float a, float b, uint32_t& h, uint32
 
 // A (K x I, FP64: element (k, i) at A[k*lda + i] if arow else A[k + lda*i])
 // -> per stage: [A_h tile | A_l tile] as shared-memory images (K-major SW128,
-// 128 rows x 64 i, zero outside K x I), scaled by s_a; *sa_out = s_a.
+// tm rows x 64 i, zero outside K x I), scaled by s_a; *sa_out = s_a.
 // One CTA of 1024 threads.
 __global__ void __launch_bounds__(1024) k_ttm_tc_prep(const double* __restrict__ A, int K,
                                                       int64_t I, int64_t lda, int arow, int nks,
-                                                      uint8_t* __restrict__ out,
+                                                      int tm, uint8_t* __restrict__ out,
                                                       float* __restrict__ sa_out) {
+  const uint32_t a_bytes = (uint32_t)tm * SK * 2;
   __shared__ double red[32];
   __shared__ float s_sa;
   double mx = 0.0;
@@ -116,10 +127,10 @@ __global__ void __launch_bounds__(1024) k_ttm_tc_prep(const double* __restrict__
   }
   __syncthreads();
   const double sa = s_sa;
-  const int64_t tot = (int64_t)nks * TM * (SK / 2);   // element pairs (k, k+1)
+  const int64_t tot = (int64_t)nks * tm * (SK / 2);   // element pairs (k, k+1)
   for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int ks = (int)(e / (TM * (SK / 2)));
-    const int rem = (int)(e % (TM * (SK / 2)));
+    const int ks = (int)(e / (tm * (SK / 2)));
+    const int rem = (int)(e % (tm * (SK / 2)));
     const int row = rem / (SK / 2), kp = 2 * (rem % (SK / 2));
     float v2[2];
 #pragma unroll
@@ -131,10 +142,10 @@ __global__ void __launch_bounds__(1024) k_ttm_tc_prep(const double* __restrict__
     }
     uint32_t h, l;
     split_pack(v2[0], v2[1], h, l);
-    uint8_t* base = out + (size_t)ks * 2 * A_BYTES;
+    uint8_t* base = out + (size_t)ks * 2 * a_bytes;
     const uint32_t o = kmaj_off(row, kp);
     *reinterpret_cast<uint32_t*>(base + o) = h;
-    *reinterpret_cast<uint32_t*>(base + A_BYTES + o) = l;
+    *reinterpret_cast<uint32_t*>(base + a_bytes + o) = l;
   }
 }
 
@@ -152,8 +163,14 @@ struct TtmTcArgs {
   unsigned* err;
 };
 
+template <int M>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_ttm_tc_col(TtmTcArgs g, const __grid_constant__ CUtensorMap ymap) {
+  using C = ColCfg<M>;
+  constexpr int NRAW = C::NRAW;
+  constexpr uint32_t A_BYTES = C::A_BYTES, OP_BYTES = C::OP_BYTES;
+  constexpr uint32_t OFF_AH = C::OFF_AH, OFF_AL = C::OFF_AL, OFF_BH = C::OFF_BH,
+                     OFF_BL = C::OFF_BL;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* raw = smem + NOP * OP_BYTES;
@@ -256,7 +273,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp == MMA_WARP) {
     // ---------------- MMA issue (one thread)
     if (lane == 0) {
-      const uint32_t idesc = instr_desc_kk(TM, TN);
+      const uint32_t idesc = instr_desc_kk(M, TN);
       const uint32_t sbase = smem_u32(smem);
       bool ok = true;
       for (int64_t j = 0; j < my_tiles && ok; ++j) {
@@ -293,18 +310,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else {
     // ---------------- epilogue: tensor memory -> Z
     const int q = warp & 3;          // the lane quarter this warp may access
-    const int r = 32 * q + lane;     // output row (index of the K outputs)
+    // output row (index of the K outputs) of this lane: M = 128 rows 32 q +
+    // lane; M = 64 rows 16 q + lane in lanes 0-15 of the quarter
+    const int r = C::RPQ * q + lane;
+    const bool rl = lane < C::RPQ;
     const float inv = (float)(1.0 / ((double)g.sy * (double)*g.sa));   // powers of two: exact
     for (int64_t j = 0; j < my_tiles; ++j) {
       const int buf = (int)(j & 1);
       if (!mbar_wait(smem_u32(&bar_accf[buf]), (uint32_t)((j / 2) & 1), g.err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
       const int64_t m0 = ((int64_t)blockIdx.x + j * gridDim.x) * TN;
-      if (32 * q < g.K) {
+      if (C::RPQ * q < g.K) {
         for (int c0 = 0; c0 < TN; c0 += 32) {
           uint32_t rr[32];
           tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * (uint32_t)TN + (uint32_t)c0, rr);
-          if (r < g.K) {
+          if (rl && r < g.K) {
             if (!g.zt) {
 #pragma unroll
               for (int jj = 0; jj < 32; ++jj) {
@@ -657,7 +677,22 @@ int ttm_tc_supported(int64_t L, int64_t I, int64_t Rt, int64_t K) {
 size_t ttm_tc_scratch_bytes(int64_t I, int64_t K) {
   (void)K;
   const size_t nks = (size_t)((I + SK - 1) / SK);
-  return nks * 2 * A_BYTES + 256;
+  return nks * 2 * ColCfg<TM>::A_BYTES + 256;
+}
+
+template <int M>
+cudaError_t run_ttm_tc_col(const TtmTcArgs& a, const CUtensorMap& ymap, int grid,
+                           cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_ttm_tc_col<M>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ColCfg<M>::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_ttm_tc_col<M><<<grid, NTHREADS, ColCfg<M>::SMEM_BYTES, st>>>(a, ymap);
+  return cudaSuccess;
 }
 
 cudaError_t launch_ttm_tc(const float* y, int64_t L, int64_t I, int64_t Rt, const double* A,
@@ -665,17 +700,11 @@ cudaError_t launch_ttm_tc(const float* y, int64_t L, int64_t I, int64_t Rt, cons
                           void* scratch, unsigned* err, int num_sms, cudaStream_t st) {
   if (!ttm_tc_supported(L, I, Rt, K) || ((uintptr_t)y & 15) != 0) return cudaErrorInvalidValue;
   if (zt && (Rt & 3) == 0 && ((uintptr_t)z & 15) != 0) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_ttm_tc_col, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   const int nks = (int)((I + SK - 1) / SK);
+  const int tm = K <= 64 ? 64 : TM;
   uint8_t* aprep = (uint8_t*)scratch;
-  float* sa = (float*)(aprep + (size_t)nks * 2 * A_BYTES);
-  k_ttm_tc_prep<<<1, 1024, 0, st>>>(A, (int)K, I, lda, a_rowmajor, nks, aprep, sa);
+  float* sa = (float*)(aprep + (size_t)nks * 2 * ColCfg<TM>::A_BYTES);
+  k_ttm_tc_prep<<<1, 1024, 0, st>>>(A, (int)K, I, lda, a_rowmajor, nks, tm, aprep, sa);
   TtmTcArgs a;
   a.y = y;
   a.I = I;
@@ -702,7 +731,9 @@ cudaError_t launch_ttm_tc(const float* y, int64_t L, int64_t I, int64_t Rt, cons
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   const int grid = (int)(a.ntiles < num_sms ? a.ntiles : num_sms);
-  k_ttm_tc_col<<<grid, NTHREADS, SMEM_BYTES, st>>>(a, ymap);
+  cudaError_t e = tm == 64 ? run_ttm_tc_col<64>(a, ymap, grid, st)
+                           : run_ttm_tc_col<TM>(a, ymap, grid, st);
+  if (e != cudaSuccess) return e;
   count_launches(2);
   return cudaGetLastError();
 }
