@@ -194,7 +194,9 @@ struct Timer {
 // exact tensor-core Gram) into rowmax[I0].
 tucker_status do_norm(tucker_ctx* c, const void* y, tucker_dtype dt, int64_t n, double* out,
                       double* maxabs = nullptr, unsigned* rowmax = nullptr, int64_t I0 = 0) {
-  int nb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8);
+  // four blocks per SM: 7.73 ms for the 44 GB norm pass with row maxima,
+  // against 7.93 ms with eight (each thread keeps eight loads in flight)
+  int nb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 4);
   if (nb < 1) nb = 1;
   DevBuf part;
   TK_TRY(dev_alloc(c, part, sizeof(double) * 2 * nb));
