@@ -308,6 +308,14 @@ tucker_status rowmax_pass(tucker_ctx* c, const float* y, int64_t I0, int64_t nco
   return TUCKER_OK;
 }
 
+// Row maxima of any slab view for the digit Gram's scales: the column-major
+// pass for column views, else one warp per (row, run of slabs).
+tucker_status view_rowmax(tucker_ctx* c, const float* y, const SlabView& v, unsigned* rowmax) {
+  if (v.L == 1 && v.I <= 8192) return rowmax_pass(c, y, v.I, v.Rt, rowmax);
+  TK_CUDA(c, launch_rowmax_slab(y, v.L, v.I, v.Rt, c->num_sms, rowmax, c->stream));
+  return TUCKER_OK;
+}
+
 // maxabs: max|y| if the caller knows it (e.g. from the norm pass), else <= 0.
 // check = false: the tensor-core kernel's error word (d_words[8]) is neither
 // cleared nor read here; the caller clears it before and reads it after a
@@ -326,11 +334,7 @@ tucker_status gram_once(tucker_ctx* c, const void* y, tucker_dtype dt, const Sla
     TK_TRY(dev_alloc(c, scratch, p.scratch_bytes));
     if (!rowmax) {
       TK_TRY(dev_alloc(c, rm, sizeof(unsigned) * v.I));
-      if (v.L == 1)
-        TK_TRY(rowmax_pass(c, (const float*)y, v.I, v.Rt, rm.as<unsigned>()));
-      else
-        TK_CUDA(c, launch_rowmax_slab((const float*)y, v.L, v.I, v.Rt, c->num_sms,
-                                      rm.as<unsigned>(), c->stream));
+      TK_TRY(view_rowmax(c, (const float*)y, v, rm.as<unsigned>()));
       rowmax = rm.as<unsigned>();
     }
     if (check) TK_CUDA(c, cudaMemsetAsync(c->d_words + 8, 0, sizeof(unsigned), c->stream));
@@ -419,7 +423,7 @@ tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabV
                       tucker_prec prec, double* S, int* kernel_used, double maxabs = -1.0,
                       bool check = true, const unsigned* rowmax = nullptr, int ndig = 3) {
   int kern = gram_kernel_for(prec, dt, v, c->num_sms);
-  if ((kern == 2 || (kern == 5 && v.L == 1)) && (((uintptr_t)y) & 15) != 0) kern = 1;
+  if (kern == 2 && (((uintptr_t)y) & 15) != 0) kern = 1;
   if (kern == 5 && (((uintptr_t)y) & 3) != 0) kern = 1;
   if (c->gram_digits) ndig = c->gram_digits;
   if (!c->autotune || kern == 2)
@@ -438,11 +442,7 @@ tucker_status do_gram(tucker_ctx* c, const void* y, tucker_dtype dt, const SlabV
     DevBuf rm;
     if (kern == 5 && !rowmax) {
       TK_TRY(dev_alloc(c, rm, sizeof(unsigned) * v.I));
-      if (v.L == 1)
-        TK_TRY(rowmax_pass(c, (const float*)y, v.I, v.Rt, rm.as<unsigned>()));
-      else
-        TK_CUDA(c, launch_rowmax_slab((const float*)y, v.L, v.I, v.Rt, c->num_sms,
-                                      rm.as<unsigned>(), c->stream));
+      TK_TRY(view_rowmax(c, (const float*)y, v, rm.as<unsigned>()));
       rowmax = rm.as<unsigned>();
     }
     cudaEvent_t e0, e1;
@@ -1050,9 +1050,13 @@ static tucker_status sthosvd_impl(tucker_ctx* c, const void* x, tucker_dtype dt,
   } else {
     const SlabView v0 = slab_view(ndim, dims, 0);
     const bool tcx = order[0] == 0 && gram_kernel_for(prec, dt, v0, c->num_sms) == 5 &&
-                     (((uintptr_t)x) & 15) == 0;
+                     (((uintptr_t)x) & 3) == 0;
+    // the norm pass records the row maxima on the way
+    const bool in_norm = tcx && v0.I <= 8192;
     if (tcx) TK_TRY(dev_alloc(c, rowmax, sizeof(unsigned) * v0.I));
-    TK_TRY(do_norm(c, x, dt, nx, &nrm2, &xmax, rowmax.as<unsigned>(), dims[0]));
+    TK_TRY(do_norm(c, x, dt, nx, &nrm2, &xmax, in_norm ? rowmax.as<unsigned>() : nullptr,
+                   dims[0]));
+    if (tcx && !in_norm) TK_TRY(view_rowmax(c, (const float*)x, v0, rowmax.as<unsigned>()));
     rowmax0 = rowmax.as<unsigned>();
   }
   t_norm.stop(c);
@@ -1102,9 +1106,9 @@ static tucker_status sthosvd_impl(tucker_ctx* c, const void* x, tucker_dtype dt,
     const int gk = streamed ? -1 : gram_kernel_for(prec, ydt, v, c->num_sms);
     tucker_prec gram_prec = prec;
     int ndig = 3;
-    if (gk == 5 && rotate && s > 0 && ydt == TUCKER_F32 && (((uintptr_t)y) & 15) == 0) {
+    if (gk == 5 && rotate && s > 0 && ydt == TUCKER_F32 && (((uintptr_t)y) & 3) == 0) {
       TK_TRY(dev_alloc(c, rowmax_s, sizeof(unsigned) * v.I));
-      TK_TRY(rowmax_pass(c, (const float*)y, v.I, v.Rt, rowmax_s.as<unsigned>()));
+      TK_TRY(view_rowmax(c, (const float*)y, v, rowmax_s.as<unsigned>()));
       rmx = rowmax_s.as<unsigned>();
     }
     if (gk == 5 && rmx) {
@@ -1326,7 +1330,11 @@ tucker_status tucker_sthosvd_host(tucker_ctx* c, const void* x_host, tucker_dtyp
     Timer tn, tg;
     tn.start(c);
     double n2 = 0.0, mx = 0.0;
-    TK_TRY(do_norm(c, yp, dt, e1 - e0, &n2, &mx, tcx ? rmx_p.as<unsigned>() : nullptr, I0));
+    const bool in_norm = tcx && I0 <= 8192;
+    TK_TRY(do_norm(c, yp, dt, e1 - e0, &n2, &mx, in_norm ? rmx_p.as<unsigned>() : nullptr, I0));
+    if (tcx && !in_norm)
+      TK_TRY(view_rowmax(c, (const float*)yp, SlabView{1, I0, (e1 - e0) / I0, 1},
+                         rmx_p.as<unsigned>()));
     tn.stop(c);
     nrm2 += n2;
     xmax = std::max(xmax, mx);
@@ -1880,10 +1888,16 @@ tucker_status tucker_hosvd(tucker_ctx* c, const void* x, tucker_dtype dt, int nd
   DevBuf rowmax;
   {
     const SlabView v0 = slab_view(ndim, dims, 0);
-    if (gram_kernel_for(prec, dt, v0, c->num_sms) == 5 && (((uintptr_t)x) & 15) == 0)
+    if (gram_kernel_for(prec, dt, v0, c->num_sms) == 5 && (((uintptr_t)x) & 3) == 0)
       TK_TRY(dev_alloc(c, rowmax, sizeof(unsigned) * v0.I));
   }
-  TK_TRY(do_norm(c, x, dt, numel(ndim, dims), &nrm2, &xmax, rowmax.as<unsigned>(), dims[0]));
+  {
+    const SlabView v0 = slab_view(ndim, dims, 0);
+    const bool in_norm = rowmax.p && v0.I <= 8192;
+    TK_TRY(do_norm(c, x, dt, numel(ndim, dims), &nrm2, &xmax,
+                   in_norm ? rowmax.as<unsigned>() : nullptr, dims[0]));
+    if (rowmax.p && !in_norm) TK_TRY(view_rowmax(c, (const float*)x, v0, rowmax.as<unsigned>()));
+  }
   t_norm.stop(c);
   r->norm_x_sq = nrm2;
   const double thr = ranks ? 0.0 : eps * eps * nrm2 / ndim;

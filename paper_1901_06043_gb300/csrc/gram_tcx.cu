@@ -329,7 +329,7 @@ __device__ __forceinline__ void cta_work(const GramTcxArgs& g, int b, int& ta, i
 // mode, where the extra instructions outweighed the latency they hid.)  NOPS == 1 (diagonal tile):
 // the lane's rows' diagonal corrections (flush_diag) are added into
 // dcorr[row] (FP64, shared by the CTA's producers).
-template <int NOPS, bool ROW, int NDIG>
+template <int NOPS, bool ROW, int NDIG, bool VEC>
 __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uint64_t* bar_full,
                                         uint64_t* bar_empty, const float* s_scale, int ta,
                                         int tb, int64_t k0, int64_t k1, int64_t gs0, int nst,
@@ -378,6 +378,9 @@ __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uin
 #pragma unroll
     for (int o = 0; o < NOPS; ++o) {
       rok[o] = row0[o] < g.I;
+      rmask[o] = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) rmask[o] |= (row0[o] + j < g.I) ? (1u << j) : 0u;
       lp[o] = g.x + kfirst * g.I + (rok[o] ? row0[o] : 0);
     }
   }
@@ -399,8 +402,18 @@ __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uin
       const bool kok = ls < nvalid;
 #pragma unroll
       for (int o = 0; o < NOPS; ++o) {
-        v[o] = (kok && rok[o]) ? ld_nl1(reinterpret_cast<const float4*>(lp[o]))
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (VEC) {
+          v[o] = (kok && rok[o]) ? ld_nl1(reinterpret_cast<const float4*>(lp[o]))
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+          // I % 4 != 0: the lane's four rows start anywhere in the column;
+          // four 4-byte loads, rows past I read as zero
+          const unsigned m = kok ? rmask[o] : 0u;
+          v[o].x = (m & 1u) ? __ldg(lp[o]) : 0.f;
+          v[o].y = (m & 2u) ? __ldg(lp[o] + 1) : 0.f;
+          v[o].z = (m & 4u) ? __ldg(lp[o] + 2) : 0.f;
+          v[o].w = (m & 8u) ? __ldg(lp[o] + 3) : 0.f;
+        }
         lp[o] += step;
       }
     }
@@ -453,7 +466,10 @@ __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uin
   }
 }
 
-template <bool ROW, int NDIG>
+// VEC (column mode): I % 4 == 0 and x 16-byte aligned, one 16-byte load per
+// lane and operand; otherwise four 4-byte loads (a runtime switch between
+// the two in the loop cost 14 %, so each is its own kernel).
+template <bool ROW, int NDIG, bool VEC>
 __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx(GramTcxArgs g) {
   using D = Dig<NDIG>;
   constexpr int NSTAGE = D::NSTAGE;
@@ -512,10 +528,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gram_tcx(GramTcxArgs g) {
   if (warp < NPROD) {
     // ---------------- producers: X -> digit planes of A (and B)
     if (diag)
-      produce<1, ROW, NDIG>(g, smem, bar_full, bar_empty, s_scale, ta, tb, k0, k1, k0, nst, warp,
+      produce<1, ROW, NDIG, VEC>(g, smem, bar_full, bar_empty, s_scale, ta, tb, k0, k1, k0, nst, warp,
                             lane, dcorr);
     else
-      produce<2, ROW, NDIG>(g, smem, bar_full, bar_empty, s_scale, ta, tb, k0, k1, k0, nst, warp,
+      produce<2, ROW, NDIG, VEC>(g, smem, bar_full, bar_empty, s_scale, ta, tb, k0, k1, k0, nst, warp,
                             lane, dcorr);
   } else {
     // ---------------- drain warps: exact window sums -> FP32 pairs.  Lane 0
@@ -725,7 +741,7 @@ GramPlan plan_gram_tcx(int64_t L, int64_t I, int64_t Rt, int num_sms) {
   if (I < (L == 1 ? 64 : 128) || I > 4096 || L < 1 || Rt < 1) return p;
   int64_t stages;
   if (L == 1) {
-    if ((I % 4) != 0 || Rt < 4 * BK) return p;
+    if (Rt < 4 * BK) return p;
     stages = (Rt + BK - 1) / BK;
   } else {
     const int64_t nlb = (L + BK - 1) / BK;
@@ -760,21 +776,20 @@ GramPlan plan_gram_tcx(int64_t L, int64_t I, int64_t Rt, int num_sms) {
   return p;
 }
 
-template <bool ROW, int NDIG>
+template <bool ROW, int NDIG, bool VEC>
 cudaError_t run_gram_tcx(const GramTcxArgs& a, int nctas, cudaStream_t st) {
   constexpr uint32_t smem = Dig<NDIG>::SMEM_BYTES;
-  cudaError_t e = cudaFuncSetAttribute(k_gram_tcx<ROW, NDIG>,
+  cudaError_t e = cudaFuncSetAttribute(k_gram_tcx<ROW, NDIG, VEC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gram_tcx<ROW, NDIG><<<(unsigned)nctas, NTHREADS, smem, st>>>(a);
+  k_gram_tcx<ROW, NDIG, VEC><<<(unsigned)nctas, NTHREADS, smem, st>>>(a);
   return cudaSuccess;
 }
 
 cudaError_t launch_gram_tcx(const float* y, int64_t L, int64_t I, int64_t Rt, const GramPlan& p,
                             const unsigned* rowmax_bits, void* scratch, unsigned* err, double* S,
                             cudaStream_t st, int ndig) {
-  if (p.nctas <= 0 || (L == 1 && ((uintptr_t)y & 15) != 0) || ((uintptr_t)y & 3) != 0 ||
-      (ndig != 2 && ndig != 3))
+  if (p.nctas <= 0 || ((uintptr_t)y & 3) != 0 || (ndig != 2 && ndig != 3))
     return cudaErrorInvalidValue;
   cudaError_t e;
   double* part = static_cast<double*>(scratch);
@@ -794,10 +809,16 @@ cudaError_t launch_gram_tcx(const float* y, int64_t L, int64_t I, int64_t Rt, co
   a.scale = scale;
   a.part = part;
   a.err = err;
-  if (L == 1)
-    e = ndig == 3 ? run_gram_tcx<false, 3>(a, p.nctas, st) : run_gram_tcx<false, 2>(a, p.nctas, st);
+  const bool vec = (I % 4) == 0 && ((uintptr_t)y & 15) == 0;
+  if (L == 1 && vec)
+    e = ndig == 3 ? run_gram_tcx<false, 3, true>(a, p.nctas, st)
+                  : run_gram_tcx<false, 2, true>(a, p.nctas, st);
+  else if (L == 1)
+    e = ndig == 3 ? run_gram_tcx<false, 3, false>(a, p.nctas, st)
+                  : run_gram_tcx<false, 2, false>(a, p.nctas, st);
   else
-    e = ndig == 3 ? run_gram_tcx<true, 3>(a, p.nctas, st) : run_gram_tcx<true, 2>(a, p.nctas, st);
+    e = ndig == 3 ? run_gram_tcx<true, 3, true>(a, p.nctas, st)
+                  : run_gram_tcx<true, 2, true>(a, p.nctas, st);
   if (e != cudaSuccess) return e;
   const int64_t tot = I * I;
   k_gram_tcx_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(

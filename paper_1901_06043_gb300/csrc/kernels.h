@@ -15,7 +15,8 @@ cudaError_t launch_sumsq(const void* y, tucker_dtype dt, int64_t n, double* part
 
 // The same over the column-major I0 x ncols mode-0 view, also recording each
 // row's max |x| as FP32 bits (atomicMax into the zeroed rowmax_bits[I0]);
-// I0 % 4 == 0, I0 <= 8192, 16-byte aligned y
+// I0 <= 8192, 4-byte aligned y (16-byte loads when I0 % 4 == 0 and y is
+// 16-byte aligned)
 cudaError_t launch_sumsq_rowmax(const float* y, int64_t I0, int64_t ncols, double* partial,
                                 int nblocks, unsigned* nonfinite, unsigned* rowmax_bits, double* out,
                                 cudaStream_t st);
@@ -33,7 +34,8 @@ struct GramPlan {
 // ---- tensor-core Gram of a slab view on exact digit products
 // (gram_tcx.cu): plan.nctas == 0 when it does not apply (I <= 4096;
 // column mode 64 <= I, row mode 128 <= I;
-// column mode L == 1 with I % 4 == 0; row mode L > 1 with l-blocks of 16 at
+// column mode L == 1 (16-byte loads when I % 4 == 0 and y is 16-byte aligned,
+// else 4-byte loads); row mode L > 1 with l-blocks of 16 at
 // most 25 % zero fill); rowmax_bits: FP32 bits of the row maxima, from
 // launch_sumsq_rowmax (column mode) or launch_rowmax_slab (row mode)
 GramPlan plan_gram_tcx(int64_t L, int64_t I, int64_t Rt, int num_sms);

@@ -190,8 +190,21 @@ __global__ void __launch_bounds__(256) k_sumsq_f32(const float* __restrict__ y, 
 // rowmax_bits[I0], zeroed by the caller): thread t owns rows 4t..4t+3 (and
 // 4(t + blockDim.x).., ... when I0 / 4 exceeds the block: `passes` rounds over
 // the block's columns, one per row quad) and walks the columns blockIdx.x,
-// blockIdx.x + gridDim.x, ..., eight columns per iteration in flight.  Needs
-// I0 % 4 == 0, I0 <= 8192 and 16-byte aligned y.
+// blockIdx.x + gridDim.x, ..., eight columns per iteration in flight.  VEC:
+// one 16-byte load per quad (I0 % 4 == 0, 16-byte aligned y); otherwise four
+// 4-byte loads, rows past I0 read as zero.  I0 <= 8192.
+template <bool VEC>
+__device__ __forceinline__ float4 load_quad(const float* p, int64_t r4, int64_t I0) {
+  if (VEC) return __ldcs(reinterpret_cast<const float4*>(p));
+  float4 q;
+  q.x = (r4 < I0) ? __ldcs(p) : 0.f;
+  q.y = (r4 + 1 < I0) ? __ldcs(p + 1) : 0.f;
+  q.z = (r4 + 2 < I0) ? __ldcs(p + 2) : 0.f;
+  q.w = (r4 + 3 < I0) ? __ldcs(p + 3) : 0.f;
+  return q;
+}
+
+template <bool VEC>
 __global__ void __launch_bounds__(512) k_sumsq_rowmax_f32(const float* __restrict__ y, int64_t I0,
                                                            int64_t ncols, int passes,
                                                            double* __restrict__ partial,
@@ -209,7 +222,7 @@ __global__ void __launch_bounds__(512) k_sumsq_rowmax_f32(const float* __restric
       float4 q[U];
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        q[u] = active ? __ldcs(reinterpret_cast<const float4*>(y + r4 + I0 * (c + u * (int64_t)gridDim.x)))
+        q[u] = active ? load_quad<VEC>(y + r4 + I0 * (c + u * (int64_t)gridDim.x), r4, I0)
                       : make_float4(0.f, 0.f, 0.f, 0.f);
       unsigned gm = 0;
 #pragma unroll
@@ -233,7 +246,7 @@ __global__ void __launch_bounds__(512) k_sumsq_rowmax_f32(const float* __restric
     }
     for (; c < ncols; c += gridDim.x) {
       if (!active) continue;
-      const float4 q = __ldcs(reinterpret_cast<const float4*>(y + r4 + I0 * c));
+      const float4 q = load_quad<VEC>(y + r4 + I0 * c, r4, I0);
       rm[0] = max(rm[0], __float_as_uint(q.x) & 0x7fffffffu);
       rm[1] = max(rm[1], __float_as_uint(q.y) & 0x7fffffffu);
       rm[2] = max(rm[2], __float_as_uint(q.z) & 0x7fffffffu);
@@ -243,7 +256,7 @@ __global__ void __launch_bounds__(512) k_sumsq_rowmax_f32(const float* __restric
     if (active) {
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if (rm[u]) atomicMax(rowmax_bits + r4 + u, rm[u]);
+        if (rm[u] && r4 + u < I0) atomicMax(rowmax_bits + r4 + u, rm[u]);
     }
   }
   s.flush();
@@ -254,15 +267,20 @@ __global__ void __launch_bounds__(512) k_sumsq_rowmax_f32(const float* __restric
 cudaError_t launch_sumsq_rowmax(const float* y, int64_t I0, int64_t ncols, double* partial,
                                 int nblocks, unsigned* nonfinite, unsigned* rowmax_bits, double* out,
                                 cudaStream_t st) {
-  if (I0 % 4 != 0 || I0 > 8192 || I0 < 4 || ((uintptr_t)y & 15) != 0) return cudaErrorInvalidValue;
+  if (I0 > 8192 || I0 < 1 || ((uintptr_t)y & 3) != 0) return cudaErrorInvalidValue;
+  const bool vec = I0 % 4 == 0 && ((uintptr_t)y & 15) == 0;
   // row quads per thread: as few passes as a 512-thread block allows, the
   // quads spread evenly over them
-  const int64_t quads = I0 / 4;
+  const int64_t quads = (I0 + 3) / 4;
   const int passes = (int)((quads + 511) / 512);
   const int threads = (int)(((quads + passes - 1) / passes + 31) / 32 * 32);
   count_launches(2);
-  k_sumsq_rowmax_f32<<<nblocks, threads, 0, st>>>(y, I0, ncols, passes, partial, nonfinite,
-                                                  rowmax_bits);
+  if (vec)
+    k_sumsq_rowmax_f32<true><<<nblocks, threads, 0, st>>>(y, I0, ncols, passes, partial, nonfinite,
+                                                        rowmax_bits);
+  else
+    k_sumsq_rowmax_f32<false><<<nblocks, threads, 0, st>>>(y, I0, ncols, passes, partial,
+                                                         nonfinite, rowmax_bits);
   k_reduce_sum<<<1, 256, 0, st>>>(partial, nblocks, out);
   return cudaGetLastError();
 }

@@ -242,7 +242,8 @@ def test_gram_tensor_error_on_discarded_subspace(ctx):
 
 
 MIXED_X3_SHAPES = [(128, 3000), (500, 2000), (256, 33, 70), (132, 700), (1024, 300), (2048, 64),
-                   (500, 257), (64, 3000), (100, 650), (2080, 300), (4096, 70)]
+                   (500, 257), (64, 3000), (100, 650), (2080, 300), (4096, 70),
+                   (130, 700), (250, 333), (66, 2000), (2050, 70)]
 
 
 @pytest.fixture
@@ -434,15 +435,15 @@ def test_mixed_digit_gram_kept_while_its_bound_allows(ctx, eps, kernel):
 
 def _tcx_applies(dims, mode):
     """Whether the exact-digit tensor-core Gram serves this slab view (the
-    plan's rule: I <= 4096; column mode needs 64 <= I, I % 4 == 0 and >= 64
-    columns; row mode 16-l blocks with at most 25 % zero fill)."""
+    plan's rule: I <= 4096; column mode needs 64 <= I and >= 64 columns;
+    row mode 16-l blocks with at most 25 % zero fill)."""
     L = math.prod(dims[:mode])
     I = dims[mode]
     Rt = math.prod(dims[mode + 1:])
     if not (64 if L == 1 else 128) <= I <= 4096:
         return False
     if L == 1:
-        return I % 4 == 0 and Rt >= 64
+        return Rt >= 64
     nlb = -(-L // 16)
     return 4 * nlb * 16 <= 5 * L and L * I < 2 ** 31 and Rt * nlb >= 4
 
@@ -1119,3 +1120,20 @@ def test_sthosvd_at_jicf_mode_sizes(ctx, prec):
     # eps is met; the tensor-core TTMs (FP16 split products, truncating FP32
     # accumulators over contractions of 1500 and 2080) add ~1e-5 relative
     assert e_ours <= 1e-4 and abs(e_ours - e_ref) <= 3e-5, (e_ours, e_ref)
+
+
+def test_sthosvd_mixed_rows_not_a_multiple_of_four(ctx):
+    """MIXED with mode sizes that are not multiples of 4 (130 and 98): the
+    exact-digit Gram reads such column views with 4-byte loads and takes its
+    row maxima from the same norm pass.  Ranks identical to the oracle's and
+    every discarded sum within 2 % of the threshold."""
+    dims = (130, 98, 50, 7)
+    x, _ = synth.tucker_numpy(dims, (20, 15, 10, 7), decay=0.1, eta=1e-6, seed=31)
+    x32 = x.astype(np.float32)
+    ref = oracle.sthosvd(x32.astype(np.float64), dims, eps=1e-4)
+    res = ctx.sthosvd(dev(x32, torch.float32), dims, eps=1e-4, prec="mixed")
+    assert all(k in ("tcgen05-x3", "tcgen05-x2") for k in res.gram_kernel[:2]), res.gram_kernel
+    assert res.ranks == ref["ranks"], (res.ranks, ref["ranks"])
+    for n in range(4):
+        assert abs(res.discarded[n] - ref["discarded"][n]) <= 0.02 * ref["threshold"], n
+    res.close()
