@@ -96,9 +96,9 @@ constexpr int TILE_ELEMS = 128 * 128;
 // sums).  Measured on a 500-row view with 15 splits of each tile: 6.84
 // against 7.25 ms per CTA.  Equal splits are kept all the same: with 16
 // splits per off-diagonal tile and 14 per diagonal one the Gram took 6.99
-// against 7.20 ms, but a diagonal CTA then reads its columns at other times
-// than the off-diagonal CTAs of the same columns, long after they have left
-// the L2, so every column comes from DRAM twice.
+// against 7.20 ms, but a diagonal CTA then reads a column up to half a run
+// apart from the off-diagonal CTAs that read it too, far longer than the L2
+// keeps it, so the input would be read from DRAM about twice.
 constexpr double kDiagCost = 1.0;
 
 // Per digit count: three 7-bit digits (all nine products, four weight
