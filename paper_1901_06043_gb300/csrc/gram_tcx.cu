@@ -93,12 +93,13 @@ constexpr uint32_t DCORR_BYTES = 128 * 8;      // diagonal corrections per row (
 constexpr int TILE_ELEMS = 128 * 128;
 // time per column of a diagonal tile's CTA relative to an off-diagonal one's
 // (the producers split 128 rows instead of 256, but also keep the diagonal
-// sums).  Measured on a 500-row view with 15 splits of each tile: 6.84
-// against 7.25 ms per CTA.  Equal splits are kept all the same: with 16
-// splits per off-diagonal tile and 14 per diagonal one the Gram took 6.99
-// against 7.20 ms, but a diagonal CTA then reads a column up to half a run
-// apart from the off-diagonal CTAs that read it too, far longer than the L2
-// keeps it, so the input would be read from DRAM about twice.
+// sums).  With the diagonal sums moved into FP64 every 256 stages, a
+// 500-row view with 15 splits of each tile took 6.84 against 7.25 ms per
+// CTA, and 16 splits per off-diagonal tile with 14 per diagonal one made the
+// Gram 3 % faster (6.99 against 7.20 ms).  Equal splits are kept: with
+// unequal ones a diagonal CTA reads a column up to half a run apart from
+// the off-diagonal CTAs that read it too, far longer than the L2 keeps it,
+// so the input would be read from DRAM about twice.
 constexpr double kDiagCost = 1.0;
 
 // Per digit count: three 7-bit digits (all nine products, four weight
@@ -165,13 +166,17 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {    // a - b, one ro
 }
 
 // Per-row sums a diagonal tile's producers keep for its diagonal entries,
-// two rows per float2 (FP32, exact or short; moved into FP64 every 256
+// two rows per float2 (FP32, exact or short; moved into FP64 every 32
 // stages): r2 = sum r^2 (r the last rounding's remainder, in units of the
 // last digit) and, with three digits, the diagonal's D3 terms as integers,
-// a3 = sum 2 d1 d2 and b3 = sum d2^2 (at most 2^21 and 2^20 over 256
-// stages, so exact).  The move is ~30 FP64 instructions per lane, each
-// holding its sub-partition's FP64 pipe for ~64 cycles: done every 32 stages
-// it took a diagonal tile's CTA a fifth of its time.
+// a3 = sum 2 d1 d2 and b3 = sum d2^2 (at most 2^18 and 2^17 over 32 stages).
+// The move is ~30 FP64 instructions per lane, each holding its
+// sub-partition's FP64 pipe for ~64 cycles, ~8,000 cycles every 32 stages.
+// That keeps a diagonal tile's CTA at the pace of the off-diagonal CTAs of
+// its K split, which read the same columns: moved every 256 stages, the
+// diagonal CTAs ran 6 % faster, drifted ahead and read their columns after
+// these had left the L2 (DRAM traffic 1.40x the input instead of 1.00x),
+// while the Gram took as long as before (the off-diagonal CTAs set it).
 struct DiagAcc {
   float2 r2[2], a3[2], b3[2];
   __device__ void zero() {
@@ -343,9 +348,9 @@ __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uin
                                         uint64_t* bar_empty, const float* s_scale, int ta,
                                         int tb, int64_t k0, int64_t k1, int64_t gs0, int nst,
                                         int warp, int lane, double* dcorr) {
-  // diagonal sums: FP32 over 256 stages (exact for the integer sums; for
-  // r^2 a short sum of at most 64, whose rounding is far below the noise the
-  // last digit leaves), then FP64 per row
+  // diagonal sums: FP32 over 32 stages (exact for the integer sums; for r^2
+  // a short sum, where small terms are not lost against a large total),
+  // then FP64 per row
   DiagAcc acc;
   acc.zero();
   double dtot[4] = {0.0, 0.0, 0.0, 0.0};
@@ -464,7 +469,7 @@ __device__ __forceinline__ void produce(const GramTcxArgs& g, uint8_t* smem, uin
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bar_full[slot]));
       if (++slot == NSTAGE) { slot = 0; eph ^= 1u; }
-      if (NOPS == 1 && (s & 255) == 255) flush_diag<NDIG>(acc, dtot);
+      if (NOPS == 1 && (s & 31) == 31) flush_diag<NDIG>(acc, dtot);
     }
   }
   if (NOPS == 1) {
