@@ -55,8 +55,9 @@
 // splits sized to one wave of the SMs; the CTAs of a split are adjacent in
 // launch order so their shared columns are served from L2.
 //
-// Roles (24 warps, 80 registers each): warps 0-15 load X with 16-byte loads,
-// split it into the digit planes of the A (rows 128 ta..) and B (rows
+// Roles (24 warps, 80 registers each): warps 0-15 load X (16-byte loads;
+// four 4-byte loads in row mode or when I % 4 != 0), split it into the digit
+// planes of the A (rows 128 ta..) and B (rows
 // 128 tb..) operands, MN-major SW128 (three-stage ring); warps 16-23 drain
 // tensor memory, two per lane quarter, 64 columns each, and one thread of
 // warp 16 issues each window's MMAs before its drain.  Every wait
