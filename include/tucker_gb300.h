@@ -240,6 +240,10 @@ tucker_status tucker_sthosvd(tucker_ctx* ctx, const void* x_dev, tucker_dtype dt
  * tucker_sthosvd on the device copy, which is freed before the call returns.
  * Results equal tucker_sthosvd's up to the order of the FP64 sums and the
  * digit count of the first Gram.  Synchronises the context stream.
+ * Calls on several contexts of one device may run at once (one host thread
+ * each): their input copies then run one call after the other, in the order
+ * the calls issue them, so each has the whole host-to-device link and one
+ * call's computation overlaps the next one's copy.
  * Errors: those of tucker_sthosvd; OOM also when the device copy does not
  * fit (predicted before anything is allocated). */
 tucker_status tucker_sthosvd_host(tucker_ctx* ctx, const void* x_host, tucker_dtype dtype,

@@ -5,6 +5,7 @@
 #include <array>
 #include <map>
 #include <mutex>
+#include <set>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -20,6 +21,27 @@ using namespace tk;
 #include <atomic>
 static std::atomic<unsigned long long> g_launches{0};
 void tk::count_launches(int n) { g_launches.fetch_add((unsigned long long)n); }
+
+cudaError_t tk::allow_max_dyn_smem(const void* f) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({dev, f})) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, f);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes);
+  if (e != cudaSuccess) return e;
+  done.insert({dev, f});
+  return cudaSuccess;
+}
 
 struct tucker_ctx {
   cudaStream_t stream = nullptr;
@@ -401,6 +423,11 @@ tucker_status gram_once(tucker_ctx* c, const void* y, tucker_dtype dt, const Sla
                               c->stream));
   return TUCKER_OK;
 }
+
+// Per device, the event of the last host-to-device input copy that
+// tucker_sthosvd_host issued (the calls chain their copies on it).
+std::mutex g_h2d_mu;
+std::map<int, cudaEvent_t> g_h2d_last;
 
 // Process-wide cache of the split-K autotuner: for each (device, kernel,
 // view shape, dtype, digits) the SM count whose one-wave plan ran fastest.
@@ -1288,13 +1315,25 @@ tucker_status tucker_sthosvd_host(tucker_ctx* c, const void* x_host, tucker_dtyp
   } cleanup{cs, ev};
   TK_CUDA(c, cudaEventRecord(c->fork_ev, c->stream));
   TK_CUDA(c, cudaStreamWaitEvent(cs, c->fork_ev, 0));
-  for (int64_t p = 0; p < npieces; ++p) {
-    const int64_t e0 = p * per, e1 = std::min(nx, e0 + per);
-    TK_CUDA(c, cudaEventCreateWithFlags(&ev[(size_t)p], cudaEventDisableTiming));
-    TK_CUDA(c, cudaMemcpyAsync(xd.as<char>() + esz * (size_t)e0,
-                               static_cast<const char*>(x_host) + esz * (size_t)e0,
-                               esz * (size_t)(e1 - e0), cudaMemcpyHostToDevice, cs));
-    TK_CUDA(c, cudaEventRecord(ev[(size_t)p], cs));
+  {
+    // The input copies of concurrent calls on one device run one call after
+    // the other (each waits for the previous call's last copy): each gets the
+    // whole host-to-device link in turn, and one call's compute and copies
+    // back overlap the next call's input.  Issued under the lock, so the
+    // chain follows the order in which calls reach this point.
+    std::lock_guard<std::mutex> lk(g_h2d_mu);
+    cudaEvent_t& last = g_h2d_last[c->device];
+    if (last) TK_CUDA(c, cudaStreamWaitEvent(cs, last, 0));
+    for (int64_t p = 0; p < npieces; ++p) {
+      const int64_t e0 = p * per, e1 = std::min(nx, e0 + per);
+      TK_CUDA(c, cudaEventCreateWithFlags(&ev[(size_t)p], cudaEventDisableTiming));
+      TK_CUDA(c, cudaMemcpyAsync(xd.as<char>() + esz * (size_t)e0,
+                                 static_cast<const char*>(x_host) + esz * (size_t)e0,
+                                 esz * (size_t)(e1 - e0), cudaMemcpyHostToDevice, cs));
+      TK_CUDA(c, cudaEventRecord(ev[(size_t)p], cs));
+    }
+    if (!last) TK_CUDA(c, cudaEventCreateWithFlags(&last, cudaEventDisableTiming));
+    TK_CUDA(c, cudaEventRecord(last, cs));
   }
 
   // per piece on the context stream: norm (+ row maxima), Gram of mode 0

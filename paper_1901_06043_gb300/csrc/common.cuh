@@ -23,6 +23,14 @@ inline size_t dtype_size(tucker_dtype d) { return d == TUCKER_F64 ? 8 : 4; }
 // Process-wide count of kernels this library has launched (diagnostics).
 void count_launches(int n);
 
+// Lets kernel f take the largest dynamic shared memory the current device
+// allows (its opt-in maximum less f's static shared memory), once per
+// (device, kernel).  A per-launch setting sized to the launch races when
+// several host threads launch f with different sizes: the attribute is
+// global to the kernel, and one thread's smaller value fails the other's
+// larger launch.
+cudaError_t allow_max_dyn_smem(const void* f);
+
 // Slab view of mode n of a tensor with dims J: element (l, i, r) at
 // l + L*(i + I*r) with L = prod_{k<n} J_k, I = J_n, Rt = prod_{k>n} J_k.
 // L0 = J_0 (n > 0) is the fastest sub-index of l.

@@ -521,7 +521,7 @@ cudaError_t launch_jacobi(const double* S, int n, double* work, const double* fr
   a.tol_rel = tol_rel; a.tol_abs = tol_abs;
   a.vwarps = vpass_warps(np);
   const size_t smem = (size_t)a.vwarps * 2 * np * sizeof(double);
-  e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = allow_max_dyn_smem((const void*)k_jacobi);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 256, smem);

@@ -303,12 +303,9 @@ cudaError_t launch_gram_tc(const float* y, int64_t L, int64_t I, int64_t Rt, con
                            float scale, double* scratch, unsigned* err, double* S, cudaStream_t st) {
   if (!p.ok || L != 1) return cudaErrorInvalidValue;
   if (((uintptr_t)y & 15) != 0) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gram_tc_col, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SMEM_BYTES);
+  {
+    cudaError_t e = allow_max_dyn_smem((const void*)k_gram_tc_col);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   cudaError_t e = cudaMemsetAsync(scratch, 0, p.scratch_bytes, st);
   if (e != cudaSuccess) return e;

@@ -910,7 +910,7 @@ cudaError_t launch_tridiag(const EigProblem* probs_dev, EigProblem* probs_host, 
     multi |= P.team_size > 1;
   }
   const size_t smem = tridiag_base_smem(nmax) + rows_max;
-  cudaError_t e = cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_dyn_smem((const void*)k_tridiag);
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(const_cast<EigProblem*>(probs_dev), probs_host, sizeof(EigProblem) * count,
                       cudaMemcpyHostToDevice, st);
@@ -936,7 +936,7 @@ cudaError_t launch_bisect(const EigProblem* probs_dev, int count, int nmax, int 
   int L = 32;
   while (L > 1 && (int64_t)total_eigs * L > (int64_t)num_sms * 4 * 32) L >>= 1;
   const size_t smem = sizeof(double) * 2 * (size_t)nmax;
-  cudaError_t e = cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_dyn_smem((const void*)k_bisect);
   if (e != cudaSuccess) return e;
   const int per_cta = BNW * (32 / L);
   k_bisect<<<dim3((nmax + per_cta - 1) / per_cta, count), BNW * 32, smem, st>>>(probs_dev, L);
@@ -975,8 +975,7 @@ cudaError_t launch_backtransform(const EigProblem* probs_dev, int count, int tot
     count_launches(1);
   }
   const size_t smem = sizeof(double) * (size_t)nmax;
-  cudaError_t e = cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_max_dyn_smem((const void*)k_backtransform);
   if (e != cudaSuccess) return e;
   k_backtransform<<<total_vectors, 256, smem, st>>>(probs_dev, count);
   count_launches(1);

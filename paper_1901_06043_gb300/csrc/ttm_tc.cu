@@ -653,17 +653,18 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 // The driver's tensor-map encoder, looked up once through the runtime (no
-// link-time dependency on the driver library).
+// link-time dependency on the driver library); the first caller of any
+// thread initialises it.
 EncodeTiledFn encode_tiled() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
+  static const EncodeTiledFn fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-  }
+      return (EncodeTiledFn)p;
+    return (EncodeTiledFn) nullptr;
+  }();
   return fn;
 }
 
@@ -683,13 +684,9 @@ size_t ttm_tc_scratch_bytes(int64_t I, int64_t K) {
 template <int M>
 cudaError_t run_ttm_tc_col(const TtmTcArgs& a, const CUtensorMap& ymap, int grid,
                            cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_ttm_tc_col<M>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ColCfg<M>::SMEM_BYTES);
+  {
+    cudaError_t e = allow_max_dyn_smem((const void*)k_ttm_tc_col<M>);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   k_ttm_tc_col<M><<<grid, NTHREADS, ColCfg<M>::SMEM_BYTES, st>>>(a, ymap);
   return cudaSuccess;
@@ -751,12 +748,9 @@ cudaError_t launch_ttm_tc_row(const float* y, int64_t L, int64_t I, int64_t Rt, 
                               int64_t K, int64_t lda, int a_rowmajor, float sy, float* z,
                               void* scratch, unsigned* err, int num_sms, cudaStream_t st) {
   if (!ttm_tc_row_supported(L, I, Rt, K) || ((uintptr_t)y & 15) != 0) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_ttm_tc_row, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)RSMEM_BYTES);
+  {
+    cudaError_t e = allow_max_dyn_smem((const void*)k_ttm_tc_row);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   const int NT = (int)((K + RN - 1) / RN);
   uint8_t* bprep = (uint8_t*)scratch;

@@ -129,3 +129,50 @@ def test_host_input_rank_specified_and_rejections(ctx):
         ctx.sthosvd_host(xh, dims, ranks=(65, 4, 3))
     with pytest.raises(ValueError):
         ctx.sthosvd_host(torch.from_numpy(x).cuda(), dims, eps=1e-3)
+
+
+def test_host_input_concurrent_calls_on_two_contexts():
+    """Two host threads, each with its own context and stream, run the call
+    on the same pinned input at once (their input copies then run one after
+    the other): both results equal the oracle's, and each other's."""
+    import threading
+    from paper_1901_06043_gb300 import tucker
+    dims, core = (96, 40, 30, 7), (12, 10, 8, 5)
+    x, xh = _host_tensor(dims, core, np.float64, 17, True)
+    ref = oracle.sthosvd(x, dims, eps=1e-5)
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    ctxs = []
+    for s in streams:
+        with torch.cuda.stream(s):
+            c = tucker.Context(stream=s.cuda_stream)
+        c.set_option(tucker.OPT_HOST_CHUNK, float(1 << 16))
+        ctxs.append(c)
+    out, errors = [[], []], []
+
+    def run(i):
+        try:
+            with torch.cuda.stream(streams[i]):
+                for _ in range(3):
+                    r = ctxs[i].sthosvd_host(xh, dims, eps=1e-5, prec="fp64")
+                    core_h, _ = r.to_host()
+                    out[i].append((r.ranks, list(r.discarded), core_h.copy()))
+                    r.close()
+        except Exception as e:
+            errors.append(e)
+
+    threads = [threading.Thread(target=run, args=(i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for c in ctxs:
+        c.close()
+    assert not errors, errors
+    first = out[0][0]
+    for i in range(2):
+        for ranks, disc, core_h in out[i]:
+            assert ranks == ref["ranks"], (ranks, ref["ranks"])
+            for n in range(len(dims)):
+                assert abs(disc[n] - ref["discarded"][n]) <= 1e-10 * ref["norm_sq"]
+            assert ranks == first[0] and disc == first[1]
+            np.testing.assert_array_equal(core_h, first[2])
