@@ -695,7 +695,9 @@ def e2e_leg(ctx, x, w, prec, args):
     input (tucker_sthosvd_host: the library copies the tensor in pieces and
     runs the norm pass and the mode-0 Gram on each piece as it lands), the
     subtensor reconstruction, and the reconstructed subtensor, the core and
-    the factors back to pinned host memory, per step."""
+    the factors back to pinned host memory, per step.  `value` is the rate of
+    two host threads running such steps at once (e2e_streams); `serial` is
+    that of one thread."""
     import torch
     xb = HostBuffer(x.numel(), x.dtype)
     rb = HostBuffer(int(np.prod(w["recon"])), x.dtype)
